@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Throughput of the batched mixed-precision particle step on GB300.
+
+One bench step = one time step of the whole ``batched_mixed`` workload (1,024
+Monte Carlo samples, 4,096..32,768 particles each, 5 St+ classes): the
+all-pairs Coulomb sum, interpolation, local forces, integration, wall contact,
+tallies (and compaction every 100 steps), i.e. every per-step row of the hot
+path.  Field build and seeding happen once before timing.
+
+value  = particle-steps/s = sum over timed steps and samples of live particles
+         / device time (CUDA events on the launching stream), summed over ranks
+         and divided by the slowest rank's time.
+e2e    = the same metric through the public API with the particle state in
+         pinned host memory: each step uploads the state, advances one step and
+         downloads the state and the tallies.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this paper
+has) on a bounded sample of the same workload, on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "particle-steps/s, batched mixed vs plain FP64 on GB300 at ≤1e-3 rel V_dep error"
+FLOPS_PER_PAIR = 21          # 3 sub, 4 minimum image, 5 r^2, 3 r^-3 q, 6 accumulate (FMA = 2); + 1 rsqrt
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched_mixed")
+    ap.add_argument("--samples", type=int, default=None, help="truncate the workload (testing only)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(name, params, counts, seconds, steps_max=50):
+    """Time the FP64 oracle on a bounded sample of the workload; extrapolate by pair count."""
+    import oracle
+    w = workloads.WORKLOADS[name]
+    of = oracle.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
+    grid = oracle.field_grid(of, oracle.field_modes(of, w["field_seed"]))
+    # sample: the first two samples of the workload
+    k = min(2, len(counts))
+    sp, sc = params[:k], counts[:k]
+    ost, off = oracle.seed(of, w["st_plus"], sc, sp, w["particle_seed"], charge_sigma=w.get("charge_sigma", 0.0))
+    c = oracle.cfg(w["dt"])
+    t0 = time.perf_counter()
+    n = 0
+    nd = na = None
+    while n < steps_max and (n == 0 or time.perf_counter() - t0 < seconds):
+        nd, na = oracle.run(of, grid, c, w["st_plus"], off, sp, ost, 1, step0=n,
+                            tallies=None if nd is None else (nd, na))
+        n += 1
+    dt = time.perf_counter() - t0
+    pairs_sample = float(np.sum(np.asarray(sc, np.float64) ** 2)) * n
+    t_pair = dt / pairs_sample
+    full_pairs = float(np.sum(np.asarray(counts, np.float64) ** 2))
+    value = float(np.sum(counts)) / (t_pair * full_pairs)
+    return {"value": value, "unit": "particle-steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "FP64 oracle, %d samples (%s particles) x %d steps = %.1f s; extrapolated to the full "
+                      "workload by sum N_s^2 (pair-dominated)" % (k, "+".join(str(int(x)) for x in sc), n, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    params, counts = workloads.workload_inputs(args.workload, args.samples)
+    base = cpu_baseline(args.workload, params, counts, seconds=max(5.0, 4.0 * (args.steps + args.warmup)),
+                        steps_max=args.steps + args.warmup)
+    out = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "particle-steps/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload},
+           "cpu_baseline": base,
+           "e2e": {"value": base["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2205_04979_gb300.pdq as pdq
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = workloads.WORKLOADS[args.workload]
+    params, counts = workloads.workload_inputs(args.workload, args.samples)
+    if world > 1 and w["samples"] > 1:      # weak scaling: each rank its own batch of samples
+        params = workloads.sample_params(len(counts), w["param_seed"] + 7919 * rank)
+    prec = pdq.MIXED if w["precision"] == "mixed" else pdq.FP64
+    phys = pdq.phys_default()
+    desc = pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        field = pdq.Field(desc, w["field_seed"], stream)
+        state = pdq.State(prec, counts, w["st_plus"])
+        prm = pdq.params_tensor(params)
+        pdq.seed_particles(field, phys, state, prm, w["particle_seed"], w.get("charge_sigma", 0.0), stream)
+        cfg = pdq.step_cfg(w["dt"], window_start=0, compact_every=w.get("compact_every", 0))
+        tally = pdq.Tally(len(counts), len(w["st_plus"]))
+        ws = pdq.workspace(state, cfg)
+        pdq.step_particles(field, phys, state, prm, cfg, args.warmup, tally, ws, stream)
+        stream.synchronize()
+        assert pdq.check_state(state, stream) == 0
+        cnt0 = state.count.cpu().numpy().astype(np.float64)
+        alive0 = int(tally.n_alive.sum().item())
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        uuid = None
+        try:
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+        except Exception:
+            pass
+        clk = ClockSampler(uuid)
+        clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pdq.step_particles(field, phys, state, prm, cfg, args.steps, tally, ws, stream)
+        e1.record(stream)
+        e1.synchronize()
+        clocks = clk.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        assert pdq.check_state(state, stream) == 0
+        cnt1 = state.count.cpu().numpy().astype(np.float64)
+        psteps = int(tally.n_alive.sum().item()) - alive0
+        pairs = 0.5 * (np.sum(cnt0 ** 2) + np.sum(cnt1 ** 2)) * args.steps
+        s0 = state.step_index - args.steps
+        n_compact = sum(1 for k in range(args.steps - 1) if cfg.compact_every and (s0 + k + 1) % cfg.compact_every == 0)
+        launches = 1 + args.steps + 2 * n_compact        # build_items, k_step per step, compact + build_items
+
+        # e2e: state in pinned host memory; upload, one step, download state + tallies
+        e2e = None
+        if args.e2e_steps > 0:
+            cur = state.current()
+            hosts = [t.cpu().pin_memory() for t in cur if t is not None]
+            hcnt = state.count.cpu().pin_memory()
+            htal = tally.n_alive.cpu().pin_memory()
+            hdep = tally.n_dep.cpu().pin_memory()
+            h2d = sum(t.numel() * t.element_size() for t in hosts) + hcnt.numel() * 4
+            d2h = h2d + htal.numel() * 8 * 2
+            alive_e = 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                for dst, src in zip([t for t in state.current() if t is not None], hosts):
+                    dst.copy_(src, non_blocking=True)
+                state.count.copy_(hcnt, non_blocking=True)
+                a0 = tally.n_alive.sum()
+                pdq.step_particles(field, phys, state, prm, cfg, 1, tally, ws, stream)
+                alive_e += tally.n_alive.sum() - a0
+                for dst, src in zip(hosts, [t for t in state.current() if t is not None]):
+                    dst.copy_(src, non_blocking=True)
+                hcnt.copy_(state.count, non_blocking=True)
+                htal.copy_(tally.n_alive, non_blocking=True)
+                hdep.copy_(tally.n_dep, non_blocking=True)
+                stream.synchronize()
+            te = time.perf_counter() - t0
+            e2e = {"value": float(alive_e.item()) / te, "unit": "particle-steps/s", "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h)}
+
+        # plain FP64 single-sample path (the comparison the metric names)
+        fp64 = None
+        if not args.no_fp64 and rank == 0:
+            w1 = workloads.WORKLOADS["single_fp64"]
+            d1 = pdq.field_desc(n_r=w1["grid"][0], n_th=w1["grid"][1], n_z=w1["grid"][2], n_modes=w1["n_modes"])
+            f1 = pdq.Field(d1, w1["field_seed"], stream)
+            s1 = pdq.State(pdq.FP64, [w1["count"]], w1["st_plus"])
+            p1 = pdq.params_tensor([workloads.NOMINAL])
+            pdq.seed_particles(f1, phys, s1, p1, w1["particle_seed"], 0.0, stream)
+            c1 = pdq.step_cfg(w1["dt"], window_start=0, use_graph=True)
+            t1 = pdq.Tally(1, 1)
+            ws1 = pdq.workspace(s1, c1)
+            pdq.step_particles(f1, phys, s1, p1, c1, 20, t1, ws1, stream)
+            a1 = t1.n_alive.sum().item()
+            x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            x0.record(stream)
+            pdq.step_particles(f1, phys, s1, p1, c1, w1["steps"], t1, ws1, stream)
+            x1.record(stream)
+            x1.synchronize()
+            fp64 = {"workload": "single_fp64 (1 sample x 1,000 particles, St+=10, 64x32x64 field, dt+=0.1)",
+                    "value": (t1.n_alive.sum().item() - a1) / (x0.elapsed_time(x1) / 1e3),
+                    "unit": "particle-steps/s", "steps": w1["steps"]}
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, float(psteps)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, psteps_all = float(tmax[0]), float(t[1])
+    else:
+        ms_max, psteps_all = ms, float(psteps)
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak_tflops = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    achieved = FLOPS_PER_PAIR * pairs / (ms / 1e3) / 1e12
+    out = {
+        "metric": METRIC, "value": psteps_all / (ms_max / 1e3), "unit": "particle-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "%s: %d samples x U{4096..32768} particles (%d total), %d St+ classes, "
+                               "%dx%dx%d field, dt+=%g, compaction every %d steps" % (
+                                   args.workload, len(counts), int(np.sum(counts)), len(w["st_plus"]),
+                                   *w["grid"], w["dt"], w.get("compact_every", 0)),
+                   "l2": "inputs larger than L2 (particle state %.2f GB)" % (
+                       sum(t.numel() * t.element_size() for t in state.current() if t is not None) / 1e9),
+                   "parallelism": "samples sharded by rank" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "k_step (all-pairs Coulomb + local step)",
+                     "note": "FP32 pipe peak = 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock); "
+                             "%d flops per ordered pair; time per step from CUDA events over the timed region"
+                             % (sm_max, FLOPS_PER_PAIR)},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "plain_fp64": fp64,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, params, counts, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * pdq.h -- C ABI of libpdq, the GB300 (sm_103a) particle-deposition library.
+ *
+ * libpdq advances the Lagrangian particle phase of the high-fidelity model of
+ * Yao, Huan & Capecelatro, "Multi-fidelity uncertainty quantification of
+ * particle deposition in turbulent pipe flow" (App. A.2, Eq. newtonlaw with
+ * the drag law Eq. part_source, the Coulomb force Eq. coulomb, the van der
+ * Waals force Eq. vdw and the rebound model of Sec. 4.3) for many Monte Carlo
+ * samples of the uncertain inputs (charge scale xi, Hamaker ratio zeta,
+ * temperature theta; Secs. 2.1 and 4.3), tallies the deposition velocity
+ * V_dep+ (Sec. 2.1) and evaluates the multi-fidelity Monte Carlo estimators
+ * of Sec. 3.  The carrier phase is a frozen synthetic pipe field (log-law mean
+ * plus divergence-free random Fourier modes) standing in for the paper's DNS.
+ *
+ * Conventions (every entry point):
+ *   - Returns an int status: PDQ_OK (0) or a negative PDQ_ERR_* code.  No
+ *     exception or abort crosses the ABI; pdq_strerror() names the code.
+ *   - Device pointers are caller-owned CUDA global memory on the current
+ *     device; host pointers are caller-owned host memory.  The library owns
+ *     only the opaque pdq_field handle.
+ *   - Work is enqueued on the caller's stream `stream` (a cudaStream_t; NULL
+ *     is the legacy default stream) and returns without synchronising, unless
+ *     stated otherwise.  Calls that read device values on the host say so.
+ *   - Units are wall units (+): length nu/u*, velocity u*, time nu/u*^2.
+ *   - Invalid sizes or NULL pointers return PDQ_ERR_INVALID_ARG before any
+ *     work is enqueued; CUDA failures return PDQ_ERR_CUDA.
+ */
+#ifndef PDQ_H
+#define PDQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* pdq_stream_t; /* cudaStream_t */
+
+/* ---------------------------------------------------------------- status */
+enum {
+    PDQ_OK = 0,
+    PDQ_ERR_INVALID_ARG = -1, /* bad size, NULL pointer, unknown enum value        */
+    PDQ_ERR_CUDA = -2,        /* a CUDA runtime call failed                        */
+    PDQ_ERR_OOM = -3,         /* device allocation failed (pdq_field only)         */
+    PDQ_ERR_NAN = -4,         /* a kernel saw a non-finite particle state          */
+    PDQ_ERR_TIMEOUT = -5,     /* a bounded device wait gave up                     */
+    PDQ_ERR_PRECOND = -6,     /* MFMC precondition (Eq. mf-precond) violated       */
+    PDQ_ERR_UNSUPPORTED = -7, /* valid request the library does not implement      */
+    PDQ_ERR_WORKSPACE = -8    /* caller workspace smaller than required            */
+};
+const char* pdq_strerror(int status);
+int pdq_version(void); /* major*10000 + minor*100 + patch */
+
+/* ------------------------------------------------------ physical constants
+ * Sec. 2.1: D = 20 mm, nu = 1.5e-5 m^2/s, Re_tau = 180, U_b = 4 m/s,
+ * rho_p = 2650 kg/m^3, q_max = 500 e (d/1um)^2, A0 = 1e-18 J; Sec. 2.2:
+ * eps0 = 8.854e-12 F/m, delta_min = 1e-9 m; Sec. 4.3: E = 70 GPa,
+ * delta_c = 0.165 nm, sigma_y0 = 200 MPa.  rho_f (gas density) is not printed;
+ * 1.2 kg/m^3 reproduces the printed tau_p+ of the three particle sizes.      */
+typedef struct pdq_phys {
+    double nu;        /* kinematic viscosity, m^2/s                 */
+    double radius;    /* pipe radius D/2, m                         */
+    double re_tau;    /* friction Reynolds number u* R / nu         */
+    double u_bulk;    /* bulk velocity, m/s (capture efficiency)    */
+    double rho_p;     /* particle material density, kg/m^3          */
+    double rho_f;     /* gas density, kg/m^3                        */
+    double eps0;      /* vacuum permittivity, F/m                   */
+    double q_unit;    /* q_max / (d/1um)^2 = 500 e, C               */
+    double hamaker0;  /* A0, J                                      */
+    double delta_min; /* vdW saturation gap, m                      */
+    double young;     /* Young's modulus E, Pa                      */
+    double delta_c;   /* cohesion length delta_c, m                 */
+    double sigma_y0;  /* yield stress at theta = 0, Pa              */
+    double g;         /* gravitational acceleration, m/s^2          */
+} pdq_phys;
+void pdq_phys_default(pdq_phys* out);
+
+/* ------------------------------------------------- synthetic carrier field
+ * Mean U+(y+) = y+ below the sublayer/log-law crossing, ln(y+)/kappa + B above
+ * (the paper's DNS field is not available); fluctuation
+ *   u' = curl( (1 - r^2/R^2)^2 sum_n b_n cos(k_n . x + phi_n) ),
+ * divergence-free and zero at the wall, modes drawn from Philox4x32-10 with
+ * key = seed: |k| log-uniform in [k_min, k_max], isotropic direction, k_z
+ * rounded to the lattice 2 pi m / L, b_n perpendicular to k_n with
+ * |b_n| = u_rms sqrt(6/n_modes) / |k_n|, phi_n uniform.  Stored at the nodes
+ * r_i = R tanh(beta i/(n_r-1))/tanh(beta), theta_j = 2 pi j/n_th,
+ * z_k = L k/n_z as Cartesian (u_x, u_y, u_z): FP64 and FP32 copies.          */
+typedef struct pdq_field_desc {
+    int32_t n_r, n_th, n_z; /* grid nodes in r (incl. axis and wall), theta, z: n_r >= 2, n_th >= 1, n_z >= 1 */
+    int32_t n_modes;        /* random Fourier modes, 0..4096            */
+    double r_plus;          /* pipe radius R+ (= Re_tau)                */
+    double l_plus;          /* periodic length L+                      */
+    double u_rms;           /* per-component rms of u' on the axis      */
+    double beta;            /* radial stretching (> 0)                  */
+    double kappa, b_log;    /* log-law constants                        */
+    double k_min, k_max;    /* wavenumber shell, 0 < k_min <= k_max     */
+} pdq_field_desc;
+
+typedef struct pdq_field pdq_field; /* opaque, owns its device memory */
+
+/* Build the field on the current device.  Allocates ~44 B per node plus the
+ * mode table, launches the mode and grid kernels on `stream` and waits for
+ * them.  *out receives the handle; destroy it with pdq_destroy_pipe_field.
+ * Errors: INVALID_ARG (desc out of range), OOM, CUDA.                        */
+int pdq_create_pipe_field(const pdq_field_desc* desc, uint64_t seed, pdq_stream_t stream, pdq_field** out);
+int pdq_destroy_pipe_field(pdq_field* field);
+/* Device views of the field: grid64 = double4 [n_z][n_th][n_r] (w unused),
+ * grid32 = float4 [n_z][n_th][n_r], modes = double [n_modes][7]
+ * (kx, ky, kz, bx, by, bz, phi).  Any output pointer may be NULL.            */
+int pdq_field_views(const pdq_field* field, pdq_field_desc* desc, const void** grid64, const void** grid32,
+                    const double** modes);
+/* Copy the field into caller buffers (device or host; NULL skips a part):
+ * grid64 = n_z*n_th*n_r*32 bytes, grid32 = n_z*n_th*n_r*16 bytes,
+ * modes = n_modes*56 bytes.  Enqueued on `stream` (cudaMemcpyAsync,
+ * direction inferred from the pointers).                                     */
+int pdq_field_copy(const pdq_field* field, void* grid64, void* grid32, void* modes, pdq_stream_t stream);
+
+/* ------------------------------------------------------------ particles */
+#define PDQ_MAX_CLASSES 16
+enum { PDQ_FP64 = 0, PDQ_MIXED = 1 };
+
+/* Caller-owned particle state of S samples.  Sample s owns the slots
+ * [offset[s], offset[s+1]); its first count[s] slots hold its particles
+ * (live ones and those deposited since the last compaction).  Arrays marked
+ * [2] are double-buffered: half `cur` holds the current state; a step writes
+ * the other half and flips `cur`.  Element types by precision:
+ *   pos[2]: FP64 double4 (x+, y+, z+, q_eff); MIXED float4 (x+, y+, z+, q_eff)
+ *           where MIXED x+, y+ are FP32 copies of xy; q_eff = charge in units
+ *           of q_unit (= xi (d/1um)^2 times the per-particle factor), 0 once
+ *           deposited.
+ *   vel[2]: FP64 double4 / MIXED float4 (vx+, vy+, vz+, alive: 1 or 0).
+ *   xy[2] : MIXED only, double2 (x+, y+), the authoritative wall-normal
+ *           position; NULL for FP64.
+ *   tag   : int2 (particle id within its sample, size class), not
+ *           double-buffered; compaction permutes it with the current half.
+ *   ctl   : int64 [8] control block the library owns the contents of (step
+ *           counter, work-queue counters, error word); zeroed by seeding.
+ * All arrays need 32-byte alignment.                                         */
+typedef struct pdq_state {
+    int32_t precision;                    /* PDQ_FP64 or PDQ_MIXED                        */
+    int32_t cur;                          /* 0 or 1, maintained by the library            */
+    int32_t n_samples;                    /* S >= 1                                       */
+    int32_t n_classes;                    /* C in 1..PDQ_MAX_CLASSES                      */
+    double st_plus[PDQ_MAX_CLASSES];      /* Stokes number tau_p+ of each size class      */
+    int64_t capacity;                     /* offset[S]                                    */
+    int64_t step;                         /* global step index (host mirror)              */
+    const int64_t* offset;                /* device [S+1], offset[0] = 0, non-decreasing  */
+    int32_t* count;                       /* device [S]                                   */
+    void* pos[2];
+    void* vel[2];
+    void* xy[2];
+    int32_t* tag;
+    int64_t* ctl;
+} pdq_state;
+
+/* Per-sample uncertain inputs (device array [S]): xi scales the charge
+ * q = xi q_max (Sec. 2.1), zeta = A/A0 (Sec. 2.1), theta the yield-stress
+ * drop sigma_y = sigma_y0 (1 - theta) (Sec. 4.3).                            */
+typedef struct pdq_sample_params {
+    double xi, zeta, theta, pad;
+} pdq_sample_params;
+
+/* Seed every sample (Sec. 2.1: particles at rest, uniformly distributed in
+ * the pipe, q = xi q_max): local particle j uses Philox4x32-10 counter
+ * (j, 0, 0, 0), key = seed, for (r, theta, z) = ((R - d/2) sqrt(u0), 2 pi u1,
+ * L u2) with u = (word + 1/2) 2^-32, and counter (j, 1, 0, 0) for the
+ * lognormal charge factor exp(sigma sqrt(-2 ln u0) cos(2 pi u1)) when
+ * charge_sigma > 0.  Class = j mod C, so all samples share their first
+ * particles (common random numbers).  Writes half 0 of every array, sets
+ * count[s] = offset[s+1] - offset[s], cur = 0, step = 0, zeroes ctl.
+ * Errors: INVALID_ARG (precision, classes, NULL arrays), CUDA.               */
+int pdq_seed_particles(const pdq_field* field, const pdq_phys* phys, double charge_sigma, uint64_t seed,
+                       const pdq_sample_params* params, pdq_state* state, pdq_stream_t stream);
+
+/* ------------------------------------------------------------------ step */
+enum { PDQ_STICK = 0, PDQ_REBOUND = 1 };
+enum { PDQ_F_DRAG = 1, PDQ_F_GRAVITY = 2, PDQ_F_COULOMB = 4, PDQ_F_IMAGE = 8, PDQ_F_VDW = 16, PDQ_F_ALL = 31 };
+
+typedef struct pdq_step_cfg {
+    double dt;            /* time step dt+ > 0                                              */
+    double gravity[3];    /* direction of gravity (scaled by g nu/u*^3); zero = none        */
+    int32_t mode;         /* PDQ_STICK (removal on wall contact, App. A) or PDQ_REBOUND      */
+    int32_t forces;       /* PDQ_F_* mask                                                    */
+    int64_t window_start; /* first global step index counted in the tallies (t+ >= t_w)      */
+    int32_t compact_every;/* compact deposited particles out every this many steps; 0 never */
+    int32_t block;        /* threads per CTA of the step kernel: 0 (auto), 128, 256 or 512   */
+    int32_t use_graph;    /* 1: replay the step sequence as a CUDA graph                     */
+    int32_t pad;
+} pdq_step_cfg;
+
+/* Caller-owned tallies, device int64 [S][C], accumulated across calls:
+ * n_dep = particles deposited during counted steps, n_alive = sum over counted
+ * steps of the particles alive at the start of the step.                     */
+typedef struct pdq_tally {
+    int64_t* n_dep;
+    int64_t* n_alive;
+} pdq_tally;
+
+/* Workspace bytes pdq_step_particles needs for this state and configuration. */
+int pdq_step_workspace_size(const pdq_state* state, const pdq_step_cfg* cfg, size_t* bytes);
+
+/* Advance all samples n_steps steps (App. A.2).  One step of particle i:
+ *   a_i = sum_{j != i, same sample} k q_i q_j (x_i - x_j) / (m_i max(|x_i - x_j|, d_c)^3)
+ *         (Eq. coulomb; minimum image in z; d_c the largest class diameter)
+ *       + image charge q_i^2 / (4 pi eps0 (2 y)^2 m_i) toward the wall (Sec. 2.2)
+ *       + 2 F_vw(delta)/m_i toward the wall (Eq. vdw; delta saturated at
+ *         delta_min, zero beyond d/4)  + gravity;
+ *   u = trilinear interpolation of the field in (s(r), theta, z);
+ *   drag (f / tau_p+)(u - v), f = 1 + 0.15 Re_p^0.687 (Eq. part_source);
+ *   exponential integrator with u, f, a frozen over the step;
+ *   wall contact when R - r - d/2 <= 0: STICK removes the particle,
+ *   REBOUND applies CoR_n of Sec. 4.3 (sticking when it is 0).
+ * FP64 runs everything in double; MIXED keeps x, y, the wall gap, the vdW
+ * term and the tallies in double and runs the pair sum, interpolation, drag
+ * and velocities in float.  `workspace` (>= pdq_step_workspace_size bytes,
+ * device, 256-byte aligned) holds the work queue.  Compaction runs after every
+ * step whose index + 1 is a multiple of compact_every.  The first call for a
+ * state reads offset[] to the host (synchronises `stream`).
+ * Errors: INVALID_ARG, WORKSPACE, CUDA.  Non-finite states set the error word
+ * read by pdq_check_state.                                                   */
+int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, pdq_state* state,
+                       const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
+                       pdq_tally* tally, void* workspace, size_t workspace_bytes, pdq_stream_t stream);
+
+/* Stream compaction of deposited particles (alive == 0) of every sample, in
+ * place and order-preserving on the current half; updates count[].          */
+int pdq_compact(pdq_state* state, pdq_stream_t stream);
+
+/* Synchronise `stream` and read the device error word: PDQ_OK, PDQ_ERR_NAN
+ * (a non-finite state appeared) or PDQ_ERR_TIMEOUT.  Clears the word.        */
+int pdq_check_state(pdq_state* state, pdq_stream_t stream);
+
+/* ---------------------------------------------------------- deposition
+ * V_dep+ = (R+/2) n_dep / (dt+ n_alive) per (sample, class): the definition
+ * J_w / (rho_pm u*) of Sec. 2.1 with J_w = (dN_dep/dt) m_p / (2 pi R L) and
+ * rho_pm = N m_p / (pi R^2 L), N integrated over the counted window.  Also
+ * the Monte Carlo mean over samples and its standard error
+ * sd / sqrt(S) per class (sd with divisor S-1; 0 when S = 1).  Outputs are
+ * device arrays: vdep [S][C], mean [C], se [C] (mean/se may be NULL).       */
+int pdq_deposition_tally(const pdq_tally* tally, int32_t n_samples, int32_t n_classes, double dt,
+                         double r_plus, double* vdep, double* mean, double* se, pdq_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDQ_H */

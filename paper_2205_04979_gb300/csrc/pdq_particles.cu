@@ -1,0 +1,838 @@
+// pdq_particles.cu -- seeding, the fused particle step, compaction and the
+// deposition tally of libpdq.
+//
+// Step kernel layout: a persistent grid pulls work items (sample s, i-tile t)
+// from a device queue ordered largest sample first.  A CTA of NT threads owns
+// NT*U particles of one sample (U per thread), streams every j-tile of that
+// sample through shared memory for the all-pairs Coulomb sum (Eq. coulomb,
+// App. A.2), then runs the local physics of its particles (interpolation,
+// drag, gravity, image charge, vdW, exponential integrator, wall contact) and
+// writes the new state into the other half of the double buffer.  Tallies are
+// reduced with warp ballots, then one shared-memory and one global atomic per
+// class.  The last CTA to finish advances the device step counter and resets
+// the queue, so consecutive launches need no host round trip.
+#include <math.h>
+#include <string.h>
+
+#include "pdq_common.cuh"
+
+namespace pdq {
+
+enum { CTL_STEP = 0, CTL_QUEUE = 1, CTL_DONE = 2, CTL_ERROR = 3, CTL_NITEMS = 4 };
+enum { ERR_NONFINITE = 1 };
+
+template <int P> struct Real;
+template <> struct Real<PDQ_FP64> { typedef double T; typedef double4_32a T4; };
+template <> struct Real<PDQ_MIXED> { typedef float T; typedef float4 T4; };
+
+// ---------------------------------------------------------------------------
+// Host: per-class constants from the physical constants (all SI -> wall units).
+// ---------------------------------------------------------------------------
+int make_step_const(const pdq_field* f, const pdq_phys* p, const pdq_state* st, StepConst* K) {
+    memset(K, 0, sizeof(*K));
+    const double ustar = p->re_tau * p->nu / p->radius;   // u* = Re_tau nu / R
+    const double ell = p->nu / ustar;                       // m per wall unit
+    const double tauf = p->nu / (ustar * ustar);
+    const double acc = p->nu / (ustar * ustar * ustar);     // SI acceleration -> wall units
+    const double ke = 1.0 / (4.0 * kPi * p->eps0);
+    if (fabs(f->desc.r_plus - p->re_tau) > 1e-9 * p->re_tau) return PDQ_ERR_INVALID_ARG;
+    double dmax = 0.0;
+    K->n_classes = st->n_classes;
+    for (int c = 0; c < st->n_classes; ++c) {
+        ClassK& k = K->cls[c];
+        const double tau = st->st_plus[c];
+        if (!(tau > 0)) return PDQ_ERR_INVALID_ARG;
+        // tau_p = rho_p d^2 / (18 rho_f nu) and tau_p+ = tau_p / tau_f  (Sec. 2.1)
+        k.tau = tau;
+        k.d_m = sqrt(18.0 * p->rho_f * p->nu * tau * tauf / p->rho_p);
+        k.d_plus = k.d_m / ell;
+        k.half_d = 0.5 * k.d_plus;
+        k.mass = p->rho_p * kPi * k.d_m * k.d_m * k.d_m / 6.0;
+        k.qfac = (k.d_m * 1e6) * (k.d_m * 1e6);
+        k.coul = ke * p->q_unit * p->q_unit / (k.mass * ell * ell) * acc;
+        k.vdw = p->hamaker0 / (3.0 * k.mass) * acc;          // 2 x (A0/6) / m
+        k.stick = 2.0 * (0.25 * kPi * k.d_m * k.d_m) * p->hamaker0 / (24.0 * kPi * p->delta_c * p->delta_c) / k.mass;
+        k.tau_f = (float)tau;
+        k.inv_tau_f = (float)(1.0 / tau);
+        k.d_plus_f = (float)k.d_plus;
+        k.half_d_f = (float)k.half_d;
+        k.coul_f = (float)k.coul;
+        k.img_f = (float)(0.25 * k.coul);                     // image at distance 2y: coul / 4 / y^2
+        if (k.d_plus > dmax) dmax = k.d_plus;
+    }
+    K->R = f->desc.r_plus;
+    K->L = f->desc.l_plus;
+    K->invL = 1.0 / K->L;
+    K->ell = ell;
+    K->delta_min = p->delta_min;
+    K->ustar = ustar;
+    K->elastic0 = p->sigma_y0 * p->sigma_y0 / (p->rho_p * p->young);
+    K->contact2 = dmax * dmax;
+    K->inv_beta = 1.0 / f->desc.beta;
+    K->tanh_beta = tanh(f->desc.beta);
+    K->n_r = f->desc.n_r; K->n_th = f->desc.n_th; K->n_z = f->desc.n_z;
+    K->Rf = (float)K->R; K->Lf = (float)K->L; K->invLf = (float)K->invL;
+    K->contact2f = (float)K->contact2;
+    K->inv_beta_f = (float)K->inv_beta; K->tanh_beta_f = (float)K->tanh_beta;
+    K->grid64 = f->grid64;
+    K->grid32 = f->grid32;
+    return PDQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Seeding.
+// ---------------------------------------------------------------------------
+struct SeedArgs {
+    const int64_t* offset; int32_t* count; int64_t* ctl;
+    const pdq_sample_params* params;
+    void* pos; void* vel; double2* xy; int2* tag;
+    int64_t capacity; int32_t S, C; double sigma; uint2 key;
+    double R, L; double half_d[PDQ_MAX_CLASSES]; double qfac[PDQ_MAX_CLASSES];
+};
+
+template <int P>
+__global__ void k_seed(const SeedArgs A) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < A.S) A.count[g] = (int32_t)(A.offset[g + 1] - A.offset[g]);
+    if (g < 8) A.ctl[g] = 0;
+    if (g >= A.capacity) return;
+    int lo = 0, hi = A.S;                       // offset[lo] <= g < offset[lo + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (A.offset[mid] <= g) lo = mid; else hi = mid;
+    }
+    const int s = lo;
+    const uint32_t j = (uint32_t)(g - A.offset[s]);
+    const int c = (int)(j % (uint32_t)A.C);
+    const uint4 a = philox4x32_10(make_uint4(j, 0u, 0u, 0u), A.key);
+    double lam = 1.0;
+    if (A.sigma > 0.0) {
+        const uint4 b = philox4x32_10(make_uint4(j, 1u, 0u, 0u), A.key);
+        lam = exp(A.sigma * sqrt(-2.0 * log(unit_open(b.x))) * cos(2.0 * kPi * unit_open(b.y)));
+    }
+    const double rr = (A.R - A.half_d[c]) * sqrt(unit_open(a.x));
+    double sth, cth;
+    sincos(2.0 * kPi * unit_open(a.y), &sth, &cth);
+    const double x = rr * cth, y = rr * sth, z = A.L * unit_open(a.z);
+    const double q = A.params[s].xi * A.qfac[c] * lam;
+    if (P == PDQ_FP64) {
+        ((double4_32a*)A.pos)[g] = make_double4_32a(x, y, z, q);
+        ((double4_32a*)A.vel)[g] = make_double4_32a(0.0, 0.0, 0.0, 1.0);
+    } else {
+        A.xy[g] = make_double2(x, y);
+        ((float4*)A.pos)[g] = make_float4((float)x, (float)y, (float)z, (float)q);
+        ((float4*)A.vel)[g] = make_float4(0.f, 0.f, 0.f, 1.f);
+    }
+    A.tag[g] = make_int2((int)j, c);
+}
+
+// ---------------------------------------------------------------------------
+// Device physics helpers.
+// ---------------------------------------------------------------------------
+// phi1(z) = (e^z - 1)/z and phi2(z) = (e^z - 1 - z)/z^2: Taylor series near 0
+// (where the closed forms cancel), expm1 elsewhere.
+__device__ __forceinline__ void phi12(double z, double& p1, double& p2) {
+    if (fabs(z) < 0.05) {
+        // Horner with explicit coefficients (1/(k+1)! and 1/(k+2)!).
+        const double c1[11] = {1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320,
+                               1.0 / 362880, 1.0 / 3628800, 1.0 / 39916800};
+        p1 = c1[10];
+        p2 = 1.0 / 479001600;
+        for (int k = 9; k >= 0; --k) p1 = p1 * z + c1[k];
+        for (int k = 9; k >= 0; --k) p2 = p2 * z + c1[k + 1];
+        return;
+    }
+    const double em = expm1(z);
+    p1 = em / z;
+    p2 = (em - z) / (z * z);
+}
+__device__ __forceinline__ void phi12(float z, float& p1, float& p2) {
+    if (fabsf(z) < 0.1f) {
+        const float c[10] = {1.f, 1.f / 2, 1.f / 6, 1.f / 24, 1.f / 120, 1.f / 720, 1.f / 5040, 1.f / 40320,
+                             1.f / 362880, 1.f / 3628800};
+        p1 = c[8];
+        p2 = c[9];
+        for (int k = 7; k >= 0; --k) p1 = fmaf(p1, z, c[k]);
+        for (int k = 8; k >= 1; --k) p2 = fmaf(p2, z, c[k]);
+        return;
+    }
+    const float em = expm1f(z);
+    p1 = em / z;
+    p2 = (em - z) / (z * z);
+}
+
+__device__ __forceinline__ double atanh_(double x) { return atanh(x); }
+__device__ __forceinline__ float atanh_(float x) { return atanhf(x); }
+__device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double floor_(double x) { return floor(x); }
+__device__ __forceinline__ float floor_(float x) { return floorf(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
+__device__ __forceinline__ float exp_(float x) { return expf(x); }
+__device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
+
+__device__ __forceinline__ double4_32a grid_at(const StepConst& K, const double4_32a*, int64_t i) { return K.grid64[i]; }
+__device__ __forceinline__ float4 grid_at(const StepConst& K, const float4*, int64_t i) { return __ldg(K.grid32 + i); }
+
+// Trilinear interpolation in (s(r), theta, z) index space: s = atanh(r tanh(beta)/R)/beta
+// inverts the node stretching; theta and z are periodic; s is clamped to [0, 1].
+template <class T, class T4>
+__device__ __forceinline__ void interp(const StepConst& K, T r, T x, T y, T z, T u[3]) {
+    const T R = (T)K.R;
+    const T rho = fmin(r / R, (T)1);
+    const T s = atanh_(rho * (T)K.tanh_beta) * (T)K.inv_beta;
+    const T fi = s * (T)(K.n_r - 1);
+    int i0 = (int)floor_(fi);
+    i0 = i0 < 0 ? 0 : (i0 > K.n_r - 2 ? K.n_r - 2 : i0);
+    const T tr = fi - (T)i0;
+    T fj = atan2_(y, x) * (T)(K.n_th / (2.0 * kPi));
+    if (fj < (T)0) fj += (T)K.n_th;
+    int j0 = (int)floor_(fj);
+    const T tt = fj - (T)j0;
+    j0 %= K.n_th;                    // any int (also a non-finite input's) maps into [0, n_th)
+    if (j0 < 0) j0 += K.n_th;
+    const int j1 = (j0 + 1 == K.n_th) ? 0 : j0 + 1;
+    const T fk = z * (T)(K.n_z * K.invL);
+    int k0 = (int)floor_(fk);
+    const T tz = fk - (T)k0;
+    k0 %= K.n_z;
+    if (k0 < 0) k0 += K.n_z;
+    const int k1 = (k0 + 1 == K.n_z) ? 0 : k0 + 1;
+    const int64_t nr = K.n_r, plane = (int64_t)K.n_r * K.n_th;
+    const int64_t b00 = k0 * plane + j0 * nr + i0, b01 = k0 * plane + j1 * nr + i0;
+    const int64_t b10 = k1 * plane + j0 * nr + i0, b11 = k1 * plane + j1 * nr + i0;
+    const T4* tag = nullptr;
+    const T4 g000 = grid_at(K, tag, b00), g001 = grid_at(K, tag, b00 + 1);
+    const T4 g010 = grid_at(K, tag, b01), g011 = grid_at(K, tag, b01 + 1);
+    const T4 g100 = grid_at(K, tag, b10), g101 = grid_at(K, tag, b10 + 1);
+    const T4 g110 = grid_at(K, tag, b11), g111 = grid_at(K, tag, b11 + 1);
+    const T wr0 = (T)1 - tr, wt0 = (T)1 - tt, wz0 = (T)1 - tz;
+    const T w000 = wr0 * wt0 * wz0, w001 = tr * wt0 * wz0, w010 = wr0 * tt * wz0, w011 = tr * tt * wz0;
+    const T w100 = wr0 * wt0 * tz, w101 = tr * wt0 * tz, w110 = wr0 * tt * tz, w111 = tr * tt * tz;
+    u[0] = w000 * g000.x + w001 * g001.x + w010 * g010.x + w011 * g011.x + w100 * g100.x + w101 * g101.x +
+           w110 * g110.x + w111 * g111.x;
+    u[1] = w000 * g000.y + w001 * g001.y + w010 * g010.y + w011 * g011.y + w100 * g100.y + w101 * g101.y +
+           w110 * g110.y + w111 * g111.y;
+    u[2] = w000 * g000.z + w001 * g001.z + w010 * g010.z + w011 * g011.z + w100 * g100.z + w101 * g101.z +
+           w110 * g110.z + w111 * g111.z;
+}
+
+// One ordered pair of the Coulomb sum: acc += q_j (x_i - x_j) / max(|x_i - x_j|, d_c)^3,
+// minimum image in z by the round-to-nearest trick (t + M) - M.
+__device__ __forceinline__ void coulomb_pair(float xi, float yi, float zi, const float4 pj, float L, float invL,
+                                             float c2, float& ax, float& ay, float& az) {
+    const float dx = xi - pj.x, dy = yi - pj.y;
+    float dz = zi - pj.z;
+    const float t = __fadd_rn(__fmaf_rn(dz, invL, 12582912.0f), -12582912.0f);
+    dz = __fmaf_rn(-L, t, dz);
+    const float r2 = fmaxf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))), c2);
+    const float ri = rsqrtf(r2);
+    const float s = __fmul_rn(__fmul_rn(pj.w, ri), __fmul_rn(ri, ri));
+    ax = __fmaf_rn(s, dx, ax);
+    ay = __fmaf_rn(s, dy, ay);
+    az = __fmaf_rn(s, dz, az);
+}
+__device__ __forceinline__ void coulomb_pair(double xi, double yi, double zi, const double4_32a pj, double L, double invL,
+                                             double c2, double& ax, double& ay, double& az) {
+    const double dx = xi - pj.x, dy = yi - pj.y;
+    double dz = zi - pj.z;
+    const double t = __dadd_rn(__fma_rn(dz, invL, 6755399441055744.0), -6755399441055744.0);
+    dz = __fma_rn(-L, t, dz);
+    const double r2 = fmax(__fma_rn(dx, dx, __fma_rn(dy, dy, dz * dz)), c2);
+    const double ri = rsqrt(r2);
+    const double s = pj.w * ri * (ri * ri);
+    ax = __fma_rn(s, dx, ax);
+    ay = __fma_rn(s, dy, ay);
+    az = __fma_rn(s, dz, az);
+}
+
+struct StepArgs {
+    StepConst K;
+    const void* pos_in; const void* vel_in; const double2* xy_in;
+    void* pos_out; void* vel_out; double2* xy_out;
+    const int2* tag; const int64_t* offset; const int32_t* count;
+    const pdq_sample_params* params;
+    const int2* items; int64_t* ctl;
+    unsigned long long* n_dep; unsigned long long* n_alive;
+};
+
+// Local physics of one particle; returns its class, whether it was alive at the
+// start of the step, and whether it deposited.
+template <int P>
+__device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typename Real<P>::T acx,
+                                             typename Real<P>::T acy, typename Real<P>::T acz,
+                                             const pdq_sample_params& sp, int& cls, bool& was_alive, bool& dep) {
+    typedef typename Real<P>::T T;
+    typedef typename Real<P>::T4 T4;
+    const StepConst& K = A.K;
+    const T4 p4 = ((const T4*)A.pos_in)[g];
+    const T4 v4 = ((const T4*)A.vel_in)[g];
+    double x, y;
+    if (P == PDQ_FP64) { x = (double)p4.x; y = (double)p4.y; }
+    else { const double2 xy = A.xy_in[g]; x = xy.x; y = xy.y; }
+    T z = p4.z;
+    const T q = p4.w;
+    cls = A.tag[g].y;
+    dep = false;
+    was_alive = v4.w > (T)0.5;
+    if (!was_alive) {
+        ((T4*)A.pos_out)[g] = p4;
+        ((T4*)A.vel_out)[g] = v4;
+        if (P == PDQ_MIXED) A.xy_out[g] = make_double2(x, y);
+        return;
+    }
+    const ClassK& c = K.cls[cls];
+    T a[3] = {(T)0, (T)0, (T)0};
+    if (K.forces & PDQ_F_COULOMB) {
+        const T kq = (P == PDQ_FP64 ? (T)c.coul : (T)c.coul_f) * q;
+        a[0] = kq * acx; a[1] = kq * acy; a[2] = kq * acz;
+    }
+    if (K.forces & PDQ_F_GRAVITY) {
+        a[0] += (T)K.grav[0]; a[1] += (T)K.grav[1]; a[2] += (T)K.grav[2];
+    }
+    const double r = sqrt(x * x + y * y);
+    if (r > 0.0 && (K.forces & (PDQ_F_IMAGE | PDQ_F_VDW))) {
+        double aw = 0.0;   // toward the wall
+        if (K.forces & PDQ_F_IMAGE) {
+            // image of opposite sign mirrored across the wall: q^2 / (4 pi eps0 (2y)^2 m), y >= d/2
+            if (P == PDQ_FP64) {
+                const double yw = fmax(K.R - r, c.half_d);
+                aw += 0.25 * c.coul * (double)q * (double)q / (yw * yw);
+            } else {
+                const float yw = fmaxf((float)(K.R - r), c.half_d_f);
+                aw += (double)(c.img_f * (float)q * (float)q / (yw * yw));
+            }
+        }
+        if (K.forces & PDQ_F_VDW) {
+            // 2 F_vw(delta): Eq. (vdw) written as A d^6 / (6 delta^2 (2d+delta)^2 (d+delta)^3)
+            const double gap = (K.R - r - c.half_d) * K.ell;
+            if (gap <= 0.25 * c.d_m) {
+                const double dl = fmax(gap, K.delta_min);
+                const double d = c.d_m;
+                const double d2 = d * d, d6 = d2 * d2 * d2;
+                const double e1 = 2.0 * d + dl, e2 = d + dl;
+                aw += sp.zeta * c.vdw * d6 / (dl * dl * e1 * e1 * e2 * e2 * e2);
+            }
+        }
+        const double inv_r = 1.0 / r;
+        a[0] += (T)(aw * x * inv_r);
+        a[1] += (T)(aw * y * inv_r);
+    }
+    T v[3] = {v4.x, v4.y, v4.z};
+    T u[3] = {(T)0, (T)0, (T)0};
+    T lam = (T)0;
+    if (K.forces & PDQ_F_DRAG) {
+        interp<T, T4>(K, (T)r, (T)x, (T)y, z, u);
+        const T rx = u[0] - v[0], ry = u[1] - v[1], rz = u[2] - v[2];
+        const T re = sqrt_(rx * rx + ry * ry + rz * rz) * (P == PDQ_FP64 ? (T)c.d_plus : (T)c.d_plus_f);
+        const T fd = (T)1 + (T)0.15 * (re > (T)0 ? pow_(re, (T)0.687) : (T)0);   // Schiller-Naumann
+        lam = fd * (P == PDQ_FP64 ? (T)(1.0 / c.tau) : (T)c.inv_tau_f);
+    }
+    const T h = (T)K.dt;
+    const T zz = -lam * h;
+    T p1, p2;
+    phi12(zz, p1, p2);
+    const T e = exp_(zz);
+    T dxv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T F = lam * u[k] + a[k];
+        dxv[k] = v[k] * h * p1 + F * (h * h) * p2;
+        v[k] = v[k] * e + F * h * p1;
+    }
+    double xn = x + (double)dxv[0];
+    double yn = y + (double)dxv[1];
+    T zn = z + dxv[2];
+    zn -= (T)K.L * floor_(zn * (T)K.invL);
+    if (zn >= (T)K.L) zn -= (T)K.L;
+    if (zn < (T)0) zn = (T)0;
+    // wall contact: gap R - r - d/2 <= 0 (App. A: removal on impact)
+    const double rn = sqrt(xn * xn + yn * yn);
+    const double gapn = K.R - rn - c.half_d;
+    bool alive = true;
+    if (gapn <= 0.0) {
+        bool stick = true;
+        if (K.mode == PDQ_REBOUND) {
+            // Bons et al. (Sec. 4.3): CoR_n = sqrt(sigma_y^2/(rho_p E) - 2 A_cont gamma_c / m) / V_n1
+            const double one_m = 1.0 - sp.theta;
+            const double arg = K.elastic0 * one_m * one_m - sp.zeta * c.stick;
+            if (arg > 0.0) {
+                stick = false;
+                const double nx = xn / rn, ny = yn / rn;
+                const double vn = (double)v[0] * nx + (double)v[1] * ny;     // outward, wall units
+                const double vn_si = vn * K.ustar;
+                const double cor = vn_si > 0.0 ? fmin(1.0, sqrt(arg) / vn_si) : 1.0;
+                const double dv = -cor * fabs(vn) - vn;
+                v[0] = (T)((double)v[0] + dv * nx);
+                v[1] = (T)((double)v[1] + dv * ny);
+                const double rref = 2.0 * (K.R - c.half_d) - rn;
+                xn = nx * rref;
+                yn = ny * rref;
+            }
+        }
+        if (stick) { alive = false; dep = true; }
+    }
+    if (!(isfinite(xn) && isfinite(yn) && isfinite((double)zn) && isfinite((double)v[0]) &&
+          isfinite((double)v[1]) && isfinite((double)v[2])))
+        atomicOr((unsigned long long*)&A.ctl[CTL_ERROR], (unsigned long long)ERR_NONFINITE);
+    if (P == PDQ_FP64) {
+        ((double4_32a*)A.pos_out)[g] = make_double4_32a(xn, yn, (double)zn, alive ? (double)q : 0.0);
+        ((double4_32a*)A.vel_out)[g] = make_double4_32a((double)v[0], (double)v[1], (double)v[2], alive ? 1.0 : 0.0);
+    } else {
+        A.xy_out[g] = make_double2(xn, yn);
+        ((float4*)A.pos_out)[g] = make_float4((float)xn, (float)yn, (float)zn, alive ? (float)q : 0.f);
+        ((float4*)A.vel_out)[g] = make_float4((float)v[0], (float)v[1], (float)v[2], alive ? 1.f : 0.f);
+    }
+}
+
+template <int P, int NT, int U>
+__global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
+    typedef typename Real<P>::T T;
+    typedef typename Real<P>::T4 T4;
+    __shared__ T4 sj[NT];
+    __shared__ int s_item;
+    __shared__ unsigned int s_alive[PDQ_MAX_CLASSES], s_dep[PDQ_MAX_CLASSES];
+    const StepConst& K = A.K;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t step = A.ctl[CTL_STEP];
+    const bool counted = step >= K.window_start;
+    const int64_t n_items = A.ctl[CTL_NITEMS];
+    const T4* __restrict__ pos_in = (const T4*)A.pos_in;
+    const T L = (T)K.L, invL = (T)K.invL;
+    const T c2 = P == PDQ_FP64 ? (T)K.contact2 : (T)K.contact2f;
+    const int C = K.n_classes;
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd((unsigned long long*)&A.ctl[CTL_QUEUE], 1ull);
+        if (tid < PDQ_MAX_CLASSES) { s_alive[tid] = 0u; s_dep[tid] = 0u; }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;
+        const int2 it = A.items[item];
+        const int s = it.x;
+        const int64_t o = A.offset[s];
+        const int64_t end = o + A.count[s];
+        const int64_t base = o + (int64_t)it.y * (NT * U);
+        T xi[U], yi[U], zi[U], ax[U], ay[U], az[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t g = base + u * NT + tid;
+            if (g < end) { const T4 p = pos_in[g]; xi[u] = p.x; yi[u] = p.y; zi[u] = p.z; }
+            else { xi[u] = (T)0; yi[u] = (T)0; zi[u] = (T)0; }
+            ax[u] = ay[u] = az[u] = (T)0;
+        }
+        if (K.forces & PDQ_F_COULOMB) {
+            for (int64_t j0 = o; j0 < end; j0 += NT) {
+                const int64_t j = j0 + tid;
+                T4 pj;
+                if (j < end) pj = pos_in[j];
+                else { pj.x = (T)0; pj.y = (T)0; pj.z = (T)0; pj.w = (T)0; }
+                sj[tid] = pj;
+                __syncthreads();
+#pragma unroll 8
+                for (int k = 0; k < NT; ++k) {
+                    const T4 p = sj[k];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) coulomb_pair(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u]);
+                }
+                __syncthreads();
+            }
+        }
+        const pdq_sample_params sp = A.params[s];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t g = base + u * NT + tid;
+            int cls = -1;
+            bool was_alive = false, dep = false;
+            if (g < end) local_update<P>(A, g, ax[u], ay[u], az[u], sp, cls, was_alive, dep);
+            if (counted) {
+                const unsigned live = __ballot_sync(0xffffffffu, was_alive);
+                if (live) {
+                    const unsigned dm = __ballot_sync(0xffffffffu, dep);
+                    for (int c = 0; c < C; ++c) {
+                        const unsigned m = __ballot_sync(0xffffffffu, cls == c);
+                        const unsigned na = __popc(m & live), nd = __popc(m & dm);
+                        if (lane == 0) {
+                            if (na) atomicAdd(&s_alive[c], na);
+                            if (nd) atomicAdd(&s_dep[c], nd);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (counted && tid < C) {
+            if (s_alive[tid]) atomicAdd(&A.n_alive[(int64_t)s * C + tid], (unsigned long long)s_alive[tid]);
+            if (s_dep[tid]) atomicAdd(&A.n_dep[(int64_t)s * C + tid], (unsigned long long)s_dep[tid]);
+        }
+    }
+    if (tid == 0) {
+        __threadfence();
+        const unsigned long long prev = atomicAdd((unsigned long long*)&A.ctl[CTL_DONE], 1ull);
+        if (prev == gridDim.x - 1) {   // last CTA: advance the step, reset the queue
+            A.ctl[CTL_QUEUE] = 0;
+            A.ctl[CTL_DONE] = 0;
+            A.ctl[CTL_STEP] = step + 1;
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Work items: samples ordered by live count (largest first), one item per i-tile.
+// Single CTA of 1024 threads; order[] and items[] live in the caller workspace.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_buf, int& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) warp_buf[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? warp_buf[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += t;
+        }
+        if (lane < nw) warp_buf[lane] = wi - w;
+        if (lane == 31) warp_buf[32] = wi;
+    }
+    __syncthreads();
+    const int ex = warp_buf[warp] + incl - v;
+    total = warp_buf[32];
+    __syncthreads();
+    return ex;
+}
+
+__global__ void __launch_bounds__(1024) k_build_items(const int32_t* __restrict__ count, int S, int TI,
+                                                      int32_t* __restrict__ order, int2* __restrict__ items,
+                                                      int64_t* __restrict__ ctl) {
+    __shared__ int warp_buf[33];
+    const int tid = threadIdx.x;
+    for (int s = tid; s < S; s += blockDim.x) {
+        if (S <= 8192) {
+            const int cs = count[s];
+            int rank = 0;
+            for (int t = 0; t < S; ++t) {
+                const int ct = count[t];
+                rank += (ct > cs) || (ct == cs && t < s);
+            }
+            order[rank] = s;
+        } else {
+            order[s] = s;
+        }
+    }
+    __syncthreads();
+    int64_t running = 0;
+    for (int k0 = 0; k0 < S; k0 += blockDim.x) {
+        const int k = k0 + tid;
+        const int sidx = k < S ? order[k] : 0;
+        const int nt = k < S ? (count[sidx] + TI - 1) / TI : 0;
+        int total;
+        const int pre = block_exclusive_scan(nt, warp_buf, total);
+        for (int t = 0; t < nt; ++t) items[running + pre + t] = make_int2(sidx, t);
+        running += total;
+    }
+    if (tid == 0) {
+        ctl[CTL_NITEMS] = running;
+        ctl[CTL_QUEUE] = 0;
+        ctl[CTL_DONE] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Compaction: one CTA per sample, chunks of blockDim particles in order; all
+// loads of a chunk precede its writes, and writes land at or before the read
+// position, so the in-place pass is stable and race-free.
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(1024) k_compact(void* pos, void* vel, double2* xy, int2* tag,
+                                                  const int64_t* __restrict__ offset, int32_t* __restrict__ count) {
+    typedef typename Real<P>::T4 T4;
+    __shared__ int warp_buf[33];
+    const int s = blockIdx.x;
+    const int64_t o = offset[s];
+    const int n = count[s];
+    int out = 0;
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        T4 p, v;
+        double2 w = make_double2(0.0, 0.0);
+        int2 tg = make_int2(0, 0);
+        bool alive = false;
+        if (i < n) {
+            p = ((T4*)pos)[o + i];
+            v = ((T4*)vel)[o + i];
+            if (P == PDQ_MIXED) w = xy[o + i];
+            tg = tag[o + i];
+            alive = v.w > 0.5;
+        }
+        int total;
+        const int pre = block_exclusive_scan(alive ? 1 : 0, warp_buf, total);
+        if (alive) {
+            const int64_t d = o + out + pre;
+            ((T4*)pos)[d] = p;
+            ((T4*)vel)[d] = v;
+            if (P == PDQ_MIXED) xy[d] = w;
+            tag[d] = tg;
+        }
+        out += total;
+    }
+    if (threadIdx.x == 0) count[s] = out;
+}
+
+// ---------------------------------------------------------------------------
+// Deposition velocity per (sample, class) and the Monte Carlo mean / SE.
+// ---------------------------------------------------------------------------
+__global__ void k_vdep(const int64_t* __restrict__ nd, const int64_t* __restrict__ na, int n, double scale,
+                       double* __restrict__ vdep) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) vdep[k] = na[k] > 0 ? scale * (double)nd[k] / (double)na[k] : 0.0;
+}
+
+// One warp per class: lane-strided FP64 sums, then a fixed shuffle tree (deterministic).
+__global__ void k_vdep_stats(const double* __restrict__ vdep, int S, int C, double* mean, double* se) {
+    const int c = blockIdx.x, lane = threadIdx.x;
+    double s1 = 0.0;
+    for (int s = lane; s < S; s += 32) s1 += vdep[(int64_t)s * C + c];
+    for (int d = 16; d > 0; d >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, d);
+    const double mu = s1 / S;
+    double s2 = 0.0;
+    for (int s = lane; s < S; s += 32) {
+        const double e = vdep[(int64_t)s * C + c] - mu;
+        s2 += e * e;
+    }
+    for (int d = 16; d > 0; d >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, d);
+    if (lane == 0) {
+        if (mean) mean[c] = mu;
+        if (se) se[c] = S > 1 ? sqrt(s2 / (S - 1) / S) : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers.
+// ---------------------------------------------------------------------------
+static int validate_state(const pdq_state* st) {
+    if (!st || st->n_samples < 1 || st->n_classes < 1 || st->n_classes > PDQ_MAX_CLASSES || st->capacity < 0 ||
+        st->capacity > ((int64_t)1 << 31) - 1 || !st->offset || !st->count || !st->tag || !st->ctl ||
+        (st->cur != 0 && st->cur != 1))
+        return PDQ_ERR_INVALID_ARG;
+    if (st->precision != PDQ_FP64 && st->precision != PDQ_MIXED) return PDQ_ERR_INVALID_ARG;
+    for (int h = 0; h < 2; ++h) {
+        if (!st->pos[h] || !st->vel[h]) return PDQ_ERR_INVALID_ARG;
+        if (st->precision == PDQ_MIXED && !st->xy[h]) return PDQ_ERR_INVALID_ARG;
+    }
+    return PDQ_OK;
+}
+
+static int tile_threads(const pdq_state* st, const pdq_step_cfg* cfg) {
+    if (cfg && cfg->block) return cfg->block;
+    return st->precision == PDQ_FP64 ? 128 : 256;
+}
+static int tile_ilp(const pdq_state* st) { return st->precision == PDQ_FP64 ? 1 : 2; }
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <int P, int NT, int U>
+static int launch_step(const StepArgs& A, cudaStream_t s) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<P, NT, U>, NT, 0);
+        if (per_sm <= 0) per_sm = 1;
+    }
+    k_step<P, NT, U><<<sm_count() * per_sm, NT, 0, s>>>(A);
+    return PDQ_OK;
+}
+
+static int dispatch_step(int prec, int NT, const StepArgs& A, cudaStream_t s) {
+    if (prec == PDQ_FP64) {
+        if (NT == 64) return launch_step<PDQ_FP64, 64, 1>(A, s);
+        if (NT == 128) return launch_step<PDQ_FP64, 128, 1>(A, s);
+        if (NT == 256) return launch_step<PDQ_FP64, 256, 1>(A, s);
+    } else {
+        if (NT == 128) return launch_step<PDQ_MIXED, 128, 2>(A, s);
+        if (NT == 256) return launch_step<PDQ_MIXED, 256, 2>(A, s);
+        if (NT == 512) return launch_step<PDQ_MIXED, 512, 2>(A, s);
+    }
+    return PDQ_ERR_INVALID_ARG;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static void workspace_layout(const pdq_state* st, int TI, size_t* items_bytes, size_t* total) {
+    const int64_t max_items = st->capacity / TI + st->n_samples + 1;
+    *items_bytes = align256(sizeof(int2) * (size_t)max_items);
+    *total = *items_bytes + align256(sizeof(int32_t) * (size_t)st->n_samples);
+}
+
+static int enqueue_compact(pdq_state* st, cudaStream_t s) {
+    const int h = st->cur;
+    if (st->precision == PDQ_FP64)
+        k_compact<PDQ_FP64><<<st->n_samples, 1024, 0, s>>>(st->pos[h], st->vel[h], nullptr, (int2*)st->tag,
+                                                          st->offset, st->count);
+    else
+        k_compact<PDQ_MIXED><<<st->n_samples, 1024, 0, s>>>(st->pos[h], st->vel[h], (double2*)st->xy[h],
+                                                           (int2*)st->tag, st->offset, st->count);
+    return PDQ_OK;
+}
+
+}  // namespace pdq
+
+using namespace pdq;
+
+extern "C" int pdq_seed_particles(const pdq_field* field, const pdq_phys* phys, double charge_sigma, uint64_t seed,
+                                  const pdq_sample_params* params, pdq_state* st, pdq_stream_t stream) {
+    if (!field || !phys || !params || !(charge_sigma >= 0)) return PDQ_ERR_INVALID_ARG;
+    int rc = validate_state(st);
+    if (rc) return rc;
+    StepConst K;
+    rc = make_step_const(field, phys, st, &K);
+    if (rc) return rc;
+    SeedArgs A;
+    memset(&A, 0, sizeof(A));
+    A.offset = st->offset; A.count = st->count; A.ctl = st->ctl; A.params = params;
+    A.pos = st->pos[0]; A.vel = st->vel[0]; A.xy = (double2*)st->xy[0]; A.tag = (int2*)st->tag;
+    A.capacity = st->capacity; A.S = st->n_samples; A.C = st->n_classes; A.sigma = charge_sigma;
+    A.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    A.R = K.R; A.L = K.L;
+    for (int c = 0; c < st->n_classes; ++c) { A.half_d[c] = K.cls[c].half_d; A.qfac[c] = K.cls[c].qfac; }
+    const int64_t n = st->capacity > st->n_samples ? st->capacity : st->n_samples;
+    const unsigned blocks = (unsigned)((n + 255) / 256) + 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (st->precision == PDQ_FP64) k_seed<PDQ_FP64><<<blocks, 256, 0, s>>>(A);
+    else k_seed<PDQ_MIXED><<<blocks, 256, 0, s>>>(A);
+    PDQ_CUDA(cudaGetLastError());
+    st->cur = 0;
+    st->step = 0;
+    return PDQ_OK;
+}
+
+extern "C" int pdq_step_workspace_size(const pdq_state* st, const pdq_step_cfg* cfg, size_t* bytes) {
+    if (!bytes) return PDQ_ERR_INVALID_ARG;
+    int rc = validate_state(st);
+    if (rc) return rc;
+    size_t ib, tot;
+    workspace_layout(st, tile_threads(st, cfg) * tile_ilp(st), &ib, &tot);
+    *bytes = tot;
+    return PDQ_OK;
+}
+
+extern "C" int pdq_compact(pdq_state* st, pdq_stream_t stream) {
+    int rc = validate_state(st);
+    if (rc) return rc;
+    enqueue_compact(st, (cudaStream_t)stream);
+    PDQ_CUDA(cudaGetLastError());
+    return PDQ_OK;
+}
+
+extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, pdq_state* st,
+                                  const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
+                                  pdq_tally* tally, void* workspace, size_t workspace_bytes, pdq_stream_t stream) {
+    if (!field || !phys || !params || !cfg || !tally || !tally->n_dep || !tally->n_alive || n_steps < 0)
+        return PDQ_ERR_INVALID_ARG;
+    int rc = validate_state(st);
+    if (rc) return rc;
+    if (!(cfg->dt > 0) || (cfg->mode != PDQ_STICK && cfg->mode != PDQ_REBOUND) || (cfg->forces & ~PDQ_F_ALL) ||
+        cfg->compact_every < 0)
+        return PDQ_ERR_INVALID_ARG;
+    const int NT = tile_threads(st, cfg), U = tile_ilp(st);
+    if (st->precision == PDQ_FP64 ? (NT != 64 && NT != 128 && NT != 256) : (NT != 128 && NT != 256 && NT != 512))
+        return PDQ_ERR_INVALID_ARG;
+    size_t items_bytes, need;
+    workspace_layout(st, NT * U, &items_bytes, &need);
+    if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return PDQ_ERR_WORKSPACE;
+    if (n_steps == 0) return PDQ_OK;
+    StepArgs A;
+    memset(&A, 0, sizeof(A));
+    rc = make_step_const(field, phys, st, &A.K);
+    if (rc) return rc;
+    A.K.dt = cfg->dt;
+    A.K.forces = cfg->forces;
+    A.K.mode = cfg->mode;
+    A.K.window_start = cfg->window_start;
+    const double gplus = phys->g * phys->nu / pow(phys->re_tau * phys->nu / phys->radius, 3);
+    for (int k = 0; k < 3; ++k) { A.K.grav[k] = gplus * cfg->gravity[k]; A.K.gravf[k] = (float)A.K.grav[k]; }
+    A.K.dtf = (float)cfg->dt;
+    A.tag = (const int2*)st->tag; A.offset = st->offset; A.count = st->count; A.params = params;
+    A.items = (const int2*)workspace; A.ctl = st->ctl;
+    A.n_dep = (unsigned long long*)tally->n_dep; A.n_alive = (unsigned long long*)tally->n_alive;
+    int2* items = (int2*)workspace;
+    int32_t* order = (int32_t*)((char*)workspace + items_bytes);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    cudaGraph_t graph = nullptr;
+    const bool use_graph = cfg->use_graph != 0;
+    if (use_graph) PDQ_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int cur = st->cur;
+    int64_t stepi = st->step;
+    k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, order, items, st->ctl);
+    for (int64_t k = 0; k < n_steps; ++k) {
+        A.pos_in = st->pos[cur]; A.vel_in = st->vel[cur]; A.xy_in = (const double2*)st->xy[cur];
+        A.pos_out = st->pos[cur ^ 1]; A.vel_out = st->vel[cur ^ 1]; A.xy_out = (double2*)st->xy[cur ^ 1];
+        dispatch_step(st->precision, NT, A, s);
+        cur ^= 1;
+        ++stepi;
+        if (cfg->compact_every > 0 && stepi % cfg->compact_every == 0 && k + 1 < n_steps) {
+            st->cur = cur;
+            enqueue_compact(st, s);
+            k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, order, items, st->ctl);
+        }
+    }
+    if (use_graph) {
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    PDQ_CUDA(cudaGetLastError());
+    st->cur = cur;
+    st->step = stepi;
+    return PDQ_OK;
+}
+
+extern "C" int pdq_check_state(pdq_state* st, pdq_stream_t stream) {
+    if (!st || !st->ctl) return PDQ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t word = 0;
+    PDQ_CUDA(cudaMemcpyAsync(&word, st->ctl + CTL_ERROR, sizeof(word), cudaMemcpyDeviceToHost, s));
+    PDQ_CUDA(cudaStreamSynchronize(s));
+    if (word) {
+        const int64_t zero = 0;
+        PDQ_CUDA(cudaMemcpy(st->ctl + CTL_ERROR, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    }
+    if (word & ERR_NONFINITE) return PDQ_ERR_NAN;
+    return word ? PDQ_ERR_TIMEOUT : PDQ_OK;
+}
+
+extern "C" int pdq_deposition_tally(const pdq_tally* t, int32_t S, int32_t C, double dt, double r_plus, double* vdep,
+                                    double* mean, double* se, pdq_stream_t stream) {
+    if (!t || !t->n_dep || !t->n_alive || S < 1 || C < 1 || !(dt > 0) || !(r_plus > 0) || !vdep)
+        return PDQ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = S * C;
+    k_vdep<<<(n + 255) / 256, 256, 0, s>>>(t->n_dep, t->n_alive, n, 0.5 * r_plus / dt, vdep);
+    if (mean || se) k_vdep_stats<<<C, 32, 0, s>>>(vdep, S, C, mean, se);
+    PDQ_CUDA(cudaGetLastError());
+    return PDQ_OK;
+}

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libpdq (include/pdq.h).
+
+Argument marshalling only: torch provides device memory and streams, every
+step of the particle path runs in libpdq's kernels.  Importing this module
+fails loudly when libpdq.so has not been built; there is no CPU fallback.
+"""
+import ctypes as C
+import math
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpdq.so")
+
+PDQ_OK = 0
+FP64, MIXED = 0, 1
+STICK, REBOUND = 0, 1
+F_DRAG, F_GRAVITY, F_COULOMB, F_IMAGE, F_VDW, F_ALL = 1, 2, 4, 8, 16, 31
+MAX_CLASSES = 16
+
+
+class PdqError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__("%s failed: %s (%d)" % (where, lib().pdq_strerror(status).decode(), status))
+        self.status = status
+
+
+class Phys(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "nu", "radius", "re_tau", "u_bulk", "rho_p", "rho_f", "eps0", "q_unit", "hamaker0", "delta_min",
+        "young", "delta_c", "sigma_y0", "g")]
+
+
+class FieldDesc(C.Structure):
+    _fields_ = [("n_r", C.c_int32), ("n_th", C.c_int32), ("n_z", C.c_int32), ("n_modes", C.c_int32),
+                ("r_plus", C.c_double), ("l_plus", C.c_double), ("u_rms", C.c_double), ("beta", C.c_double),
+                ("kappa", C.c_double), ("b_log", C.c_double), ("k_min", C.c_double), ("k_max", C.c_double)]
+
+
+class StateStruct(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("cur", C.c_int32), ("n_samples", C.c_int32), ("n_classes", C.c_int32),
+                ("st_plus", C.c_double * MAX_CLASSES), ("capacity", C.c_int64), ("step", C.c_int64),
+                ("offset", C.c_void_p), ("count", C.c_void_p), ("pos", C.c_void_p * 2), ("vel", C.c_void_p * 2),
+                ("xy", C.c_void_p * 2), ("tag", C.c_void_p), ("ctl", C.c_void_p)]
+
+
+class StepCfg(C.Structure):
+    _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("mode", C.c_int32), ("forces", C.c_int32),
+                ("window_start", C.c_int64), ("compact_every", C.c_int32), ("block", C.c_int32),
+                ("use_graph", C.c_int32), ("pad", C.c_int32)]
+
+
+class TallyStruct(C.Structure):
+    _fields_ = [("n_dep", C.c_void_p), ("n_alive", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libpdq.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libpdq.so is not built (%s); run __graft_entry__.build() on a machine with nvcc"
+                              % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        sig = {
+            "pdq_strerror": (C.c_char_p, [C.c_int]),
+            "pdq_version": (C.c_int, []),
+            "pdq_phys_default": (None, [C.POINTER(Phys)]),
+            "pdq_create_pipe_field": (C.c_int, [C.POINTER(FieldDesc), C.c_uint64, P, C.POINTER(P)]),
+            "pdq_destroy_pipe_field": (C.c_int, [P]),
+            "pdq_field_views": (C.c_int, [P, C.POINTER(FieldDesc), P, P, P]),
+            "pdq_field_copy": (C.c_int, [P, P, P, P, P]),
+            "pdq_seed_particles": (C.c_int, [P, C.POINTER(Phys), C.c_double, C.c_uint64, P,
+                                             C.POINTER(StateStruct), P]),
+            "pdq_step_workspace_size": (C.c_int, [C.POINTER(StateStruct), C.POINTER(StepCfg),
+                                                  C.POINTER(C.c_size_t)]),
+            "pdq_step_particles": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P, C.POINTER(StepCfg),
+                                             C.c_int64, C.POINTER(TallyStruct), P, C.c_size_t, P]),
+            "pdq_compact": (C.c_int, [C.POINTER(StateStruct), P]),
+            "pdq_check_state": (C.c_int, [C.POINTER(StateStruct), P]),
+            "pdq_deposition_tally": (C.c_int, [C.POINTER(TallyStruct), C.c_int32, C.c_int32, C.c_double,
+                                               C.c_double, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype, fn.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != PDQ_OK:
+        raise PdqError(rc, where)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def phys_default():
+    p = Phys()
+    lib().pdq_phys_default(C.byref(p))
+    return p
+
+
+def field_desc(n_r=64, n_th=32, n_z=64, n_modes=64, r_plus=180.0, l_over_r=4.0, u_rms=1.0, beta=2.0,
+               kappa=0.41, b_log=5.2, lam_min=20.0, lam_max=400.0):
+    """Field descriptor; the mode shell spans wavelengths lam_min..lam_max (wall units)."""
+    return FieldDesc(n_r, n_th, n_z, n_modes, r_plus, l_over_r * r_plus, u_rms, beta, kappa, b_log,
+                     2 * math.pi / lam_max, 2 * math.pi / lam_min)
+
+
+class Field:
+    """Owning wrapper of a pdq_field handle."""
+
+    def __init__(self, desc, seed, stream=None):
+        self.desc = desc
+        h = C.c_void_p()
+        _check(lib().pdq_create_pipe_field(C.byref(desc), seed, _stream(stream), C.byref(h)), "create_pipe_field")
+        self.handle = h
+
+    def grids(self, stream=None):
+        d = self.desc
+        g64 = torch.empty((d.n_z, d.n_th, d.n_r, 4), dtype=torch.float64, device="cuda")
+        g32 = torch.empty((d.n_z, d.n_th, d.n_r, 4), dtype=torch.float32, device="cuda")
+        modes = torch.empty((max(d.n_modes, 1), 7), dtype=torch.float64, device="cuda")
+        _check(lib().pdq_field_copy(self.handle, _ptr(g64), _ptr(g32), _ptr(modes), _stream(stream)), "field_copy")
+        return g64, g32, modes[: d.n_modes]
+
+    def close(self):
+        if self.handle:
+            lib().pdq_destroy_pipe_field(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class State:
+    """Caller-owned particle state (torch tensors) plus its pdq_state struct."""
+
+    def __init__(self, precision, counts, st_plus, device="cuda"):
+        counts = [int(c) for c in counts]
+        S = len(counts)
+        if not 1 <= len(st_plus) <= MAX_CLASSES:
+            raise ValueError("1..16 size classes")
+        off = [0]
+        for c in counts:
+            off.append(off[-1] + c)
+        n = max(off[-1], 1)
+        dev = torch.device(device)
+        self.precision = precision
+        self.counts0 = counts
+        self.offset = torch.tensor(off, dtype=torch.int64, device=dev)
+        self.count = torch.tensor(counts, dtype=torch.int32, device=dev)
+        fdt = torch.float64 if precision == FP64 else torch.float32
+        self.pos = [torch.zeros((n, 4), dtype=fdt, device=dev) for _ in range(2)]
+        self.vel = [torch.zeros((n, 4), dtype=fdt, device=dev) for _ in range(2)]
+        self.xy = [torch.zeros((n, 2), dtype=torch.float64, device=dev) for _ in range(2)] if precision == MIXED else None
+        self.tag = torch.zeros((n, 2), dtype=torch.int32, device=dev)
+        self.ctl = torch.zeros(8, dtype=torch.int64, device=dev)
+        s = StateStruct()
+        s.precision, s.cur, s.n_samples, s.n_classes = precision, 0, S, len(st_plus)
+        for k, v in enumerate(st_plus):
+            s.st_plus[k] = float(v)
+        s.capacity, s.step = off[-1], 0
+        s.offset, s.count = self.offset.data_ptr(), self.count.data_ptr()
+        for h in range(2):
+            s.pos[h] = self.pos[h].data_ptr()
+            s.vel[h] = self.vel[h].data_ptr()
+            s.xy[h] = self.xy[h].data_ptr() if self.xy else None
+        s.tag, s.ctl = self.tag.data_ptr(), self.ctl.data_ptr()
+        self.st = s
+        self.n_samples, self.n_classes, self.st_plus = S, len(st_plus), list(st_plus)
+
+    @property
+    def cur(self):
+        return self.st.cur
+
+    @property
+    def step_index(self):
+        return self.st.step
+
+    def current(self):
+        """(pos, vel, xy or None) tensors of the current half."""
+        h = self.st.cur
+        return self.pos[h], self.vel[h], (self.xy[h] if self.xy else None)
+
+    def positions64(self):
+        """[N, 3] float64 positions of the current half (x, y from the FP64 copy in MIXED)."""
+        pos, _, xy = self.current()
+        out = pos[:, :3].double().clone()
+        if xy is not None:
+            out[:, :2] = xy
+        return out
+
+
+class Tally:
+    def __init__(self, n_samples, n_classes, device="cuda"):
+        self.n_dep = torch.zeros((n_samples, n_classes), dtype=torch.int64, device=device)
+        self.n_alive = torch.zeros((n_samples, n_classes), dtype=torch.int64, device=device)
+        self.t = TallyStruct(self.n_dep.data_ptr(), self.n_alive.data_ptr())
+
+    def zero_(self):
+        self.n_dep.zero_()
+        self.n_alive.zero_()
+
+
+def step_cfg(dt, forces=F_ALL, mode=STICK, gravity=(0.0, 0.0, 1.0), window_start=0, compact_every=0, block=0,
+             use_graph=False):
+    c = StepCfg()
+    c.dt = dt
+    for k in range(3):
+        c.gravity[k] = gravity[k]
+    c.mode, c.forces, c.window_start = mode, forces, window_start
+    c.compact_every, c.block, c.use_graph = compact_every, block, int(bool(use_graph))
+    return c
+
+
+def params_tensor(params, device="cuda"):
+    """[S, 3] (xi, zeta, theta) -> device pdq_sample_params[S] (float64 [S, 4])."""
+    p = torch.as_tensor(params, dtype=torch.float64).reshape(-1, 3)
+    out = torch.zeros((p.shape[0], 4), dtype=torch.float64)
+    out[:, :3] = p
+    return out.to(device)
+
+
+def seed_particles(field, phys, state, params_dev, seed, charge_sigma=0.0, stream=None):
+    _check(lib().pdq_seed_particles(field.handle, C.byref(phys), charge_sigma, seed, _ptr(params_dev),
+                                    C.byref(state.st), _stream(stream)), "seed_particles")
+
+
+def workspace(state, cfg):
+    n = C.c_size_t()
+    _check(lib().pdq_step_workspace_size(C.byref(state.st), C.byref(cfg), C.byref(n)), "step_workspace_size")
+    return torch.empty(max(int(n.value), 256), dtype=torch.uint8, device="cuda")
+
+
+def step_particles(field, phys, state, params_dev, cfg, n_steps, tally, ws, stream=None):
+    _check(lib().pdq_step_particles(field.handle, C.byref(phys), C.byref(state.st), _ptr(params_dev), C.byref(cfg),
+                                    int(n_steps), C.byref(tally.t), _ptr(ws), ws.numel(), _stream(stream)),
+           "step_particles")
+
+
+def compact(state, stream=None):
+    _check(lib().pdq_compact(C.byref(state.st), _stream(stream)), "compact")
+
+
+def check_state(state, stream=None):
+    return lib().pdq_check_state(C.byref(state.st), _stream(stream))
+
+
+def deposition_tally(tally, dt, r_plus=180.0, stream=None):
+    """(vdep [S, C], mean [C], se [C]) device float64 tensors."""
+    S, Cn = tally.n_dep.shape
+    vdep = torch.empty((S, Cn), dtype=torch.float64, device="cuda")
+    mean = torch.empty(Cn, dtype=torch.float64, device="cuda")
+    se = torch.empty(Cn, dtype=torch.float64, device="cuda")
+    _check(lib().pdq_deposition_tally(C.byref(tally.t), S, Cn, dt, r_plus, _ptr(vdep), _ptr(mean), _ptr(se),
+                                      _stream(stream)), "deposition_tally")
+    return vdep, mean, se

@@ -1,0 +1,64 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+function include/pdq.h declares, and rejects invalid arguments before touching a device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pdq():
+    from paper_2205_04979_gb300 import build
+    build.build()
+    import paper_2205_04979_gb300.pdq as p
+    p.lib()
+    return p
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pdq.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pdq_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_function(pdq):
+    names = declared_functions()
+    assert len(names) >= 12
+    L = pdq.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_status_strings_and_defaults(pdq):
+    L = pdq.lib()
+    assert L.pdq_strerror(0) == b"ok"
+    assert b"invalid" in L.pdq_strerror(-1)
+    assert L.pdq_version() >= 100
+    p = pdq.phys_default()
+    assert p.re_tau == 180.0 and p.rho_p == 2650.0 and p.delta_min == 1e-9
+
+
+def test_invalid_arguments_rejected_on_host(pdq):
+    L = pdq.lib()
+    P = C.c_void_p
+    # NULL descriptor / handle
+    assert L.pdq_create_pipe_field(None, 0, None, None) == -1
+    d = pdq.field_desc(n_r=1)
+    h = C.c_void_p()
+    assert L.pdq_create_pipe_field(C.byref(d), 0, None, C.byref(h)) == -1
+    d = pdq.field_desc(n_modes=5000)
+    assert L.pdq_create_pipe_field(C.byref(d), 0, None, C.byref(h)) == -1
+    assert L.pdq_destroy_pipe_field(None) == -1
+    # state with bad precision / class count
+    s = pdq.StateStruct()
+    s.precision, s.n_samples, s.n_classes = 7, 1, 1
+    n = C.c_size_t()
+    assert L.pdq_step_workspace_size(C.byref(s), None, C.byref(n)) == -1
+    s.precision, s.n_classes = 0, 0
+    assert L.pdq_step_workspace_size(C.byref(s), None, C.byref(n)) == -1
+    t = pdq.TallyStruct()
+    assert L.pdq_deposition_tally(C.byref(t), 1, 1, 0.1, 180.0, None, None, None, None) == -1
+    assert L.pdq_step_particles(None, None, None, None, None, 1, None, None, 0, None) == -1

@@ -1,0 +1,279 @@
+"""GPU-vs-oracle parity of the particle path, through the C ABI (libpdq).
+
+Sizes span several CTA tiles with a ragged tail.  Tolerances: FP64 states
+agree to 1e-12 relative after one step and 1e-9 after 50 steps (the kernels
+sum the Coulomb pairs in the oracle's order; differences come from rounding
+of rsqrt, FMA contraction and libm); integer data (ids, classes, tallies) are
+bit-exact.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pdq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_04979_gb300 import build
+    build.build()
+    import paper_2205_04979_gb300.pdq as p
+    return p
+
+
+GRID = dict(n_r=33, n_th=16, n_z=32)
+
+
+@pytest.fixture(scope="module")
+def fields(pdq):
+    f = pdq.Field(pdq.field_desc(**GRID), 0)
+    of = oracle.field_desc(**GRID)
+    modes = oracle.field_modes(of, 0)
+    return f, of, oracle.field_grid(of, modes), modes
+
+
+def test_field_parity(pdq, fields):
+    f, of, grid, modes = fields
+    g64, g32, m = f.grids()
+    assert np.allclose(m.cpu().numpy(), modes, rtol=1e-13, atol=1e-15)
+    g64 = g64.cpu().numpy()[..., :3]
+    assert np.max(np.abs(g64 - grid)) < 1e-11
+    g32 = g32.cpu().numpy()[..., :3]
+    assert np.max(np.abs(g32 - grid)) < 1e-5 * (1 + np.max(np.abs(grid)))
+
+
+def test_field_full_size_against_analytic(pdq):
+    # 128 x 64 x 128 grid (2^20 nodes): sampled nodes against the oracle's analytic field
+    desc = pdq.field_desc(n_r=128, n_th=64, n_z=128)
+    f = pdq.Field(desc, 0)
+    g64, _, _ = f.grids()
+    of = oracle.field_desc(n_r=128, n_th=64, n_z=128)
+    m = oracle.field_modes(of, 0)
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, [128, 64, 128], size=(200, 3))
+    k, j, i = idx[:, 0], idx[:, 1], idx[:, 2]
+    r = 180.0 * np.tanh(2.0 * i / 127) / np.tanh(2.0)
+    th = 2 * np.pi * j / 64
+    P = np.stack([r * np.cos(th), r * np.sin(th), of.l_plus * k / 128], 1)
+    ref = oracle.field_velocity(of, m, P)
+    got = g64.cpu().numpy()[k, j, i, :3]
+    assert np.max(np.abs(got - ref)) < 1e-11
+
+
+def _setup(pdq, fields, precision, counts, st_plus, params, sigma=0.0, seed=1):
+    f, of, grid, _ = fields
+    phys = pdq.phys_default()
+    st = pdq.State(precision, counts, st_plus)
+    prm = pdq.params_tensor(params)
+    pdq.seed_particles(f, phys, st, prm, seed, charge_sigma=sigma)
+    ost, off = oracle.seed(of, st_plus, counts, params, seed, charge_sigma=sigma)
+    return phys, st, prm, ost, off
+
+
+def _gpu_arrays(st):
+    pos, vel, _ = st.current()
+    x = st.positions64().cpu().numpy()
+    v = vel.double().cpu().numpy()
+    q = pos[:, 3].double().cpu().numpy()
+    tag = st.tag.cpu().numpy()
+    return x, v, q, tag
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_seed_parity(pdq, fields, precision):
+    st_plus = [0.1, 1.0, 10.0]
+    counts = [1000, 333, 1]
+    params = np.array([[0.05, 0.5, 0.5], [0.1, 0.2, 0.3], [0.02, 0.9, 0.1]])
+    _, st, _, ost, off = _setup(pdq, fields, precision, counts, st_plus, params, sigma=0.5)
+    x, v, q, tag = _gpu_arrays(st)
+    ref = np.stack([ost.x, ost.y, ost.z], 1)
+    assert np.array_equal(tag[:, 0], ost.id) and np.array_equal(tag[:, 1], ost.cls)
+    assert np.array_equal(st.count.cpu().numpy(), counts)
+    if precision == 0:
+        assert np.max(np.abs(x - ref)) < 1e-12 and np.allclose(q, ost.q, rtol=1e-13)
+    else:
+        assert np.max(np.abs(x[:, :2] - ref[:, :2])) < 1e-12            # FP64 wall-normal position
+        assert np.max(np.abs(x[:, 2] - ref[:, 2])) < 1e-4 and np.allclose(q, ost.q, rtol=1e-6)
+    assert np.all(v[:, :3] == 0) and np.all(v[:, 3] == 1)
+
+
+def _run_both(pdq, fields, precision, counts, st_plus, params, n_steps, cfg_kw, sigma=0.0, block=0):
+    f, of, grid, _ = fields
+    phys, st, prm, ost, off = _setup(pdq, fields, precision, counts, st_plus, params, sigma)
+    cfg = pdq.step_cfg(0.1, block=block, **cfg_kw)
+    tally = pdq.Tally(len(counts), len(st_plus))
+    ws = pdq.workspace(st, cfg)
+    pdq.step_particles(f, phys, st, prm, cfg, n_steps, tally, ws)
+    assert pdq.check_state(st) == 0
+    ocfg = oracle.cfg(0.1, **{k: v for k, v in cfg_kw.items() if k != "compact_every"})
+    nd, na = oracle.run(of, grid, ocfg, st_plus, off, params, ost, n_steps)
+    return st, tally, ost, nd, na
+
+
+def _compare_by_id(st, ost, off, tol_x, tol_v, max_flip=0):
+    """Match live GPU particles to oracle particles by (sample, id); compare states."""
+    x, v, q, tag = _gpu_arrays(st)
+    counts = st.count.cpu().numpy()
+    offs = st.offset.cpu().numpy()
+    ref_x = np.stack([ost.x, ost.y, ost.z], 1)
+    ref_v = np.stack([ost.vx, ost.vy, ost.vz], 1)
+    n_live = 0
+    for s in range(len(counts)):
+        sl = slice(offs[s], offs[s] + counts[s])
+        ids = tag[sl, 0]
+        alive = v[sl, 3] > 0.5
+        gidx = off[s] + ids
+        live = alive & (ost.alive[gidx] == 1)
+        mism = np.sum(alive != (ost.alive[gidx] == 1))
+        assert mism <= max_flip * len(ids), "deposition decisions differ for %d particles" % mism
+        dx = np.abs(x[sl][live] - ref_x[gidx[live]])
+        dz = dx[:, 2]
+        dz = np.minimum(dz, 720.0 - dz)          # periodic z, checked against the length L = 720
+        dx[:, 2] = dz
+        scale = 1 + np.abs(ref_x[gidx[live]])
+        scale[:, 2] = 720.0
+        assert np.all(dx <= tol_x * scale), np.max(dx / scale)
+        dv = np.abs(v[sl][live, :3] - ref_v[gidx[live]])
+        assert np.all(dv <= tol_v * (1 + np.abs(ref_v[gidx[live]]))), np.max(dv)
+        n_live += live.sum()
+    return n_live
+
+
+ST3 = [0.1, 1.0, 10.0]
+PRM3 = np.array([[0.1, 0.5, 0.5], [0.08, 0.7, 0.2], [0.05, 0.3, 0.9]])
+
+
+def test_fp64_one_step_parity(pdq, fields):
+    counts = [1000, 333, 129]
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3, 1, {})
+    assert _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 1e-12, 1e-12) > 0
+    assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
+
+
+@pytest.mark.parametrize("block", [64, 128, 256])
+def test_fp64_fifty_steps_parity(pdq, fields, block):
+    counts = [1000, 333, 129]
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3, 50, {"window_start": 10}, block=block)
+    assert _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 1e-9, 1e-9) > 0
+    assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
+    assert nd.sum() > 0          # particles did deposit
+
+
+def test_fp64_compaction_parity(pdq, fields):
+    counts = [1000, 333, 129]
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3, 50,
+                                       {"window_start": 0, "compact_every": 7})
+    n_live = _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 1e-9, 1e-9)
+    assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
+    # compaction kept exactly the live particles, in id order
+    cnt = st.count.cpu().numpy()
+    assert cnt.sum() == n_live == ost.alive.sum()
+    tag = st.tag.cpu().numpy()
+    offs = st.offset.cpu().numpy()
+    for s in range(3):
+        ids = tag[offs[s]:offs[s] + cnt[s], 0]
+        assert np.all(np.diff(ids) > 0)
+
+
+def test_fp64_rebound_parity(pdq, fields):
+    # Rebounding particles bounce inside the stiff vdW zone (accelerations ~1e4 wall units),
+    # which amplifies rounding differences: the bound is 10x the oracle's own response to a
+    # 1e-14 relative perturbation of the initial positions, floored at 1e-9.
+    f, of, grid, _ = fields
+    counts = [700, 300]
+    prm = np.array([[0.1, 0.05, 0.1], [0.1, 1.0, 0.9]])   # mostly rebound / mostly stick
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, prm, 50, {"mode": 1})
+    a, off = oracle.seed(of, ST3, counts, prm, 1)
+    b = a.copy()
+    b.x *= 1 + 1e-14
+    oracle.run(of, grid, oracle.cfg(0.1, mode=1), ST3, off, prm, a, 50)
+    oracle.run(of, grid, oracle.cfg(0.1, mode=1), ST3, off, prm, b, 50)
+    sens = np.max(np.abs(a.x - b.x)[(a.alive == 1) & (b.alive == 1)])
+    _compare_by_id(st, ost, off, max(1e-9, 10 * sens / 180.0), max(1e-9, 10 * sens))
+    assert np.array_equal(tally.n_dep.cpu().numpy(), nd)
+
+
+def test_fp64_rebound_one_step_exact(pdq, fields):
+    # constructed states just inside the wall, moving outward: every particle hits the wall in
+    # this step; low zeta rebounds (CoR from Sec. 4.3), high zeta sticks
+    f, of, grid, _ = fields
+    phys = pdq.phys_default()
+    n = 600
+    rng = np.random.default_rng(3)
+    cls = (np.arange(n) % 3).astype(np.int32)
+    dplus = oracle.class_table(ST3)[:, 1]
+    gap = rng.uniform(0.0, 0.3, n)
+    r = 180.0 - 0.5 * dplus[cls] - gap
+    th = rng.uniform(0, 2 * np.pi, n)
+    vr = rng.uniform(4.0, 40.0, n)
+    x, y, z = r * np.cos(th), r * np.sin(th), rng.uniform(0, 720.0, n)
+    vx, vy, vz = vr * np.cos(th), vr * np.sin(th), rng.uniform(-5, 5, n)
+    q = 0.05 * oracle.class_table(ST3)[cls, 4]
+    counts = [400, 200]
+    prm = np.array([[0.05, 0.02, 0.0], [0.05, 1.0, 0.95]])
+    st = pdq.State(0, counts, ST3)
+    pos, vel, _ = st.current()
+    pos.copy_(torch.tensor(np.stack([x, y, z, q], 1)))
+    vel.copy_(torch.tensor(np.stack([vx, vy, vz, np.ones(n)], 1)))
+    st.tag.copy_(torch.tensor(np.stack([np.r_[np.arange(400), np.arange(200)], cls], 1), dtype=torch.int32))
+    cfg = pdq.step_cfg(0.1, mode=1)
+    tally = pdq.Tally(2, 3)
+    pdq.step_particles(f, phys, st, pdq.params_tensor(prm), cfg, 1, tally, pdq.workspace(st, cfg))
+    ost = oracle.State(n)
+    ost.x, ost.y, ost.z, ost.vx, ost.vy, ost.vz, ost.q = x.copy(), y.copy(), z.copy(), vx.copy(), vy.copy(), vz.copy(), q
+    ost.cls = cls.copy()
+    off = np.array([0, 400, 600])
+    nd, _ = oracle.run(of, grid, oracle.cfg(0.1, mode=1), ST3, off, prm, ost, 1)
+    assert nd[0].sum() == 0 and nd[1].sum() > 100          # sample 0 rebounds, sample 1 mostly sticks
+    _compare_by_id(st, ost, off, 1e-12, 1e-12)
+    assert np.array_equal(tally.n_dep.cpu().numpy(), nd)
+
+
+def test_fp64_lognormal_charge_parity(pdq, fields):
+    counts = [900]
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3[:1], 20, {}, sigma=0.5)
+    _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 1e-9, 1e-9)
+
+
+def test_mixed_parity(pdq, fields):
+    # FP32 pair sum / interpolation / velocities, FP64 wall-normal position
+    counts = [1000, 333, 129]
+    st, tally, ost, nd, na = _run_both(pdq, fields, 1, counts, ST3, PRM3, 20, {})
+    _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 2e-6, 2e-5, max_flip=0.005)
+
+
+def test_vdep_tally_parity(pdq, fields):
+    counts = [1000, 333, 129]
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3, 50, {"window_start": 10})
+    vdep, mean, se = pdq.deposition_tally(tally, 0.1)
+    ref = oracle.vdep(nd, na, 0.1)
+    assert np.allclose(vdep.cpu().numpy(), ref, rtol=1e-14, atol=0)
+    assert np.allclose(mean.cpu().numpy(), ref.mean(0), rtol=1e-13)
+    assert np.allclose(se.cpu().numpy(), ref.std(0, ddof=1) / np.sqrt(3), rtol=1e-12)
+
+
+def test_edge_cases(pdq, fields):
+    f, of, grid, _ = fields
+    phys = pdq.phys_default()
+    # an empty sample between non-empty ones, and a single-particle sample
+    counts = [0, 5, 1, 0]
+    st = pdq.State(0, counts, [1.0])
+    prm = pdq.params_tensor(np.tile([0.05, 0.5, 0.5], (4, 1)))
+    pdq.seed_particles(f, phys, st, prm, 1)
+    cfg = pdq.step_cfg(0.1, compact_every=1)
+    tally = pdq.Tally(4, 1)
+    ws = pdq.workspace(st, cfg)
+    pdq.step_particles(f, phys, st, prm, cfg, 0, tally, ws)        # zero steps: no-op
+    pdq.step_particles(f, phys, st, prm, cfg, 3, tally, ws)
+    assert pdq.check_state(st) == 0
+    assert st.step_index == 3
+    ost, off = oracle.seed(of, [1.0], counts, prm.cpu().numpy()[:, :3], 1)
+    oracle.run(of, grid, oracle.cfg(0.1), [1.0], off, prm.cpu().numpy()[:, :3], ost, 3)
+    _compare_by_id(st, ost, off, 1e-12, 1e-12)
+    # workspace too small
+    with pytest.raises(pdq.PdqError):
+        pdq.step_particles(f, phys, st, prm, cfg, 1, tally, ws[:16])
