@@ -223,6 +223,33 @@ int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, pdq_state* 
                        const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
                        pdq_tally* tally, void* workspace, size_t workspace_bytes, pdq_stream_t stream);
 
+/* Built-in scratch size of pdq_step_particles_noalloc, bytes. */
+#define PDQ_NOALLOC_SCRATCH_BYTES (1u << 20)
+
+/* pdq_step_particles for callers that cannot allocate device memory: for
+ * example a host program whose device memory is owned by another allocator or
+ * held under a hard cap, or a latency-critical loop that must not call
+ * cudaMalloc (which can synchronise the device).  The paper has no
+ * counterpart; this is a deployment variant of the step above, with the same
+ * arguments and results except that the work queue lives in a 1 MiB array
+ * compiled into libpdq (PDQ_NOALLOC_SCRATCH_BYTES), which every GPU that
+ * loads the library keeps until the process exits.  The call allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * Limits: the state must fit the scratch, i.e. pdq_step_workspace_size() <=
+ * PDQ_NOALLOC_SCRATCH_BYTES (about capacity / (threads x particles per
+ * thread) + 1.5 S items of 8 bytes), else PDQ_ERR_WORKSPACE; cfg->use_graph
+ * must be 0 (PDQ_ERR_INVALID_ARG otherwise).
+ * Set-up: the first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.
+ * Sharing: all calls share the one array and it keeps the last call's
+ * contents; each call rebuilds the work queue before using it, so nothing
+ * needs clearing, but calls whose GPU work overlaps (different streams, or
+ * host threads, without ordering between them) race on it.                  */
+int pdq_step_particles_noalloc(const pdq_field* field, const pdq_phys* phys, pdq_state* state,
+                               const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
+                               pdq_tally* tally, pdq_stream_t stream);
+
 /* Stream compaction of deposited particles (alive == 0) of every sample, in
  * place and order-preserving on the current half; updates count[].          */
 int pdq_compact(pdq_state* state, pdq_stream_t stream);

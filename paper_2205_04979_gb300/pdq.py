@@ -81,6 +81,8 @@ def lib():
                                                   C.POINTER(C.c_size_t)]),
             "pdq_step_particles": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P, C.POINTER(StepCfg),
                                              C.c_int64, C.POINTER(TallyStruct), P, C.c_size_t, P]),
+            "pdq_step_particles_noalloc": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P,
+                                                     C.POINTER(StepCfg), C.c_int64, C.POINTER(TallyStruct), P]),
             "pdq_compact": (C.c_int, [C.POINTER(StateStruct), P]),
             "pdq_check_state": (C.c_int, [C.POINTER(StateStruct), P]),
             "pdq_deposition_tally": (C.c_int, [C.POINTER(TallyStruct), C.c_int32, C.c_int32, C.c_double,
@@ -253,6 +255,13 @@ def step_particles(field, phys, state, params_dev, cfg, n_steps, tally, ws, stre
     _check(lib().pdq_step_particles(field.handle, C.byref(phys), C.byref(state.st), _ptr(params_dev), C.byref(cfg),
                                     int(n_steps), C.byref(tally.t), _ptr(ws), ws.numel(), _stream(stream)),
            "step_particles")
+
+
+def step_particles_noalloc(field, phys, state, params_dev, cfg, n_steps, tally, stream=None):
+    """The step without a caller workspace (uses libpdq's built-in 1 MiB scratch)."""
+    _check(lib().pdq_step_particles_noalloc(field.handle, C.byref(phys), C.byref(state.st), _ptr(params_dev),
+                                            C.byref(cfg), int(n_steps), C.byref(tally.t), _stream(stream)),
+           "step_particles_noalloc")
 
 
 def compact(state, stream=None):
