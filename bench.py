@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--block", type=int, default=0, help="threads per CTA of the step kernel (0 = library default)")
+    ap.add_argument("--variant", type=int, default=0, help="MIXED pair-math variant")
     return ap.parse_args()
 
 
@@ -185,7 +187,8 @@ def run_ours(args):
         state = pdq.State(prec, counts, w["st_plus"])
         prm = pdq.params_tensor(params)
         pdq.seed_particles(field, phys, state, prm, w["particle_seed"], w.get("charge_sigma", 0.0), stream)
-        cfg = pdq.step_cfg(w["dt"], window_start=0, compact_every=w.get("compact_every", 0))
+        cfg = pdq.step_cfg(w["dt"], window_start=0, compact_every=w.get("compact_every", 0), block=args.block,
+                           variant=args.variant)
         tally = pdq.Tally(len(counts), len(w["st_plus"]))
         ws = pdq.workspace(state, cfg)
         pdq.step_particles(field, phys, state, prm, cfg, args.warmup, tally, ws, stream)
@@ -302,7 +305,12 @@ def run_ours(args):
                        sum(t.numel() * t.element_size() for t in state.current() if t is not None) / 1e9),
                    "parallelism": "samples sharded by rank" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
+                     "frac": achieved / peak_tflops,
+                     # dram bytes read + written per launch from the ncu capture in
+                     # profiles/k_step_mixed_batched.md (484.2 MB for 4,557,792 particles),
+                     # scaled by the particle count of this launch
+                     "traffic": 484.2e6 / 4557792 * float(np.sum(counts)) if args.variant == 0 and prec == pdq.MIXED
+                     else None,
                      "kernel": "k_step (all-pairs Coulomb + local step)",
                      "note": "FP32 pipe peak = 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock); "
                              "%d flops per ordered pair; time per step from CUDA events over the timed region"

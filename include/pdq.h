@@ -184,9 +184,9 @@ typedef struct pdq_step_cfg {
     int32_t forces;       /* PDQ_F_* mask                                                    */
     int64_t window_start; /* first global step index counted in the tallies (t+ >= t_w)      */
     int32_t compact_every;/* compact deposited particles out every this many steps; 0 never */
-    int32_t block;        /* threads per CTA of the step kernel: 0 (auto), 128, 256 or 512   */
+    int32_t block;        /* threads per CTA of the step kernel: 0 (auto), 64, 128 or 256    */
     int32_t use_graph;    /* 1: replay the step sequence as a CUDA graph                     */
-    int32_t pad;
+    int32_t variant;      /* MIXED pair-math variant: 0 packed f32x2, 1 packed + scalar sums */
 } pdq_step_cfg;
 
 /* Caller-owned tallies, device int64 [S][C], accumulated across calls:

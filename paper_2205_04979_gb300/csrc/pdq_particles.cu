@@ -249,6 +249,76 @@ __device__ __forceinline__ void coulomb_pair(double xi, double yi, double zi, co
     az = __fma_rn(s, dz, az);
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32 pair math (sm_100+ f32x2 instructions): one 64-bit register holds
+// the same quantity for two i-particles, so each FMA-pipe instruction serves
+// two pairs.  rsqrt is the flush-to-zero hardware approximation (no denormal
+// fix-up path; pair distances are clamped at the contact distance anyway).
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) { f2 d; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) { f2 d; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) { f2 d; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Two ordered pairs (i_a, j), (i_b, j) of the Coulomb sum in packed form.
+// j = (xj, xj), (yj, yj), (zj, zj), (qj, qj); the minimum image in z uses
+// (dz/L + M) - M = rint(dz/L) with M = 1.5 * 2^23.
+__device__ __forceinline__ void coulomb_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 qj, f2 invL2, f2 M2,
+                                                f2 nM2, f2 nL2, float c2, f2& ax, f2& ay, f2& az) {
+    const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj);
+    f2 dz = f2_sub(zi, zj);
+    const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
+    dz = f2_fma(nL2, t, dz);
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    const f2 ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
+    const f2 s = f2_mul(f2_mul(ri, qj), f2_mul(ri, ri));
+    ax = f2_fma(s, dx, ax);
+    ay = f2_fma(s, dy, ay);
+    az = f2_fma(s, dz, az);
+}
+
+// Same pairs, with the three accumulations issued as scalar FFMA (two per
+// component) so that they can run on the FMA-lite pipe beside the packed work.
+__device__ __forceinline__ void coulomb_pair_x2s(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 qj, f2 invL2, f2 M2,
+                                                 f2 nM2, f2 nL2, float c2, float (&ax)[2], float (&ay)[2],
+                                                 float (&az)[2]) {
+    const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj);
+    f2 dz = f2_sub(zi, zj);
+    const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
+    dz = f2_fma(nL2, t, dz);
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    const f2 ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
+    const f2 s = f2_mul(f2_mul(ri, qj), f2_mul(ri, ri));
+    float s0, s1, x0, x1, y0, y1, z0, z1;
+    f2_unpack(s, s0, s1);
+    f2_unpack(dx, x0, x1);
+    f2_unpack(dy, y0, y1);
+    f2_unpack(dz, z0, z1);
+    ax[0] = __fmaf_rn(s0, x0, ax[0]); ax[1] = __fmaf_rn(s1, x1, ax[1]);
+    ay[0] = __fmaf_rn(s0, y0, ay[0]); ay[1] = __fmaf_rn(s1, y1, ay[1]);
+    az[0] = __fmaf_rn(s0, z0, az[0]); az[1] = __fmaf_rn(s1, z1, az[1]);
+}
+
 struct StepArgs {
     StepConst K;
     const void* pos_in; const void* vel_in; const double2* xy_in;
@@ -388,11 +458,13 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
     }
 }
 
-template <int P, int NT, int U>
+template <int P, int NT, int U, int V>
 __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
     typedef typename Real<P>::T T;
     typedef typename Real<P>::T4 T4;
-    __shared__ T4 sj[NT];
+    // j-tile: FP64 holds double4 (x, y, z, q); MIXED holds each value twice,
+    // (x, x, y, y), (z, z, q, q), so packed f32x2 operands load without moves.
+    __shared__ __align__(32) unsigned char smem_raw[NT * 32];
     __shared__ int s_item;
     __shared__ unsigned int s_alive[PDQ_MAX_CLASSES], s_dep[PDQ_MAX_CLASSES];
     const StepConst& K = A.K;
@@ -424,20 +496,73 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
             ax[u] = ay[u] = az[u] = (T)0;
         }
         if (K.forces & PDQ_F_COULOMB) {
-            for (int64_t j0 = o; j0 < end; j0 += NT) {
-                const int64_t j = j0 + tid;
-                T4 pj;
-                if (j < end) pj = pos_in[j];
-                else { pj.x = (T)0; pj.y = (T)0; pj.z = (T)0; pj.w = (T)0; }
-                sj[tid] = pj;
-                __syncthreads();
-#pragma unroll 8
-                for (int k = 0; k < NT; ++k) {
-                    const T4 p = sj[k];
+            if constexpr (P == PDQ_MIXED) {
+                static_assert(U % 2 == 0, "packed pairs need an even number of i-particles per thread");
+                constexpr int H = U / 2;
+                ulonglong2* sj2 = reinterpret_cast<ulonglong2*>(smem_raw);
+                const float M = 12582912.0f;
+                const f2 invL2 = f2_pack((float)invL, (float)invL), M2 = f2_pack(M, M), nM2 = f2_pack(-M, -M);
+                const f2 nL2 = f2_pack(-(float)L, -(float)L);
+                f2 X[H], Y[H], Z[H], AX[H], AY[H], AZ[H];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) coulomb_pair(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u]);
+                for (int h = 0; h < H; ++h) {
+                    X[h] = f2_pack(xi[2 * h], xi[2 * h + 1]);
+                    Y[h] = f2_pack(yi[2 * h], yi[2 * h + 1]);
+                    Z[h] = f2_pack(zi[2 * h], zi[2 * h + 1]);
+                    AX[h] = AY[h] = AZ[h] = 0ull;
                 }
-                __syncthreads();
+                for (int64_t j0 = o; j0 < end; j0 += NT) {
+                    const int64_t j = j0 + tid;
+                    const float4 pj = j < end ? ((const float4*)pos_in)[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    sj2[2 * tid] = make_ulonglong2(f2_pack(pj.x, pj.x), f2_pack(pj.y, pj.y));
+                    sj2[2 * tid + 1] = make_ulonglong2(f2_pack(pj.z, pj.z), f2_pack(pj.w, pj.w));
+                    __syncthreads();
+#pragma unroll 4
+                    for (int k = 0; k < NT; ++k) {
+                        const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            if constexpr (V == 1) {
+                                float(&sx)[2] = *reinterpret_cast<float(*)[2]>(&ax[2 * h]);
+                                float(&sy)[2] = *reinterpret_cast<float(*)[2]>(&ay[2 * h]);
+                                float(&sz)[2] = *reinterpret_cast<float(*)[2]>(&az[2 * h]);
+                                coulomb_pair_x2s(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, (float)c2,
+                                                 sx, sy, sz);
+                            } else {
+                                coulomb_pair_x2(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, (float)c2,
+                                                AX[h], AY[h], AZ[h]);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+                if constexpr (V != 1) {
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        float a0, a1;
+                        f2_unpack(AX[h], a0, a1); ax[2 * h] = a0; ax[2 * h + 1] = a1;
+                        f2_unpack(AY[h], a0, a1); ay[2 * h] = a0; ay[2 * h + 1] = a1;
+                        f2_unpack(AZ[h], a0, a1); az[2 * h] = a0; az[2 * h + 1] = a1;
+                    }
+                }
+            } else {
+                T4* sj = reinterpret_cast<T4*>(smem_raw);
+                for (int64_t j0 = o; j0 < end; j0 += NT) {
+                    const int64_t j = j0 + tid;
+                    T4 pj;
+                    if (j < end) pj = pos_in[j];
+                    else { pj.x = (T)0; pj.y = (T)0; pj.z = (T)0; pj.w = (T)0; }
+                    sj[tid] = pj;
+                    __syncthreads();
+#pragma unroll 8
+                    for (int k = 0; k < NT; ++k) {
+                        const T4 p = sj[k];
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            coulomb_pair(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u]);
+                    }
+                    __syncthreads();
+                }
             }
         }
         const pdq_sample_params sp = A.params[s];
@@ -635,9 +760,9 @@ static int validate_state(const pdq_state* st) {
 
 static int tile_threads(const pdq_state* st, const pdq_step_cfg* cfg) {
     if (cfg && cfg->block) return cfg->block;
-    return st->precision == PDQ_FP64 ? 128 : 256;
+    return st->precision == PDQ_FP64 ? 128 : 128;
 }
-static int tile_ilp(const pdq_state* st) { return st->precision == PDQ_FP64 ? 1 : 2; }
+static int tile_ilp(const pdq_state* st) { return st->precision == PDQ_FP64 ? 1 : 4; }
 
 static int sm_count() {
     static int n = 0;
@@ -650,26 +775,31 @@ static int sm_count() {
     return n;
 }
 
-template <int P, int NT, int U>
+template <int P, int NT, int U, int V>
 static int launch_step(const StepArgs& A, cudaStream_t s) {
     static int per_sm = 0;
     if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<P, NT, U>, NT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<P, NT, U, V>, NT, 0);
         if (per_sm <= 0) per_sm = 1;
     }
-    k_step<P, NT, U><<<sm_count() * per_sm, NT, 0, s>>>(A);
+    k_step<P, NT, U, V><<<sm_count() * per_sm, NT, 0, s>>>(A);
     return PDQ_OK;
 }
 
-static int dispatch_step(int prec, int NT, const StepArgs& A, cudaStream_t s) {
+// variant: MIXED pair math, 0 = all packed f32x2, 1 = packed with scalar accumulation.
+static int dispatch_step(int prec, int NT, int variant, const StepArgs& A, cudaStream_t s) {
     if (prec == PDQ_FP64) {
-        if (NT == 64) return launch_step<PDQ_FP64, 64, 1>(A, s);
-        if (NT == 128) return launch_step<PDQ_FP64, 128, 1>(A, s);
-        if (NT == 256) return launch_step<PDQ_FP64, 256, 1>(A, s);
+        if (NT == 64) return launch_step<PDQ_FP64, 64, 1, 0>(A, s);
+        if (NT == 128) return launch_step<PDQ_FP64, 128, 1, 0>(A, s);
+        if (NT == 256) return launch_step<PDQ_FP64, 256, 1, 0>(A, s);
+    } else if (variant == 1) {
+        if (NT == 64) return launch_step<PDQ_MIXED, 64, 4, 1>(A, s);
+        if (NT == 128) return launch_step<PDQ_MIXED, 128, 4, 1>(A, s);
+        if (NT == 256) return launch_step<PDQ_MIXED, 256, 4, 1>(A, s);
     } else {
-        if (NT == 128) return launch_step<PDQ_MIXED, 128, 2>(A, s);
-        if (NT == 256) return launch_step<PDQ_MIXED, 256, 2>(A, s);
-        if (NT == 512) return launch_step<PDQ_MIXED, 512, 2>(A, s);
+        if (NT == 64) return launch_step<PDQ_MIXED, 64, 4, 0>(A, s);
+        if (NT == 128) return launch_step<PDQ_MIXED, 128, 4, 0>(A, s);
+        if (NT == 256) return launch_step<PDQ_MIXED, 256, 4, 0>(A, s);
     }
     return PDQ_ERR_INVALID_ARG;
 }
@@ -750,11 +880,10 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
     int rc = validate_state(st);
     if (rc) return rc;
     if (!(cfg->dt > 0) || (cfg->mode != PDQ_STICK && cfg->mode != PDQ_REBOUND) || (cfg->forces & ~PDQ_F_ALL) ||
-        cfg->compact_every < 0)
+        cfg->compact_every < 0 || cfg->variant < 0 || cfg->variant > 1)
         return PDQ_ERR_INVALID_ARG;
     const int NT = tile_threads(st, cfg), U = tile_ilp(st);
-    if (st->precision == PDQ_FP64 ? (NT != 64 && NT != 128 && NT != 256) : (NT != 128 && NT != 256 && NT != 512))
-        return PDQ_ERR_INVALID_ARG;
+    if (NT != 64 && NT != 128 && NT != 256) return PDQ_ERR_INVALID_ARG;
     size_t items_bytes, need;
     workspace_layout(st, NT * U, &items_bytes, &need);
     if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return PDQ_ERR_WORKSPACE;
@@ -786,7 +915,7 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
     for (int64_t k = 0; k < n_steps; ++k) {
         A.pos_in = st->pos[cur]; A.vel_in = st->vel[cur]; A.xy_in = (const double2*)st->xy[cur];
         A.pos_out = st->pos[cur ^ 1]; A.vel_out = st->vel[cur ^ 1]; A.xy_out = (double2*)st->xy[cur ^ 1];
-        dispatch_step(st->precision, NT, A, s);
+        dispatch_step(st->precision, NT, cfg->variant, A, s);
         cur ^= 1;
         ++stepi;
         if (cfg->compact_every > 0 && stepi % cfg->compact_every == 0 && k + 1 < n_steps) {

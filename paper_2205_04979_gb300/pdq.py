@@ -48,7 +48,7 @@ class StateStruct(C.Structure):
 class StepCfg(C.Structure):
     _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("mode", C.c_int32), ("forces", C.c_int32),
                 ("window_start", C.c_int64), ("compact_every", C.c_int32), ("block", C.c_int32),
-                ("use_graph", C.c_int32), ("pad", C.c_int32)]
+                ("use_graph", C.c_int32), ("variant", C.c_int32)]
 
 
 class TallyStruct(C.Structure):
@@ -222,13 +222,13 @@ class Tally:
 
 
 def step_cfg(dt, forces=F_ALL, mode=STICK, gravity=(0.0, 0.0, 1.0), window_start=0, compact_every=0, block=0,
-             use_graph=False):
+             use_graph=False, variant=0):
     c = StepCfg()
     c.dt = dt
     for k in range(3):
         c.gravity[k] = gravity[k]
     c.mode, c.forces, c.window_start = mode, forces, window_start
-    c.compact_every, c.block, c.use_graph = compact_every, block, int(bool(use_graph))
+    c.compact_every, c.block, c.use_graph, c.variant = compact_every, block, int(bool(use_graph)), variant
     return c
 
 
