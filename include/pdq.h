@@ -268,6 +268,46 @@ int pdq_check_state(pdq_state* state, pdq_stream_t stream);
 int pdq_deposition_tally(const pdq_tally* tally, int32_t n_samples, int32_t n_classes, double dt,
                          double r_plus, double* vdep, double* mean, double* se, pdq_stream_t stream);
 
+/* ---------------------------------------------------- multi-fidelity MC
+ * Optimal MFMC allocation (Sec. 3.2, Eqs. opt1-opt3 and mf-precond) for k
+ * models sorted by decreasing correlation with model 1 (host arrays [k]:
+ * rho[0] = 1, sigma > 0, unit costs w > 0).  budget = p; with d_inputs > 0 the
+ * Sobol' effective budget p/(d+2) of Sec. 4 is used.  rho_{1,k+1} is read as 0.
+ * Outputs (host): m_out = floor(m_i*) made non-decreasing, alpha_out
+ * (alpha_1 = 1), optional m_real_out = m_i*, optional gamma_out = MSE of the
+ * MFMC mean over the MSE of plain MC at the same budget (equals
+ * (sqrt(1 - rho^2) + rho sqrt(w2/w1))^2 for k = 2, Sec. 4.1).
+ * Errors: INVALID_ARG, PRECOND (precondition violated or rho not decreasing).
+ * Host-only; touches no device.                                              */
+int pdq_mfmc_allocate(int32_t k, const double* rho, const double* sigma, const double* w, double budget,
+                      int32_t d_inputs, int64_t* m_out, double* alpha_out, double* m_real_out, double* gamma_out);
+
+/* Workspace bytes of pdq_mfmc_sobol: 8 (1 + n_boot) k 2 C (4 + 2d).          */
+int pdq_mfmc_workspace_size(int32_t k, int32_t d, int32_t C, int32_t n_boot, size_t* bytes);
+
+/* MFMC mean, variance and Sobol' main / total indices (Sec. 3.3: Owen's
+ * main-effect and Jansen's total-effect estimators inside the control-variate
+ * form of Eq. MFMC_mean, same alpha and m for all statistics; Var(Y) is the
+ * MFMC variance estimate).  y[i] is a device array [n_i >= m_i][d+2][C] of
+ * model i's pick-freeze groups: column 0 = f(x), 1 = f(x'), 2+j = f(z^(j))
+ * with z^(j) = x' except input j taken from x; the first m_{i-1} groups of
+ * every model are the samples shared with model i-1 (host arrays y[k],
+ * m[k] (2 <= m_1 <= ... <= m_k < 2^32), alpha[k]).  1 <= d <= 16, C >= 1
+ * outputs.  n_boot > 0 adds percentile bootstrap intervals (2.5 %, 97.5 %):
+ * replicate b maps group position t in the nesting block [m_{l-1}, m_l)
+ * (m_0 = 0) to m_{l-1} + ((philox(t, b, 0, 2).x * (m_l - m_{l-1})) >> 32)
+ * (Philox4x32-10, key = seed); model i reads positions t < m_i, so it never
+ * reads beyond its own m_i groups.
+ * FP64 sums on the device (one deterministic CTA reduction per model,
+ * prefix, output and replicate), assembly on the host.  Host outputs: mean[C],
+ * var[C], s_main[d][C], s_total[d][C], s_main_ci / s_total_ci [d][C][2]
+ * (may be NULL when n_boot = 0).  Synchronises `stream`.
+ * Errors: INVALID_ARG, WORKSPACE, CUDA.                                      */
+int pdq_mfmc_sobol(int32_t k, const double* const* y, const int64_t* m, const double* alpha, int32_t d, int32_t C,
+                   int32_t n_boot, uint64_t seed, double* mean, double* var, double* s_main, double* s_total,
+                   double* s_main_ci, double* s_total_ci, void* workspace, size_t workspace_bytes,
+                   pdq_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,7 @@ def lib():
             "orc_wall_accel": (None, [P, Fp, Cp, C.c_int, _D, C.c_int, _D, _D, _D, _I32, C.c_double, _D]),
             "orc_cor": (C.c_double, [P, C.c_double, C.c_double, C.c_double, C.c_double]),
             "orc_philox": (None, [_U32, _U32, _U32]),
+            "orc_boot_indices": (None, [C.c_uint64, C.c_uint32, C.c_int, _I64, _I64]),
             "orc_num_threads": (C.c_int, []),
         }
         for name, (res, args) in sig.items():
@@ -264,6 +265,14 @@ def cor(st_plus, zeta, theta, vn1, p=None):
 def philox(ctr, key):
     out = np.zeros(4, np.uint32)
     lib().orc_philox(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def boot_indices(seed, b, m):
+    """Group indices of bootstrap replicate b for nested counts m (resampled within each nesting block)."""
+    m = np.ascontiguousarray(m, np.int64)
+    out = np.zeros(int(m[-1]), np.int64)
+    lib().orc_boot_indices(seed, b, len(m), m, out)
     return out
 
 

@@ -171,3 +171,21 @@ def pick_freeze_inputs(x, xp):
         z[:, j] = x[:, j]
         out[:, 2 + j] = z
     return out
+
+
+def bootstrap_ci(groups, m, alpha, boot_index, n_boot):
+    """Percentile intervals (ranks round(0.025 (B-1)), round(0.975 (B-1))) of the MFMC Sobol' indices.
+
+    boot_index(b) gives the resampled group indices (length m[-1]) of replicate b, drawn within
+    the nesting blocks [m[i-1], m[i]); model i uses the first m[i] of them.
+    """
+    reps_m, reps_t = [], []
+    for b in range(1, n_boot + 1):
+        idx = boot_index(b)
+        g = [np.asarray(gr)[idx[: m[i]]] for i, gr in enumerate(groups)]
+        sm, st, _, _ = mfmc_sobol(g, m, alpha)
+        reps_m.append(sm)
+        reps_t.append(st)
+    reps_m, reps_t = np.sort(np.array(reps_m), axis=0), np.sort(np.array(reps_t), axis=0)
+    lo, hi = int(round(0.025 * (n_boot - 1))), int(round(0.975 * (n_boot - 1)))
+    return np.stack([reps_m[lo], reps_m[hi]], -1), np.stack([reps_t[lo], reps_t[hi]], -1)

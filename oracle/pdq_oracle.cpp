@@ -765,6 +765,21 @@ double orc_cor(const OrcPhys* p, double st_plus, double zeta, double theta, doub
     return std::min(1.0, std::sqrt(arg) / vn1);
 }
 
+// Bootstrap resampling of group position t in replicate b: Philox4x32-10 counter
+// (t, b, 0, 2), key = seed; position t in the nesting block [m_{l-1}, m_l)
+// draws m_{l-1} + (word0 (m_l - m_{l-1})) >> 32.
+void orc_boot_indices(uint64_t seed, uint32_t b, int k, const int64_t* m, int64_t* out) {
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t t = 0; t < m[k - 1]; ++t) {
+        int l = 0;
+        while (t >= m[l]) ++l;
+        int64_t lo = l > 0 ? m[l - 1] : 0;
+        uint32_t c[4] = {(uint32_t)t, b, 0u, 2u}, w[4];
+        philox4x32_10(c, key, w);
+        out[t] = lo + (int64_t)(((uint64_t)w[0] * (uint64_t)(m[l] - lo)) >> 32);
+    }
+}
+
 // Philox known-answer access for the pin test.
 void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
 

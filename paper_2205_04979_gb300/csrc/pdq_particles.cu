@@ -15,15 +15,13 @@
 #include <string.h>
 
 #include "pdq_common.cuh"
+#include "pdq_device.cuh"
 
 namespace pdq {
 
 enum { CTL_STEP = 0, CTL_QUEUE = 1, CTL_DONE = 2, CTL_ERROR = 3, CTL_NITEMS = 4 };
 enum { ERR_NONFINITE = 1 };
 
-template <int P> struct Real;
-template <> struct Real<PDQ_FP64> { typedef double T; typedef double4_32a T4; };
-template <> struct Real<PDQ_MIXED> { typedef float T; typedef float4 T4; };
 
 // ---------------------------------------------------------------------------
 // Host: per-class constants from the physical constants (all SI -> wall units).
@@ -124,129 +122,6 @@ __global__ void k_seed(const SeedArgs A) {
         ((float4*)A.vel)[g] = make_float4(0.f, 0.f, 0.f, 1.f);
     }
     A.tag[g] = make_int2((int)j, c);
-}
-
-// ---------------------------------------------------------------------------
-// Device physics helpers.
-// ---------------------------------------------------------------------------
-// phi1(z) = (e^z - 1)/z and phi2(z) = (e^z - 1 - z)/z^2: Taylor series near 0
-// (where the closed forms cancel), expm1 elsewhere.
-__device__ __forceinline__ void phi12(double z, double& p1, double& p2) {
-    if (fabs(z) < 0.05) {
-        // Horner with explicit coefficients (1/(k+1)! and 1/(k+2)!).
-        const double c1[11] = {1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320,
-                               1.0 / 362880, 1.0 / 3628800, 1.0 / 39916800};
-        p1 = c1[10];
-        p2 = 1.0 / 479001600;
-        for (int k = 9; k >= 0; --k) p1 = p1 * z + c1[k];
-        for (int k = 9; k >= 0; --k) p2 = p2 * z + c1[k + 1];
-        return;
-    }
-    const double em = expm1(z);
-    p1 = em / z;
-    p2 = (em - z) / (z * z);
-}
-__device__ __forceinline__ void phi12(float z, float& p1, float& p2) {
-    if (fabsf(z) < 0.1f) {
-        const float c[10] = {1.f, 1.f / 2, 1.f / 6, 1.f / 24, 1.f / 120, 1.f / 720, 1.f / 5040, 1.f / 40320,
-                             1.f / 362880, 1.f / 3628800};
-        p1 = c[8];
-        p2 = c[9];
-        for (int k = 7; k >= 0; --k) p1 = fmaf(p1, z, c[k]);
-        for (int k = 8; k >= 1; --k) p2 = fmaf(p2, z, c[k]);
-        return;
-    }
-    const float em = expm1f(z);
-    p1 = em / z;
-    p2 = (em - z) / (z * z);
-}
-
-__device__ __forceinline__ double atanh_(double x) { return atanh(x); }
-__device__ __forceinline__ float atanh_(float x) { return atanhf(x); }
-__device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
-__device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
-__device__ __forceinline__ double floor_(double x) { return floor(x); }
-__device__ __forceinline__ float floor_(float x) { return floorf(x); }
-__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-__device__ __forceinline__ double exp_(double x) { return exp(x); }
-__device__ __forceinline__ float exp_(float x) { return expf(x); }
-__device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
-__device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
-
-__device__ __forceinline__ double4_32a grid_at(const StepConst& K, const double4_32a*, int64_t i) { return K.grid64[i]; }
-__device__ __forceinline__ float4 grid_at(const StepConst& K, const float4*, int64_t i) { return __ldg(K.grid32 + i); }
-
-// Trilinear interpolation in (s(r), theta, z) index space: s = atanh(r tanh(beta)/R)/beta
-// inverts the node stretching; theta and z are periodic; s is clamped to [0, 1].
-template <class T, class T4>
-__device__ __forceinline__ void interp(const StepConst& K, T r, T x, T y, T z, T u[3]) {
-    const T R = (T)K.R;
-    const T rho = fmin(r / R, (T)1);
-    const T s = atanh_(rho * (T)K.tanh_beta) * (T)K.inv_beta;
-    const T fi = s * (T)(K.n_r - 1);
-    int i0 = (int)floor_(fi);
-    i0 = i0 < 0 ? 0 : (i0 > K.n_r - 2 ? K.n_r - 2 : i0);
-    const T tr = fi - (T)i0;
-    T fj = atan2_(y, x) * (T)(K.n_th / (2.0 * kPi));
-    if (fj < (T)0) fj += (T)K.n_th;
-    int j0 = (int)floor_(fj);
-    const T tt = fj - (T)j0;
-    j0 %= K.n_th;                    // any int (also a non-finite input's) maps into [0, n_th)
-    if (j0 < 0) j0 += K.n_th;
-    const int j1 = (j0 + 1 == K.n_th) ? 0 : j0 + 1;
-    const T fk = z * (T)(K.n_z * K.invL);
-    int k0 = (int)floor_(fk);
-    const T tz = fk - (T)k0;
-    k0 %= K.n_z;
-    if (k0 < 0) k0 += K.n_z;
-    const int k1 = (k0 + 1 == K.n_z) ? 0 : k0 + 1;
-    const int64_t nr = K.n_r, plane = (int64_t)K.n_r * K.n_th;
-    const int64_t b00 = k0 * plane + j0 * nr + i0, b01 = k0 * plane + j1 * nr + i0;
-    const int64_t b10 = k1 * plane + j0 * nr + i0, b11 = k1 * plane + j1 * nr + i0;
-    const T4* tag = nullptr;
-    const T4 g000 = grid_at(K, tag, b00), g001 = grid_at(K, tag, b00 + 1);
-    const T4 g010 = grid_at(K, tag, b01), g011 = grid_at(K, tag, b01 + 1);
-    const T4 g100 = grid_at(K, tag, b10), g101 = grid_at(K, tag, b10 + 1);
-    const T4 g110 = grid_at(K, tag, b11), g111 = grid_at(K, tag, b11 + 1);
-    const T wr0 = (T)1 - tr, wt0 = (T)1 - tt, wz0 = (T)1 - tz;
-    const T w000 = wr0 * wt0 * wz0, w001 = tr * wt0 * wz0, w010 = wr0 * tt * wz0, w011 = tr * tt * wz0;
-    const T w100 = wr0 * wt0 * tz, w101 = tr * wt0 * tz, w110 = wr0 * tt * tz, w111 = tr * tt * tz;
-    u[0] = w000 * g000.x + w001 * g001.x + w010 * g010.x + w011 * g011.x + w100 * g100.x + w101 * g101.x +
-           w110 * g110.x + w111 * g111.x;
-    u[1] = w000 * g000.y + w001 * g001.y + w010 * g010.y + w011 * g011.y + w100 * g100.y + w101 * g101.y +
-           w110 * g110.y + w111 * g111.y;
-    u[2] = w000 * g000.z + w001 * g001.z + w010 * g010.z + w011 * g011.z + w100 * g100.z + w101 * g101.z +
-           w110 * g110.z + w111 * g111.z;
-}
-
-// One ordered pair of the Coulomb sum: acc += q_j (x_i - x_j) / max(|x_i - x_j|, d_c)^3,
-// minimum image in z by the round-to-nearest trick (t + M) - M.
-__device__ __forceinline__ void coulomb_pair(float xi, float yi, float zi, const float4 pj, float L, float invL,
-                                             float c2, float& ax, float& ay, float& az) {
-    const float dx = xi - pj.x, dy = yi - pj.y;
-    float dz = zi - pj.z;
-    const float t = __fadd_rn(__fmaf_rn(dz, invL, 12582912.0f), -12582912.0f);
-    dz = __fmaf_rn(-L, t, dz);
-    const float r2 = fmaxf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))), c2);
-    const float ri = rsqrtf(r2);
-    const float s = __fmul_rn(__fmul_rn(pj.w, ri), __fmul_rn(ri, ri));
-    ax = __fmaf_rn(s, dx, ax);
-    ay = __fmaf_rn(s, dy, ay);
-    az = __fmaf_rn(s, dz, az);
-}
-__device__ __forceinline__ void coulomb_pair(double xi, double yi, double zi, const double4_32a pj, double L, double invL,
-                                             double c2, double& ax, double& ay, double& az) {
-    const double dx = xi - pj.x, dy = yi - pj.y;
-    double dz = zi - pj.z;
-    const double t = __dadd_rn(__fma_rn(dz, invL, 6755399441055744.0), -6755399441055744.0);
-    dz = __fma_rn(-L, t, dz);
-    const double r2 = fmax(__fma_rn(dx, dx, __fma_rn(dy, dy, dz * dz)), c2);
-    const double ri = rsqrt(r2);
-    const double s = pj.w * ri * (ri * ri);
-    ax = __fma_rn(s, dx, ax);
-    ay = __fma_rn(s, dy, ay);
-    az = __fma_rn(s, dz, az);
 }
 
 // ---------------------------------------------------------------------------

@@ -87,6 +87,11 @@ def lib():
             "pdq_check_state": (C.c_int, [C.POINTER(StateStruct), P]),
             "pdq_deposition_tally": (C.c_int, [C.POINTER(TallyStruct), C.c_int32, C.c_int32, C.c_double,
                                                C.c_double, P, P, P, P]),
+            "pdq_mfmc_allocate": (C.c_int, [C.c_int32, P, P, P, C.c_double, C.c_int32, P, P, P, P]),
+            "pdq_mfmc_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                                  C.POINTER(C.c_size_t)]),
+            "pdq_mfmc_sobol": (C.c_int, [C.c_int32, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
+                                         P, P, P, P, P, P, P, C.c_size_t, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -281,3 +286,50 @@ def deposition_tally(tally, dt, r_plus=180.0, stream=None):
     _check(lib().pdq_deposition_tally(C.byref(tally.t), S, Cn, dt, r_plus, _ptr(vdep), _ptr(mean), _ptr(se),
                                       _stream(stream)), "deposition_tally")
     return vdep, mean, se
+
+
+# ---------------------------------------------------------------------------
+# Multi-fidelity Monte Carlo (host arrays via numpy)
+# ---------------------------------------------------------------------------
+def _np_ptr(a):
+    return C.c_void_p(a.ctypes.data)
+
+
+def mfmc_allocate(rho, sigma, w, budget, d_inputs=0):
+    """(m [k] int64, alpha [k], m_real [k], gamma) of the optimal MFMC allocation."""
+    import numpy as np
+    rho, sigma, w = (np.ascontiguousarray(v, np.float64) for v in (rho, sigma, w))
+    k = len(rho)
+    m = np.zeros(k, np.int64)
+    alpha, m_real = np.zeros(k), np.zeros(k)
+    gamma = C.c_double()
+    _check(lib().pdq_mfmc_allocate(k, _np_ptr(rho), _np_ptr(sigma), _np_ptr(w), float(budget), int(d_inputs),
+                                   _np_ptr(m), _np_ptr(alpha), _np_ptr(m_real), C.byref(gamma)), "mfmc_allocate")
+    return m, alpha, m_real, gamma.value
+
+
+def mfmc_sobol(ys, m, alpha, n_boot=0, seed=0, stream=None):
+    """MFMC Sobol' analysis of device tensors ys[i] [n_i, d+2, C] (float64).
+
+    Returns dict(mean [C], var [C], s_main [d, C], s_total [d, C], s_main_ci, s_total_ci [d, C, 2]).
+    """
+    import numpy as np
+    k = len(ys)
+    d = ys[0].shape[1] - 2
+    Cn = ys[0].shape[2]
+    ys = [t.contiguous() for t in ys]
+    yp = (C.c_void_p * k)(*[t.data_ptr() for t in ys])
+    m = np.ascontiguousarray(m, np.int64)
+    alpha = np.ascontiguousarray(alpha, np.float64)
+    n = C.c_size_t()
+    _check(lib().pdq_mfmc_workspace_size(k, d, Cn, n_boot, C.byref(n)), "mfmc_workspace_size")
+    ws = torch.empty(max(n.value, 8), dtype=torch.uint8, device=ys[0].device)
+    out = {"mean": np.zeros(Cn), "var": np.zeros(Cn), "s_main": np.zeros((d, Cn)), "s_total": np.zeros((d, Cn)),
+           "s_main_ci": np.zeros((d, Cn, 2)), "s_total_ci": np.zeros((d, Cn, 2))}
+    _check(lib().pdq_mfmc_sobol(k, C.cast(yp, C.c_void_p), _np_ptr(m), _np_ptr(alpha), d, Cn, n_boot, seed,
+                                *(_np_ptr(out[q]) for q in ("mean", "var", "s_main", "s_total", "s_main_ci",
+                                                            "s_total_ci")),
+                                _ptr(ws), ws.numel(), _stream(stream)), "mfmc_sobol")
+    if n_boot == 0:
+        del out["s_main_ci"], out["s_total_ci"]
+    return out

@@ -62,3 +62,35 @@ def test_invalid_arguments_rejected_on_host(pdq):
     t = pdq.TallyStruct()
     assert L.pdq_deposition_tally(C.byref(t), 1, 1, 0.1, 180.0, None, None, None, None) == -1
     assert L.pdq_step_particles(None, None, None, None, None, 1, None, None, 0, None) == -1
+
+
+def test_mfmc_allocate_host_logic(pdq):
+    # host-only entry point: matches the oracle's allocation and the paper's Table 3 / gamma values
+    import json
+    import numpy as np
+    from oracle import mfmc
+    tab = json.load(open(os.path.join(ROOT, "tests", "golden", "mfmc_tables.json")))
+    for case in tab["cases"]:
+        rho = [1.0, case["rho12"]]
+        sig = [case["sigma1"], case["sigma2"]]
+        w = [1.0, tab["w2"]]
+        for p, key in ((36, "p36"), (72, "p72")):
+            m, alpha, m_real, gamma = pdq.mfmc_allocate(rho, sig, w, p, d_inputs=2)
+            a_ref, _, m_ref = mfmc.mfmc_allocation(rho, sig, w, p / 4)
+            assert np.allclose(alpha, a_ref, rtol=1e-14) and np.allclose(m_real, m_ref, rtol=1e-13)
+            assert m[0] == case[key]["m1"]
+            assert round(gamma, 3) == case["gamma"]
+            assert abs(gamma - mfmc.gamma_two_model(rho[1], w[1])) < 1e-12
+    # three models: gamma from the general MSE formula is below the two-model value
+    m, alpha, m_real, g3 = pdq.mfmc_allocate([1.0, 0.99, 0.9], [1.0, 1.0, 1.0], [1.0, 1e-2, 1e-4], 100.0)
+    assert m[0] <= m[1] <= m[2] and 0 < g3 < mfmc.gamma_two_model(0.99, 1e-2)
+    # precondition violated / unsorted correlations
+    L = pdq.lib()
+    import ctypes as C
+    for rho, w in (([1.0, 0.3], [1.0, 0.5]), ([1.0, 0.5, 0.9], [1.0, 0.1, 0.01])):
+        rho, sig, w = (np.ascontiguousarray(v, np.float64) for v in (rho, np.ones(len(rho)), w))
+        mo, ao = np.zeros(len(rho), np.int64), np.zeros(len(rho))
+        rc = L.pdq_mfmc_allocate(len(rho), C.c_void_p(rho.ctypes.data), C.c_void_p(sig.ctypes.data),
+                                 C.c_void_p(w.ctypes.data), 10.0, 0, C.c_void_p(mo.ctypes.data),
+                                 C.c_void_p(ao.ctypes.data), None, None)
+        assert rc == -6
