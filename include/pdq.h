@@ -268,6 +268,44 @@ int pdq_check_state(pdq_state* state, pdq_stream_t stream);
 int pdq_deposition_tally(const pdq_tally* tally, int32_t n_samples, int32_t n_classes, double dt,
                          double r_plus, double* vdep, double* mean, double* se, pdq_stream_t stream);
 
+/* ---------------------------------------------------------------- adjoint
+ * Batch description for the adjoint (it seeds and owns its own particle
+ * state inside the workspace): offset is a device array [S+1] as in
+ * pdq_state; st_plus the class Stokes numbers.                               */
+typedef struct pdq_batch {
+    int32_t precision;                 /* PDQ_FP64 or PDQ_MIXED             */
+    int32_t n_samples;                 /* S >= 1                            */
+    int32_t n_classes;                 /* 1..PDQ_MAX_CLASSES                */
+    int32_t pad;
+    double st_plus[PDQ_MAX_CLASSES];
+    int64_t capacity;                  /* offset[S]                         */
+    const int64_t* offset;             /* device [S+1]                      */
+} pdq_batch;
+
+/* Workspace bytes of pdq_adjoint_run: FP64 storage of 7 arrays per particle
+ * per checkpoint (ceil(n_steps/K) of them), 10 per step of one segment
+ * (K + 1 levels), 12 for cotangents and charges, plus 4 [S][C] tallies.      */
+int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_steps, int32_t K, size_t* bytes);
+
+/* Smoothed deposition functional and its hand-written reverse-mode adjoint.
+ * Forward (App. A.2 step of pdq_step_particles, STICK mode only) with the wall
+ * removal replaced by a weight update w' = w (1 - sigma(-gap'/eps)),
+ * sigma(a) = 1/(1+e^-a), gap' = R - r' - d/2, and the Coulomb sum taken over
+ * weighted charges w_j q_j; per (sample, class) over the counted steps
+ * J = (R+/2) sum_n sum_p (w_n - w_{n+1}) / (dt+ sum_n sum_p w_n), which tends
+ * to V_dep+ (Sec. 2.1) as eps -> 0.  The particles are seeded inside as
+ * pdq_seed_particles(seed, charge_sigma) would (common random numbers).
+ * Reverse: checkpoints every K steps; each of the n_vec cotangent vectors
+ * gbar[v] (device [S][C]) gives pbar[v] (device [S][3]) = sum_c gbar[v][s][c]
+ * dJ[s][c]/d(xi_s, zeta_s, theta_s); theta only enters the rebound model, so
+ * its component is 0.  J (device [S][C]) is always written.  The first call
+ * reads offset[] to the host (synchronises `stream`).
+ * Errors: INVALID_ARG, UNSUPPORTED (cfg->mode != PDQ_STICK), WORKSPACE, CUDA. */
+int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
+                    const pdq_sample_params* params, double charge_sigma, uint64_t seed, const pdq_step_cfg* cfg,
+                    int64_t n_steps, int32_t K, double eps, int32_t n_vec, const double* gbar, double* J,
+                    double* pbar, void* workspace, size_t workspace_bytes, pdq_stream_t stream);
+
 /* ---------------------------------------------------- multi-fidelity MC
  * Optimal MFMC allocation (Sec. 3.2, Eqs. opt1-opt3 and mf-precond) for k
  * models sorted by decreasing correlation with model 1 (host arrays [k]:

@@ -443,7 +443,12 @@ template <class T> static T phi2(const T& zz) {
     return (expm1(zz) - zz) / (zz * zz);
 }
 
-template <class T> static T logistic(const T& a) { return 1.0 / (1.0 + exp(-a)); }
+// logistic(a) = 1 / (1 + e^-a), evaluated without overflow for either sign of a
+template <class T> static T logistic(const T& a) {
+    if (val(a) >= 0) return 1.0 / (1.0 + exp(-a));
+    T e = exp(a);
+    return e / (1.0 + e);
+}
 
 enum { F_DRAG = 1, F_GRAV = 2, F_COUL = 4, F_IMAGE = 8, F_VDW = 16 };
 

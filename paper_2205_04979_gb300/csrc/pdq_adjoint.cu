@@ -1,0 +1,725 @@
+// pdq_adjoint.cu -- hand-written reverse-mode adjoint of the particle step.
+//
+// Functional (a smoothed form of V_dep+, Sec. 2.1): particles are never
+// removed; each carries a weight w, updated after the step as
+//   w' = w (1 - sigma(-gap'/eps)),  sigma(a) = 1 / (1 + exp(-a)),
+// with gap' = R - r' - d/2 the wall gap after the step.  Over the counted
+// steps, per (sample, class):
+//   num = sum_n sum_p (w_n - w_{n+1}),  den = sum_n sum_p w_n,
+//   J = (R+/2) num / (dt+ den),
+// which tends to the all-stick V_dep+ as eps -> 0.  The Coulomb sum uses the
+// weighted charges w_j q_j.  Gradients are taken with respect to the
+// per-sample inputs (xi, zeta, theta); theta only enters the rebound model, so
+// under all-stick its derivative is exactly zero.
+//
+// Schedule: one forward sweep stores a checkpoint every K steps and the
+// functional; every backward sweep (one per cotangent vector) recomputes each
+// segment of K steps from its checkpoint, storing each state and its raw
+// Coulomb sum S_i = sum_j w_j q_j G(x_i - x_j), then walks the segment
+// backwards with two kernels per step: the local adjoint (weights, wall
+// sigmoid, exponential integrator, drag, interpolation gradient, image charge,
+// van der Waals) and the all-pairs adjoint of the Coulomb sum.
+//
+// Storage is FP64 in both precisions; PDQ_MIXED computes the pair sums, the
+// interpolation, drag and integrator in FP32 like the forward step, the
+// wall-normal position, wall forces and weights in FP64.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pdq_common.cuh"
+#include "pdq_device.cuh"
+
+namespace pdq {
+
+struct Slot {   // one time level, SoA (FP64)
+    double *x, *y, *z, *vx, *vy, *vz, *w, *sx, *sy, *sz;
+};
+
+struct AdjArgs {
+    StepConst K;
+    const int64_t* offset;
+    int32_t S, C;
+    const int32_t* cls;
+    const double* qhat;                 // charge per unit xi
+    const pdq_sample_params* params;
+    double eps;
+    Slot in, out;                       // state n (S_n written here) and state n+1
+    int64_t step;
+    int32_t tally;
+    double *num, *den;                  // [S][C]
+    double *xb, *yb, *zb, *vxb, *vyb, *vzb, *wb, *qb;   // cotangents [N]
+    double *cx, *cy, *cz;               // c = coul q abar [N]
+    const double *nbar, *dbar;          // cotangents of num and den [S][C]
+    double* pbar;                       // [S][3]
+    // seeding
+    uint2 key;
+    double sigma;
+};
+
+__device__ __forceinline__ double logistic(double a) {
+    if (a >= 0.0) return 1.0 / (1.0 + exp(-a));
+    const double e = exp(a);   // no overflow for large -a
+    return e / (1.0 + e);
+}
+
+// Everything the local part of a step computes from (x, v, w) and the Coulomb
+// sum S, in the forward step's precisions; GRAD adds the interpolation Jacobian
+// and the derivatives the adjoint needs.
+template <class T>
+struct Local {
+    double x, y, r, nx, ny;
+    T z, v[3];
+    double w, q;
+    // wall: a_wall = A (nx, ny), A = A_img + A_vdw; dA/dr and the vdW factor per unit zeta
+    double A, dAdr, img_q, vdw_z;
+    T a[3];
+    T u[3], du[3][3];   // du[k][m] = d u_k / d x_m
+    T rel[3], relm, Re, lam;
+    T zz, e, p1, p2, dp1, dp2;
+    T F[3];
+    double xn, yn;
+    T zn, vn[3];
+    double rn, gap, Sg, wn;
+};
+
+template <class T, class T4, bool GRAD>
+__device__ __forceinline__ void interp_jac(const StepConst& K, double r, double x, double y, T z, T u[3], T du[3][3]) {
+    // value: the same routine as the forward step
+    interp<T, T4>(K, (T)r, (T)x, (T)y, z, u);
+    if (!GRAD) return;
+    // derivatives of the trilinear weights in (s(r), theta, z) chained to (x, y, z)
+    const T R = (T)K.R;
+    const T rho = fmin((T)r / R, (T)1);
+    const T s = atanh_(rho * (T)K.tanh_beta) * (T)K.inv_beta;
+    const T fi = s * (T)(K.n_r - 1);
+    int i0 = (int)floor_(fi);
+    i0 = i0 < 0 ? 0 : (i0 > K.n_r - 2 ? K.n_r - 2 : i0);
+    const T tr = fi - (T)i0;
+    T fj = atan2_((T)y, (T)x) * (T)(K.n_th / (2.0 * kPi));
+    if (fj < (T)0) fj += (T)K.n_th;
+    int j0 = (int)floor_(fj);
+    const T tt = fj - (T)j0;
+    j0 %= K.n_th;
+    if (j0 < 0) j0 += K.n_th;
+    const int j1 = (j0 + 1 == K.n_th) ? 0 : j0 + 1;
+    const T fk = z * (T)(K.n_z * K.invL);
+    int k0 = (int)floor_(fk);
+    const T tz = fk - (T)k0;
+    k0 %= K.n_z;
+    if (k0 < 0) k0 += K.n_z;
+    const int k1 = (k0 + 1 == K.n_z) ? 0 : k0 + 1;
+    const int64_t nr = K.n_r, plane = (int64_t)K.n_r * K.n_th;
+    const int64_t b00 = k0 * plane + j0 * nr + i0, b01 = k0 * plane + j1 * nr + i0;
+    const int64_t b10 = k1 * plane + j0 * nr + i0, b11 = k1 * plane + j1 * nr + i0;
+    const T4* tag = nullptr;
+    const T4 g[8] = {grid_at(K, tag, b00), grid_at(K, tag, b00 + 1), grid_at(K, tag, b01), grid_at(K, tag, b01 + 1),
+                     grid_at(K, tag, b10), grid_at(K, tag, b10 + 1), grid_at(K, tag, b11), grid_at(K, tag, b11 + 1)};
+    // corner c = (dk, dj, di) with index 4 dk + 2 dj + di
+    T dtr[3] = {0, 0, 0}, dtt[3] = {0, 0, 0}, dtz[3] = {0, 0, 0};
+    for (int c = 0; c < 8; ++c) {
+        const int di = c & 1, dj = (c >> 1) & 1, dk = c >> 2;
+        const T wr = di ? tr : (T)1 - tr, wt = dj ? tt : (T)1 - tt, wz = dk ? tz : (T)1 - tz;
+        const T sr = di ? (T)1 : (T)-1, st = dj ? (T)1 : (T)-1, sz = dk ? (T)1 : (T)-1;
+        const T gv[3] = {g[c].x, g[c].y, g[c].z};
+        for (int k = 0; k < 3; ++k) {
+            dtr[k] += sr * wt * wz * gv[k];
+            dtt[k] += wr * st * wz * gv[k];
+            dtz[k] += wr * wt * sz * gv[k];
+        }
+    }
+    // d tr / d r, d tt / d(x, y), d tz / dz
+    T dsdr = (T)0;
+    if ((T)r < R) {
+        const T a = rho * (T)K.tanh_beta;
+        dsdr = (T)K.tanh_beta * (T)K.inv_beta / (R * ((T)1 - a * a));
+    }
+    const T dtr_dr = dsdr * (T)(K.n_r - 1);
+    T drdx = 0, drdy = 0, dthdx = 0, dthdy = 0;
+    if (r > 1e-12) {
+        drdx = (T)(x / r);
+        drdy = (T)(y / r);
+        const T k2 = (T)(K.n_th / (2.0 * kPi)) / (T)(r * r);
+        dthdx = -(T)y * k2;
+        dthdy = (T)x * k2;
+    }
+    const T dtz_dz = (T)(K.n_z * K.invL);
+    for (int k = 0; k < 3; ++k) {
+        du[k][0] = dtr[k] * dtr_dr * drdx + dtt[k] * dthdx;
+        du[k][1] = dtr[k] * dtr_dr * drdy + dtt[k] * dthdy;
+        du[k][2] = dtz[k] * dtz_dz;
+    }
+}
+
+// phi1' = sum_k (k+1) z^k/(k+2)!, phi2' = sum_k (k+1) z^k/(k+3)! near 0; closed forms elsewhere.
+__device__ __forceinline__ void dphi12(double z, double p1, double p2, double e, double& d1, double& d2) {
+    if (fabs(z) < 0.05) {
+        double a = 0.0, b = 0.0, f2 = 1.0;   // f2 tracks (k+2)! as k rises
+        double zk = 1.0;
+        for (int k = 0; k <= 10; ++k) {
+            f2 *= (k + 2);                    // (k+2)!
+            a += (k + 1) * zk / f2;
+            b += (k + 1) * zk / (f2 * (k + 3));
+            zk *= z;
+        }
+        d1 = a;
+        d2 = b;
+        return;
+    }
+    d1 = (e - p1) / z;
+    d2 = (p1 - 2.0 * p2) / z;
+}
+__device__ __forceinline__ void dphi12(float z, float p1, float p2, float e, float& d1, float& d2) {
+    if (fabsf(z) < 0.1f) {
+        float a = 0.f, b = 0.f, f2 = 1.f, zk = 1.f;
+        for (int k = 0; k <= 8; ++k) {
+            f2 *= (float)(k + 2);
+            a += (float)(k + 1) * zk / f2;
+            b += (float)(k + 1) * zk / (f2 * (float)(k + 3));
+            zk *= z;
+        }
+        d1 = a;
+        d2 = b;
+        return;
+    }
+    d1 = (e - p1) / z;
+    d2 = (p1 - 2.f * p2) / z;
+}
+
+template <int P, bool GRAD>
+__device__ __forceinline__ void local_step(const AdjArgs& A, const ClassK& c, const pdq_sample_params& sp,
+                                           Local<typename Real<P>::T>& L, typename Real<P>::T sx,
+                                           typename Real<P>::T sy, typename Real<P>::T sz) {
+    typedef typename Real<P>::T T;
+    typedef typename Real<P>::T4 T4;
+    const StepConst& K = A.K;
+    for (int k = 0; k < 3; ++k) L.a[k] = (T)0;
+    if (K.forces & PDQ_F_COULOMB) {
+        const T kq = (P == PDQ_FP64 ? (T)c.coul : (T)c.coul_f) * (T)L.q;
+        L.a[0] = kq * sx; L.a[1] = kq * sy; L.a[2] = kq * sz;
+    }
+    if (K.forces & PDQ_F_GRAVITY) {
+        L.a[0] += (T)K.grav[0]; L.a[1] += (T)K.grav[1]; L.a[2] += (T)K.grav[2];
+    }
+    L.r = sqrt(L.x * L.x + L.y * L.y);
+    L.A = 0.0; L.dAdr = 0.0; L.img_q = 0.0; L.vdw_z = 0.0;
+    L.nx = 0.0; L.ny = 0.0;
+    if (L.r > 0.0 && (K.forces & (PDQ_F_IMAGE | PDQ_F_VDW))) {
+        L.nx = L.x / L.r;
+        L.ny = L.y / L.r;
+        if (K.forces & PDQ_F_IMAGE) {
+            const double yw = fmax(K.R - L.r, c.half_d);
+            const double ai = 0.25 * c.coul * L.q * L.q / (yw * yw);
+            L.A += ai;
+            L.img_q = 0.5 * c.coul * L.q / (yw * yw);                 // d A_img / d q
+            if (K.R - L.r > c.half_d) L.dAdr += 2.0 * ai / yw;         // d/dr of 1/(R-r)^2
+        }
+        if (K.forces & PDQ_F_VDW) {
+            const double gap = (K.R - L.r - c.half_d) * K.ell;
+            if (gap <= 0.25 * c.d_m) {
+                const double dl = fmax(gap, K.delta_min);
+                const double d = c.d_m, d2 = d * d, d6 = d2 * d2 * d2;
+                const double e1 = 2.0 * d + dl, e2 = d + dl;
+                const double F = d6 / (dl * dl * e1 * e1 * e2 * e2 * e2);
+                L.vdw_z = c.vdw * F;
+                L.A += sp.zeta * L.vdw_z;
+                if (gap > K.delta_min) {
+                    const double dlogF = -2.0 / dl - 2.0 / e1 - 3.0 / e2;   // d ln F / d delta
+                    L.dAdr += sp.zeta * L.vdw_z * dlogF * (-K.ell);
+                }
+            }
+        }
+        L.a[0] += (T)(L.A * L.nx);
+        L.a[1] += (T)(L.A * L.ny);
+    }
+    for (int k = 0; k < 3; ++k) L.u[k] = (T)0;
+    L.lam = (T)0;
+    L.Re = (T)0;
+    L.relm = (T)0;
+    if (K.forces & PDQ_F_DRAG) {
+        interp_jac<T, T4, GRAD>(K, L.r, L.x, L.y, L.z, L.u, L.du);
+        for (int k = 0; k < 3; ++k) L.rel[k] = L.u[k] - L.v[k];
+        L.relm = sqrt_(L.rel[0] * L.rel[0] + L.rel[1] * L.rel[1] + L.rel[2] * L.rel[2]);
+        L.Re = L.relm * (P == PDQ_FP64 ? (T)c.d_plus : (T)c.d_plus_f);
+        const T fd = (T)1 + (T)0.15 * (L.Re > (T)0 ? pow_(L.Re, (T)0.687) : (T)0);
+        L.lam = fd * (P == PDQ_FP64 ? (T)(1.0 / c.tau) : (T)c.inv_tau_f);
+    }
+    const T h = (T)K.dt;
+    L.zz = -L.lam * h;
+    phi12(L.zz, L.p1, L.p2);
+    L.e = exp_(L.zz);
+    if (GRAD) dphi12(L.zz, L.p1, L.p2, L.e, L.dp1, L.dp2);
+    T dxv[3];
+    for (int k = 0; k < 3; ++k) {
+        L.F[k] = L.lam * L.u[k] + L.a[k];
+        dxv[k] = L.v[k] * h * L.p1 + L.F[k] * (h * h) * L.p2;
+        L.vn[k] = L.v[k] * L.e + L.F[k] * h * L.p1;
+    }
+    L.xn = L.x + (double)dxv[0];
+    L.yn = L.y + (double)dxv[1];
+    T zn = L.z + dxv[2];
+    zn -= (T)K.L * floor_(zn * (T)K.invL);
+    if (zn >= (T)K.L) zn -= (T)K.L;
+    if (zn < (T)0) zn = (T)0;
+    L.zn = zn;
+    L.rn = sqrt(L.xn * L.xn + L.yn * L.yn);
+    L.gap = K.R - L.rn - c.half_d;
+    L.Sg = logistic(-L.gap / A.eps);
+    L.wn = L.w * (1.0 - L.Sg);
+}
+
+// Sum over a warp of v for the lanes whose class is c, for every class; lane 0 adds to dst[c].
+__device__ __forceinline__ void warp_class_add(double v, int cls, int C, double* dst) {
+    for (int c = 0; c < C; ++c) {
+        double t = cls == c ? v : 0.0;
+        for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+        if ((threadIdx.x & 31) == 0 && t != 0.0) atomicAdd(dst + c, t);
+    }
+}
+__device__ __forceinline__ void warp_add(double v, double* dst) {
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
+}
+
+// ---------------------------------------------------------------------------
+// Kernels.  Grid (tiles, samples), NT threads, one particle per thread.
+// ---------------------------------------------------------------------------
+__global__ void k_adj_seed(const AdjArgs A) {
+    const int s = blockIdx.y;
+    const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t g = o + i;
+    const int c = (int)((uint32_t)i % (uint32_t)A.C);
+    double x, y, z, qh;
+    seed_particle(A.key, (uint32_t)i, A.sigma, A.K.R, A.K.L, A.K.cls[c].half_d, A.K.cls[c].qfac, x, y, z, qh);
+    A.out.x[g] = x; A.out.y[g] = y; A.out.z[g] = z;
+    A.out.vx[g] = 0.0; A.out.vy[g] = 0.0; A.out.vz[g] = 0.0; A.out.w[g] = 1.0;
+    ((int32_t*)A.cls)[g] = c;
+    ((double*)A.qhat)[g] = qh;
+}
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
+    typedef typename Real<P>::T T;
+    typedef typename Real<P>::T4 T4;
+    __shared__ T4 sj[NT];
+    const int s = blockIdx.y, tid = threadIdx.x;
+    const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
+    if ((int64_t)blockIdx.x * NT >= n) return;
+    const int64_t i = (int64_t)blockIdx.x * NT + tid;
+    const bool valid = i < n;
+    const int64_t g = o + (valid ? i : 0);
+    const pdq_sample_params sp = A.params[s];
+    const StepConst& K = A.K;
+    const T xi = valid ? (T)A.in.x[g] : (T)0, yi = valid ? (T)A.in.y[g] : (T)0, zi = valid ? (T)A.in.z[g] : (T)0;
+    T ax = 0, ay = 0, az = 0;
+    if (K.forces & PDQ_F_COULOMB) {
+        const T L = (T)K.L, invL = (T)K.invL;
+        const T c2 = P == PDQ_FP64 ? (T)K.contact2 : (T)K.contact2f;
+        for (int64_t j0 = 0; j0 < n; j0 += NT) {
+            const int64_t j = j0 + tid;
+            T4 p;
+            if (j < n) {
+                const int64_t gj = o + j;
+                p.x = (T)A.in.x[gj]; p.y = (T)A.in.y[gj]; p.z = (T)A.in.z[gj];
+                p.w = (T)(A.in.w[gj] * sp.xi * A.qhat[gj]);
+            } else {
+                p.x = (T)0; p.y = (T)0; p.z = (T)0; p.w = (T)0;
+            }
+            sj[tid] = p;
+            __syncthreads();
+            for (int k = 0; k < NT; ++k) coulomb_pair(xi, yi, zi, sj[k], L, invL, c2, ax, ay, az);
+            __syncthreads();
+        }
+    }
+    int cls = -1;
+    double dnum = 0.0, dden = 0.0;
+    if (valid) {
+        cls = A.cls[g];
+        Local<T> Lc;
+        Lc.x = A.in.x[g]; Lc.y = A.in.y[g]; Lc.z = (T)A.in.z[g];
+        Lc.v[0] = (T)A.in.vx[g]; Lc.v[1] = (T)A.in.vy[g]; Lc.v[2] = (T)A.in.vz[g];
+        Lc.w = A.in.w[g];
+        Lc.q = sp.xi * A.qhat[g];
+        local_step<P, false>(A, K.cls[cls], sp, Lc, ax, ay, az);
+        A.in.sx[g] = (double)ax; A.in.sy[g] = (double)ay; A.in.sz[g] = (double)az;
+        A.out.x[g] = Lc.xn; A.out.y[g] = Lc.yn; A.out.z[g] = (double)Lc.zn;
+        A.out.vx[g] = (double)Lc.vn[0]; A.out.vy[g] = (double)Lc.vn[1]; A.out.vz[g] = (double)Lc.vn[2];
+        A.out.w[g] = Lc.wn;
+        dnum = Lc.w - Lc.wn;
+        dden = Lc.w;
+    }
+    if (A.tally && A.step >= K.window_start) {
+        warp_class_add(dnum, cls, A.C, A.num + (int64_t)s * A.C);
+        warp_class_add(dden, cls, A.C, A.den + (int64_t)s * A.C);
+    }
+}
+
+// Local adjoint of step n: cotangents of state n+1 (in xb..wb) -> cotangents of
+// state n (partial: the Coulomb pair terms follow), c = coul q abar, qbar, zeta-bar.
+template <int P>
+__global__ void __launch_bounds__(128) k_adj_local(const AdjArgs A) {
+    typedef typename Real<P>::T T;
+    const int s = blockIdx.y;
+    const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
+    if ((int64_t)blockIdx.x * blockDim.x >= n) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    const pdq_sample_params sp = A.params[s];
+    const StepConst& K = A.K;
+    double zeta_bar = 0.0;
+    if (valid) {
+        const int64_t g = o + i;
+        const int cls = A.cls[g];
+        const ClassK& c = K.cls[cls];
+        Local<T> L;
+        L.x = A.in.x[g]; L.y = A.in.y[g]; L.z = (T)A.in.z[g];
+        L.v[0] = (T)A.in.vx[g]; L.v[1] = (T)A.in.vy[g]; L.v[2] = (T)A.in.vz[g];
+        L.w = A.in.w[g];
+        L.q = sp.xi * A.qhat[g];
+        const T S3[3] = {(T)A.in.sx[g], (T)A.in.sy[g], (T)A.in.sz[g]};
+        local_step<P, true>(A, c, sp, L, S3[0], S3[1], S3[2]);
+        const double h = K.dt;
+        double xb[3] = {A.xb[g], A.yb[g], A.zb[g]};
+        double vb[3] = {A.vxb[g], A.vyb[g], A.vzb[g]};
+        double wb_next = A.wb[g];
+        // tally of step n: num += w_n - w_{n+1}, den += w_n
+        double wbar = 0.0;
+        if (A.step >= K.window_start) {
+            const double nb = A.nbar[(int64_t)s * A.C + cls], db = A.dbar[(int64_t)s * A.C + cls];
+            wbar += nb + db;
+            wb_next -= nb;
+        }
+        // weight update w' = w (1 - Sg), Sg = sigma(-gap'/eps)
+        wbar += wb_next * (1.0 - L.Sg);
+        const double gapbar = wb_next * L.w * L.Sg * (1.0 - L.Sg) / A.eps;
+        if (L.rn > 0.0) {   // gap' = R - r' - d/2
+            xb[0] += -gapbar * L.xn / L.rn;
+            xb[1] += -gapbar * L.yn / L.rn;
+        }
+        // exponential integrator: x' = x + v h phi1 + F h^2 phi2, v' = v e + F h phi1
+        double vbar[3], Fbar[3], lambar = 0.0;
+        const double p1 = (double)L.p1, p2 = (double)L.p2, e = (double)L.e;
+        const double p1l = -h * (double)L.dp1, p2l = -h * (double)L.dp2, el = -h * e;   // d/d lambda
+        for (int k = 0; k < 3; ++k) {
+            const double v = (double)L.v[k], F = (double)L.F[k];
+            vbar[k] = xb[k] * h * p1 + vb[k] * e;
+            Fbar[k] = xb[k] * h * h * p2 + vb[k] * h * p1;
+            lambar += xb[k] * (v * h * p1l + F * h * h * p2l) + vb[k] * (v * el + F * h * p1l);
+            lambar += Fbar[k] * (double)L.u[k];
+        }
+        double ubar[3] = {Fbar[0] * (double)L.lam, Fbar[1] * (double)L.lam, Fbar[2] * (double)L.lam};
+        const double abar[3] = {Fbar[0], Fbar[1], Fbar[2]};
+        double xbn[3] = {xb[0], xb[1], xb[2]};   // dx'/dx = I
+        if (K.forces & PDQ_F_DRAG) {
+            // lambda = f / tau, f = 1 + 0.15 Re^0.687, Re = |u - v| d+
+            const double fbar = lambar / c.tau;
+            const double Re = (double)L.Re;
+            const double rebar = Re > 0.0 ? fbar * 0.15 * 0.687 * pow(Re, -0.313) : 0.0;
+            const double relm = (double)L.relm;
+            if (relm > 0.0) {
+                const double mbar = rebar * c.d_plus;
+                for (int k = 0; k < 3; ++k) {
+                    const double rb = mbar * (double)L.rel[k] / relm;
+                    ubar[k] += rb;
+                    vbar[k] -= rb;
+                }
+            }
+            for (int m = 0; m < 3; ++m)
+                for (int k = 0; k < 3; ++k) xbn[m] += ubar[k] * (double)L.du[k][m];
+        }
+        // wall forces a_wall = A(r) n, n = (x, y)/r
+        double qbar = 0.0;
+        if (L.r > 0.0 && (K.forces & (PDQ_F_IMAGE | PDQ_F_VDW))) {
+            const double Abar = abar[0] * L.nx + abar[1] * L.ny;
+            xbn[0] += L.dAdr * Abar * L.nx + L.A * (abar[0] - Abar * L.nx) / L.r;
+            xbn[1] += L.dAdr * Abar * L.ny + L.A * (abar[1] - Abar * L.ny) / L.r;
+            qbar += Abar * L.img_q;
+            zeta_bar = Abar * L.vdw_z;
+        }
+        // Coulomb a_C = coul q S: qbar += coul abar . S; c = coul q abar for the pair adjoint
+        double cx = 0.0, cy = 0.0, cz = 0.0;
+        if (K.forces & PDQ_F_COULOMB) {
+            qbar += c.coul * (abar[0] * (double)S3[0] + abar[1] * (double)S3[1] + abar[2] * (double)S3[2]);
+            cx = c.coul * L.q * abar[0];
+            cy = c.coul * L.q * abar[1];
+            cz = c.coul * L.q * abar[2];
+        }
+        A.xb[g] = xbn[0]; A.yb[g] = xbn[1]; A.zb[g] = xbn[2];
+        A.vxb[g] = vbar[0]; A.vyb[g] = vbar[1]; A.vzb[g] = vbar[2];
+        A.wb[g] = wbar;
+        A.qb[g] = qbar;
+        A.cx[g] = cx; A.cy[g] = cy; A.cz[g] = cz;
+    }
+    warp_add(zeta_bar, A.pbar + (int64_t)s * 3 + 1);
+}
+
+// All-pairs adjoint of S_m = sum_j Q_j G(x_m - x_j), Q = w q, G(d) = d / max(|d|, d_c)^3:
+//   xbar_m += sum_j J(d_mj) (Q_j c_m - Q_m c_j),  J = (I - 3 d d^T / |d|^2) / |d|^3 (|d| > d_c) or I / d_c^3,
+//   Qbar_m  = -sum_j c_j . G(d_mj);  then qbar_m += w_m Qbar_m, wbar_m += q_m Qbar_m, xi-bar += qbar_m qhat_m.
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
+    typedef typename Real<P>::T T;
+    __shared__ T sj[7][NT];
+    const int s = blockIdx.y, tid = threadIdx.x;
+    const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
+    if ((int64_t)blockIdx.x * NT >= n) return;
+    const int64_t i = (int64_t)blockIdx.x * NT + tid;
+    const bool valid = i < n;
+    const int64_t g = o + (valid ? i : 0);
+    const pdq_sample_params sp = A.params[s];
+    const StepConst& K = A.K;
+    double xi_bar = 0.0;
+    if (K.forces & PDQ_F_COULOMB) {
+        const T xm = valid ? (T)A.in.x[g] : (T)0, ym = valid ? (T)A.in.y[g] : (T)0, zm = valid ? (T)A.in.z[g] : (T)0;
+        const double qm = sp.xi * A.qhat[g];
+        const T Qm = valid ? (T)(A.in.w[g] * qm) : (T)0;
+        const T cmx = valid ? (T)A.cx[g] : (T)0, cmy = valid ? (T)A.cy[g] : (T)0, cmz = valid ? (T)A.cz[g] : (T)0;
+        const T L = (T)K.L, invL = (T)K.invL;
+        const T c2 = P == PDQ_FP64 ? (T)K.contact2 : (T)K.contact2f;
+        T bx = 0, by = 0, bz = 0, Qb = 0;
+        for (int64_t j0 = 0; j0 < n; j0 += NT) {
+            const int64_t j = j0 + tid;
+            if (j < n) {
+                const int64_t gj = o + j;
+                sj[0][tid] = (T)A.in.x[gj]; sj[1][tid] = (T)A.in.y[gj]; sj[2][tid] = (T)A.in.z[gj];
+                sj[3][tid] = (T)(A.in.w[gj] * sp.xi * A.qhat[gj]);
+                sj[4][tid] = (T)A.cx[gj]; sj[5][tid] = (T)A.cy[gj]; sj[6][tid] = (T)A.cz[gj];
+            } else {
+                for (int q = 0; q < 7; ++q) sj[q][tid] = (T)0;
+            }
+            __syncthreads();
+            for (int k = 0; k < NT; ++k) {
+                const T dx = xm - sj[0][k], dy = ym - sj[1][k];
+                T dz = zm - sj[2][k];
+                dz -= L * rint(dz * invL);
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                const T r2c = r2 > c2 ? r2 : c2;
+                const T ri = (T)1 / sqrt_(r2c);
+                const T ri3 = ri * ri * ri;
+                const T Qj = sj[3][k];
+                const T vx = Qj * cmx - Qm * sj[4][k], vy = Qj * cmy - Qm * sj[5][k], vz = Qj * cmz - Qm * sj[6][k];
+                const T dv = dx * vx + dy * vy + dz * vz;
+                const T kk = r2 > c2 ? (T)-3 * ri3 * ri * ri * dv : (T)0;
+                bx += ri3 * vx + kk * dx;
+                by += ri3 * vy + kk * dy;
+                bz += ri3 * vz + kk * dz;
+                Qb -= ri3 * (sj[4][k] * dx + sj[5][k] * dy + sj[6][k] * dz);
+            }
+            __syncthreads();
+        }
+        if (valid) {
+            A.xb[g] += (double)bx;
+            A.yb[g] += (double)by;
+            A.zb[g] += (double)bz;
+            const double w = A.in.w[g];
+            A.wb[g] += (double)Qb * qm;
+            const double qbar = A.qb[g] + (double)Qb * w;
+            xi_bar = qbar * A.qhat[g];
+        }
+    } else if (valid) {
+        xi_bar = A.qb[g] * A.qhat[g];
+    }
+    warp_add(xi_bar, A.pbar + (int64_t)s * 3 + 0);
+}
+
+// J = (R+/2) num / (dt den) and the cotangents of num and den for one vector gbar.
+__global__ void k_adj_finish(const double* num, const double* den, const double* gbar, int n, double R, double dt,
+                             double* J, double* nbar, double* dbar) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double d = den[k];
+    const double f = d > 0.0 ? 0.5 * R / dt : 0.0;
+    if (J) J[k] = d > 0.0 ? f * num[k] / d : 0.0;
+    if (gbar) {
+        nbar[k] = d > 0.0 ? gbar[k] * f / d : 0.0;
+        dbar[k] = d > 0.0 ? -gbar[k] * f * num[k] / (d * d) : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host.
+// ---------------------------------------------------------------------------
+struct AdjLayout {
+    int64_t N;
+    int64_t n_ck;       // checkpoints (states at 0, K, 2K, ...)
+    int32_t K;
+    size_t bytes;
+};
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static AdjLayout adj_layout(int64_t N, int32_t S, int32_t C, int64_t n_steps, int32_t K) {
+    AdjLayout L;
+    L.N = N;
+    L.K = K;
+    L.n_ck = (n_steps + K - 1) / K;
+    if (L.n_ck < 1) L.n_ck = 1;
+    const size_t vec = a256(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    size_t b = 0;
+    b += vec * 7 * (size_t)L.n_ck;                 // checkpoints
+    b += vec * 10 * (size_t)(K + 1);               // segment slots
+    b += vec * 11;                                 // cotangents, c
+    b += vec;                                      // qhat
+    b += a256(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));   // classes
+    b += a256(sizeof(double) * (size_t)S * C) * 4; // num, den, nbar, dbar
+    L.bytes = b;
+    return L;
+}
+
+}  // namespace pdq
+
+using namespace pdq;
+
+extern "C" int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_steps, int32_t K, size_t* bytes) {
+    if (!batch || !bytes || batch->n_samples < 1 || batch->n_classes < 1 || batch->n_classes > PDQ_MAX_CLASSES ||
+        batch->capacity < 0 || n_steps < 1 || K < 1)
+        return PDQ_ERR_INVALID_ARG;
+    *bytes = adj_layout(batch->capacity, batch->n_samples, batch->n_classes, n_steps, K).bytes;
+    return PDQ_OK;
+}
+
+extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
+                               const pdq_sample_params* params, double charge_sigma, uint64_t seed,
+                               const pdq_step_cfg* cfg, int64_t n_steps, int32_t K, double eps, int32_t n_vec,
+                               const double* gbar, double* J, double* pbar, void* workspace, size_t workspace_bytes,
+                               pdq_stream_t stream) {
+    if (!field || !phys || !batch || !params || !cfg || !J || n_steps < 1 || K < 1 || !(eps > 0) || n_vec < 0 ||
+        (n_vec > 0 && (!gbar || !pbar)) || !(charge_sigma >= 0))
+        return PDQ_ERR_INVALID_ARG;
+    if (cfg->mode != PDQ_STICK) return PDQ_ERR_UNSUPPORTED;
+    if (!(cfg->dt > 0) || (cfg->forces & ~PDQ_F_ALL)) return PDQ_ERR_INVALID_ARG;
+    if (batch->precision != PDQ_FP64 && batch->precision != PDQ_MIXED) return PDQ_ERR_INVALID_ARG;
+    size_t need = 0;
+    int rc = pdq_adjoint_workspace_size(batch, n_steps, K, &need);
+    if (rc) return rc;
+    if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return PDQ_ERR_WORKSPACE;
+    if (batch->capacity > ((int64_t)1 << 31) - 1) return PDQ_ERR_INVALID_ARG;
+    pdq_state st;   // only the class description is read by make_step_const
+    memset(&st, 0, sizeof(st));
+    st.n_classes = batch->n_classes;
+    st.n_samples = batch->n_samples;
+    for (int c = 0; c < batch->n_classes; ++c) st.st_plus[c] = batch->st_plus[c];
+    AdjArgs A;
+    memset(&A, 0, sizeof(A));
+    rc = make_step_const(field, phys, &st, &A.K);
+    if (rc) return rc;
+    A.K.dt = cfg->dt;
+    A.K.dtf = (float)cfg->dt;
+    A.K.forces = cfg->forces;
+    A.K.mode = PDQ_STICK;
+    A.K.window_start = cfg->window_start;
+    const double gplus = phys->g * phys->nu / pow(phys->re_tau * phys->nu / phys->radius, 3);
+    for (int k = 0; k < 3; ++k) { A.K.grav[k] = gplus * cfg->gravity[k]; A.K.gravf[k] = (float)A.K.grav[k]; }
+    A.offset = batch->offset;
+    A.S = batch->n_samples;
+    A.C = batch->n_classes;
+    A.params = params;
+    A.eps = eps;
+    A.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    A.sigma = charge_sigma;
+
+    const AdjLayout Ly = adj_layout(batch->capacity, A.S, A.C, n_steps, K);
+    const int64_t N = Ly.N;
+    const size_t vec = a256(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    char* p = (char*)workspace;
+    auto take = [&](size_t n) { char* r = p; p += n; return r; };
+    std::vector<Slot> ck(Ly.n_ck), seg(K + 1);
+    for (auto& s : ck) {
+        s.x = (double*)take(vec); s.y = (double*)take(vec); s.z = (double*)take(vec);
+        s.vx = (double*)take(vec); s.vy = (double*)take(vec); s.vz = (double*)take(vec); s.w = (double*)take(vec);
+        s.sx = s.sy = s.sz = nullptr;
+    }
+    for (auto& s : seg) {
+        s.x = (double*)take(vec); s.y = (double*)take(vec); s.z = (double*)take(vec);
+        s.vx = (double*)take(vec); s.vy = (double*)take(vec); s.vz = (double*)take(vec); s.w = (double*)take(vec);
+        s.sx = (double*)take(vec); s.sy = (double*)take(vec); s.sz = (double*)take(vec);
+    }
+    A.xb = (double*)take(vec); A.yb = (double*)take(vec); A.zb = (double*)take(vec);
+    A.vxb = (double*)take(vec); A.vyb = (double*)take(vec); A.vzb = (double*)take(vec);
+    A.wb = (double*)take(vec); A.qb = (double*)take(vec);
+    A.cx = (double*)take(vec); A.cy = (double*)take(vec); A.cz = (double*)take(vec);
+    A.qhat = (double*)take(vec);
+    A.cls = (int32_t*)take(a256(sizeof(int32_t) * (size_t)(N > 0 ? N : 1)));
+    const size_t sc = a256(sizeof(double) * (size_t)A.S * A.C);
+    A.num = (double*)take(sc); A.den = (double*)take(sc);
+    double* nbar = (double*)take(sc);
+    double* dbar = (double*)take(sc);
+    A.nbar = nbar; A.dbar = dbar;
+
+    // largest sample -> tiles per grid row
+    std::vector<int64_t> off(A.S + 1);
+    cudaStream_t s = (cudaStream_t)stream;
+    PDQ_CUDA(cudaMemcpyAsync(off.data(), batch->offset, sizeof(int64_t) * (A.S + 1), cudaMemcpyDeviceToHost, s));
+    PDQ_CUDA(cudaStreamSynchronize(s));
+    int64_t nmax = 0;
+    for (int k = 0; k < A.S; ++k) nmax = std::max(nmax, off[k + 1] - off[k]);
+    if (off[A.S] != N) return PDQ_ERR_INVALID_ARG;
+    if (nmax == 0) nmax = 1;
+    const int NT = 128;
+    const dim3 grid((unsigned)((nmax + NT - 1) / NT), (unsigned)A.S);
+    const bool mixed = batch->precision == PDQ_MIXED;
+
+    auto fwd = [&](const Slot& in, const Slot& out, int64_t step, int tally) {
+        A.in = in; A.out = out; A.step = step; A.tally = tally;
+        if (mixed) k_adj_forward<PDQ_MIXED, NT><<<grid, NT, 0, s>>>(A);
+        else k_adj_forward<PDQ_FP64, NT><<<grid, NT, 0, s>>>(A);
+    };
+    auto copy_state = [&](const Slot& dst, const Slot& src) -> cudaError_t {
+        const size_t nb = sizeof(double) * (size_t)N;
+        double* const d[7] = {dst.x, dst.y, dst.z, dst.vx, dst.vy, dst.vz, dst.w};
+        double* const r[7] = {src.x, src.y, src.z, src.vx, src.vy, src.vz, src.w};
+        for (int q = 0; q < 7; ++q) {
+            cudaError_t e = cudaMemcpyAsync(d[q], r[q], nb, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+
+    // seed into segment slot 0, save as checkpoint 0
+    A.out = seg[0];
+    k_adj_seed<<<grid, NT, 0, s>>>(A);
+    PDQ_CUDA(cudaMemsetAsync(A.num, 0, sc, s));
+    PDQ_CUDA(cudaMemsetAsync(A.den, 0, sc, s));
+    PDQ_CUDA(copy_state(ck[0], seg[0]));
+    // forward sweep: ping-pong between segment slots 0 and 1, checkpoint every K steps
+    for (int64_t n = 0; n < n_steps; ++n) {
+        fwd(seg[n & 1], seg[(n + 1) & 1], n, 1);
+        if ((n + 1) % K == 0 && (n + 1) < n_steps) PDQ_CUDA(copy_state(ck[(n + 1) / K], seg[(n + 1) & 1]));
+    }
+    const int nsc = A.S * A.C;
+    k_adj_finish<<<(nsc + 255) / 256, 256, 0, s>>>(A.num, A.den, nullptr, nsc, A.K.R, A.K.dt, J, nullptr, nullptr);
+    PDQ_CUDA(cudaGetLastError());
+
+    // backward sweeps, one per cotangent vector
+    for (int v = 0; v < n_vec; ++v) {
+        k_adj_finish<<<(nsc + 255) / 256, 256, 0, s>>>(A.num, A.den, gbar + (size_t)v * nsc, nsc, A.K.R, A.K.dt,
+                                                       nullptr, nbar, dbar);
+        A.pbar = pbar + (size_t)v * A.S * 3;
+        PDQ_CUDA(cudaMemsetAsync(A.pbar, 0, sizeof(double) * A.S * 3, s));
+        for (double* q : {A.xb, A.yb, A.zb, A.vxb, A.vyb, A.vzb, A.wb}) PDQ_CUDA(cudaMemsetAsync(q, 0, vec, s));
+        for (int64_t kseg = Ly.n_ck - 1; kseg >= 0; --kseg) {
+            const int64_t n0 = kseg * K;
+            const int64_t len = std::min<int64_t>(K, n_steps - n0);
+            PDQ_CUDA(copy_state(seg[0], ck[kseg]));
+            for (int64_t t = 0; t < len; ++t) fwd(seg[t], seg[t + 1], n0 + t, 0);
+            for (int64_t t = len - 1; t >= 0; --t) {
+                A.in = seg[t];
+                A.step = n0 + t;
+                if (mixed) {
+                    k_adj_local<PDQ_MIXED><<<dim3((unsigned)((nmax + 127) / 128), (unsigned)A.S), 128, 0, s>>>(A);
+                    k_adj_pairs<PDQ_MIXED, NT><<<grid, NT, 0, s>>>(A);
+                } else {
+                    k_adj_local<PDQ_FP64><<<dim3((unsigned)((nmax + 127) / 128), (unsigned)A.S), 128, 0, s>>>(A);
+                    k_adj_pairs<PDQ_FP64, NT><<<grid, NT, 0, s>>>(A);
+                }
+            }
+            PDQ_CUDA(cudaGetLastError());
+        }
+    }
+    PDQ_CUDA(cudaGetLastError());
+    return PDQ_OK;
+}

@@ -102,17 +102,9 @@ __global__ void k_seed(const SeedArgs A) {
     const int s = lo;
     const uint32_t j = (uint32_t)(g - A.offset[s]);
     const int c = (int)(j % (uint32_t)A.C);
-    const uint4 a = philox4x32_10(make_uint4(j, 0u, 0u, 0u), A.key);
-    double lam = 1.0;
-    if (A.sigma > 0.0) {
-        const uint4 b = philox4x32_10(make_uint4(j, 1u, 0u, 0u), A.key);
-        lam = exp(A.sigma * sqrt(-2.0 * log(unit_open(b.x))) * cos(2.0 * kPi * unit_open(b.y)));
-    }
-    const double rr = (A.R - A.half_d[c]) * sqrt(unit_open(a.x));
-    double sth, cth;
-    sincos(2.0 * kPi * unit_open(a.y), &sth, &cth);
-    const double x = rr * cth, y = rr * sth, z = A.L * unit_open(a.z);
-    const double q = A.params[s].xi * A.qfac[c] * lam;
+    double x, y, z, qhat;
+    seed_particle(A.key, j, A.sigma, A.R, A.L, A.half_d[c], A.qfac[c], x, y, z, qhat);
+    const double q = A.params[s].xi * qhat;
     if (P == PDQ_FP64) {
         ((double4_32a*)A.pos)[g] = make_double4_32a(x, y, z, q);
         ((double4_32a*)A.vel)[g] = make_double4_32a(0.0, 0.0, 0.0, 1.0);

@@ -51,6 +51,11 @@ class StepCfg(C.Structure):
                 ("use_graph", C.c_int32), ("variant", C.c_int32)]
 
 
+class BatchStruct(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("n_samples", C.c_int32), ("n_classes", C.c_int32), ("pad", C.c_int32),
+                ("st_plus", C.c_double * MAX_CLASSES), ("capacity", C.c_int64), ("offset", C.c_void_p)]
+
+
 class TallyStruct(C.Structure):
     _fields_ = [("n_dep", C.c_void_p), ("n_alive", C.c_void_p)]
 
@@ -88,6 +93,11 @@ def lib():
             "pdq_deposition_tally": (C.c_int, [C.POINTER(TallyStruct), C.c_int32, C.c_int32, C.c_double,
                                                C.c_double, P, P, P, P]),
             "pdq_mfmc_allocate": (C.c_int, [C.c_int32, P, P, P, C.c_double, C.c_int32, P, P, P, P]),
+            "pdq_adjoint_workspace_size": (C.c_int, [C.POINTER(BatchStruct), C.c_int64, C.c_int32,
+                                                     C.POINTER(C.c_size_t)]),
+            "pdq_adjoint_run": (C.c_int, [P, C.POINTER(Phys), C.POINTER(BatchStruct), P, C.c_double, C.c_uint64,
+                                          C.POINTER(StepCfg), C.c_int64, C.c_int32, C.c_double, C.c_int32, P, P, P,
+                                          P, C.c_size_t, P]),
             "pdq_mfmc_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                                   C.POINTER(C.c_size_t)]),
             "pdq_mfmc_sobol": (C.c_int, [C.c_int32, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
@@ -333,3 +343,65 @@ def mfmc_sobol(ys, m, alpha, n_boot=0, seed=0, stream=None):
     if n_boot == 0:
         del out["s_main_ci"], out["s_total_ci"]
     return out
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of the smoothed deposition functional
+# ---------------------------------------------------------------------------
+class Batch:
+    """Sample layout for the adjoint (it seeds its own particles)."""
+
+    def __init__(self, precision, counts, st_plus, device="cuda"):
+        off = [0]
+        for c in counts:
+            off.append(off[-1] + int(c))
+        self.offset = torch.tensor(off, dtype=torch.int64, device=device)
+        b = BatchStruct()
+        b.precision, b.n_samples, b.n_classes = precision, len(counts), len(st_plus)
+        for k, v in enumerate(st_plus):
+            b.st_plus[k] = float(v)
+        b.capacity, b.offset = off[-1], self.offset.data_ptr()
+        self.b = b
+        self.n_samples, self.n_classes = len(counts), len(st_plus)
+
+
+def adjoint_run(field, phys, batch, params_dev, cfg, n_steps, K, eps, seed, charge_sigma=0.0, gbar=None,
+                stream=None):
+    """J [S, C] and, for cotangents gbar [V, S, C], pbar [V, S, 3] = gbar . dJ/d(xi, zeta, theta)."""
+    n = C.c_size_t()
+    _check(lib().pdq_adjoint_workspace_size(C.byref(batch.b), int(n_steps), int(K), C.byref(n)),
+           "adjoint_workspace_size")
+    ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+    S, Cn = batch.n_samples, batch.n_classes
+    J = torch.empty((S, Cn), dtype=torch.float64, device="cuda")
+    nv = 0 if gbar is None else gbar.shape[0]
+    pbar = torch.zeros((max(nv, 1), S, 3), dtype=torch.float64, device="cuda")
+    g = gbar.contiguous().to(torch.float64) if gbar is not None else None
+    _check(lib().pdq_adjoint_run(field.handle, C.byref(phys), C.byref(batch.b), _ptr(params_dev), charge_sigma,
+                                 seed, C.byref(cfg), int(n_steps), int(K), float(eps), nv, _ptr(g), _ptr(J),
+                                 _ptr(pbar), _ptr(ws), ws.numel(), _stream(stream)), "adjoint_run")
+    return J, (pbar[:nv] if nv else None)
+
+
+class PdqDeposition(torch.autograd.Function):
+    """J = smoothed V_dep+ [S, C] of the particle model as a function of params [S, 3] = (xi, zeta, theta).
+
+    forward runs the smoothed forward sweep; backward runs the hand-written adjoint with the
+    incoming gradient as cotangent (one forward + one reverse sweep with checkpoints every K steps).
+    """
+
+    @staticmethod
+    def forward(ctx, params, field, phys, batch, cfg, n_steps, K, eps, seed, charge_sigma):
+        J, _ = adjoint_run(field, phys, batch, params_tensor(params.detach()), cfg, n_steps, K, eps, seed,
+                           charge_sigma)
+        ctx.save_for_backward(params.detach())
+        ctx.args = (field, phys, batch, cfg, n_steps, K, eps, seed, charge_sigma)
+        return J
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (params,) = ctx.saved_tensors
+        field, phys, batch, cfg, n_steps, K, eps, seed, charge_sigma = ctx.args
+        _, pbar = adjoint_run(field, phys, batch, params_tensor(params), cfg, n_steps, K, eps, seed, charge_sigma,
+                              gbar=grad_out.detach().to(torch.float64).unsqueeze(0))
+        return (pbar[0].to(device=params.device, dtype=params.dtype),) + (None,) * 9
