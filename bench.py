@@ -307,9 +307,9 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
                      # dram bytes read + written per launch from the ncu capture in
-                     # profiles/k_step_mixed_batched.md (484.2 MB for 4,557,792 particles),
-                     # scaled by the particle count of this launch
-                     "traffic": 484.2e6 / 4557792 * float(np.sum(counts)) if args.variant == 0 and prec == pdq.MIXED
+                     # profiles/k_step_mixed_batched.md (476.8 MB for 4,557,792 particles,
+                     # z-binned kernel), scaled by the particle count of this launch
+                     "traffic": 476.8e6 / 4557792 * float(np.sum(counts)) if args.variant == 0 and prec == pdq.MIXED
                      else None,
                      "kernel": "k_step (all-pairs Coulomb + local step)",
                      "note": "FP32 pipe peak = 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock); "

@@ -162,6 +162,21 @@ __device__ __forceinline__ void coulomb_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 y
     az = f2_fma(s, dz, az);
 }
 
+// Same pairs when no pair of the (i-tile, j-tile) combination needs the
+// periodic image: dz = (z_i - shift) - z_j directly (the shift is folded into zi).
+__device__ __forceinline__ void coulomb_pair_x2_direct(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 qj, float c2,
+                                                       f2& ax, f2& ay, f2& az) {
+    const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj), dz = f2_sub(zi, zj);
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    const f2 ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
+    const f2 s = f2_mul(f2_mul(ri, qj), f2_mul(ri, ri));
+    ax = f2_fma(s, dx, ax);
+    ay = f2_fma(s, dy, ay);
+    az = f2_fma(s, dz, az);
+}
+
 // Same pairs, with the three accumulations issued as scalar FFMA (two per
 // component) so that they can run on the FMA-lite pipe beside the packed work.
 __device__ __forceinline__ void coulomb_pair_x2s(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 qj, f2 invL2, f2 M2,
@@ -332,6 +347,8 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
     // j-tile: FP64 holds double4 (x, y, z, q); MIXED holds each value twice,
     // (x, x, y, y), (z, z, q, q), so packed f32x2 operands load without moves.
     __shared__ __align__(32) unsigned char smem_raw[NT * 32];
+    __shared__ float2 s_zr[NT / 32];      // per-warp z range of the staged j-tile
+    __shared__ float2 s_zi[NT / 32];      // per-warp z range of this CTA's i-particles
     __shared__ int s_item;
     __shared__ unsigned int s_alive[PDQ_MAX_CLASSES], s_dep[PDQ_MAX_CLASSES];
     const StepConst& K = A.K;
@@ -378,26 +395,74 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                     Z[h] = f2_pack(zi[2 * h], zi[2 * h + 1]);
                     AX[h] = AY[h] = AZ[h] = 0ull;
                 }
+                // z range of this CTA's i-particles (the tiles of a z-binned sample are narrow)
+                float ilo = INFINITY, ihi = -INFINITY;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (base + u * NT + tid < end) { ilo = fminf(ilo, (float)zi[u]); ihi = fmaxf(ihi, (float)zi[u]); }
+                for (int d = 16; d > 0; d >>= 1) {
+                    ilo = fminf(ilo, __shfl_xor_sync(0xffffffffu, ilo, d));
+                    ihi = fmaxf(ihi, __shfl_xor_sync(0xffffffffu, ihi, d));
+                }
+                if (lane == 0) s_zi[tid >> 5] = make_float2(ilo, ihi);
+                const float Lf = (float)L, halfL = 0.5f * Lf;
                 for (int64_t j0 = o; j0 < end; j0 += NT) {
                     const int64_t j = j0 + tid;
                     const float4 pj = j < end ? ((const float4*)pos_in)[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float jlo = j < end ? pj.z : INFINITY, jhi = j < end ? pj.z : -INFINITY;
+                    for (int d = 16; d > 0; d >>= 1) {
+                        jlo = fminf(jlo, __shfl_xor_sync(0xffffffffu, jlo, d));
+                        jhi = fmaxf(jhi, __shfl_xor_sync(0xffffffffu, jhi, d));
+                    }
+                    if (lane == 0) s_zr[tid >> 5] = make_float2(jlo, jhi);
                     sj2[2 * tid] = make_ulonglong2(f2_pack(pj.x, pj.x), f2_pack(pj.y, pj.y));
                     sj2[2 * tid + 1] = make_ulonglong2(f2_pack(pj.z, pj.z), f2_pack(pj.w, pj.w));
                     __syncthreads();
-#pragma unroll 4
-                    for (int k = 0; k < NT; ++k) {
-                        const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+                    // dz = z_i - z_j over the tile pair lies in [a_lo - b_hi, a_hi - b_lo]; when that
+                    // interval sits strictly inside one period window, the minimum image is a
+                    // uniform shift of 0 or +-L and the per-pair rounding step is skipped.
+                    float alo = INFINITY, ahi = -INFINITY, blo = INFINITY, bhi = -INFINITY;
 #pragma unroll
-                        for (int h = 0; h < H; ++h) {
-                            if constexpr (V == 1) {
-                                float(&sx)[2] = *reinterpret_cast<float(*)[2]>(&ax[2 * h]);
-                                float(&sy)[2] = *reinterpret_cast<float(*)[2]>(&ay[2 * h]);
-                                float(&sz)[2] = *reinterpret_cast<float(*)[2]>(&az[2 * h]);
-                                coulomb_pair_x2s(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, (float)c2,
-                                                 sx, sy, sz);
-                            } else {
-                                coulomb_pair_x2(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, (float)c2,
-                                                AX[h], AY[h], AZ[h]);
+                    for (int w = 0; w < NT / 32; ++w) {
+                        alo = fminf(alo, s_zi[w].x); ahi = fmaxf(ahi, s_zi[w].y);
+                        blo = fminf(blo, s_zr[w].x); bhi = fmaxf(bhi, s_zr[w].y);
+                    }
+                    const float dlo = alo - bhi, dhi = ahi - blo;
+                    float shift = 0.f;
+                    bool direct = V == 0;
+                    if (dlo > -halfL && dhi < halfL) shift = 0.f;
+                    else if (dlo > halfL && dhi < 3.f * halfL) shift = Lf;
+                    else if (dhi < -halfL && dlo > -3.f * halfL) shift = -Lf;
+                    else direct = false;
+                    if (direct) {
+                        const f2 sh = f2_pack(shift, shift);
+                        f2 Zs[H];
+#pragma unroll
+                        for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+#pragma unroll 4
+                        for (int k = 0; k < NT; ++k) {
+                            const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+#pragma unroll
+                            for (int h = 0; h < H; ++h)
+                                coulomb_pair_x2_direct(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, (float)c2, AX[h], AY[h],
+                                                       AZ[h]);
+                        }
+                    } else {
+#pragma unroll 4
+                        for (int k = 0; k < NT; ++k) {
+                            const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+#pragma unroll
+                            for (int h = 0; h < H; ++h) {
+                                if constexpr (V == 1) {
+                                    float(&sx)[2] = *reinterpret_cast<float(*)[2]>(&ax[2 * h]);
+                                    float(&sy)[2] = *reinterpret_cast<float(*)[2]>(&ay[2 * h]);
+                                    float(&sz)[2] = *reinterpret_cast<float(*)[2]>(&az[2 * h]);
+                                    coulomb_pair_x2s(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2,
+                                                     (float)c2, sx, sy, sz);
+                                } else {
+                                    coulomb_pair_x2(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2,
+                                                    (float)c2, AX[h], AY[h], AZ[h]);
+                                }
                             }
                         }
                     }
@@ -582,6 +647,78 @@ __global__ void __launch_bounds__(1024) k_compact(void* pos, void* vel, double2*
 }
 
 // ---------------------------------------------------------------------------
+// Compaction with z-binning (MIXED): one CTA per sample copies the live
+// particles of the current half into the other half, grouped by 256 bins of z
+// and in their previous order inside a bin (a stable counting sort: histogram,
+// bin bases, then chunks in order with ranks from __match_any_sync).  Tiles of
+// a binned sample cover short z-intervals, which lets the step skip the
+// per-pair minimum image for most tile pairs.  Tags go to `tag_out` (scratch).
+// ---------------------------------------------------------------------------
+constexpr int kZBins = 256;
+
+__global__ void __launch_bounds__(1024) k_sort_compact(const float4* __restrict__ pos_in, const float4* __restrict__ vel_in,
+                                                       const double2* __restrict__ xy_in, const int2* __restrict__ tag_in,
+                                                       float4* __restrict__ pos_out, float4* __restrict__ vel_out,
+                                                       double2* __restrict__ xy_out, int2* __restrict__ tag_out,
+                                                       const int64_t* __restrict__ offset, int32_t* __restrict__ count,
+                                                       float bins_per_length) {
+    __shared__ int base[kZBins];
+    __shared__ int running[kZBins];
+    __shared__ int wcnt[32][kZBins];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t o = offset[s];
+    const int n = count[s];
+    for (int b = tid; b < kZBins; b += blockDim.x) { base[b] = 0; running[b] = 0; }
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+        if (vel_in[o + i].w > 0.5f) {
+            const int b = min(kZBins - 1, max(0, (int)(pos_in[o + i].z * bins_per_length)));
+            atomicAdd(&base[b], 1);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int b = 0; b < kZBins; ++b) { const int h = base[b]; base[b] = acc; acc += h; }
+        count[s] = acc;
+    }
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        for (int q = tid; q < 32 * kZBins; q += blockDim.x) (&wcnt[0][0])[q] = 0;
+        const int i = c0 + tid;
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
+        double2 w = make_double2(0.0, 0.0);
+        int2 tg = make_int2(0, 0);
+        int b = -1;
+        if (i < n) {
+            p = pos_in[o + i];
+            v = vel_in[o + i];
+            w = xy_in[o + i];
+            tg = tag_in[o + i];
+            if (v.w > 0.5f) b = min(kZBins - 1, max(0, (int)(p.z * bins_per_length)));
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        __syncthreads();                                   // wcnt cleared
+        if (b >= 0 && rank == 0) wcnt[warp][b] = __popc(peers);
+        __syncthreads();
+        if (tid < kZBins) {                                // per bin: offsets of the warps, in warp order
+            int acc = running[tid];
+            for (int q = 0; q < 32; ++q) { const int c = wcnt[q][tid]; wcnt[q][tid] = acc; acc += c; }
+            running[tid] = acc;
+        }
+        __syncthreads();
+        if (b >= 0) {
+            const int64_t d = o + base[b] + wcnt[warp][b] + rank;
+            pos_out[d] = p;
+            vel_out[d] = v;
+            xy_out[d] = w;
+            tag_out[d] = tg;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Deposition velocity per (sample, class) and the Monte Carlo mean / SE.
 // ---------------------------------------------------------------------------
 __global__ void k_vdep(const int64_t* __restrict__ nd, const int64_t* __restrict__ na, int n, double scale,
@@ -677,6 +814,21 @@ static void workspace_layout(const pdq_state* st, int TI, size_t* items_bytes, s
     const int64_t max_items = st->capacity / TI + st->n_samples + 1;
     *items_bytes = align256(sizeof(int2) * (size_t)max_items);
     *total = *items_bytes + align256(sizeof(int32_t) * (size_t)st->n_samples);
+    if (st->precision == PDQ_MIXED) *total += align256(sizeof(int2) * (size_t)(st->capacity > 0 ? st->capacity : 1));
+}
+
+// MIXED: z-binned compaction from the current half into the other half, tags
+// through the workspace scratch, then flip the current half.
+static int enqueue_sort_compact(pdq_state* st, int2* tag_scratch, float bins_per_length, cudaStream_t s) {
+    const int h = st->cur;
+    k_sort_compact<<<st->n_samples, 1024, 0, s>>>((const float4*)st->pos[h], (const float4*)st->vel[h],
+                                                  (const double2*)st->xy[h], (const int2*)st->tag,
+                                                  (float4*)st->pos[h ^ 1], (float4*)st->vel[h ^ 1],
+                                                  (double2*)st->xy[h ^ 1], tag_scratch, st->offset, st->count,
+                                                  bins_per_length);
+    PDQ_CUDA(cudaMemcpyAsync(st->tag, tag_scratch, sizeof(int2) * (size_t)st->capacity, cudaMemcpyDeviceToDevice, s));
+    st->cur = h ^ 1;
+    return PDQ_OK;
 }
 
 static int enqueue_compact(pdq_state* st, cudaStream_t s) {
@@ -776,6 +928,15 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
     cudaGraph_t graph = nullptr;
     const bool use_graph = cfg->use_graph != 0;
     if (use_graph) PDQ_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    // MIXED with compaction enabled: particles are z-binned (at the start of the call and at
+    // every compaction) so that most tile pairs skip the per-pair minimum image.
+    const bool binned = st->precision == PDQ_MIXED && cfg->compact_every > 0;
+    int2* tag_scratch = (int2*)((char*)workspace + items_bytes + align256(sizeof(int32_t) * (size_t)st->n_samples));
+    const float bins_per_length = (float)(kZBins / A.K.L);
+    if (binned) {
+        int rc2 = enqueue_sort_compact(st, tag_scratch, bins_per_length, s);
+        if (rc2) return rc2;
+    }
     int cur = st->cur;
     int64_t stepi = st->step;
     k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, order, items, st->ctl);
@@ -787,7 +948,13 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
         ++stepi;
         if (cfg->compact_every > 0 && stepi % cfg->compact_every == 0 && k + 1 < n_steps) {
             st->cur = cur;
-            enqueue_compact(st, s);
+            if (binned) {
+                int rc2 = enqueue_sort_compact(st, tag_scratch, bins_per_length, s);
+                if (rc2) return rc2;
+                cur = st->cur;
+            } else {
+                enqueue_compact(st, s);
+            }
             k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, order, items, st->ctl);
         }
     }
