@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--block", type=int, default=0, help="threads per CTA of the step kernel (0 = library default)")
     ap.add_argument("--variant", type=int, default=0, help="MIXED pair-math variant")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -190,6 +191,8 @@ def run_ours(args):
         cfg = pdq.step_cfg(w["dt"], window_start=0, compact_every=w.get("compact_every", 0), block=args.block,
                            variant=args.variant)
         tally = pdq.Tally(len(counts), len(w["st_plus"]))
+        if args.block == 0 and args.variant == 0 and not args.no_autotune:
+            pdq.autotune(field, phys, state, prm, cfg, stream)      # project autotuner picks block / variant
         ws = pdq.workspace(state, cfg)
         pdq.step_particles(field, phys, state, prm, cfg, args.warmup, tally, ws, stream)
         stream.synchronize()
@@ -303,7 +306,9 @@ def run_ours(args):
                                    *w["grid"], w["dt"], w.get("compact_every", 0)),
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (
                        sum(t.numel() * t.element_size() for t in state.current() if t is not None) / 1e9),
-                   "parallelism": "samples sharded by rank" if world > 1 else "1 GPU"},
+                   "parallelism": "samples sharded by rank" if world > 1 else "1 GPU",
+                   "tile": {"block": cfg.block, "i_per_thread": 4 if prec == pdq.MIXED else 1,
+                            "variant": cfg.variant, "autotuned": args.block == 0 and not args.no_autotune}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
                      # dram bytes read + written per launch from the ncu capture in

@@ -185,7 +185,9 @@ typedef struct pdq_step_cfg {
     int64_t window_start; /* first global step index counted in the tallies (t+ >= t_w)      */
     int32_t compact_every;/* compact deposited particles out every this many steps; 0 never */
     int32_t block;        /* threads per CTA of the step kernel: 0 (auto), 64, 128 or 256    */
-    int32_t use_graph;    /* 1: replay the step sequence as a CUDA graph                     */
+    int32_t use_graph;    /* 1: capture the call as a CUDA graph (first call with a given      */
+                          /*    argument set) and replay it afterwards; needs a created        */
+                          /*    (non-default) stream; see pdq_release_graphs                   */
     int32_t variant;      /* MIXED pair-math variant: 0 packed f32x2, 1 packed + scalar sums */
 } pdq_step_cfg;
 
@@ -249,6 +251,25 @@ int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, pdq_state* 
 int pdq_step_particles_noalloc(const pdq_field* field, const pdq_phys* phys, pdq_state* state,
                                const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
                                pdq_tally* tally, pdq_stream_t stream);
+
+/* Autotuner: times one step of each candidate tile shape (threads per CTA 64,
+ * 128, 256) and, for PDQ_MIXED, each pair-math variant on this state, and
+ * writes the fastest into cfg->block / cfg->variant.  The timed steps write
+ * the scratch half and a scratch tally; the current half, state->cur,
+ * state->step and the device step counter are restored.  With PDQ_MIXED and
+ * cfg->compact_every > 0 the state is z-binned first (live particles
+ * reordered and compacted, as pdq_step_particles does at the start of a call).
+ * Results are cached per (precision, log2 capacity, log2 samples, forces);
+ * a cached entry costs no device work.  Synchronises `stream`.
+ * Errors: INVALID_ARG, WORKSPACE, CUDA.                                      */
+int pdq_autotune_workspace_size(const pdq_state* state, size_t* bytes);
+int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_state* state, const pdq_sample_params* params,
+                 pdq_step_cfg* cfg, void* workspace, size_t workspace_bytes, pdq_stream_t stream);
+
+/* Destroy every cached step graph (use_graph = 1).  A cached graph bakes in
+ * the device pointers of its call: release the graphs before freeing or
+ * reusing those buffers for another purpose.                                 */
+int pdq_release_graphs(void);
 
 /* Stream compaction of deposited particles (alive == 0) of every sample, in
  * place and order-preserving on the current half; updates count[].          */

@@ -14,6 +14,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <string>
+
 #include "pdq_common.cuh"
 #include "pdq_device.cuh"
 
@@ -842,6 +846,29 @@ static int enqueue_compact(pdq_state* st, cudaStream_t s) {
     return PDQ_OK;
 }
 
+// Cache of instantiated step graphs, keyed by every argument that the captured
+// launches bake in (pointers, configuration, buffer parity, step phase of the
+// compaction schedule).
+struct GraphEntry {
+    cudaGraphExec_t exec;
+    int cur_after;
+};
+static std::mutex g_graph_mu;
+static std::map<std::string, GraphEntry> g_graphs;
+
+static std::string graph_key(const pdq_field* field, const pdq_phys* phys, const pdq_state* st,
+                             const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
+                             const pdq_tally* tally, const void* ws, size_t ws_bytes, cudaStream_t s) {
+    pdq_state k = *st;
+    k.step = cfg->compact_every > 0 ? st->step % cfg->compact_every : 0;
+    std::string key;
+    auto put = [&](const void* p, size_t n) { key.append((const char*)p, n); };
+    put(&field, sizeof(field)); put(phys, sizeof(*phys)); put(&k, sizeof(k)); put(&params, sizeof(params));
+    put(cfg, sizeof(*cfg)); put(&n_steps, sizeof(n_steps)); put(tally, sizeof(*tally)); put(&ws, sizeof(ws));
+    put(&ws_bytes, sizeof(ws_bytes)); put(&s, sizeof(s));
+    return key;
+}
+
 }  // namespace pdq
 
 using namespace pdq;
@@ -925,52 +952,96 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
     int32_t* order = (int32_t*)((char*)workspace + items_bytes);
     cudaStream_t s = (cudaStream_t)stream;
 
-    cudaGraph_t graph = nullptr;
-    const bool use_graph = cfg->use_graph != 0;
-    if (use_graph) PDQ_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     // MIXED with compaction enabled: particles are z-binned (at the start of the call and at
     // every compaction) so that most tile pairs skip the per-pair minimum image.
     const bool binned = st->precision == PDQ_MIXED && cfg->compact_every > 0;
     int2* tag_scratch = (int2*)((char*)workspace + items_bytes + align256(sizeof(int32_t) * (size_t)st->n_samples));
     const float bins_per_length = (float)(kZBins / A.K.L);
-    if (binned) {
-        int rc2 = enqueue_sort_compact(st, tag_scratch, bins_per_length, s);
-        if (rc2) return rc2;
-    }
-    int cur = st->cur;
-    int64_t stepi = st->step;
-    k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, order, items, st->ctl);
-    for (int64_t k = 0; k < n_steps; ++k) {
-        A.pos_in = st->pos[cur]; A.vel_in = st->vel[cur]; A.xy_in = (const double2*)st->xy[cur];
-        A.pos_out = st->pos[cur ^ 1]; A.vel_out = st->vel[cur ^ 1]; A.xy_out = (double2*)st->xy[cur ^ 1];
-        dispatch_step(st->precision, NT, cfg->variant, A, s);
-        cur ^= 1;
-        ++stepi;
-        if (cfg->compact_every > 0 && stepi % cfg->compact_every == 0 && k + 1 < n_steps) {
-            st->cur = cur;
-            if (binned) {
-                int rc2 = enqueue_sort_compact(st, tag_scratch, bins_per_length, s);
-                if (rc2) return rc2;
-                cur = st->cur;
-            } else {
-                enqueue_compact(st, s);
+    auto enqueue = [&]() -> int {
+        if (binned) {
+            const int r = enqueue_sort_compact(st, tag_scratch, bins_per_length, s);
+            if (r) return r;
+        }
+        int cur = st->cur;
+        int64_t stepi = st->step;
+        k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, order, items, st->ctl);
+        for (int64_t k = 0; k < n_steps; ++k) {
+            A.pos_in = st->pos[cur]; A.vel_in = st->vel[cur]; A.xy_in = (const double2*)st->xy[cur];
+            A.pos_out = st->pos[cur ^ 1]; A.vel_out = st->vel[cur ^ 1]; A.xy_out = (double2*)st->xy[cur ^ 1];
+            dispatch_step(st->precision, NT, cfg->variant, A, s);
+            cur ^= 1;
+            ++stepi;
+            if (cfg->compact_every > 0 && stepi % cfg->compact_every == 0 && k + 1 < n_steps) {
+                st->cur = cur;
+                if (binned) {
+                    const int r = enqueue_sort_compact(st, tag_scratch, bins_per_length, s);
+                    if (r) return r;
+                    cur = st->cur;
+                } else {
+                    enqueue_compact(st, s);
+                }
+                k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, order, items, st->ctl);
             }
-            k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, order, items, st->ctl);
+        }
+        st->cur = cur;
+        st->step = stepi;
+        return PDQ_OK;
+    };
+    if (!cfg->use_graph) {
+        rc = enqueue();
+        if (rc) return rc;
+        PDQ_CUDA(cudaGetLastError());
+        return PDQ_OK;
+    }
+    // Graph mode: the whole call (binning, work lists, n_steps step launches, compactions) is
+    // captured once per distinct argument set and replayed afterwards.
+    const std::string key = graph_key(field, phys, st, params, cfg, n_steps, tally, workspace, workspace_bytes, s);
+    {
+        std::lock_guard<std::mutex> lock(g_graph_mu);
+        auto it = g_graphs.find(key);
+        if (it != g_graphs.end()) {
+            PDQ_CUDA(cudaGraphLaunch(it->second.exec, s));
+            st->cur = it->second.cur_after;
+            st->step += n_steps;
+            return PDQ_OK;
         }
     }
-    if (use_graph) {
-        cudaError_t e = cudaStreamEndCapture(s, &graph);
-        if (e != cudaSuccess) return cuda_status(e);
-        cudaGraphExec_t exec = nullptr;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
-        if (exec) cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_status(e);
+    const int cur0 = st->cur;
+    const int64_t step0 = st->step;
+    PDQ_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        st->cur = cur0;
+        st->step = step0;
+        return rc ? rc : cuda_status(e);
     }
-    PDQ_CUDA(cudaGetLastError());
-    st->cur = cur;
-    st->step = stepi;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        st->cur = cur0;
+        st->step = step0;
+        return cuda_status(e);
+    }
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        st->cur = cur0;
+        st->step = step0;
+        return cuda_status(e);
+    }
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    g_graphs[key] = GraphEntry{exec, st->cur};
+    return PDQ_OK;
+}
+
+extern "C" int pdq_release_graphs(void) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (auto& kv : g_graphs) cudaGraphExecDestroy(kv.second.exec);
+    g_graphs.clear();
     return PDQ_OK;
 }
 
@@ -997,5 +1068,111 @@ extern "C" int pdq_deposition_tally(const pdq_tally* t, int32_t S, int32_t C, do
     k_vdep<<<(n + 255) / 256, 256, 0, s>>>(t->n_dep, t->n_alive, n, 0.5 * r_plus / dt, vdep);
     if (mean || se) k_vdep_stats<<<C, 32, 0, s>>>(vdep, S, C, mean, se);
     PDQ_CUDA(cudaGetLastError());
+    return PDQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times one step of every (block, pair variant) candidate on the
+// caller's state and writes the fastest into cfg.  Each timed step writes the
+// scratch half of the double buffer and a scratch tally, then the state's
+// current half, step counter and control block are restored, so the state is
+// unchanged apart from one z-binned compaction (MIXED with compaction on),
+// which only reorders live particles.  Results are cached per (precision,
+// log2 capacity, log2 samples, forces) for the process lifetime.
+// ---------------------------------------------------------------------------
+#include <map>
+#include <mutex>
+#include <tuple>
+
+namespace pdq {
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
+static int ilog2(int64_t v) { int r = 0; while (v > 1) { v >>= 1; ++r; } return r; }
+static size_t autotune_scratch_offset(const pdq_state* st) {
+    size_t ib, tot;
+    workspace_layout(st, 64 * tile_ilp(st), &ib, &tot);
+    return tot;
+}
+}  // namespace pdq
+
+extern "C" int pdq_autotune_workspace_size(const pdq_state* st, size_t* bytes) {
+    if (!bytes) return PDQ_ERR_INVALID_ARG;
+    int rc = validate_state(st);
+    if (rc) return rc;
+    *bytes = autotune_scratch_offset(st) + 2 * align256(sizeof(int64_t) * (size_t)st->n_samples * st->n_classes);
+    return PDQ_OK;
+}
+
+extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_state* st,
+                            const pdq_sample_params* params, pdq_step_cfg* cfg, void* workspace,
+                            size_t workspace_bytes, pdq_stream_t stream) {
+    if (!field || !phys || !params || !cfg) return PDQ_ERR_INVALID_ARG;
+    size_t need = 0;
+    int rc = pdq_autotune_workspace_size(st, &need);
+    if (rc) return rc;
+    if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return PDQ_ERR_WORKSPACE;
+    const auto key = std::make_tuple(st->precision, ilog2(st->capacity), ilog2(st->n_samples), cfg->forces);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            cfg->block = it->second.first;
+            cfg->variant = it->second.second;
+            return PDQ_OK;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t step_ws = autotune_scratch_offset(st);
+    const size_t tb = align256(sizeof(int64_t) * (size_t)st->n_samples * st->n_classes);
+    pdq_tally scratch;
+    scratch.n_dep = (int64_t*)((char*)workspace + step_ws);
+    scratch.n_alive = (int64_t*)((char*)workspace + step_ws + tb);
+    if (st->precision == PDQ_MIXED && cfg->compact_every > 0) {
+        StepConst K;
+        rc = make_step_const(field, phys, st, &K);
+        if (rc) return rc;
+        size_t ib, tot;
+        workspace_layout(st, 64 * tile_ilp(st), &ib, &tot);
+        int2* tag_scratch = (int2*)((char*)workspace + ib + align256(sizeof(int32_t) * (size_t)st->n_samples));
+        rc = enqueue_sort_compact(st, tag_scratch, (float)(kZBins / K.L), s);
+        if (rc) return rc;
+    }
+    const int blocks[3] = {64, 128, 256};
+    const int n_var = st->precision == PDQ_MIXED ? 2 : 1;
+    cudaEvent_t e0, e1;
+    PDQ_CUDA(cudaEventCreate(&e0));
+    PDQ_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_b = tile_threads(st, nullptr), best_v = 0;
+    const int cur0 = st->cur;
+    const int64_t step0 = st->step;
+    for (int bi = 0; bi < 3 && rc == PDQ_OK; ++bi) {
+        for (int v = 0; v < n_var && rc == PDQ_OK; ++v) {
+            pdq_step_cfg c = *cfg;
+            c.block = blocks[bi];
+            c.variant = v;
+            c.compact_every = 0;
+            c.use_graph = 0;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rc == PDQ_OK; ++rep) {      // rep 0 warms up
+                cudaEventRecord(e0, s);
+                rc = pdq_step_particles(field, phys, st, params, &c, 1, &scratch, workspace, step_ws, stream);
+                cudaEventRecord(e1, s);
+                st->cur = cur0;
+                st->step = step0;
+                cudaMemcpyAsync(st->ctl, &step0, sizeof(int64_t), cudaMemcpyHostToDevice, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = PDQ_ERR_CUDA;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (rc == PDQ_OK && ms < best) { best = ms; best_b = blocks[bi]; best_v = v; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    cfg->block = best_b;
+    cfg->variant = best_v;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = std::make_pair(best_b, best_v);
     return PDQ_OK;
 }

@@ -89,6 +89,10 @@ def lib():
             "pdq_step_particles_noalloc": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P,
                                                      C.POINTER(StepCfg), C.c_int64, C.POINTER(TallyStruct), P]),
             "pdq_compact": (C.c_int, [C.POINTER(StateStruct), P]),
+            "pdq_release_graphs": (C.c_int, []),
+            "pdq_autotune_workspace_size": (C.c_int, [C.POINTER(StateStruct), C.POINTER(C.c_size_t)]),
+            "pdq_autotune": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P, C.POINTER(StepCfg), P,
+                                       C.c_size_t, P]),
             "pdq_check_state": (C.c_int, [C.POINTER(StateStruct), P]),
             "pdq_deposition_tally": (C.c_int, [C.POINTER(TallyStruct), C.c_int32, C.c_int32, C.c_double,
                                                C.c_double, P, P, P, P]),
@@ -277,6 +281,20 @@ def step_particles_noalloc(field, phys, state, params_dev, cfg, n_steps, tally, 
     _check(lib().pdq_step_particles_noalloc(field.handle, C.byref(phys), C.byref(state.st), _ptr(params_dev),
                                             C.byref(cfg), int(n_steps), C.byref(tally.t), _stream(stream)),
            "step_particles_noalloc")
+
+
+def autotune(field, phys, state, params_dev, cfg, stream=None):
+    """Pick cfg.block / cfg.variant by timing one step of each candidate (cached per size bucket)."""
+    n = C.c_size_t()
+    _check(lib().pdq_autotune_workspace_size(C.byref(state.st), C.byref(n)), "autotune_workspace_size")
+    ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+    _check(lib().pdq_autotune(field.handle, C.byref(phys), C.byref(state.st), _ptr(params_dev), C.byref(cfg),
+                              _ptr(ws), ws.numel(), _stream(stream)), "autotune")
+    return cfg
+
+
+def release_graphs():
+    _check(lib().pdq_release_graphs(), "release_graphs")
 
 
 def compact(state, stream=None):
