@@ -149,6 +149,28 @@ def cpu_baseline(name, params, counts, seconds, steps_max=50):
                       "workload by sum N_s^2 (pair-dominated)" % (k, "+".join(str(int(x)) for x in sc), n, dt)}
 
 
+def rank_workload(name, rank, world, samples=None):
+    """(params, counts) of one rank: weak scaling gives every rank a full batch of its own samples."""
+    w = workloads.WORKLOADS[name]
+    params, counts = workloads.workload_inputs(name, samples)
+    if world > 1 and w["samples"] > 1:
+        params = workloads.sample_params(len(counts), w["param_seed"] + 7919 * rank)
+    return params, counts
+
+
+def reduce_over_ranks(ms, psteps, world, device):
+    """(slowest rank's time, particle-steps summed over ranks); no collective when world == 1."""
+    if world == 1:
+        return ms, float(psteps)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, float(psteps)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -176,9 +198,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     w = workloads.WORKLOADS[args.workload]
-    params, counts = workloads.workload_inputs(args.workload, args.samples)
-    if world > 1 and w["samples"] > 1:      # weak scaling: each rank its own batch of samples
-        params = workloads.sample_params(len(counts), w["param_seed"] + 7919 * rank)
+    params, counts = rank_workload(args.workload, rank, world, args.samples)
     prec = pdq.MIXED if w["precision"] == "mixed" else pdq.FP64
     phys = pdq.phys_default()
     desc = pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
@@ -280,15 +300,7 @@ def run_ours(args):
                     "value": (t1.n_alive.sum().item() - a1) / (x0.elapsed_time(x1) / 1e3),
                     "unit": "particle-steps/s", "steps": w1["steps"]}
 
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, float(psteps)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max, psteps_all = float(tmax[0]), float(t[1])
-    else:
-        ms_max, psteps_all = ms, float(psteps)
+    ms_max, psteps_all = reduce_over_ranks(ms, psteps, world, "cuda")
     if rank != 0:
         return
     peaks = measured_peaks()

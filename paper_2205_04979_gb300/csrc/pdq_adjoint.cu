@@ -90,6 +90,10 @@ __device__ __forceinline__ void interp_jac(const StepConst& K, double r, double 
     // value: the same routine as the forward step
     interp<T, T4>(K, (T)r, (T)x, (T)y, z, u);
     if (!GRAD) return;
+    if (!(isfinite(r) && isfinite(x) && isfinite(y) && isfinite((double)z))) {
+        for (int k = 0; k < 3; ++k) du[k][0] = du[k][1] = du[k][2] = (T)NAN;
+        return;
+    }
     // derivatives of the trilinear weights in (s(r), theta, z) chained to (x, y, z)
     const T R = (T)K.R;
     const T rho = fmin((T)r / R, (T)1);

@@ -66,6 +66,11 @@ __device__ __forceinline__ float4 grid_at(const StepConst& K, const float4*, int
 // inverts the node stretching; theta and z are periodic; s is clamped to [0, 1].
 template <class T, class T4>
 __device__ __forceinline__ void interp(const StepConst& K, T r, T x, T y, T z, T u[3]) {
+    if (!(isfinite(r) && isfinite(x) && isfinite(y) && isfinite(z))) {
+        // a non-finite position (reported through the error word) never forms a cell index
+        u[0] = u[1] = u[2] = (T)NAN;
+        return;
+    }
     const T R = (T)K.R;
     const T rho = fmin(r / R, (T)1);
     const T s = atanh_(rho * (T)K.tanh_beta) * (T)K.inv_beta;

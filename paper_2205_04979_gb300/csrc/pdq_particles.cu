@@ -676,7 +676,8 @@ __global__ void __launch_bounds__(1024) k_sort_compact(const float4* __restrict_
     __syncthreads();
     for (int i = tid; i < n; i += blockDim.x) {
         if (vel_in[o + i].w > 0.5f) {
-            const int b = min(kZBins - 1, max(0, (int)(pos_in[o + i].z * bins_per_length)));
+            const float zb = pos_in[o + i].z * bins_per_length;
+            const int b = isfinite(zb) ? min(kZBins - 1, max(0, (int)zb)) : 0;
             atomicAdd(&base[b], 1);
         }
     }
@@ -698,7 +699,10 @@ __global__ void __launch_bounds__(1024) k_sort_compact(const float4* __restrict_
             v = vel_in[o + i];
             w = xy_in[o + i];
             tg = tag_in[o + i];
-            if (v.w > 0.5f) b = min(kZBins - 1, max(0, (int)(p.z * bins_per_length)));
+            if (v.w > 0.5f) {
+                const float zb = p.z * bins_per_length;
+                b = isfinite(zb) ? min(kZBins - 1, max(0, (int)zb)) : 0;
+            }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, b);
         const int rank = __popc(peers & ((1u << lane) - 1u));

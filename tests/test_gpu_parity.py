@@ -299,3 +299,25 @@ def test_mixed_binned_compaction_parity(pdq, fields):
         # binned at the last compaction (step 15), then moved for 5 steps: bins stay nearly ordered
         b = np.floor(zs * 256 / 720.0)
         assert np.mean(np.diff(b) >= -2) > 0.95
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nonfinite_state_reported(pdq, fields, precision):
+    # failure made on the host: one particle's velocity is set to NaN; the step runs to the end,
+    # the kernels set the device error word, pdq_check_state reports PDQ_ERR_NAN once and clears it
+    f = fields[0]
+    phys = pdq.phys_default()
+    st = pdq.State(precision, [200, 100], ST3)
+    prm = pdq.params_tensor(PRM3[:2])
+    pdq.seed_particles(f, phys, st, prm, 1)
+    _, vel, _ = st.current()
+    vel[17, 0] = float("nan")
+    cfg = pdq.step_cfg(0.1, compact_every=2 if precision == 1 else 0)
+    tally = pdq.Tally(2, 3)
+    pdq.step_particles(f, phys, st, prm, cfg, 4, tally, pdq.workspace(st, cfg))
+    assert pdq.check_state(st) == -4           # PDQ_ERR_NAN
+    assert pdq.check_state(st) == 0            # cleared
+    # the other sample is untouched by the NaN
+    _, vel, _ = st.current()
+    off, cnt = st.offset.cpu().numpy(), st.count.cpu().numpy()
+    assert torch.isfinite(vel[off[1]:off[1] + cnt[1]]).all()
