@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--block", type=int, default=0, help="threads per CTA of the step kernel (0 = library default)")
     ap.add_argument("--variant", type=int, default=0, help="MIXED pair-math variant")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-vdep-check", action="store_true")
     return ap.parse_args()
 
 
@@ -169,6 +170,38 @@ def reduce_over_ranks(ms, psteps, world, device):
     dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(tmax[0]), float(t[1])
+
+
+def vdep_check(pdq, stream, samples=16, count=4096, steps=600, dt=0.05, t_window=10.0):
+    """V_dep+ of the batched MIXED path against the plain FP64 GPU path on the same seeds."""
+    import torch
+    w = workloads.WORKLOADS["batched_mixed"]
+    params = workloads.sample_params(samples, 4242)
+    phys = pdq.phys_default()
+    desc = pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
+    field = pdq.Field(desc, w["field_seed"], stream)
+    out = {}
+    for name, prec in (("mixed", pdq.MIXED), ("fp64", pdq.FP64)):
+        with torch.cuda.stream(stream):
+            st = pdq.State(prec, [count] * samples, w["st_plus"])
+            prm = pdq.params_tensor(params)
+            pdq.seed_particles(field, phys, st, prm, w["particle_seed"], 0.0, stream)
+            cfg = pdq.step_cfg(dt, window_start=workloads.window_start_step(t_window, dt), compact_every=100)
+            tally = pdq.Tally(samples, len(w["st_plus"]))
+            pdq.step_particles(field, phys, st, prm, cfg, steps, tally, pdq.workspace(st, cfg), stream)
+            vdep, _, _ = pdq.deposition_tally(tally, dt, stream=stream)
+            stream.synchronize()
+            out[name] = (vdep.cpu().numpy(), tally.n_dep.cpu().numpy())
+    vm, nm = out["mixed"]
+    vf, nf = out["fp64"]
+    mean_m, mean_f = vm.mean(0), vf.mean(0)
+    se = vf.std(0, ddof=1) / np.sqrt(samples)
+    rel = np.abs(mean_m - mean_f) / np.where(mean_f > 0, mean_f, 1.0)
+    return {"workload": "%d samples x %d particles, %d St+ classes, %d steps at dt+=%g, window t+>=%g" % (
+                samples, count, len(w["st_plus"]), steps, dt, t_window),
+            "vdep_fp64_mean": mean_f.tolist(), "vdep_mixed_mean": mean_m.tolist(), "mc_se_fp64": se.tolist(),
+            "rel_err": rel.tolist(), "err_over_se": (np.abs(mean_m - mean_f) / np.where(se > 0, se, 1.0)).tolist(),
+            "deposits_fp64": int(nf.sum()), "deposit_count_diff": int(np.abs(nm - nf).sum())}
 
 
 def run_reference(args):
@@ -337,6 +370,8 @@ def run_ours(args):
         "e2e": e2e,
         "plain_fp64": fp64,
     }
+    if not args.no_vdep_check and rank == 0:
+        out["vdep_check"] = vdep_check(pdq, stream)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, params, counts, args.cpu_seconds)
     print(json.dumps(out), flush=True)
