@@ -36,6 +36,7 @@ import workloads  # noqa: E402
 METRIC = "particle-steps/s, batched mixed vs plain FP64 on GB300 at ≤1e-3 rel V_dep error"
 FLOPS_PER_PAIR = 21          # 3 sub, 4 minimum image, 5 r^2, 3 r^-3 q, 6 accumulate (FMA = 2); + 1 rsqrt
 SM_COUNT, FP32_LANES = 152, 128
+FP64_NOMINAL_TFLOPS = 1.25
 
 
 def parse():
@@ -317,7 +318,7 @@ def run_ours(args):
 
         # plain FP64 single-sample path (the comparison the metric names)
         fp64 = None
-        if not args.no_fp64 and rank == 0:
+        if not args.no_fp64 and rank == 0 and args.workload == "batched_mixed":
             w1 = workloads.WORKLOADS["single_fp64"]
             d1 = pdq.field_desc(n_r=w1["grid"][0], n_th=w1["grid"][1], n_z=w1["grid"][2], n_modes=w1["n_modes"])
             f1 = pdq.Field(d1, w1["field_seed"], stream)
@@ -343,17 +344,24 @@ def run_ours(args):
         return
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak_tflops = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    if prec == pdq.MIXED:
+        peak_tflops = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+        peak_note = "FP32 pipe peak = 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % sm_max
+    else:
+        peak_tflops = FP64_NOMINAL_TFLOPS
+        peak_note = "FP64 nominal dense peak of the GB300 (1.25 TFLOP/s)"
     achieved = FLOPS_PER_PAIR * pairs / (ms / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": psteps_all / (ms_max / 1e3), "unit": "particle-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == pdq.MIXED else "f64",
         "data": "synthetic",
-        "config": {"workload": "%s: %d samples x U{4096..32768} particles (%d total), %d St+ classes, "
-                               "%dx%dx%d field, dt+=%g, compaction every %d steps" % (
-                                   args.workload, len(counts), int(np.sum(counts)), len(w["st_plus"]),
-                                   *w["grid"], w["dt"], w.get("compact_every", 0)),
+        "config": {"workload": "%s: %d samples, %d..%d particles each (%d total), %d St+ classes, "
+                               "%dx%dx%d field, dt+=%g, compaction every %d steps, %s" % (
+                                   args.workload, len(counts), int(np.min(counts)), int(np.max(counts)),
+                                   int(np.sum(counts)), len(w["st_plus"]), *w["grid"], w["dt"],
+                                   w.get("compact_every", 0), w["precision"]),
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (
                        sum(t.numel() * t.element_size() for t in state.current() if t is not None) / 1e9),
                    "parallelism": "samples sharded by rank" if world > 1 else "1 GPU",
@@ -367,18 +375,79 @@ def run_ours(args):
                      "traffic": 476.8e6 / 4557792 * float(np.sum(counts)) if args.variant == 0 and prec == pdq.MIXED
                      else None,
                      "kernel": "k_step (all-pairs Coulomb + local step)",
-                     "note": "FP32 pipe peak = 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock); "
-                             "%d flops per ordered pair; time per step from CUDA events over the timed region"
-                             % (sm_max, FLOPS_PER_PAIR)},
+                     "note": "%s; %d flops per ordered pair; time per step from CUDA events over the timed "
+                             "region" % (peak_note, FLOPS_PER_PAIR)},
         "clocks": clocks,
         "gpu_launches": int(launches),
         "e2e": e2e,
         "plain_fp64": fp64,
     }
-    if not args.no_vdep_check and rank == 0:
+    if not args.no_vdep_check and rank == 0 and args.workload == "batched_mixed":
         out["vdep_check"] = vdep_check(pdq, stream)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, params, counts, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint(args):
+    """Forward + reverse sweep of the smoothed-V_dep adjoint on 256 samples x 16,384 particles."""
+    import torch
+    import paper_2205_04979_gb300.pdq as pdq
+    w = workloads.WORKLOADS["adjoint"]
+    S = args.samples or w["samples"]
+    params = workloads.sample_params(S, w["param_seed"])
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    phys = pdq.phys_default()
+    K = min(w["checkpoint"], max(1, args.steps // 2))
+    with torch.cuda.stream(stream):
+        field = pdq.Field(pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2],
+                                         n_modes=w["n_modes"]), w["field_seed"], stream)
+        batch = pdq.Batch(pdq.MIXED, [w["count"]] * S, w["st_plus"])
+        cfg = pdq.step_cfg(w["dt"], window_start=0)
+        prm = pdq.params_tensor(params)
+        gbar = torch.ones((1, S, len(w["st_plus"])), dtype=torch.float64, device="cuda")
+        pdq.adjoint_run(field, phys, batch, prm, cfg, max(2, args.warmup), 1, w["eps"][1], w["particle_seed"],
+                        gbar=gbar, stream=stream)
+        stream.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        J, _ = pdq.adjoint_run(field, phys, batch, prm, cfg, args.steps, K, w["eps"][1], w["particle_seed"],
+                               stream=stream)
+        e[1].record(stream)
+        J2, pbar = pdq.adjoint_run(field, phys, batch, prm, cfg, args.steps, K, w["eps"][1], w["particle_seed"],
+                                   gbar=gbar, stream=stream)
+        e[2].record(stream)
+        e[2].synchronize()
+    fwd_ms, tot_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    psteps = float(S) * w["count"] * args.steps
+    out = {"metric": "gradient particle-steps/s (smoothed V_dep, forward + reverse sweep)",
+           "value": psteps / (tot_ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "adjoint: %d samples x %d particles, classes %s, checkpoint every %d steps, "
+                                  "eps+=%g" % (S, w["count"], w["st_plus"], K, w["eps"][1])},
+           "forward_only": {"value": psteps / (fwd_ms / 1e3), "unit": "particle-steps/s"},
+           "grad_mean_abs": np.abs(pbar.cpu().numpy()).mean(axis=(0, 1)).tolist(),
+           "J_mean": J2.mean(0).cpu().numpy().tolist()}
+    print(json.dumps(out), flush=True)
+
+
+def run_sobol(args):
+    """End-to-end Sobol' study of V_dep+ (high-fidelity model only) through paper_2205_04979_gb300.uq."""
+    import torch
+    from paper_2205_04979_gb300 import uq
+    torch.cuda.set_device(0)
+    m = args.samples or 64
+    uq.sobol_deposition(4, 1024, 10)                          # warm-up (builds, first launches)
+    r = uq.sobol_deposition(m, 4096, args.steps, n_boot=200)
+    out = {"metric": "Sobol' study: particle-steps/s of the pick-freeze runs", "value": r["particle_steps"] / (
+               r["ms"] / 1e3), "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "sobol: %d pick-freeze groups x 5 runs x 4096 particles, classes (0.1, 1, 10), "
+                                  "xi in [0, 0.1], zeta in [0, 1], theta in [0, 1]" % m},
+           "mean_vdep": r["mean"].tolist(), "s_main": r["s_main"].tolist(), "s_total": r["s_total"].tolist(),
+           "s_main_ci": r["s_main_ci"].tolist()}
     print(json.dumps(out), flush=True)
 
 
@@ -386,6 +455,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
+    elif args.workload == "sobol":
+        run_sobol(args)
     else:
         run_ours(args)
 
