@@ -309,17 +309,24 @@ template <int P, int NT>
 __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
     typedef typename Real<P>::T T;
     typedef typename Real<P>::T4 T4;
+    constexpr int U = 2;                     // particles per thread (ILP over the shared j-tile)
     __shared__ T4 sj[NT];
     const int s = blockIdx.y, tid = threadIdx.x;
     const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
-    if ((int64_t)blockIdx.x * NT >= n) return;
-    const int64_t i = (int64_t)blockIdx.x * NT + tid;
-    const bool valid = i < n;
-    const int64_t g = o + (valid ? i : 0);
+    if ((int64_t)blockIdx.x * NT * U >= n) return;
     const pdq_sample_params sp = A.params[s];
     const StepConst& K = A.K;
-    const T xi = valid ? (T)A.in.x[g] : (T)0, yi = valid ? (T)A.in.y[g] : (T)0, zi = valid ? (T)A.in.z[g] : (T)0;
-    T ax = 0, ay = 0, az = 0;
+    T xi[U], yi[U], zi[U], ax[U], ay[U], az[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t i = (int64_t)blockIdx.x * NT * U + u * NT + tid;
+        const bool valid = i < n;
+        const int64_t g = o + (valid ? i : 0);
+        xi[u] = valid ? (T)A.in.x[g] : (T)0;
+        yi[u] = valid ? (T)A.in.y[g] : (T)0;
+        zi[u] = valid ? (T)A.in.z[g] : (T)0;
+        ax[u] = ay[u] = az[u] = (T)0;
+    }
     if (K.forces & PDQ_F_COULOMB) {
         const T L = (T)K.L, invL = (T)K.invL;
         const T c2 = P == PDQ_FP64 ? (T)K.contact2 : (T)K.contact2f;
@@ -335,30 +342,41 @@ __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
             }
             sj[tid] = p;
             __syncthreads();
-            for (int k = 0; k < NT; ++k) coulomb_pair(xi, yi, zi, sj[k], L, invL, c2, ax, ay, az);
+#pragma unroll 4
+            for (int k = 0; k < NT; ++k) {
+                const T4 q = sj[k];
+#pragma unroll
+                for (int u = 0; u < U; ++u) coulomb_pair(xi[u], yi[u], zi[u], q, L, invL, c2, ax[u], ay[u], az[u]);
+            }
             __syncthreads();
         }
     }
-    int cls = -1;
-    double dnum = 0.0, dden = 0.0;
-    if (valid) {
-        cls = A.cls[g];
-        Local<T> Lc;
-        Lc.x = A.in.x[g]; Lc.y = A.in.y[g]; Lc.z = (T)A.in.z[g];
-        Lc.v[0] = (T)A.in.vx[g]; Lc.v[1] = (T)A.in.vy[g]; Lc.v[2] = (T)A.in.vz[g];
-        Lc.w = A.in.w[g];
-        Lc.q = sp.xi * A.qhat[g];
-        local_step<P, false>(A, K.cls[cls], sp, Lc, ax, ay, az);
-        A.in.sx[g] = (double)ax; A.in.sy[g] = (double)ay; A.in.sz[g] = (double)az;
-        A.out.x[g] = Lc.xn; A.out.y[g] = Lc.yn; A.out.z[g] = (double)Lc.zn;
-        A.out.vx[g] = (double)Lc.vn[0]; A.out.vy[g] = (double)Lc.vn[1]; A.out.vz[g] = (double)Lc.vn[2];
-        A.out.w[g] = Lc.wn;
-        dnum = Lc.w - Lc.wn;
-        dden = Lc.w;
-    }
-    if (A.tally && A.step >= K.window_start) {
-        warp_class_add(dnum, cls, A.C, A.num + (int64_t)s * A.C);
-        warp_class_add(dden, cls, A.C, A.den + (int64_t)s * A.C);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t i = (int64_t)blockIdx.x * NT * U + u * NT + tid;
+        const bool valid = i < n;
+        int cls = -1;
+        double dnum = 0.0, dden = 0.0;
+        if (valid) {
+            const int64_t g = o + i;
+            cls = A.cls[g];
+            Local<T> Lc;
+            Lc.x = A.in.x[g]; Lc.y = A.in.y[g]; Lc.z = (T)A.in.z[g];
+            Lc.v[0] = (T)A.in.vx[g]; Lc.v[1] = (T)A.in.vy[g]; Lc.v[2] = (T)A.in.vz[g];
+            Lc.w = A.in.w[g];
+            Lc.q = sp.xi * A.qhat[g];
+            local_step<P, false>(A, K.cls[cls], sp, Lc, ax[u], ay[u], az[u]);
+            A.in.sx[g] = (double)ax[u]; A.in.sy[g] = (double)ay[u]; A.in.sz[g] = (double)az[u];
+            A.out.x[g] = Lc.xn; A.out.y[g] = Lc.yn; A.out.z[g] = (double)Lc.zn;
+            A.out.vx[g] = (double)Lc.vn[0]; A.out.vy[g] = (double)Lc.vn[1]; A.out.vz[g] = (double)Lc.vn[2];
+            A.out.w[g] = Lc.wn;
+            dnum = Lc.w - Lc.wn;
+            dden = Lc.w;
+        }
+        if (A.tally && A.step >= K.window_start) {
+            warp_class_add(dnum, cls, A.C, A.num + (int64_t)s * A.C);
+            warp_class_add(dden, cls, A.C, A.den + (int64_t)s * A.C);
+        }
     }
 }
 
@@ -467,24 +485,36 @@ __global__ void __launch_bounds__(128) k_adj_local(const AdjArgs A) {
 template <int P, int NT>
 __global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
     typedef typename Real<P>::T T;
+    constexpr int U = 2;                     // particles m per thread
     __shared__ T sj[7][NT];
     const int s = blockIdx.y, tid = threadIdx.x;
     const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
-    if ((int64_t)blockIdx.x * NT >= n) return;
-    const int64_t i = (int64_t)blockIdx.x * NT + tid;
-    const bool valid = i < n;
-    const int64_t g = o + (valid ? i : 0);
+    if ((int64_t)blockIdx.x * NT * U >= n) return;
     const pdq_sample_params sp = A.params[s];
     const StepConst& K = A.K;
-    double xi_bar = 0.0;
+    double xi_bar[U] = {0.0, 0.0};
     if (K.forces & PDQ_F_COULOMB) {
-        const T xm = valid ? (T)A.in.x[g] : (T)0, ym = valid ? (T)A.in.y[g] : (T)0, zm = valid ? (T)A.in.z[g] : (T)0;
-        const double qm = sp.xi * A.qhat[g];
-        const T Qm = valid ? (T)(A.in.w[g] * qm) : (T)0;
-        const T cmx = valid ? (T)A.cx[g] : (T)0, cmy = valid ? (T)A.cy[g] : (T)0, cmz = valid ? (T)A.cz[g] : (T)0;
+        T xm[U], ym[U], zm[U], Qm[U], cmx[U], cmy[U], cmz[U];
+        // per m: A1 = sum_j Q_j / r^3, A2 = sum_j c_j / r^3, A3 = sum_j k_mj d (J's outer-product term),
+        // Qb = -sum_j c_j . d / r^3; then xbar_m = c_m A1 - Q_m A2 + A3
+        T A1[U], A2x[U], A2y[U], A2z[U], A3x[U], A3y[U], A3z[U], Qb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = (int64_t)blockIdx.x * NT * U + u * NT + tid;
+            const bool valid = i < n;
+            const int64_t g = o + (valid ? i : 0);
+            xm[u] = valid ? (T)A.in.x[g] : (T)0;
+            ym[u] = valid ? (T)A.in.y[g] : (T)0;
+            zm[u] = valid ? (T)A.in.z[g] : (T)0;
+            Qm[u] = valid ? (T)(A.in.w[g] * sp.xi * A.qhat[g]) : (T)0;
+            cmx[u] = valid ? (T)A.cx[g] : (T)0;
+            cmy[u] = valid ? (T)A.cy[g] : (T)0;
+            cmz[u] = valid ? (T)A.cz[g] : (T)0;
+            A1[u] = A2x[u] = A2y[u] = A2z[u] = A3x[u] = A3y[u] = A3z[u] = Qb[u] = (T)0;
+        }
         const T L = (T)K.L, invL = (T)K.invL;
         const T c2 = P == PDQ_FP64 ? (T)K.contact2 : (T)K.contact2f;
-        T bx = 0, by = 0, bz = 0, Qb = 0;
+        const T M = P == PDQ_FP64 ? (T)6755399441055744.0 : (T)12582912.0f;   // 1.5 * 2^52 / 1.5 * 2^23
         for (int64_t j0 = 0; j0 < n; j0 += NT) {
             const int64_t j = j0 + tid;
             if (j < n) {
@@ -496,38 +526,53 @@ __global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
                 for (int q = 0; q < 7; ++q) sj[q][tid] = (T)0;
             }
             __syncthreads();
+#pragma unroll 2
             for (int k = 0; k < NT; ++k) {
-                const T dx = xm - sj[0][k], dy = ym - sj[1][k];
-                T dz = zm - sj[2][k];
-                dz -= L * rint(dz * invL);
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                const T r2c = r2 > c2 ? r2 : c2;
-                const T ri = (T)1 / sqrt_(r2c);
-                const T ri3 = ri * ri * ri;
-                const T Qj = sj[3][k];
-                const T vx = Qj * cmx - Qm * sj[4][k], vy = Qj * cmy - Qm * sj[5][k], vz = Qj * cmz - Qm * sj[6][k];
-                const T dv = dx * vx + dy * vy + dz * vz;
-                const T kk = r2 > c2 ? (T)-3 * ri3 * ri * ri * dv : (T)0;
-                bx += ri3 * vx + kk * dx;
-                by += ri3 * vy + kk * dy;
-                bz += ri3 * vz + kk * dz;
-                Qb -= ri3 * (sj[4][k] * dx + sj[5][k] * dy + sj[6][k] * dz);
+                const T xj = sj[0][k], yj = sj[1][k], zj = sj[2][k], Qj = sj[3][k];
+                const T cjx = sj[4][k], cjy = sj[5][k], cjz = sj[6][k];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const T dx = xm[u] - xj, dy = ym[u] - yj;
+                    T dz = zm[u] - zj;
+                    const T t = (dz * invL + M) - M;                 // rint(dz / L)
+                    dz -= L * t;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    const T ri = rsqrt_ftz(r2 > c2 ? r2 : c2);
+                    const T ri2 = ri * ri, ri3 = ri2 * ri;
+                    const T dcj = dx * cjx + dy * cjy + dz * cjz;      // d . c_j
+                    const T dcm = dx * cmx[u] + dy * cmy[u] + dz * cmz[u];
+                    A1[u] += Qj * ri3;
+                    A2x[u] += ri3 * cjx; A2y[u] += ri3 * cjy; A2z[u] += ri3 * cjz;
+                    // J v with v = Q_j c_m - Q_m c_j: the -3 d (d . v) / r^5 part, zero inside the contact clamp
+                    const T kk = r2 > c2 ? (T)-3 * ri3 * ri2 * (Qj * dcm - Qm[u] * dcj) : (T)0;
+                    A3x[u] += kk * dx; A3y[u] += kk * dy; A3z[u] += kk * dz;
+                    Qb[u] -= ri3 * dcj;
+                }
             }
             __syncthreads();
         }
-        if (valid) {
-            A.xb[g] += (double)bx;
-            A.yb[g] += (double)by;
-            A.zb[g] += (double)bz;
-            const double w = A.in.w[g];
-            A.wb[g] += (double)Qb * qm;
-            const double qbar = A.qb[g] + (double)Qb * w;
-            xi_bar = qbar * A.qhat[g];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = (int64_t)blockIdx.x * NT * U + u * NT + tid;
+            if (i < n) {
+                const int64_t g = o + i;
+                A.xb[g] += (double)(cmx[u] * A1[u] - Qm[u] * A2x[u] + A3x[u]);
+                A.yb[g] += (double)(cmy[u] * A1[u] - Qm[u] * A2y[u] + A3y[u]);
+                A.zb[g] += (double)(cmz[u] * A1[u] - Qm[u] * A2z[u] + A3z[u]);
+                const double qm = sp.xi * A.qhat[g];
+                const double w = A.in.w[g];
+                A.wb[g] += (double)Qb[u] * qm;
+                xi_bar[u] = (A.qb[g] + (double)Qb[u] * w) * A.qhat[g];
+            }
         }
-    } else if (valid) {
-        xi_bar = A.qb[g] * A.qhat[g];
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = (int64_t)blockIdx.x * NT * U + u * NT + tid;
+            if (i < n) xi_bar[u] = A.qb[o + i] * A.qhat[o + i];
+        }
     }
-    warp_add(xi_bar, A.pbar + (int64_t)s * 3 + 0);
+    warp_add(xi_bar[0] + xi_bar[1], A.pbar + (int64_t)s * 3 + 0);
 }
 
 // J = (R+/2) num / (dt den) and the cotangents of num and den for one vector gbar.
@@ -664,7 +709,7 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
     if (off[A.S] != N) return PDQ_ERR_INVALID_ARG;
     if (nmax == 0) nmax = 1;
     const int NT = 128;
-    const dim3 grid((unsigned)((nmax + NT - 1) / NT), (unsigned)A.S);
+    const dim3 grid((unsigned)((nmax + 2 * NT - 1) / (2 * NT)), (unsigned)A.S);   // 2 particles per thread
     const bool mixed = batch->precision == PDQ_MIXED;
 
     auto fwd = [&](const Slot& in, const Slot& out, int64_t step, int tally) {
@@ -685,7 +730,7 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
 
     // seed into segment slot 0, save as checkpoint 0
     A.out = seg[0];
-    k_adj_seed<<<grid, NT, 0, s>>>(A);
+    k_adj_seed<<<dim3((unsigned)((nmax + NT - 1) / NT), (unsigned)A.S), NT, 0, s>>>(A);
     PDQ_CUDA(cudaMemsetAsync(A.num, 0, sc, s));
     PDQ_CUDA(cudaMemsetAsync(A.den, 0, sc, s));
     PDQ_CUDA(copy_state(ck[0], seg[0]));

@@ -112,6 +112,15 @@ __device__ __forceinline__ void interp(const StepConst& K, T r, T x, T y, T z, T
 
 // One ordered pair of the Coulomb sum: acc += q_j (x_i - x_j) / max(|x_i - x_j|, d_c)^3,
 // minimum image in z by the round-to-nearest trick (t + M) - M.
+// Hardware reciprocal square root without the denormal fix-up path (arguments
+// here are clamped away from zero by the contact distance).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rsqrt_ftz(double x) { return rsqrt(x); }
+
 __device__ __forceinline__ void coulomb_pair(float xi, float yi, float zi, const float4 pj, float L, float invL,
                                              float c2, float& ax, float& ay, float& az) {
     const float dx = xi - pj.x, dy = yi - pj.y;
@@ -119,7 +128,7 @@ __device__ __forceinline__ void coulomb_pair(float xi, float yi, float zi, const
     const float t = __fadd_rn(__fmaf_rn(dz, invL, 12582912.0f), -12582912.0f);
     dz = __fmaf_rn(-L, t, dz);
     const float r2 = fmaxf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))), c2);
-    const float ri = rsqrtf(r2);
+    const float ri = rsqrt_ftz(r2);
     const float s = __fmul_rn(__fmul_rn(pj.w, ri), __fmul_rn(ri, ri));
     ax = __fmaf_rn(s, dx, ax);
     ay = __fmaf_rn(s, dy, ay);

@@ -141,11 +141,6 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
-__device__ __forceinline__ float rsqrt_ftz(float x) {
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 // Two ordered pairs (i_a, j), (i_b, j) of the Coulomb sum in packed form.
 // j = (xj, xj), (yj, yj), (zj, zj), (qj, qj); the minimum image in z uses
