@@ -188,7 +188,8 @@ typedef struct pdq_step_cfg {
     int32_t use_graph;    /* 1: capture the call as a CUDA graph (first call with a given      */
                           /*    argument set) and replay it afterwards; needs a created        */
                           /*    (non-default) stream; see pdq_release_graphs                   */
-    int32_t variant;      /* MIXED pair-math variant: 0 packed f32x2, 1 packed + scalar sums */
+    int32_t variant;      /* MIXED pair math: 0 packed f32x2 (4 particles per thread),      */
+                          /* 1 packed with scalar sums, 2 packed with 8 particles per thread  */
 } pdq_step_cfg;
 
 /* Caller-owned tallies, device int64 [S][C], accumulated across calls:

@@ -769,7 +769,11 @@ static int tile_threads(const pdq_state* st, const pdq_step_cfg* cfg) {
     if (cfg && cfg->block) return cfg->block;
     return st->precision == PDQ_FP64 ? 128 : 128;
 }
-static int tile_ilp(const pdq_state* st) { return st->precision == PDQ_FP64 ? 1 : 4; }
+// particles per thread: FP64 1; MIXED 4 (two packed pairs), 8 for pair variant 2
+static int tile_ilp(const pdq_state* st, const pdq_step_cfg* cfg = nullptr) {
+    if (st->precision == PDQ_FP64) return 1;
+    return (cfg && cfg->variant == 2) ? 8 : 4;
+}
 
 static int sm_count() {
     static int n = 0;
@@ -803,6 +807,10 @@ static int dispatch_step(int prec, int NT, int variant, const StepArgs& A, cudaS
         if (NT == 64) return launch_step<PDQ_MIXED, 64, 4, 1>(A, s);
         if (NT == 128) return launch_step<PDQ_MIXED, 128, 4, 1>(A, s);
         if (NT == 256) return launch_step<PDQ_MIXED, 256, 4, 1>(A, s);
+    } else if (variant == 2) {          // packed pairs, 8 particles per thread
+        if (NT == 64) return launch_step<PDQ_MIXED, 64, 8, 0>(A, s);
+        if (NT == 128) return launch_step<PDQ_MIXED, 128, 8, 0>(A, s);
+        if (NT == 256) return launch_step<PDQ_MIXED, 256, 8, 0>(A, s);
     } else {
         if (NT == 64) return launch_step<PDQ_MIXED, 64, 4, 0>(A, s);
         if (NT == 128) return launch_step<PDQ_MIXED, 128, 4, 0>(A, s);
@@ -904,7 +912,7 @@ extern "C" int pdq_step_workspace_size(const pdq_state* st, const pdq_step_cfg* 
     int rc = validate_state(st);
     if (rc) return rc;
     size_t ib, tot;
-    workspace_layout(st, tile_threads(st, cfg) * tile_ilp(st), &ib, &tot);
+    workspace_layout(st, tile_threads(st, cfg) * tile_ilp(st, cfg), &ib, &tot);
     *bytes = tot;
     return PDQ_OK;
 }
@@ -925,9 +933,9 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
     int rc = validate_state(st);
     if (rc) return rc;
     if (!(cfg->dt > 0) || (cfg->mode != PDQ_STICK && cfg->mode != PDQ_REBOUND) || (cfg->forces & ~PDQ_F_ALL) ||
-        cfg->compact_every < 0 || cfg->variant < 0 || cfg->variant > 1)
+        cfg->compact_every < 0 || cfg->variant < 0 || cfg->variant > 2)
         return PDQ_ERR_INVALID_ARG;
-    const int NT = tile_threads(st, cfg), U = tile_ilp(st);
+    const int NT = tile_threads(st, cfg), U = tile_ilp(st, cfg);
     if (NT != 64 && NT != 128 && NT != 256) return PDQ_ERR_INVALID_ARG;
     size_t items_bytes, need;
     workspace_layout(st, NT * U, &items_bytes, &need);
@@ -1137,7 +1145,7 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
         if (rc) return rc;
     }
     const int blocks[3] = {64, 128, 256};
-    const int n_var = st->precision == PDQ_MIXED ? 2 : 1;
+    const int n_var = st->precision == PDQ_MIXED ? 3 : 1;
     cudaEvent_t e0, e1;
     PDQ_CUDA(cudaEventCreate(&e0));
     PDQ_CUDA(cudaEventCreate(&e1));

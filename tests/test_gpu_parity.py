@@ -109,7 +109,7 @@ def _run_both(pdq, fields, precision, counts, st_plus, params, n_steps, cfg_kw, 
     ws = pdq.workspace(st, cfg)
     pdq.step_particles(f, phys, st, prm, cfg, n_steps, tally, ws)
     assert pdq.check_state(st) == 0
-    ocfg = oracle.cfg(0.1, **{k: v for k, v in cfg_kw.items() if k != "compact_every"})
+    ocfg = oracle.cfg(0.1, **{k: v for k, v in cfg_kw.items() if k not in ("compact_every", "variant")})
     nd, na = oracle.run(of, grid, ocfg, st_plus, off, params, ost, n_steps)
     return st, tally, ost, nd, na
 
@@ -279,12 +279,14 @@ def test_edge_cases(pdq, fields):
         pdq.step_particles(f, phys, st, prm, cfg, 1, tally, ws[:16])
 
 
-def test_mixed_binned_compaction_parity(pdq, fields):
+@pytest.mark.parametrize("variant", [0, 2])
+def test_mixed_binned_compaction_parity(pdq, fields, variant):
     # MIXED with compaction: particles are z-binned at the start of the call and at every
     # compaction, and most tile pairs skip the per-pair minimum image (uniform shift of 0 or
-    # +-L); results must still match the oracle particle by particle.
+    # +-L); results must still match the oracle particle by particle (4 and 8 particles per thread).
     counts = [1000, 333, 129]
-    st, tally, ost, nd, na = _run_both(pdq, fields, 1, counts, ST3, PRM3, 20, {"compact_every": 5})
+    st, tally, ost, nd, na = _run_both(pdq, fields, 1, counts, ST3, PRM3, 20,
+                                       {"compact_every": 5, "variant": variant})
     n_live = _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 2e-6, 2e-5, max_flip=0.005)
     cnt = st.count.cpu().numpy()
     pos, vel, _ = st.current()
