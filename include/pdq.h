@@ -319,14 +319,19 @@ int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_steps, int32_t 
  * pdq_seed_particles(seed, charge_sigma) would (common random numbers).
  * Reverse: checkpoints every K steps; each of the n_vec cotangent vectors
  * gbar[v] (device [S][C]) gives pbar[v] (device [S][3]) = sum_c gbar[v][s][c]
- * dJ[s][c]/d(xi_s, zeta_s, theta_s); theta only enters the rebound model, so
- * its component is 0.  J (device [S][C]) is always written.  The first call
- * reads offset[] to the host (synchronises `stream`).
- * Errors: INVALID_ARG, UNSUPPORTED (cfg->mode != PDQ_STICK), WORKSPACE, CUDA. */
+ * dJ[s][c]/d(xi_s, zeta_s, theta_s).  Under PDQ_STICK theta does not enter
+ * and its component is exactly 0.  With cfg->mode = PDQ_REBOUND (Sec. 4.3) the
+ * weight loss is multiplied by the smoothed sticking probability
+ * sigma(-arg/eps_stick), arg = sigma_y0^2 (1-theta)^2/(rho_p E)
+ * - 2 A_cont gamma_c/m (m^2/s^2; eps_stick > 0 required), and the rest of the
+ * particle rebounds with CoR_n (0 when arg <= 0, capped at 1), mirrored into
+ * the pipe.  J (device [S][C]) is always written.  Reads offset[] to the host
+ * (synchronises `stream`).
+ * Errors: INVALID_ARG, WORKSPACE, CUDA.                                      */
 int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
                     const pdq_sample_params* params, double charge_sigma, uint64_t seed, const pdq_step_cfg* cfg,
-                    int64_t n_steps, int32_t K, double eps, int32_t n_vec, const double* gbar, double* J,
-                    double* pbar, void* workspace, size_t workspace_bytes, pdq_stream_t stream);
+                    int64_t n_steps, int32_t K, double eps, double eps_stick, int32_t n_vec, const double* gbar,
+                    double* J, double* pbar, void* workspace, size_t workspace_bytes, pdq_stream_t stream);
 
 /* ---------------------------------------------------- multi-fidelity MC
  * Optimal MFMC allocation (Sec. 3.2, Eqs. opt1-opt3 and mf-precond) for k

@@ -45,7 +45,8 @@ class Field(C.Structure):
 
 class Cfg(C.Structure):
     _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("mode", C.c_int32),
-                ("forces", C.c_int32), ("window_start", C.c_int64), ("smooth_eps", C.c_double)]
+                ("forces", C.c_int32), ("window_start", C.c_int64), ("smooth_eps", C.c_double),
+                ("stick_eps", C.c_double)]
 
 
 F_DRAG, F_GRAV, F_COUL, F_IMAGE, F_VDW = 1, 2, 4, 8, 16
@@ -114,12 +115,12 @@ def field_desc(n_r=64, n_th=32, n_z=64, n_modes=64, r_plus=180.0, l_over_r=4.0, 
                  2 * np.pi / lam_max, 2 * np.pi / lam_min)
 
 
-def cfg(dt, forces=F_ALL, mode=STICK, gravity=(0.0, 0.0, 1.0), window_start=0, smooth_eps=0.0):
+def cfg(dt, forces=F_ALL, mode=STICK, gravity=(0.0, 0.0, 1.0), window_start=0, smooth_eps=0.0, stick_eps=0.0):
     c = Cfg()
     c.dt = dt
     for k in range(3):
         c.gravity[k] = gravity[k]
-    c.mode, c.forces, c.window_start, c.smooth_eps = mode, forces, window_start, smooth_eps
+    c.mode, c.forces, c.window_start, c.smooth_eps, c.stick_eps = mode, forces, window_start, smooth_eps, stick_eps
     return c
 
 

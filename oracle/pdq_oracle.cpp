@@ -135,6 +135,7 @@ struct OrcCfg {
     int32_t forces;            // bit mask: 1 drag, 2 gravity, 4 coulomb, 8 image, 16 vdw
     int64_t window_start;      // first step index counted in the tallies
     double smooth_eps;         // > 0: smoothed wall indicator of this width (no removal)
+    double stick_eps;          // smoothed rebound: width (m^2/s^2) of the sticking probability
 };
 
 void orc_phys_default(OrcPhys* p) {
@@ -578,7 +579,35 @@ static void step_sample(const Run<T>& rn, int n, T* x, T* y, T* z, T* vx, T* vy,
         T rnew = sqrt(pos[0] * pos[0] + pos[1] * pos[1]);
         T gap = R - rnew - 0.5 * c.d_plus;
         if (smooth) {
-            T wn = w[i] * (1.0 - logistic(-gap / cfg.smooth_eps));
+            // smoothed removal: the weight drops by the contact indicator sigma(-gap/eps), times,
+            // in rebound mode, the sticking probability sigma(-arg/eps_s) of the Bons model; the
+            // weight that does not stick rebounds with CoR_n (Sec. 4.3; CoR_n = 0 when arg <= 0)
+            T pstick(1.0);
+            if (cfg.mode == 1) {
+                const OrcPhys& p = *rn.p;
+                T sy = p.sigma_y0 * (1.0 - theta);
+                T gc = zeta * p.hamaker0 / (24.0 * M_PI * p.delta_c * p.delta_c);
+                double acont = M_PI * c.d * c.d / 4.0;
+                T arg = sy * sy / (p.rho_p * p.young) - 2.0 * acont * gc / c.mass;
+                pstick = logistic(-arg / cfg.stick_eps);
+                if (val(gap) <= 0) {
+                    T nx = pos[0] / rnew, ny = pos[1] / rnew;
+                    T vn1 = v[0] * nx + v[1] * ny;
+                    T vn1_si = vn1 * rn.un.ustar;
+                    T cor(0.0);
+                    if (val(arg) > 0) {
+                        cor = T(1.0);
+                        if (val(vn1_si) > 0) cor = vmin(T(1.0), sqrt(arg) / vn1_si);
+                    }
+                    T vabs = val(vn1) >= 0 ? vn1 : -vn1;
+                    T dv = -cor * vabs - vn1;
+                    v[0] = v[0] + dv * nx; v[1] = v[1] + dv * ny;
+                    T rc = R - 0.5 * c.d_plus;
+                    T rref = 2.0 * rc - rnew;
+                    pos[0] = nx * rref; pos[1] = ny * rref;
+                }
+            }
+            T wn = w[i] * (1.0 - logistic(-gap / cfg.smooth_eps) * pstick);
             if (counted) { num[ci] = num[ci] + (w[i] - wn); den[ci] = den[ci] + w[i]; }
             w[i] = wn;
         } else {
@@ -661,12 +690,14 @@ void orc_vdep(int n, const int64_t* ndep, const int64_t* nalive, double dt, doub
 // w^{n+1} = w^n (1 - logistic(-gap^{n+1}/eps)),
 // J_eps = (R+/2) sum_n sum_p (w^n - w^{n+1}) / (dt sum_n sum_p w^n), per class.
 // With want_grad, the forward-mode dual numbers give dJ/d(xi, zeta, theta).
+// Rebound mode (mode 1) multiplies the weight loss by the smoothed sticking
+// probability sigma(-arg/stick_eps) and reflects the rest of the particle.
 int orc_smooth_run(const OrcPhys* p, const OrcField* f, const double* grid, const OrcCfg* cfg,
                    int n_classes, const double* st_plus, int n_samples, const int64_t* offset,
                    const double* params, int64_t n_steps,
                    const double* x0, const double* y0, const double* z0, const double* qhat /*charge per unit xi*/,
                    const int32_t* cls, int want_grad, double* J /*[S][C]*/, double* dJ /*[S][C][3]*/) {
-    if (cfg->smooth_eps <= 0 || cfg->mode != 0) return -1;
+    if (cfg->smooth_eps <= 0 || (cfg->mode == 1 && !(cfg->stick_eps > 0))) return -1;
     for (int s = 0; s < n_samples; ++s) {
         int64_t o = offset[s];
         int n = (int)(offset[s + 1] - o);

@@ -45,7 +45,9 @@ struct AdjArgs {
     const int32_t* cls;
     const double* qhat;                 // charge per unit xi
     const pdq_sample_params* params;
-    double eps;
+    double eps;                         // width of the smoothed wall indicator (wall units)
+    double eps_stick;                   // width of the smoothed sticking probability (m^2/s^2)
+    int32_t mode;                       // PDQ_STICK or PDQ_REBOUND
     Slot in, out;                       // state n (S_n written here) and state n+1
     int64_t step;
     int32_t tally;
@@ -80,9 +82,14 @@ struct Local {
     T rel[3], relm, Re, lam;
     T zz, e, p1, p2, dp1, dp2;
     T F[3];
-    double xn, yn;
+    double xn, yn;                      // after integration (before a rebound)
     T zn, vn[3];
     double rn, gap, Sg, wn;
+    // smoothed rebound: sticking probability, and the reflection of the rest
+    double arg, pst, dv, nxa, nya, vnrm;
+    int rcase;                          // 0 CoR = 0, 1 inward (no change), 2 CoR capped at 1, 3 CoR < 1
+    bool reflect;
+    double xr, yr, vr[3];               // final state (after a rebound)
 };
 
 template <class T, class T4, bool GRAD>
@@ -271,7 +278,43 @@ __device__ __forceinline__ void local_step(const AdjArgs& A, const ClassK& c, co
     L.rn = sqrt(L.xn * L.xn + L.yn * L.yn);
     L.gap = K.R - L.rn - c.half_d;
     L.Sg = logistic(-L.gap / A.eps);
-    L.wn = L.w * (1.0 - L.Sg);
+    L.pst = 1.0;
+    L.reflect = false;
+    L.rcase = 0;
+    L.dv = 0.0;
+    L.xr = L.xn; L.yr = L.yn;
+    for (int k = 0; k < 3; ++k) L.vr[k] = (double)L.vn[k];
+    if (A.mode == PDQ_REBOUND) {
+        // Bons et al. (Sec. 4.3): sticking probability sigma(-arg/eps_s) with
+        // arg = sigma_y0^2 (1 - theta)^2 / (rho_p E) - 2 A_cont gamma_c / m; the rest rebounds
+        const double one_m = 1.0 - sp.theta;
+        L.arg = K.elastic0 * one_m * one_m - sp.zeta * c.stick;
+        L.pst = logistic(-L.arg / A.eps_stick);
+        if (L.gap <= 0.0 && L.rn > 0.0) {
+            L.reflect = true;
+            L.nxa = L.xn / L.rn;
+            L.nya = L.yn / L.rn;
+            L.vnrm = (double)L.vn[0] * L.nxa + (double)L.vn[1] * L.nya;
+            double cor = 0.0;
+            L.rcase = 0;
+            if (L.arg > 0.0) {
+                cor = 1.0;
+                L.rcase = 1;
+                const double vsi = L.vnrm * K.ustar;
+                if (vsi > 0.0) {
+                    const double ratio = sqrt(L.arg) / vsi;
+                    if (ratio >= 1.0) { L.rcase = 2; } else { cor = ratio; L.rcase = 3; }
+                }
+            }
+            L.dv = -cor * fabs(L.vnrm) - L.vnrm;
+            L.vr[0] = (double)L.vn[0] + L.dv * L.nxa;
+            L.vr[1] = (double)L.vn[1] + L.dv * L.nya;
+            const double rref = 2.0 * (K.R - c.half_d) - L.rn;
+            L.xr = L.nxa * rref;
+            L.yr = L.nya * rref;
+        }
+    }
+    L.wn = L.w * (1.0 - L.Sg * L.pst);
 }
 
 // Sum over a warp of v for the lanes whose class is c, for every class; lane 0 adds to dst[c].
@@ -367,8 +410,8 @@ __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
             Lc.q = sp.xi * A.qhat[g];
             local_step<P, false>(A, K.cls[cls], sp, Lc, ax[u], ay[u], az[u]);
             A.in.sx[g] = (double)ax[u]; A.in.sy[g] = (double)ay[u]; A.in.sz[g] = (double)az[u];
-            A.out.x[g] = Lc.xn; A.out.y[g] = Lc.yn; A.out.z[g] = (double)Lc.zn;
-            A.out.vx[g] = (double)Lc.vn[0]; A.out.vy[g] = (double)Lc.vn[1]; A.out.vz[g] = (double)Lc.vn[2];
+            A.out.x[g] = Lc.xr; A.out.y[g] = Lc.yr; A.out.z[g] = (double)Lc.zn;
+            A.out.vx[g] = (double)(T)Lc.vr[0]; A.out.vy[g] = (double)(T)Lc.vr[1]; A.out.vz[g] = (double)Lc.vn[2];
             A.out.w[g] = Lc.wn;
             dnum = Lc.w - Lc.wn;
             dden = Lc.w;
@@ -392,7 +435,7 @@ __global__ void __launch_bounds__(128) k_adj_local(const AdjArgs A) {
     const bool valid = i < n;
     const pdq_sample_params sp = A.params[s];
     const StepConst& K = A.K;
-    double zeta_bar = 0.0;
+    double zeta_bar = 0.0, theta_bar = 0.0;
     if (valid) {
         const int64_t g = o + i;
         const int cls = A.cls[g];
@@ -415,9 +458,37 @@ __global__ void __launch_bounds__(128) k_adj_local(const AdjArgs A) {
             wbar += nb + db;
             wb_next -= nb;
         }
-        // weight update w' = w (1 - Sg), Sg = sigma(-gap'/eps)
-        wbar += wb_next * (1.0 - L.Sg);
-        const double gapbar = wb_next * L.w * L.Sg * (1.0 - L.Sg) / A.eps;
+        // weight update w' = w (1 - Sg pst), Sg = sigma(-gap'/eps), pst = sigma(-arg/eps_s) (1 under all-stick)
+        wbar += wb_next * (1.0 - L.Sg * L.pst);
+        const double gapbar = wb_next * L.w * L.pst * L.Sg * (1.0 - L.Sg) / A.eps;
+        double argbar = 0.0;
+        if (A.mode == PDQ_REBOUND) argbar += wb_next * L.w * L.Sg * L.pst * (1.0 - L.pst) / A.eps_stick;
+        if (L.reflect) {
+            // rebound: x'' = x' (2 rc / r' - 1), v'' = v' + dv n, n = x'/r', dv = f(v'.n, arg)
+            const double nx = L.nxa, ny = L.nya, rp = L.rn, rc = K.R - c.half_d;
+            const double dvbar = vb[0] * nx + vb[1] * ny;
+            double nbx = L.dv * vb[0], nby = L.dv * vb[1];
+            double vnbar = 0.0;
+            if (L.rcase == 0) vnbar = -dvbar;                            // dv = -v_n
+            else if (L.rcase == 2) vnbar = -2.0 * dvbar;                 // dv = -2 v_n
+            else if (L.rcase == 3) {                                     // dv = -v_n - sqrt(arg)/u*
+                vnbar = -dvbar;
+                argbar += dvbar * (-0.5 / (K.ustar * sqrt(L.arg)));
+            }
+            vb[0] += vnbar * nx;
+            vb[1] += vnbar * ny;
+            nbx += vnbar * (double)L.vn[0];
+            nby += vnbar * (double)L.vn[1];
+            const double gm = 2.0 * rc / rp - 1.0;
+            const double gbar = xb[0] * L.xn + xb[1] * L.yn;
+            double xbx = gm * xb[0], xby = gm * xb[1];
+            const double rbar = gbar * (-2.0 * rc / (rp * rp));
+            const double nn = nbx * nx + nby * ny;
+            xbx += (nbx - nn * nx) / rp + rbar * nx;
+            xby += (nby - nn * ny) / rp + rbar * ny;
+            xb[0] = xbx;
+            xb[1] = xby;
+        }
         if (L.rn > 0.0) {   // gap' = R - r' - d/2
             xb[0] += -gapbar * L.xn / L.rn;
             xb[1] += -gapbar * L.yn / L.rn;
@@ -460,7 +531,7 @@ __global__ void __launch_bounds__(128) k_adj_local(const AdjArgs A) {
             xbn[0] += L.dAdr * Abar * L.nx + L.A * (abar[0] - Abar * L.nx) / L.r;
             xbn[1] += L.dAdr * Abar * L.ny + L.A * (abar[1] - Abar * L.ny) / L.r;
             qbar += Abar * L.img_q;
-            zeta_bar = Abar * L.vdw_z;
+            zeta_bar += Abar * L.vdw_z;
         }
         // Coulomb a_C = coul q S: qbar += coul abar . S; c = coul q abar for the pair adjoint
         double cx = 0.0, cy = 0.0, cz = 0.0;
@@ -470,6 +541,11 @@ __global__ void __launch_bounds__(128) k_adj_local(const AdjArgs A) {
             cy = c.coul * L.q * abar[1];
             cz = c.coul * L.q * abar[2];
         }
+        if (A.mode == PDQ_REBOUND) {
+            // arg = elastic0 (1 - theta)^2 - zeta stick
+            zeta_bar += argbar * (-c.stick);
+            theta_bar = argbar * (-2.0 * K.elastic0 * (1.0 - sp.theta));
+        }
         A.xb[g] = xbn[0]; A.yb[g] = xbn[1]; A.zb[g] = xbn[2];
         A.vxb[g] = vbar[0]; A.vyb[g] = vbar[1]; A.vzb[g] = vbar[2];
         A.wb[g] = wbar;
@@ -477,6 +553,7 @@ __global__ void __launch_bounds__(128) k_adj_local(const AdjArgs A) {
         A.cx[g] = cx; A.cy[g] = cy; A.cz[g] = cz;
     }
     warp_add(zeta_bar, A.pbar + (int64_t)s * 3 + 1);
+    if (A.mode == PDQ_REBOUND) warp_add(theta_bar, A.pbar + (int64_t)s * 3 + 2);
 }
 
 // All-pairs adjoint of S_m = sum_j Q_j G(x_m - x_j), Q = w q, G(d) = d / max(|d|, d_c)^3:
@@ -633,13 +710,14 @@ extern "C" int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_step
 
 extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
                                const pdq_sample_params* params, double charge_sigma, uint64_t seed,
-                               const pdq_step_cfg* cfg, int64_t n_steps, int32_t K, double eps, int32_t n_vec,
-                               const double* gbar, double* J, double* pbar, void* workspace, size_t workspace_bytes,
-                               pdq_stream_t stream) {
+                               const pdq_step_cfg* cfg, int64_t n_steps, int32_t K, double eps, double eps_stick,
+                               int32_t n_vec, const double* gbar, double* J, double* pbar, void* workspace,
+                               size_t workspace_bytes, pdq_stream_t stream) {
     if (!field || !phys || !batch || !params || !cfg || !J || n_steps < 1 || K < 1 || !(eps > 0) || n_vec < 0 ||
         (n_vec > 0 && (!gbar || !pbar)) || !(charge_sigma >= 0))
         return PDQ_ERR_INVALID_ARG;
-    if (cfg->mode != PDQ_STICK) return PDQ_ERR_UNSUPPORTED;
+    if (cfg->mode != PDQ_STICK && cfg->mode != PDQ_REBOUND) return PDQ_ERR_INVALID_ARG;
+    if (cfg->mode == PDQ_REBOUND && !(eps_stick > 0)) return PDQ_ERR_INVALID_ARG;
     if (!(cfg->dt > 0) || (cfg->forces & ~PDQ_F_ALL)) return PDQ_ERR_INVALID_ARG;
     if (batch->precision != PDQ_FP64 && batch->precision != PDQ_MIXED) return PDQ_ERR_INVALID_ARG;
     size_t need = 0;
@@ -659,7 +737,7 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
     A.K.dt = cfg->dt;
     A.K.dtf = (float)cfg->dt;
     A.K.forces = cfg->forces;
-    A.K.mode = PDQ_STICK;
+    A.K.mode = cfg->mode;
     A.K.window_start = cfg->window_start;
     const double gplus = phys->g * phys->nu / pow(phys->re_tau * phys->nu / phys->radius, 3);
     for (int k = 0; k < 3; ++k) { A.K.grav[k] = gplus * cfg->gravity[k]; A.K.gravf[k] = (float)A.K.grav[k]; }
@@ -668,6 +746,8 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
     A.C = batch->n_classes;
     A.params = params;
     A.eps = eps;
+    A.eps_stick = eps_stick;
+    A.mode = cfg->mode;
     A.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     A.sigma = charge_sigma;
 

@@ -100,8 +100,8 @@ def lib():
             "pdq_adjoint_workspace_size": (C.c_int, [C.POINTER(BatchStruct), C.c_int64, C.c_int32,
                                                      C.POINTER(C.c_size_t)]),
             "pdq_adjoint_run": (C.c_int, [P, C.POINTER(Phys), C.POINTER(BatchStruct), P, C.c_double, C.c_uint64,
-                                          C.POINTER(StepCfg), C.c_int64, C.c_int32, C.c_double, C.c_int32, P, P, P,
-                                          P, C.c_size_t, P]),
+                                          C.POINTER(StepCfg), C.c_int64, C.c_int32, C.c_double, C.c_double,
+                                          C.c_int32, P, P, P, P, C.c_size_t, P]),
             "pdq_mfmc_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                                   C.POINTER(C.c_size_t)]),
             "pdq_mfmc_sobol": (C.c_int, [C.c_int32, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
@@ -384,7 +384,7 @@ class Batch:
 
 
 def adjoint_run(field, phys, batch, params_dev, cfg, n_steps, K, eps, seed, charge_sigma=0.0, gbar=None,
-                stream=None):
+                stream=None, eps_stick=10.0):
     """J [S, C] and, for cotangents gbar [V, S, C], pbar [V, S, 3] = gbar . dJ/d(xi, zeta, theta)."""
     n = C.c_size_t()
     _check(lib().pdq_adjoint_workspace_size(C.byref(batch.b), int(n_steps), int(K), C.byref(n)),
@@ -396,8 +396,8 @@ def adjoint_run(field, phys, batch, params_dev, cfg, n_steps, K, eps, seed, char
     pbar = torch.zeros((max(nv, 1), S, 3), dtype=torch.float64, device="cuda")
     g = gbar.contiguous().to(torch.float64) if gbar is not None else None
     _check(lib().pdq_adjoint_run(field.handle, C.byref(phys), C.byref(batch.b), _ptr(params_dev), charge_sigma,
-                                 seed, C.byref(cfg), int(n_steps), int(K), float(eps), nv, _ptr(g), _ptr(J),
-                                 _ptr(pbar), _ptr(ws), ws.numel(), _stream(stream)), "adjoint_run")
+                                 seed, C.byref(cfg), int(n_steps), int(K), float(eps), float(eps_stick), nv, _ptr(g),
+                                 _ptr(J), _ptr(pbar), _ptr(ws), ws.numel(), _stream(stream)), "adjoint_run")
     return J, (pbar[:nv] if nv else None)
 
 

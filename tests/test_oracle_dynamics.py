@@ -228,3 +228,24 @@ def test_dual_numbers_match_finite_differences(orc, smooth_case):
                                          window_start=5), st_plus, off, p0[None], x0, y0, z0, qhat, cls, 40,
                            want_grad=False)
     assert np.allclose(Js, v, rtol=0.15)
+
+
+def test_smoothed_rebound_dual_numbers(orc):
+    # rebound mode of the smoothed functional: the weight loss carries the smoothed sticking
+    # probability sigma(-arg/eps_s) of the Bons model (Sec. 4.3), so theta now matters
+    f = orc.field_desc(n_r=33, n_th=16, n_z=32)
+    g = orc.field_grid(f, orc.field_modes(f, 0))
+    st_plus = [10.0, 100.0]
+    p0 = np.array([[0.09, 0.9, 0.6], [0.06, 0.5, 0.7]])
+    st, off = orc.seed(f, st_plus, [300, 129], np.c_[np.ones(2), p0[:, 1:]], 11)
+    c = orc.cfg(0.1, mode=orc.REBOUND, gravity=(1, 0, 0), smooth_eps=0.05, stick_eps=10.0, window_start=5)
+    J, dJ = orc.smooth_run(f, g, c, st_plus, off, p0, st.x, st.y, st.z, st.q, st.cls, 60)
+    assert np.all(np.abs(dJ[:, 1, 2]) > 0)          # theta derivative of the large class
+    for k in range(3):
+        pp, pm = p0.copy(), p0.copy()
+        pp[:, k] += 1e-6
+        pm[:, k] -= 1e-6
+        Jp, _ = orc.smooth_run(f, g, c, st_plus, off, pp, st.x, st.y, st.z, st.q, st.cls, 60, want_grad=False)
+        Jm, _ = orc.smooth_run(f, g, c, st_plus, off, pm, st.x, st.y, st.z, st.q, st.cls, 60, want_grad=False)
+        fd = (Jp - Jm) / 2e-6
+        assert np.allclose(dJ[..., k], fd, rtol=1e-4, atol=1e-6 * np.max(np.abs(fd)))
