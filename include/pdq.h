@@ -373,6 +373,18 @@ int pdq_mfmc_sobol(int32_t k, const double* const* y, const int64_t* m, const do
                    double* s_main_ci, double* s_total_ci, void* workspace, size_t workspace_bytes,
                    pdq_stream_t stream);
 
+/* Derivative-based upper bounds on the total Sobol' indices (Sobol' and
+ * Kucherenko, for inputs uniform on [a_j, b_j]):
+ *   s_j^t <= (b_j - a_j)^2 nu_j / (pi^2 Var f),  nu_j = E[(df/dx_j)^2],
+ * from S >= 2 Monte Carlo samples: grad device [S][C][d] (e.g. from
+ * pdq_adjoint_run with one-hot cotangents), y device [S][C] the outputs,
+ * width host [d] = b_j - a_j.  Host outputs nu [d][C], bound [d][C] (NaN
+ * where Var f = 0).  FP64 fixed-order reductions on the device.  Uses a
+ * (d+1) x C scratch from the stream-ordered allocator; synchronises `stream`.
+ * Errors: INVALID_ARG, CUDA.                                                 */
+int pdq_dgsm_bounds(int32_t S, int32_t C, int32_t d, const double* grad, const double* y, const double* width,
+                    double* nu, double* bound, pdq_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

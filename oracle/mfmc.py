@@ -189,3 +189,25 @@ def bootstrap_ci(groups, m, alpha, boot_index, n_boot):
     reps_m, reps_t = np.sort(np.array(reps_m), axis=0), np.sort(np.array(reps_t), axis=0)
     lo, hi = int(round(0.025 * (n_boot - 1))), int(round(0.975 * (n_boot - 1)))
     return np.stack([reps_m[lo], reps_m[hi]], -1), np.stack([reps_t[lo], reps_t[hi]], -1)
+
+
+def dgsm_bound(grad, y, width):
+    """Sobol'-Kucherenko bound s_j^t <= (b_j - a_j)^2 E[(df/dx_j)^2] / (pi^2 Var f), inputs uniform.
+
+    grad [S, ..., d], y [S, ...]; returns (nu [d, ...], bound [d, ...]).
+    """
+    grad, y = np.asarray(grad, np.float64), np.asarray(y, np.float64)
+    S = y.shape[0]
+    nu = np.moveaxis((grad ** 2).sum(axis=0) / S, -1, 0)
+    var = ((y - y.sum(axis=0) / S) ** 2).sum(axis=0) / (S - 1)
+    w = np.asarray(width, np.float64).reshape((-1,) + (1,) * (nu.ndim - 1))
+    return nu, w ** 2 * nu / (np.pi ** 2 * var)
+
+
+def ishigami_grad(x, a=7.0, b=0.1):
+    x = np.asarray(x, np.float64)
+    g = np.empty_like(x)
+    g[..., 0] = np.cos(x[..., 0]) * (1 + b * x[..., 2] ** 4)
+    g[..., 1] = 2 * a * np.sin(x[..., 1]) * np.cos(x[..., 1])
+    g[..., 2] = 4 * b * x[..., 2] ** 3 * np.sin(x[..., 0])
+    return g

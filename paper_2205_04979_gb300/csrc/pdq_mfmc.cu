@@ -229,3 +229,75 @@ extern "C" int pdq_mfmc_sobol(int32_t k, const double* const* y, const int64_t* 
     }
     return PDQ_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Derivative-based global sensitivity (DGSM) bounds on the total Sobol'
+// indices (Sobol' & Kucherenko): for inputs uniform on [a_j, b_j],
+//   s_j^t <= (b_j - a_j)^2 nu_j / (pi^2 Var f),  nu_j = E[(df/dx_j)^2],
+// from S samples of the gradient.  One CTA per (output c, input j) reduces
+// sum (df/dx_j)^2; one CTA per output computes the sample variance (two
+// passes, divisor S - 1); fixed-order reductions.
+// ---------------------------------------------------------------------------
+namespace pdq {
+__device__ __forceinline__ double block_sum_256(double v, double* red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_dgsm(const double* __restrict__ grad, const double* __restrict__ y, int S,
+                                              int C, int d, double* __restrict__ out /*[d+1][C]*/) {
+    __shared__ double red[256];
+    const int c = blockIdx.x, j = blockIdx.y;   // j == d: variance of y
+    if (j < d) {
+        double acc = 0.0;
+        for (int s = threadIdx.x; s < S; s += blockDim.x) {
+            const double gv = grad[((int64_t)s * C + c) * d + j];
+            acc += gv * gv;
+        }
+        const double tot = block_sum_256(acc, red);
+        if (threadIdx.x == 0) out[(int64_t)j * C + c] = tot / S;
+    } else {
+        double acc = 0.0;
+        for (int s = threadIdx.x; s < S; s += blockDim.x) acc += y[(int64_t)s * C + c];
+        const double mu = block_sum_256(acc, red) / S;
+        double acc2 = 0.0;
+        for (int s = threadIdx.x; s < S; s += blockDim.x) {
+            const double e = y[(int64_t)s * C + c] - mu;
+            acc2 += e * e;
+        }
+        const double tot = block_sum_256(acc2, red);
+        if (threadIdx.x == 0) out[(int64_t)d * C + c] = tot / (S - 1);
+    }
+}
+}  // namespace pdq
+
+extern "C" int pdq_dgsm_bounds(int32_t S, int32_t C, int32_t d, const double* grad, const double* y,
+                               const double* width, double* nu, double* bound, pdq_stream_t stream) {
+    if (S < 2 || C < 1 || d < 1 || d > 64 || !grad || !y || !width || !nu || !bound) return PDQ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* dev = nullptr;
+    // small result buffer on the stream's device (d+1) x C doubles
+    PDQ_CUDA(cudaMallocAsync(&dev, sizeof(double) * (size_t)(d + 1) * C, s));
+    k_dgsm<<<dim3(C, d + 1), 256, 0, s>>>(grad, y, S, C, d, dev);
+    std::vector<double> h((size_t)(d + 1) * C);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dev, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(dev, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const double pi2 = kPi * kPi;
+    for (int j = 0; j < d; ++j)
+        for (int c = 0; c < C; ++c) {
+            const double n = h[(size_t)j * C + c], var = h[(size_t)d * C + c];
+            nu[(size_t)j * C + c] = n;
+            bound[(size_t)j * C + c] = var > 0 ? width[j] * width[j] * n / (pi2 * var) : NAN;
+        }
+    return PDQ_OK;
+}

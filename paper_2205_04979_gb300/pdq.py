@@ -102,6 +102,7 @@ def lib():
             "pdq_adjoint_run": (C.c_int, [P, C.POINTER(Phys), C.POINTER(BatchStruct), P, C.c_double, C.c_uint64,
                                           C.POINTER(StepCfg), C.c_int64, C.c_int32, C.c_double, C.c_double,
                                           C.c_int32, P, P, P, P, C.c_size_t, P]),
+            "pdq_dgsm_bounds": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P]),
             "pdq_mfmc_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                                   C.POINTER(C.c_size_t)]),
             "pdq_mfmc_sobol": (C.c_int, [C.c_int32, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
@@ -423,3 +424,15 @@ class PdqDeposition(torch.autograd.Function):
         _, pbar = adjoint_run(field, phys, batch, params_tensor(params), cfg, n_steps, K, eps, seed, charge_sigma,
                               gbar=grad_out.detach().to(torch.float64).unsqueeze(0))
         return (pbar[0].to(device=params.device, dtype=params.dtype),) + (None,) * 9
+
+
+def dgsm_bounds(grad, y, width, stream=None):
+    """(nu [d, C], bound [d, C]) from device grad [S, C, d] and y [S, C] (float64)."""
+    import numpy as np
+    S, Cn, d = grad.shape
+    w = np.ascontiguousarray(width, np.float64)
+    nu, bound = np.zeros((d, Cn)), np.zeros((d, Cn))
+    g, yy = grad.contiguous().to(torch.float64), y.contiguous().to(torch.float64)
+    _check(lib().pdq_dgsm_bounds(S, Cn, d, _ptr(g), _ptr(yy), _np_ptr(w), _np_ptr(nu), _np_ptr(bound),
+                                 _stream(stream)), "dgsm_bounds")
+    return nu, bound

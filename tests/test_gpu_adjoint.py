@@ -138,3 +138,14 @@ def test_autograd_function(pdq):
     expect = np.einsum("sc,sck->sk", w.cpu().numpy(), dJ_ref)
     assert np.allclose(p.grad.numpy()[:, 0], expect[:, 0], rtol=1e-8)
     assert np.all(p.grad.numpy()[:, 2] == 0)
+
+
+def test_dgsm_pipeline(pdq):
+    from paper_2205_04979_gb300 import uq
+    from oracle import mfmc
+    r = uq.dgsm_deposition(16, 256, 40, st_plus=(10.0, 100.0), grid=(33, 16, 32), t_window=1.0, eps=0.05,
+                           precision=0)
+    assert r["grad"].shape == (16, 2, 3) and np.all(r["grad"][..., 2] == 0)      # theta: 0 under all-stick
+    nu, bound = mfmc.dgsm_bound(r["grad"], r["J"], [0.1, 1.0, 1.0])
+    assert np.allclose(r["nu"], nu, rtol=1e-12) and np.allclose(r["bound"], bound, rtol=1e-12, equal_nan=True)
+    assert np.all(r["bound"][2] == 0)

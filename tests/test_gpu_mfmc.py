@@ -71,3 +71,13 @@ def test_bootstrap_intervals_match_oracle(pdq):
     assert np.allclose(out["s_total_ci"], ci_t, rtol=1e-10, atol=1e-12)
     lo, hi = out["s_main_ci"][..., 0], out["s_main_ci"][..., 1]
     assert np.all(lo <= hi)
+
+
+def test_dgsm_bounds_match_oracle(pdq):
+    rng = np.random.default_rng(14)
+    X = rng.uniform(-np.pi, np.pi, (5000, 3))
+    g = np.stack([mfmc.ishigami_grad(X), 2 * mfmc.ishigami_grad(X)], 1)     # [S, 2 outputs, 3]
+    y = np.stack([mfmc.ishigami(X), 2 * mfmc.ishigami(X)], 1)
+    nu, bound = pdq.dgsm_bounds(torch.tensor(g, device="cuda"), torch.tensor(y, device="cuda"), [2 * np.pi] * 3)
+    nu_ref, b_ref = mfmc.dgsm_bound(g, y, [2 * np.pi] * 3)
+    assert np.allclose(nu, nu_ref, rtol=1e-12) and np.allclose(bound, b_ref, rtol=1e-12)

@@ -128,3 +128,18 @@ def test_mfmc_variance_reduction_matches_gamma():
     gamma = mfmc.gamma_two_model(rho, w[1] / w[0])
     assert 0.7 * gamma < ratio < 1.3 * gamma
     assert abs(est_mf.mean() - 3.5) < 4 * est_mf.std() / np.sqrt(reps)   # unbiased
+
+
+def test_dgsm_bound_linear_and_ishigami():
+    # f = x on [0, 1]: s^t = 1, nu = 1, Var = 1/12 -> bound = 12/pi^2 (>= 1)
+    rng = np.random.default_rng(13)
+    x = rng.random((200_000, 1))
+    nu, bound = mfmc.dgsm_bound(np.ones_like(x), x[:, 0], [1.0])
+    assert nu[0] == 1.0 and abs(bound[0] - 12 / np.pi ** 2) < 0.01
+    # Ishigami: every total index lies below its DGSM bound (Sobol'-Kucherenko inequality)
+    X = rng.uniform(-np.pi, np.pi, (400_000, 3))
+    nu, bound = mfmc.dgsm_bound(mfmc.ishigami_grad(X), mfmc.ishigami(X), [2 * np.pi] * 3)
+    _, _, _, st = mfmc.ishigami_indices()
+    assert np.all(st <= bound)
+    # analytic nu_2 = E[(a sin 2 x2)^2] = a^2 / 2
+    assert abs(nu[1] - 7.0 ** 2 / 2) < 0.1
