@@ -326,6 +326,7 @@ def run_ours(args):
             p1 = pdq.params_tensor([workloads.NOMINAL])
             pdq.seed_particles(f1, phys, s1, p1, w1["particle_seed"], 0.0, stream)
             c1 = pdq.step_cfg(w1["dt"], window_start=0, use_graph=True)
+            pdq.autotune(f1, phys, s1, p1, c1, stream)
             t1 = pdq.Tally(1, 1)
             ws1 = pdq.workspace(s1, c1)
             pdq.step_particles(f1, phys, s1, p1, c1, 20, t1, ws1, stream)
@@ -433,21 +434,31 @@ def run_adjoint(args):
     print(json.dumps(out), flush=True)
 
 
+def _finite(x):
+    """JSON-safe copy of nested lists: non-finite entries (classes with zero variance) become null."""
+    if isinstance(x, list):
+        return [_finite(v) for v in x]
+    return x if np.isfinite(x) else None
+
+
 def run_sobol(args):
     """End-to-end Sobol' study of V_dep+ (high-fidelity model only) through paper_2205_04979_gb300.uq."""
     import torch
-    from paper_2205_04979_gb300 import uq
+    from paper_2205_04979_gb300 import uq, pdq
     torch.cuda.set_device(0)
     m = args.samples or 64
     uq.sobol_deposition(4, 1024, 10)                          # warm-up (builds, first launches)
     r = uq.sobol_deposition(m, 4096, args.steps, n_boot=200)
+    rc = uq.sobol_deposition(m, 4096, args.steps, n_boot=200, mode=pdq.REBOUND, qoi="ce")
     out = {"metric": "Sobol' study: particle-steps/s of the pick-freeze runs", "value": r["particle_steps"] / (
                r["ms"] / 1e3), "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": "sobol: %d pick-freeze groups x 5 runs x 4096 particles, classes (0.1, 1, 10), "
                                   "xi in [0, 0.1], zeta in [0, 1], theta in [0, 1]" % m},
-           "mean_vdep": r["mean"].tolist(), "s_main": r["s_main"].tolist(), "s_total": r["s_total"].tolist(),
-           "s_main_ci": r["s_main_ci"].tolist()}
+           "mean_vdep": _finite(r["mean"].tolist()), "s_main": _finite(r["s_main"].tolist()), "s_total": _finite(r["s_total"].tolist()),
+           "s_main_ci": _finite(r["s_main_ci"].tolist()),
+           "ce_rebound": {"mean": _finite(rc["mean"].tolist()), "s_main": _finite(rc["s_main"].tolist()),
+                          "s_total": _finite(rc["s_total"].tolist())}}
     print(json.dumps(out), flush=True)
 
 

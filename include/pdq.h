@@ -184,7 +184,8 @@ typedef struct pdq_step_cfg {
     int32_t forces;       /* PDQ_F_* mask                                                    */
     int64_t window_start; /* first global step index counted in the tallies (t+ >= t_w)      */
     int32_t compact_every;/* compact deposited particles out every this many steps; 0 never */
-    int32_t block;        /* threads per CTA of the step kernel: 0 (auto), 64, 128 or 256    */
+    int32_t block;        /* threads per CTA of the step kernel: 0 (auto), 64, 128, 256      */
+                          /* (and 32 for PDQ_FP64)                                           */
     int32_t use_graph;    /* 1: capture the call as a CUDA graph (first call with a given      */
                           /*    argument set) and replay it afterwards; needs a created        */
                           /*    (non-default) stream; see pdq_release_graphs                   */
@@ -254,7 +255,8 @@ int pdq_step_particles_noalloc(const pdq_field* field, const pdq_phys* phys, pdq
                                pdq_tally* tally, pdq_stream_t stream);
 
 /* Autotuner: times one step of each candidate tile shape (threads per CTA 64,
- * 128, 256) and, for PDQ_MIXED, each pair-math variant on this state, and
+ * 128, 256, and 32 for PDQ_FP64) and, for PDQ_MIXED, each pair-math variant
+ * on this state, and
  * writes the fastest into cfg->block / cfg->variant.  The timed steps write
  * the scratch half and a scratch tally; the current half, state->cur,
  * state->step and the device step counter are restored.  With PDQ_MIXED and
@@ -289,6 +291,14 @@ int pdq_check_state(pdq_state* state, pdq_stream_t stream);
  * device arrays: vdep [S][C], mean [C], se [C] (mean/se may be NULL).       */
 int pdq_deposition_tally(const pdq_tally* tally, int32_t n_samples, int32_t n_classes, double dt,
                          double r_plus, double* vdep, double* mean, double* se, pdq_stream_t stream);
+
+/* Capture efficiency (Sec. 4.3): ce[k] = (4 L / D) (u* / U_b) vdep[k] for n
+ * device values, L = the field's periodic length, D = 2R, u* = Re_tau nu / R,
+ * U_b = phys->u_bulk.  With rebound-mode tallies (only sticking particles
+ * counted) vdep is V_dep+|stick and ce the capture efficiency; under all-stick
+ * it is the upper bound the paper states.  Errors: INVALID_ARG, CUDA.        */
+int pdq_capture_efficiency(const pdq_field* field, const pdq_phys* phys, const double* vdep, int64_t n, double* ce,
+                           pdq_stream_t stream);
 
 /* ---------------------------------------------------------------- adjoint
  * Batch description for the adjoint (it seeds and owns its own particle

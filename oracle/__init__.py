@@ -90,6 +90,7 @@ def lib():
             "orc_philox": (None, [_U32, _U32, _U32]),
             "orc_boot_indices": (None, [C.c_uint64, C.c_uint32, C.c_int, _I64, _I64]),
             "orc_num_threads": (C.c_int, []),
+            "orc_capture_factor": (C.c_double, [P, Fp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -300,3 +301,8 @@ def mean_profile(yplus, kappa=0.41, b_log=5.2):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def capture_factor(f, p=None):
+    p = p or phys()
+    return lib().orc_capture_factor(C.byref(p), C.byref(f))

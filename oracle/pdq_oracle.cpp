@@ -816,6 +816,12 @@ void orc_boot_indices(uint64_t seed, uint32_t b, int k, const int64_t* m, int64_
     }
 }
 
+// Capture efficiency factor of Sec. 4.3: CE = (4 L / D) (u* / U_b) V_dep+|stick.
+double orc_capture_factor(const OrcPhys* p, const OrcField* f) {
+    Units u = units(*p);
+    return 4.0 * (f->l_plus / (2.0 * f->r_plus)) * (u.ustar / p->u_bulk);
+}
+
 // Philox known-answer access for the pin test.
 void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
 

@@ -800,6 +800,7 @@ static int launch_step(const StepArgs& A, cudaStream_t s) {
 // variant: MIXED pair math, 0 = all packed f32x2, 1 = packed with scalar accumulation.
 static int dispatch_step(int prec, int NT, int variant, const StepArgs& A, cudaStream_t s) {
     if (prec == PDQ_FP64) {
+        if (NT == 32) return launch_step<PDQ_FP64, 32, 1, 0>(A, s);
         if (NT == 64) return launch_step<PDQ_FP64, 64, 1, 0>(A, s);
         if (NT == 128) return launch_step<PDQ_FP64, 128, 1, 0>(A, s);
         if (NT == 256) return launch_step<PDQ_FP64, 256, 1, 0>(A, s);
@@ -936,7 +937,7 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
         cfg->compact_every < 0 || cfg->variant < 0 || cfg->variant > 2)
         return PDQ_ERR_INVALID_ARG;
     const int NT = tile_threads(st, cfg), U = tile_ilp(st, cfg);
-    if (NT != 64 && NT != 128 && NT != 256) return PDQ_ERR_INVALID_ARG;
+    if (NT != 64 && NT != 128 && NT != 256 && !(NT == 32 && st->precision == PDQ_FP64)) return PDQ_ERR_INVALID_ARG;
     size_t items_bytes, need;
     workspace_layout(st, NT * U, &items_bytes, &need);
     if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return PDQ_ERR_WORKSPACE;
@@ -1095,9 +1096,10 @@ namespace pdq {
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
 static int ilog2(int64_t v) { int r = 0; while (v > 1) { v >>= 1; ++r; } return r; }
+static int min_tile(const pdq_state* st) { return st->precision == PDQ_FP64 ? 32 : 64 * tile_ilp(st); }
 static size_t autotune_scratch_offset(const pdq_state* st) {
     size_t ib, tot;
-    workspace_layout(st, 64 * tile_ilp(st), &ib, &tot);
+    workspace_layout(st, min_tile(st), &ib, &tot);
     return tot;
 }
 }  // namespace pdq
@@ -1139,12 +1141,13 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
         rc = make_step_const(field, phys, st, &K);
         if (rc) return rc;
         size_t ib, tot;
-        workspace_layout(st, 64 * tile_ilp(st), &ib, &tot);
+        workspace_layout(st, min_tile(st), &ib, &tot);
         int2* tag_scratch = (int2*)((char*)workspace + ib + align256(sizeof(int32_t) * (size_t)st->n_samples));
         rc = enqueue_sort_compact(st, tag_scratch, (float)(kZBins / K.L), s);
         if (rc) return rc;
     }
-    const int blocks[3] = {64, 128, 256};
+    const int blocks[4] = {64, 128, 256, 32};
+    const int n_blk = st->precision == PDQ_FP64 ? 4 : 3;    // 32-thread tiles: FP64 only
     const int n_var = st->precision == PDQ_MIXED ? 3 : 1;
     cudaEvent_t e0, e1;
     PDQ_CUDA(cudaEventCreate(&e0));
@@ -1153,7 +1156,7 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
     int best_b = tile_threads(st, nullptr), best_v = 0;
     const int cur0 = st->cur;
     const int64_t step0 = st->step;
-    for (int bi = 0; bi < 3 && rc == PDQ_OK; ++bi) {
+    for (int bi = 0; bi < n_blk && rc == PDQ_OK; ++bi) {
         for (int v = 0; v < n_var && rc == PDQ_OK; ++v) {
             pdq_step_cfg c = *cfg;
             c.block = blocks[bi];
@@ -1181,5 +1184,27 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
     cfg->variant = best_v;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = std::make_pair(best_b, best_v);
+    return PDQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Capture efficiency (Sec. 4.3): CE = (4 L / D) (u* / U_b) V_dep+|stick, where the
+// tallies of a rebound-mode run count only the particles that stick.
+// ---------------------------------------------------------------------------
+namespace pdq {
+__global__ void k_scale(const double* __restrict__ in, int64_t n, double f, double* __restrict__ out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = f * in[k];
+}
+}  // namespace pdq
+
+extern "C" int pdq_capture_efficiency(const pdq_field* field, const pdq_phys* phys, const double* vdep, int64_t n,
+                                      double* ce, pdq_stream_t stream) {
+    if (!field || !phys || !vdep || !ce || n < 0 || !(phys->u_bulk > 0)) return PDQ_ERR_INVALID_ARG;
+    const double ustar = phys->re_tau * phys->nu / phys->radius;
+    const double f = 4.0 * (field->desc.l_plus / (2.0 * field->desc.r_plus)) * (ustar / phys->u_bulk);
+    if (n == 0) return PDQ_OK;
+    k_scale<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(vdep, n, f, ce);
+    PDQ_CUDA(cudaGetLastError());
     return PDQ_OK;
 }

@@ -103,6 +103,7 @@ def lib():
                                           C.POINTER(StepCfg), C.c_int64, C.c_int32, C.c_double, C.c_double,
                                           C.c_int32, P, P, P, P, C.c_size_t, P]),
             "pdq_dgsm_bounds": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P]),
+            "pdq_capture_efficiency": (C.c_int, [P, C.POINTER(Phys), P, C.c_int64, P, P]),
             "pdq_mfmc_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                                   C.POINTER(C.c_size_t)]),
             "pdq_mfmc_sobol": (C.c_int, [C.c_int32, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
@@ -304,6 +305,15 @@ def compact(state, stream=None):
 
 def check_state(state, stream=None):
     return lib().pdq_check_state(C.byref(state.st), _stream(stream))
+
+
+def capture_efficiency(field, phys, vdep, stream=None):
+    """CE = (4 L / D)(u*/U_b) V_dep+ (Sec. 4.3) of a device float64 tensor."""
+    v = vdep.contiguous()
+    ce = torch.empty_like(v)
+    _check(lib().pdq_capture_efficiency(field.handle, C.byref(phys), _ptr(v), v.numel(), _ptr(ce), _stream(stream)),
+           "capture_efficiency")
+    return ce
 
 
 def deposition_tally(tally, dt, r_plus=180.0, stream=None):

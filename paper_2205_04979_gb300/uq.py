@@ -29,8 +29,9 @@ def pick_freeze(x, xp):
 
 def sobol_deposition(m, particles, steps, st_plus=(0.1, 1.0, 10.0), ranges=((0.0, 0.1), (0.0, 1.0), (0.0, 1.0)),
                      dt=0.05, t_window=10.0, mode=pdq.STICK, grid=(64, 32, 64), n_modes=64, seed=0, n_boot=200,
-                     precision=pdq.MIXED, stream=None):
-    """Main and total Sobol' indices of V_dep+ per class from m pick-freeze groups.
+                     precision=pdq.MIXED, qoi="vdep", stream=None):
+    """Main and total Sobol' indices of V_dep+ (qoi="vdep") or of the capture efficiency
+    (qoi="ce", Sec. 4.3; use mode=pdq.REBOUND) per class from m pick-freeze groups.
 
     Returns a dict with s_main / s_total [d, C], their bootstrap intervals, mean and variance of
     V_dep+ [C], the V_dep+ table [m, d+2, C] and the device time of the particle runs (ms).
@@ -59,6 +60,8 @@ def sobol_deposition(m, particles, steps, st_plus=(0.1, 1.0, 10.0), ranges=((0.0
         pdq.step_particles(field, phys, state, params, cfg, steps, tally, ws, stream)
         e1.record(stream)
         vdep, _, _ = pdq.deposition_tally(tally, dt, stream=stream)
+        if qoi == "ce":
+            vdep = pdq.capture_efficiency(field, phys, vdep, stream)
         e1.synchronize()
         y = vdep.reshape(m, d + 2, len(st_plus)).contiguous()
         out = pdq.mfmc_sobol([y], [m], [1.0], n_boot=n_boot, seed=seed + 2, stream=stream)

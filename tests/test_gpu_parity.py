@@ -323,3 +323,10 @@ def test_nonfinite_state_reported(pdq, fields, precision):
     _, vel, _ = st.current()
     off, cnt = st.offset.cpu().numpy(), st.count.cpu().numpy()
     assert torch.isfinite(vel[off[1]:off[1] + cnt[1]]).all()
+
+
+def test_capture_efficiency(pdq, fields):
+    f, of, _, _ = fields
+    v = torch.tensor([[1e-3, 2e-2], [0.0, 5e-1]], dtype=torch.float64, device="cuda")
+    ce = pdq.capture_efficiency(f, pdq.phys_default(), v)
+    assert torch.allclose(ce.cpu(), v.cpu() * oracle.capture_factor(of), rtol=1e-14, atol=0)

@@ -211,3 +211,10 @@ def test_rebound_model(orc):
     vn1 = 20.0
     assert orc.cor(st, 0.05, 0.5, vn1) == pytest.approx(np.sqrt(elastic - 0.05 * per_zeta) / vn1, rel=1e-12)
     assert orc.cor(st, 0.0, 0.0, 0.1) == 1.0
+
+
+def test_capture_efficiency_factor(orc):
+    # Sec. 4.3: CE = (4L/D)(u*/U_b) V_dep; for the paper's L = 10 D and U_b = 4 m/s, u* = 0.27 m/s
+    f = orc.field_desc(l_over_r=20.0)
+    assert orc.capture_factor(f) == pytest.approx(40 * 0.27 / 4.0, rel=1e-12)
+    assert orc.capture_factor(orc.field_desc()) == pytest.approx(8 * 0.27 / 4.0, rel=1e-12)
