@@ -338,7 +338,7 @@ def run_ours(args):
             x1.synchronize()
             fp64 = {"workload": "single_fp64 (1 sample x 1,000 particles, St+=10, 64x32x64 field, dt+=0.1)",
                     "value": (t1.n_alive.sum().item() - a1) / (x0.elapsed_time(x1) / 1e3),
-                    "unit": "particle-steps/s", "steps": w1["steps"]}
+                    "unit": "particle-steps/s", "steps": w1["steps"], "block": c1.block}
 
     ms_max, psteps_all = reduce_over_ranks(ms, psteps, world, "cuda")
     if rank != 0:

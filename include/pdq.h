@@ -201,7 +201,10 @@ typedef struct pdq_tally {
     int64_t* n_alive;
 } pdq_tally;
 
-/* Workspace bytes pdq_step_particles needs for this state and configuration. */
+/* Workspace bytes pdq_step_particles needs for this state and configuration
+ * (the work-item table; MIXED: the z-binning sort's scratch; PDQ_FP64 with few
+ * i-tiles: per-chunk partial pair sums, 24 B x particles x chunks, chunks <= 16,
+ * chosen from the capacity, the tile and the device's SM count).             */
 int pdq_step_workspace_size(const pdq_state* state, const pdq_step_cfg* cfg, size_t* bytes);
 
 /* Advance all samples n_steps steps (App. A.2).  One step of particle i:

@@ -208,6 +208,10 @@ struct StepArgs {
     const pdq_sample_params* params;
     const int2* items; int64_t* ctl;
     unsigned long long* n_dep; unsigned long long* n_alive;
+    // j-split (FP64 only; 1 otherwise): each i-tile's pair sum is cut into jsplit
+    // chunks, one work item each; partial sums go to part[(chunk*3 + k)*cap + g] and
+    // the last chunk to finish (tile_cnt) adds them in chunk order and does the update.
+    int jsplit; int64_t cap; double* part; int* tile_cnt;
 };
 
 // Local physics of one particle; returns its class, whether it was alive at the
@@ -348,7 +352,7 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
     __shared__ __align__(32) unsigned char smem_raw[NT * 32];
     __shared__ float2 s_zr[NT / 32];      // per-warp z range of the staged j-tile
     __shared__ float2 s_zi[NT / 32];      // per-warp z range of this CTA's i-particles
-    __shared__ int s_item;
+    __shared__ int s_item, s_last;
     __shared__ unsigned int s_alive[PDQ_MAX_CLASSES], s_dep[PDQ_MAX_CLASSES];
     const StepConst& K = A.K;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -369,7 +373,9 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
         const int s = it.x;
         const int64_t o = A.offset[s];
         const int64_t end = o + A.count[s];
-        const int64_t base = o + (int64_t)it.y * (NT * U);
+        const int JS = P == PDQ_FP64 ? A.jsplit : 1;
+        const int tile = it.y / JS, jc = it.y - tile * JS;
+        const int64_t base = o + (int64_t)tile * (NT * U);
         T xi[U], yi[U], zi[U], ax[U], ay[U], az[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -478,10 +484,16 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                 }
             } else {
                 T4* sj = reinterpret_cast<T4*>(smem_raw);
-                for (int64_t j0 = o; j0 < end; j0 += NT) {
+                int64_t jb = o, je = end;
+                if (JS > 1) {      // chunk jc of the sample's j range, a whole number of j-tiles long
+                    const int64_t ch = ((end - o + JS - 1) / JS + NT - 1) / NT * NT;
+                    jb = o + jc * ch;
+                    je = jb + ch < end ? jb + ch : end;
+                }
+                for (int64_t j0 = jb; j0 < je; j0 += NT) {
                     const int64_t j = j0 + tid;
                     T4 pj;
-                    if (j < end) pj = pos_in[j];
+                    if (j < je) pj = pos_in[j];
                     else { pj.x = (T)0; pj.y = (T)0; pj.z = (T)0; pj.w = (T)0; }
                     sj[tid] = pj;
                     __syncthreads();
@@ -494,6 +506,42 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                     }
                     __syncthreads();
                 }
+            }
+        }
+        if constexpr (P == PDQ_FP64) {
+            if (JS > 1) {
+                double* part = A.part;
+                const int64_t cap = A.cap;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t g = base + u * NT + tid;
+                    if (g < end) {
+                        part[(jc * 3 + 0) * cap + g] = ax[u];
+                        part[(jc * 3 + 1) * cap + g] = ay[u];
+                        part[(jc * 3 + 2) * cap + g] = az[u];
+                    }
+                }
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) s_last = atomicAdd(&A.tile_cnt[item / JS], 1) == JS - 1;
+                __syncthreads();
+                if (!s_last) continue;          // another chunk of this tile finishes it
+                __threadfence();
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t g = base + u * NT + tid;
+                    if (g < end) {
+                        double sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll 4
+                        for (int c = 0; c < JS; ++c) {
+                            sx += __ldcg(&part[(c * 3 + 0) * cap + g]);
+                            sy += __ldcg(&part[(c * 3 + 1) * cap + g]);
+                            sz += __ldcg(&part[(c * 3 + 2) * cap + g]);
+                        }
+                        ax[u] = sx; ay[u] = sy; az[u] = sz;
+                    }
+                }
+                if (tid == 0) A.tile_cnt[item / JS] = 0;
             }
         }
         const pdq_sample_params sp = A.params[s];
@@ -537,7 +585,8 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// Work items: samples ordered by live count (largest first), one item per i-tile.
+// Work items: samples ordered by live count (largest first), JS items per i-tile
+// (one per j-chunk; JS = 1 unless the FP64 j-split is on), item.y = tile * JS + chunk.
 // Single CTA of 1024 threads; order[] and items[] live in the caller workspace.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_buf, int& total) {
@@ -568,7 +617,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_buf, int& t
     return ex;
 }
 
-__global__ void __launch_bounds__(1024) k_build_items(const int32_t* __restrict__ count, int S, int TI,
+__global__ void __launch_bounds__(1024) k_build_items(const int32_t* __restrict__ count, int S, int TI, int JS,
                                                       int32_t* __restrict__ order, int2* __restrict__ items,
                                                       int64_t* __restrict__ ctl) {
     __shared__ int warp_buf[33];
@@ -591,7 +640,7 @@ __global__ void __launch_bounds__(1024) k_build_items(const int32_t* __restrict_
     for (int k0 = 0; k0 < S; k0 += blockDim.x) {
         const int k = k0 + tid;
         const int sidx = k < S ? order[k] : 0;
-        const int nt = k < S ? (count[sidx] + TI - 1) / TI : 0;
+        const int nt = k < S ? (count[sidx] + TI - 1) / TI * JS : 0;
         int total;
         const int pre = block_exclusive_scan(nt, warp_buf, total);
         for (int t = 0; t < nt; ++t) items[running + pre + t] = make_int2(sidx, t);
@@ -822,11 +871,37 @@ static int dispatch_step(int prec, int NT, int variant, const StepArgs& A, cudaS
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static void workspace_layout(const pdq_state* st, int TI, size_t* items_bytes, size_t* total) {
-    const int64_t max_items = st->capacity / TI + st->n_samples + 1;
-    *items_bytes = align256(sizeof(int2) * (size_t)max_items);
+// FP64 j-split factor.  The FP64 pipe is narrow and split over the four schedulers
+// of an SM, so the step wants about 1024 busy warps (~7 per SM) however few
+// particles there are; when the i-tiles alone give fewer, each tile's pair sum is
+// spread over JS work items (j-chunks of at least one j-tile).  MIXED never splits
+// (its batches have thousands of tiles).
+static int j_split(const pdq_state* st, int TI) {
+    if (st->precision != PDQ_FP64) return 1;
+    const int64_t cap = st->capacity > 0 ? st->capacity : 1;
+    const int64_t tile_warps = (cap + TI - 1) / TI * ((TI + 31) / 32);
+    int64_t js = (1024 + tile_warps - 1) / tile_warps;
+    const int64_t max_js = (cap + TI - 1) / TI;       // chunks are whole j-tiles of TI particles
+    if (js > max_js) js = max_js;
+    if (js > 64) js = 64;
+    return js < 1 ? 1 : (int)js;
+}
+
+// Workspace: items | order | MIXED: tag scratch of the z-binning sort;
+// FP64 with JS > 1: tile counters | partial sums [JS][3][capacity].
+static void workspace_layout(const pdq_state* st, int TI, size_t* items_bytes, size_t* total,
+                             size_t* cnt_off = nullptr, size_t* part_off = nullptr) {
+    const int JS = j_split(st, TI);
+    const int64_t max_tiles = st->capacity / TI + st->n_samples + 1;
+    *items_bytes = align256(sizeof(int2) * (size_t)max_tiles * JS);
     *total = *items_bytes + align256(sizeof(int32_t) * (size_t)st->n_samples);
     if (st->precision == PDQ_MIXED) *total += align256(sizeof(int2) * (size_t)(st->capacity > 0 ? st->capacity : 1));
+    if (JS > 1) {
+        if (cnt_off) *cnt_off = *total;
+        *total += align256(sizeof(int) * (size_t)max_tiles);
+        if (part_off) *part_off = *total;
+        *total += align256(sizeof(double) * 3 * (size_t)JS * (size_t)st->capacity);
+    }
 }
 
 // MIXED: z-binned compaction from the current half into the other half, tags
@@ -938,9 +1013,10 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
         return PDQ_ERR_INVALID_ARG;
     const int NT = tile_threads(st, cfg), U = tile_ilp(st, cfg);
     if (NT != 64 && NT != 128 && NT != 256 && !(NT == 32 && st->precision == PDQ_FP64)) return PDQ_ERR_INVALID_ARG;
-    size_t items_bytes, need;
-    workspace_layout(st, NT * U, &items_bytes, &need);
+    size_t items_bytes, need, cnt_off = 0, part_off = 0;
+    workspace_layout(st, NT * U, &items_bytes, &need, &cnt_off, &part_off);
     if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return PDQ_ERR_WORKSPACE;
+    const int JS = j_split(st, NT * U);
     if (n_steps == 0) return PDQ_OK;
     StepArgs A;
     memset(&A, 0, sizeof(A));
@@ -956,6 +1032,12 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
     A.tag = (const int2*)st->tag; A.offset = st->offset; A.count = st->count; A.params = params;
     A.items = (const int2*)workspace; A.ctl = st->ctl;
     A.n_dep = (unsigned long long*)tally->n_dep; A.n_alive = (unsigned long long*)tally->n_alive;
+    A.jsplit = JS;
+    A.cap = st->capacity;
+    if (JS > 1) {
+        A.tile_cnt = (int*)((char*)workspace + cnt_off);
+        A.part = (double*)((char*)workspace + part_off);
+    }
     int2* items = (int2*)workspace;
     int32_t* order = (int32_t*)((char*)workspace + items_bytes);
     cudaStream_t s = (cudaStream_t)stream;
@@ -972,7 +1054,12 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
         }
         int cur = st->cur;
         int64_t stepi = st->step;
-        k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, order, items, st->ctl);
+        if (JS > 1) {   // each tile's last chunk resets its counter, so zeroing once per call suffices
+            const cudaError_t e = cudaMemsetAsync(A.tile_cnt, 0, sizeof(int) * (size_t)(st->capacity / (NT * U) +
+                                                                                          st->n_samples + 1), s);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, JS, order, items, st->ctl);
         for (int64_t k = 0; k < n_steps; ++k) {
             A.pos_in = st->pos[cur]; A.vel_in = st->vel[cur]; A.xy_in = (const double2*)st->xy[cur];
             A.pos_out = st->pos[cur ^ 1]; A.vel_out = st->vel[cur ^ 1]; A.xy_out = (double2*)st->xy[cur ^ 1];
@@ -988,7 +1075,7 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
                 } else {
                     enqueue_compact(st, s);
                 }
-                k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, order, items, st->ctl);
+                k_build_items<<<1, 1024, 0, s>>>(st->count, st->n_samples, NT * U, JS, order, items, st->ctl);
             }
         }
         st->cur = cur;
@@ -1097,10 +1184,18 @@ static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
 static int ilog2(int64_t v) { int r = 0; while (v > 1) { v >>= 1; ++r; } return r; }
 static int min_tile(const pdq_state* st) { return st->precision == PDQ_FP64 ? 32 : 64 * tile_ilp(st); }
+// largest step workspace over the candidate tiles (the FP64 j-split makes it grow with the tile)
 static size_t autotune_scratch_offset(const pdq_state* st) {
-    size_t ib, tot;
-    workspace_layout(st, min_tile(st), &ib, &tot);
-    return tot;
+    const bool f64 = st->precision == PDQ_FP64;
+    const int tiles_f64[4] = {32, 64, 128, 256};
+    const int tiles_mixed[6] = {64 * 4, 128 * 4, 256 * 4, 64 * 8, 128 * 8, 256 * 8};
+    size_t best = 0;
+    for (int k = 0; k < (f64 ? 4 : 6); ++k) {
+        size_t ib, tot;
+        workspace_layout(st, f64 ? tiles_f64[k] : tiles_mixed[k], &ib, &tot);
+        if (tot > best) best = tot;
+    }
+    return best;
 }
 }  // namespace pdq
 

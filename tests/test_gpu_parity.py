@@ -154,13 +154,24 @@ def test_fp64_one_step_parity(pdq, fields):
     assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
 
 
-@pytest.mark.parametrize("block", [64, 128, 256])
+@pytest.mark.parametrize("block", [32, 64, 128, 256])
 def test_fp64_fifty_steps_parity(pdq, fields, block):
     counts = [1000, 333, 129]
     st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3, 50, {"window_start": 10}, block=block)
     assert _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 1e-9, 1e-9) > 0
     assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
     assert nd.sum() > 0          # particles did deposit
+
+
+@pytest.mark.parametrize("block", [32, 256])
+def test_fp64_single_sample_jsplit_parity(pdq, fields, block):
+    # one 1,000-particle sample fills few i-tiles, so each tile's pair sum is split over
+    # j-chunks (some empty at block 256) and summed by the last chunk to finish
+    counts = [1000]
+    prm = PRM3[:1]
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, [10.0], prm, 20, {"window_start": 5}, block=block)
+    assert _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 1e-10, 1e-10) > 0
+    assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
 
 
 def test_fp64_compaction_parity(pdq, fields):
