@@ -35,6 +35,7 @@ import workloads  # noqa: E402
 
 METRIC = "particle-steps/s, batched mixed vs plain FP64 on GB300 at ≤1e-3 rel V_dep error"
 FLOPS_PER_PAIR = 21          # 3 sub, 4 minimum image, 5 r^2, 3 r^-3 q, 6 accumulate (FMA = 2); + 1 rsqrt
+KSTEP_DRAM_BYTES = {0: 476.8e6, 2: 486.3e6}   # per k_step launch on 4,557,792 particles (ncu)
 SM_COUNT, FP32_LANES = 152, 128
 FP64_NOMINAL_TFLOPS = 1.25
 
@@ -366,15 +367,16 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (
                        sum(t.numel() * t.element_size() for t in state.current() if t is not None) / 1e9),
                    "parallelism": "samples sharded by rank" if world > 1 else "1 GPU",
-                   "tile": {"block": cfg.block, "i_per_thread": 4 if prec == pdq.MIXED else 1,
+                   "tile": {"block": cfg.block, "i_per_thread": (8 if cfg.variant == 2 else 4) if prec == pdq.MIXED else 1,
                             "variant": cfg.variant, "autotuned": args.block == 0 and not args.no_autotune}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
-                     # dram bytes read + written per launch from the ncu capture in
-                     # profiles/k_step_mixed_batched.md (476.8 MB for 4,557,792 particles,
-                     # z-binned kernel), scaled by the particle count of this launch
-                     "traffic": 476.8e6 / 4557792 * float(np.sum(counts)) if args.variant == 0 and prec == pdq.MIXED
-                     else None,
+                     # dram bytes read + written per launch from the ncu captures in
+                     # profiles/k_step_mixed_batched.md (4,557,792 particles, z-binned kernel:
+                     # 476.8 MB for pair variant 0, 486.3 MB for variant 2), scaled by the
+                     # particle count of this launch
+                     "traffic": KSTEP_DRAM_BYTES[cfg.variant] / 4557792 * float(np.sum(counts))
+                     if prec == pdq.MIXED and cfg.variant in KSTEP_DRAM_BYTES else None,
                      "kernel": "k_step (all-pairs Coulomb + local step)",
                      "note": "%s; %d flops per ordered pair; time per step from CUDA events over the timed "
                              "region" % (peak_note, FLOPS_PER_PAIR)},
