@@ -35,7 +35,7 @@ import workloads  # noqa: E402
 
 METRIC = "particle-steps/s, batched mixed vs plain FP64 on GB300 at ≤1e-3 rel V_dep error"
 FLOPS_PER_PAIR = 21          # 3 sub, 4 minimum image, 5 r^2, 3 r^-3 q, 6 accumulate (FMA = 2); + 1 rsqrt
-KSTEP_DRAM_BYTES = {0: 476.8e6, 2: 486.3e6}   # per k_step launch on 4,557,792 particles (ncu)
+KSTEP_DRAM_BYTES = {2: 495.4e6}   # per k_step launch on 4,557,792 particles (ncu, current kernel)
 SM_COUNT, FP32_LANES = 152, 128
 FP64_NOMINAL_TFLOPS = 1.25
 
@@ -371,10 +371,10 @@ def run_ours(args):
                             "variant": cfg.variant, "autotuned": args.block == 0 and not args.no_autotune}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
-                     # dram bytes read + written per launch from the ncu captures in
-                     # profiles/k_step_mixed_batched.md (4,557,792 particles, z-binned kernel:
-                     # 476.8 MB for pair variant 0, 486.3 MB for variant 2), scaled by the
-                     # particle count of this launch
+                     # dram bytes read + written per launch from the ncu capture in
+                     # profiles/k_step_mixed_batched.md (4,557,792 particles, z-binned kernel with
+                     # clamp-free tile pairs, pair variant 2: 495.4 MB), scaled by the particle
+                     # count of this launch; null for a variant without a capture of this kernel
                      "traffic": KSTEP_DRAM_BYTES[cfg.variant] / 4557792 * float(np.sum(counts))
                      if prec == pdq.MIXED and cfg.variant in KSTEP_DRAM_BYTES else None,
                      "kernel": "k_step (all-pairs Coulomb + local step)",

@@ -163,13 +163,17 @@ __device__ __forceinline__ void coulomb_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 y
 
 // Same pairs when no pair of the (i-tile, j-tile) combination needs the
 // periodic image: dz = (z_i - shift) - z_j directly (the shift is folded into zi).
+// CLAMP = false when every |dz| of the tile pair exceeds the contact distance, so
+// r^2 > c2 and the clamp could not change a result.
+template <bool CLAMP>
 __device__ __forceinline__ void coulomb_pair_x2_direct(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 qj, float c2,
                                                        f2& ax, f2& ay, f2& az) {
     const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj), dz = f2_sub(zi, zj);
     const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
     float ra, rb;
     f2_unpack(r2, ra, rb);
-    const f2 ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
+    if constexpr (CLAMP) { ra = fmaxf(ra, c2); rb = fmaxf(rb, c2); }
+    const f2 ri = f2_pack(rsqrt_ftz(ra), rsqrt_ftz(rb));
     const f2 s = f2_mul(f2_mul(ri, qj), f2_mul(ri, ri));
     ax = f2_fma(s, dx, ax);
     ay = f2_fma(s, dy, ay);
@@ -411,6 +415,7 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                 }
                 if (lane == 0) s_zi[tid >> 5] = make_float2(ilo, ihi);
                 const float Lf = (float)L, halfL = 0.5f * Lf;
+                const float dcz = sqrtf((float)c2) + 1e-3f;     // contact distance + rounding margin
                 for (int64_t j0 = o; j0 < end; j0 += NT) {
                     const int64_t j = j0 + tid;
                     const float4 pj = j < end ? ((const float4*)pos_in)[j] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -444,13 +449,27 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                         f2 Zs[H];
 #pragma unroll
                         for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+                        // z-separated tiles: every |dz| clears the contact distance by a margin far
+                        // above the rounding of dz, so the r^2 clamp is dropped for this tile pair
+                        const bool apart = (dlo - shift > dcz) || (dhi - shift < -dcz);
+                        if (apart) {
 #pragma unroll 4
-                        for (int k = 0; k < NT; ++k) {
-                            const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+                            for (int k = 0; k < NT; ++k) {
+                                const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
 #pragma unroll
-                            for (int h = 0; h < H; ++h)
-                                coulomb_pair_x2_direct(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, (float)c2, AX[h], AY[h],
-                                                       AZ[h]);
+                                for (int h = 0; h < H; ++h)
+                                    coulomb_pair_x2_direct<false>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, (float)c2,
+                                                                  AX[h], AY[h], AZ[h]);
+                            }
+                        } else {
+#pragma unroll 4
+                            for (int k = 0; k < NT; ++k) {
+                                const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+#pragma unroll
+                                for (int h = 0; h < H; ++h)
+                                    coulomb_pair_x2_direct<true>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, (float)c2,
+                                                                 AX[h], AY[h], AZ[h]);
+                            }
                         }
                     } else {
 #pragma unroll 4
@@ -846,7 +865,8 @@ static int launch_step(const StepArgs& A, cudaStream_t s) {
     return PDQ_OK;
 }
 
-// variant: MIXED pair math, 0 = all packed f32x2, 1 = packed with scalar accumulation.
+// variant: MIXED pair math, 0 = all packed f32x2, 1 = packed with scalar accumulation,
+// 2 = as 0 with 8 particles per thread.
 static int dispatch_step(int prec, int NT, int variant, const StepArgs& A, cudaStream_t s) {
     if (prec == PDQ_FP64) {
         if (NT == 32) return launch_step<PDQ_FP64, 32, 1, 0>(A, s);
