@@ -33,7 +33,8 @@ def build(force=False):
 class Phys(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "nu", "radius", "re_tau", "u_bulk", "rho_p", "rho_f", "eps0", "qmax_coef",
-        "hamaker0", "delta_min", "young", "delta_c", "sigma_y0", "g")]
+        "hamaker0", "delta_min", "young", "delta_c", "sigma_y0", "g",
+        "restitution", "tau_col_steps", "neg_charge_frac")]
 
 
 class Field(C.Structure):
@@ -51,6 +52,8 @@ class Cfg(C.Structure):
 
 F_DRAG, F_GRAV, F_COUL, F_IMAGE, F_VDW = 1, 2, 4, 8, 16
 F_ALL = 31
+F_COLLIDE, F_VDWPP = 32, 64          # particle-particle contact (soft-sphere collisions, Eq. vdw)
+F_CONTACT = F_COLLIDE | F_VDWPP
 STICK, REBOUND = 0, 1
 
 _D = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")

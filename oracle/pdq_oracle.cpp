@@ -108,13 +108,17 @@ template <class T> static inline T vmin(const T& a, const T& b) { return val(a) 
 // reproduces the printed tau_p+ = 0.1, 1, 10 for d_p = 1.6, 5, 16 um);
 // eps0 = 8.854e-12 (Eq. coulomb); q_max = 500 e (d_p/1um)^2 (Eq. q_max);
 // A0 = 1e-18 J (Sec. 2.1); delta_min = 1e-9 m (Sec. 2.2);
-// E = 70 GPa, delta_c = 0.165 nm, sigma_y0 = 200 MPa (Sec. 4.3).
+// E = 70 GPa, delta_c = 0.165 nm, sigma_y0 = 200 MPa (Sec. 4.3);
+// restitution e = 0.9 and contact time tau_col = 15 dt of the soft-sphere
+// collisions (App. A.2, collision force); neg_charge_frac = share of particles
+// seeded with a negative charge (0: the paper's like-signed charges).
 // ---------------------------------------------------------------------------
 extern "C" {
 
 struct OrcPhys {
     double nu, radius, re_tau, u_bulk, rho_p, rho_f, eps0, qmax_coef,
-           hamaker0, delta_min, young, delta_c, sigma_y0, g;
+           hamaker0, delta_min, young, delta_c, sigma_y0, g,
+           restitution, tau_col_steps, neg_charge_frac;
 };
 
 struct OrcField {
@@ -132,7 +136,8 @@ struct OrcCfg {
     double dt;                 // time step, wall units
     double gravity[3];         // gravity direction (unit vector or zero)
     int32_t mode;              // 0 = all-stick, 1 = rebound (Bons et al.)
-    int32_t forces;            // bit mask: 1 drag, 2 gravity, 4 coulomb, 8 image, 16 vdw
+    int32_t forces;            // bit mask: 1 drag, 2 gravity, 4 coulomb, 8 image, 16 vdw (wall),
+                               // 32 soft-sphere collisions, 64 particle-particle vdw
     int64_t window_start;      // first step index counted in the tallies
     double smooth_eps;         // > 0: smoothed wall indicator of this width (no removal)
     double stick_eps;          // smoothed rebound: width (m^2/s^2) of the sticking probability
@@ -143,6 +148,7 @@ void orc_phys_default(OrcPhys* p) {
     p->rho_p = 2650.0; p->rho_f = 1.2; p->eps0 = 8.854e-12; p->qmax_coef = 500.0 * 1.6e-19;
     p->hamaker0 = 1e-18; p->delta_min = 1e-9; p->young = 70e9; p->delta_c = 0.165e-9;
     p->sigma_y0 = 200e6; p->g = 9.81;
+    p->restitution = 0.9; p->tau_col_steps = 15.0; p->neg_charge_frac = 0.0;
 }
 
 }  // extern "C"
@@ -404,11 +410,17 @@ extern "C" int orc_seed(const OrcPhys* p, const OrcField* f, int n_classes, cons
             philox4x32_10(c0, key, a);
             int c = (int)(j % (uint32_t)n_classes);
             double lam = 1.0;
+            if (p->neg_charge_frac > 0) {
+                // sign of the charge: negative with probability neg_charge_frac (counter word 2)
+                uint32_t c2[4] = {j, 2u, 0u, 0u}, b[4];
+                philox4x32_10(c2, key, b);
+                if (u01(b[0]) < p->neg_charge_frac) lam = -1.0;
+            }
             if (charge_sigma > 0) {
                 uint32_t c1[4] = {j, 1u, 0u, 0u}, b[4];
                 philox4x32_10(c1, key, b);
                 double nrm = std::sqrt(-2.0 * std::log(u01(b[0]))) * std::cos(2.0 * M_PI * u01(b[1]));
-                lam = std::exp(charge_sigma * nrm);
+                lam *= std::exp(charge_sigma * nrm);
             }
             double rr = (f->r_plus - 0.5 * cp[c].d_plus) * std::sqrt(u01(a[0]));
             double th = 2.0 * M_PI * u01(a[1]);
@@ -451,7 +463,7 @@ template <class T> static T logistic(const T& a) {
     return e / (1.0 + e);
 }
 
-enum { F_DRAG = 1, F_GRAV = 2, F_COUL = 4, F_IMAGE = 8, F_VDW = 16 };
+enum { F_DRAG = 1, F_GRAV = 2, F_COUL = 4, F_IMAGE = 8, F_VDW = 16, F_COLLIDE = 32, F_VDWPP = 64 };
 
 struct SampleParams { double xi, zeta, theta; };
 
@@ -501,6 +513,67 @@ static void wall_and_body(const Run<T>& rn, const ClassProps& c, const T& x, con
     }
 }
 
+// Contact accelerations (wall units) added to a*[i].
+//  Collision: a linear spring-dashpot between the two surfaces (normal direction only: the
+//  paper names tangential collisions but prints no friction coefficient).  For a pair with
+//  effective mass m_ij = m_i m_j / (m_i + m_j) the relative normal motion obeys
+//  delta'' + H delta' + K delta = 0 while the spheres overlap by delta; choosing
+//  K = (pi^2 + ln^2 e) / tau_col^2 and H = -2 ln e / tau_col makes a contact last exactly
+//  tau_col and return the approach speed times e (the damped-oscillator solution).  Particle
+//  i receives m_ij / m_i of that relative acceleration, along n = (x_i - x_j) / r.
+//  Van der Waals: Eq. (vdw) for equal spheres, evaluated with the effective diameter
+//  2 d_i d_j / (d_i + d_j) (so that its contact limit is the Derjaguin force of the two
+//  unequal spheres), surface gap saturated at delta_min, zero beyond a quarter of that
+//  diameter (Sec. 2.2); attractive, along -n.  Overlapping spheres keep the saturated value
+//  (the modified cohesion model the paper cites is not printed).
+template <class T>
+static void contact_forces(const Run<T>& rn, int n, const T* x, const T* y, const T* z, const T* vx,
+                           const T* vy, const T* vz, const int32_t* alive, const int32_t* cls, const T& zeta,
+                           T* ax, T* ay, T* az) {
+    const OrcCfg& cfg = *rn.cfg;
+    const OrcPhys& p = *rn.p;
+    const double L = rn.f->l_plus, h = cfg.dt;
+    const double tc = p.tau_col_steps * cfg.dt;
+    const double le = std::log(p.restitution);
+    const double Kc = (M_PI * M_PI + le * le) / (tc * tc);
+    const double Hc = -2.0 * le / tc;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < n; ++i) {
+        if (!alive[i]) continue;
+        const ClassProps& ci = rn.cp[cls[i]];
+        for (int j = 0; j < n; ++j) {
+            if (j == i || !alive[j]) continue;
+            const ClassProps& cj = rn.cp[cls[j]];
+            // separation at the mid-step predicted positions x + v dt/2
+            T dx = x[i] - x[j] + 0.5 * h * (vx[i] - vx[j]);
+            T dy = y[i] - y[j] + 0.5 * h * (vy[i] - vy[j]);
+            T dz = z[i] - z[j] + 0.5 * h * (vz[i] - vz[j]);
+            dz = dz - L * std::rint(val(dz) / L);
+            T r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (val(r) <= 0) continue;
+            T nx = dx / r, ny = dy / r, nz = dz / r;
+            const double contact = 0.5 * (ci.d_plus + cj.d_plus);
+            if ((cfg.forces & F_COLLIDE) && val(r) < contact) {
+                T overlap = contact - r;
+                T vn = (vx[i] - vx[j]) * nx + (vy[i] - vy[j]) * ny + (vz[i] - vz[j]) * nz;
+                double mu = cj.mass / (ci.mass + cj.mass);   // m_ij / m_i
+                T a = mu * (Kc * overlap - Hc * vn);
+                ax[i] += a * nx; ay[i] += a * ny; az[i] += a * nz;
+            }
+            if (cfg.forces & F_VDWPP) {
+                double deff = 2.0 * ci.d * cj.d / (ci.d + cj.d);   // m
+                T gap = (r - contact) * rn.un.ell;                 // surface gap, m
+                if (val(gap) <= 0.25 * deff) {
+                    double g = std::max(val(gap), p.delta_min);
+                    double F = orc_vdw_pp(val(zeta) * p.hamaker0, deff, g);
+                    T a = T(F / ci.mass * rn.un.acc);
+                    ax[i] -= a * nx; ay[i] -= a * ny; az[i] -= a * nz;
+                }
+            }
+        }
+    }
+}
+
 // Advance one sample by one step.  State arrays are this sample's slice.
 // Returns per-class deposited count and alive-at-start count (STICK/REBOUND),
 // or the smoothed sums (smooth mode) through num/den.
@@ -545,6 +618,10 @@ static void step_sample(const Run<T>& rn, int n, T* x, T* y, T* z, T* vx, T* vy,
     } else {
         for (int i = 0; i < n; ++i) ax[i] = ay[i] = az[i] = T(0.0);
     }
+    // 1b) particle-particle contact (App. A.2): soft-sphere normal collisions and the van der
+    //     Waals attraction of Eq. (vdw), pair by pair over the live particles of the sample.
+    if (!smooth && (cfg.forces & (F_COLLIDE | F_VDWPP))) contact_forces(rn, n, x, y, z, vx, vy, vz, alive, cls,
+                                                                         zeta, ax.data(), ay.data(), az.data());
     // 2) local forces, integration, wall contact, tallies.
     for (int i = 0; i < n; ++i) {
         if (!smooth && !alive[i]) continue;
@@ -698,6 +775,7 @@ int orc_smooth_run(const OrcPhys* p, const OrcField* f, const double* grid, cons
                    const double* x0, const double* y0, const double* z0, const double* qhat /*charge per unit xi*/,
                    const int32_t* cls, int want_grad, double* J /*[S][C]*/, double* dJ /*[S][C][3]*/) {
     if (cfg->smooth_eps <= 0 || (cfg->mode == 1 && !(cfg->stick_eps > 0))) return -1;
+    if (cfg->forces & (F_COLLIDE | F_VDWPP)) return -1;     // contact forces: plain runs only
     for (int s = 0; s < n_samples; ++s) {
         int64_t o = offset[s];
         int n = (int)(offset[s + 1] - o);
