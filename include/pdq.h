@@ -73,6 +73,10 @@ typedef struct pdq_phys {
     double delta_c;   /* cohesion length delta_c, m                 */
     double sigma_y0;  /* yield stress at theta = 0, Pa              */
     double g;         /* gravitational acceleration, m/s^2          */
+    double restitution;     /* soft-sphere collisions: coefficient of restitution e (0.9, App. A.2) */
+    double tau_col_steps;   /* collision time tau_col in steps (15, App. A.2)                       */
+    double neg_charge_frac; /* seeding: share of particles with a negative charge (0: like-signed,   */
+                            /* as in the paper; the sign draws Philox counter word 2)               */
 } pdq_phys;
 void pdq_phys_default(pdq_phys* out);
 
@@ -175,7 +179,21 @@ int pdq_seed_particles(const pdq_field* field, const pdq_phys* phys, double char
 
 /* ------------------------------------------------------------------ step */
 enum { PDQ_STICK = 0, PDQ_REBOUND = 1 };
-enum { PDQ_F_DRAG = 1, PDQ_F_GRAVITY = 2, PDQ_F_COULOMB = 4, PDQ_F_IMAGE = 8, PDQ_F_VDW = 16, PDQ_F_ALL = 31 };
+/* PDQ_F_ALL: the forces of the batched model (drag, gravity, Coulomb, image
+ * charge, wall vdW).  PDQ_F_COLLIDE / PDQ_F_VDW_PP add particle-particle
+ * contact (App. A.2 collision force and Eq. vdw between particles):
+ *  - collisions: linear spring-dashpot along the line of centres while the
+ *    spheres overlap, K = (pi^2 + ln^2 e)/tau_col^2, H = -2 ln e / tau_col per
+ *    unit effective mass, so a contact lasts tau_col = tau_col_steps dt and
+ *    returns e times the approach speed; normal direction only;
+ *  - vdW: Eq. vdw with the effective diameter 2 d_i d_j / (d_i + d_j), gap
+ *    saturated at delta_min (also while overlapping), zero beyond a quarter of
+ *    that diameter, Hamaker constant zeta A0;
+ *  - both are evaluated at the mid-step predicted positions x + v dt/2.
+ * Contact runs use 4 particles per thread (MIXED), no FP64 j-split, and ignore
+ * cfg->variant; pdq_adjoint_run rejects them.                                */
+enum { PDQ_F_DRAG = 1, PDQ_F_GRAVITY = 2, PDQ_F_COULOMB = 4, PDQ_F_IMAGE = 8, PDQ_F_VDW = 16, PDQ_F_ALL = 31,
+       PDQ_F_COLLIDE = 32, PDQ_F_VDW_PP = 64, PDQ_F_CONTACT = 96 };
 
 typedef struct pdq_step_cfg {
     double dt;            /* time step dt+ > 0                                              */

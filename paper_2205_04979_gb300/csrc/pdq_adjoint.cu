@@ -58,7 +58,7 @@ struct AdjArgs {
     double* pbar;                       // [S][3]
     // seeding
     uint2 key;
-    double sigma;
+    double sigma, neg_frac;
 };
 
 __device__ __forceinline__ double logistic(double a) {
@@ -341,7 +341,8 @@ __global__ void k_adj_seed(const AdjArgs A) {
     const int64_t g = o + i;
     const int c = (int)((uint32_t)i % (uint32_t)A.C);
     double x, y, z, qh;
-    seed_particle(A.key, (uint32_t)i, A.sigma, A.K.R, A.K.L, A.K.cls[c].half_d, A.K.cls[c].qfac, x, y, z, qh);
+    seed_particle(A.key, (uint32_t)i, A.sigma, A.neg_frac, A.K.R, A.K.L, A.K.cls[c].half_d, A.K.cls[c].qfac, x, y,
+                  z, qh);
     A.out.x[g] = x; A.out.y[g] = y; A.out.z[g] = z;
     A.out.vx[g] = 0.0; A.out.vy[g] = 0.0; A.out.vz[g] = 0.0; A.out.w[g] = 1.0;
     ((int32_t*)A.cls)[g] = c;
@@ -750,6 +751,7 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
     A.mode = cfg->mode;
     A.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     A.sigma = charge_sigma;
+    A.neg_frac = phys->neg_charge_frac;
 
     const AdjLayout Ly = adj_layout(batch->capacity, A.S, A.C, n_steps, K);
     const int64_t N = Ly.N;

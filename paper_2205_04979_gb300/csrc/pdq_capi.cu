@@ -50,4 +50,7 @@ extern "C" void pdq_phys_default(pdq_phys* p) {
     p->delta_c = 0.165e-9;
     p->sigma_y0 = 200e6;
     p->g = 9.81;
+    p->restitution = 0.9;
+    p->tau_col_steps = 15.0;
+    p->neg_charge_frac = 0.0;
 }

@@ -64,6 +64,8 @@ struct ClassK {
     double coul;      // Coulomb: a+ = coul * q_i * sum_j q_j r_ij / |r_ij|^3 (q in q_unit, r in wall units)
     double vdw;       // vdW: a+ = zeta * vdw * d^6 / (delta^2 (2d+delta)^2 (d+delta)^3)  (SI lengths)
     double stick;     // 2 A_cont gamma_c / (m zeta) = pi d^2 A0 / (24 pi delta_c^2 m) * ... (m^2/s^2 per unit zeta)
+    double d3;        // d+^3 (mass ratios of the contact forces)
+    double vdw_pp;    // particle-particle vdW: a+ = zeta * vdw_pp * d^6 / (delta^2 (2d+delta)^2 (d+delta)^3), SI lengths
     float tau_f, inv_tau_f, d_plus_f, half_d_f, coul_f, img_f;
 };
 
@@ -82,6 +84,8 @@ struct StepConst {
     double elastic0;         // sigma_y0^2 / (rho_p E), m^2/s^2
     double grav[3];          // gravity acceleration vector, wall units
     double contact2;         // (largest class diameter)^2, wall units
+    double near;             // range of the contact forces: 1.25 x largest diameter, wall units
+    double col_k, col_h;     // collision spring and damping rates per unit effective mass (wall units)
     double inv_beta, tanh_beta;
     float Rf, Lf, invLf, contact2f, dtf, inv_beta_f, tanh_beta_f, gravf[3];
     const double4_32a* grid64;

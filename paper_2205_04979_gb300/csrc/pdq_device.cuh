@@ -153,13 +153,18 @@ __device__ __forceinline__ void coulomb_pair(double xi, double yi, double zi, co
 // Philox4x32-10 counter (j, 0, 0, 0) gives (r, theta, z) = ((R - d/2) sqrt(u0),
 // 2 pi u1, L u2); counter (j, 1, 0, 0) the lognormal charge factor
 // exp(sigma sqrt(-2 ln u0) cos(2 pi u1)).  qhat = charge per unit xi (units of q_unit).
-__device__ __forceinline__ void seed_particle(uint2 key, uint32_t j, double sigma, double R, double L, double half_d,
-                                              double qfac, double& x, double& y, double& z, double& qhat) {
+__device__ __forceinline__ void seed_particle(uint2 key, uint32_t j, double sigma, double neg_frac, double R, double L,
+                                              double half_d, double qfac, double& x, double& y, double& z,
+                                              double& qhat) {
     const uint4 a = philox4x32_10(make_uint4(j, 0u, 0u, 0u), key);
     double lam = 1.0;
+    if (neg_frac > 0.0) {      // negative charge with probability neg_frac (counter word 2)
+        const uint4 b = philox4x32_10(make_uint4(j, 2u, 0u, 0u), key);
+        if (unit_open(b.x) < neg_frac) lam = -1.0;
+    }
     if (sigma > 0.0) {
         const uint4 b = philox4x32_10(make_uint4(j, 1u, 0u, 0u), key);
-        lam = exp(sigma * sqrt(-2.0 * log(unit_open(b.x))) * cos(2.0 * kPi * unit_open(b.y)));
+        lam *= exp(sigma * sqrt(-2.0 * log(unit_open(b.x))) * cos(2.0 * kPi * unit_open(b.y)));
     }
     const double rr = (R - half_d) * sqrt(unit_open(a.x));
     double sth, cth;

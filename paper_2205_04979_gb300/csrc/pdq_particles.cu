@@ -54,6 +54,8 @@ int make_step_const(const pdq_field* f, const pdq_phys* p, const pdq_state* st, 
         k.coul = ke * p->q_unit * p->q_unit / (k.mass * ell * ell) * acc;
         k.vdw = p->hamaker0 / (3.0 * k.mass) * acc;          // 2 x (A0/6) / m
         k.stick = 2.0 * (0.25 * kPi * k.d_m * k.d_m) * p->hamaker0 / (24.0 * kPi * p->delta_c * p->delta_c) / k.mass;
+        k.d3 = k.d_plus * k.d_plus * k.d_plus;
+        k.vdw_pp = p->hamaker0 / (6.0 * k.mass) * acc;
         k.tau_f = (float)tau;
         k.inv_tau_f = (float)(1.0 / tau);
         k.d_plus_f = (float)k.d_plus;
@@ -70,6 +72,7 @@ int make_step_const(const pdq_field* f, const pdq_phys* p, const pdq_state* st, 
     K->ustar = ustar;
     K->elastic0 = p->sigma_y0 * p->sigma_y0 / (p->rho_p * p->young);
     K->contact2 = dmax * dmax;
+    K->near = 1.25 * dmax;      // (d_i + d_j)/2 + d_eff/4 <= 1.25 d_max
     K->inv_beta = 1.0 / f->desc.beta;
     K->tanh_beta = tanh(f->desc.beta);
     K->n_r = f->desc.n_r; K->n_th = f->desc.n_th; K->n_z = f->desc.n_z;
@@ -88,7 +91,7 @@ struct SeedArgs {
     const int64_t* offset; int32_t* count; int64_t* ctl;
     const pdq_sample_params* params;
     void* pos; void* vel; double2* xy; int2* tag;
-    int64_t capacity; int32_t S, C; double sigma; uint2 key;
+    int64_t capacity; int32_t S, C; double sigma, neg_frac; uint2 key;
     double R, L; double half_d[PDQ_MAX_CLASSES]; double qfac[PDQ_MAX_CLASSES];
 };
 
@@ -107,7 +110,7 @@ __global__ void k_seed(const SeedArgs A) {
     const uint32_t j = (uint32_t)(g - A.offset[s]);
     const int c = (int)(j % (uint32_t)A.C);
     double x, y, z, qhat;
-    seed_particle(A.key, j, A.sigma, A.R, A.L, A.half_d[c], A.qfac[c], x, y, z, qhat);
+    seed_particle(A.key, j, A.sigma, A.neg_frac, A.R, A.L, A.half_d[c], A.qfac[c], x, y, z, qhat);
     const double q = A.params[s].xi * qhat;
     if (P == PDQ_FP64) {
         ((double4_32a*)A.pos)[g] = make_double4_32a(x, y, z, q);
@@ -145,8 +148,10 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
 // Two ordered pairs (i_a, j), (i_b, j) of the Coulomb sum in packed form.
 // j = (xj, xj), (yj, yj), (zj, zj), (qj, qj); the minimum image in z uses
 // (dz/L + M) - M = rint(dz/L) with M = 1.5 * 2^23.
+// TRACK: also keep the smallest r^2 seen (contact-force runs look for near pairs).
+template <bool TRACK = false>
 __device__ __forceinline__ void coulomb_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 qj, f2 invL2, f2 M2,
-                                                f2 nM2, f2 nL2, float c2, f2& ax, f2& ay, f2& az) {
+                                                f2 nM2, f2 nL2, float c2, f2& ax, f2& ay, f2& az, float& mn) {
     const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj);
     f2 dz = f2_sub(zi, zj);
     const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
@@ -154,6 +159,7 @@ __device__ __forceinline__ void coulomb_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 y
     const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
     float ra, rb;
     f2_unpack(r2, ra, rb);
+    if constexpr (TRACK) mn = fminf(mn, fminf(ra, rb));
     const f2 ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
     const f2 s = f2_mul(f2_mul(ri, qj), f2_mul(ri, ri));
     ax = f2_fma(s, dx, ax);
@@ -165,13 +171,14 @@ __device__ __forceinline__ void coulomb_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 y
 // periodic image: dz = (z_i - shift) - z_j directly (the shift is folded into zi).
 // CLAMP = false when every |dz| of the tile pair exceeds the contact distance, so
 // r^2 > c2 and the clamp could not change a result.
-template <bool CLAMP>
+template <bool CLAMP, bool TRACK = false>
 __device__ __forceinline__ void coulomb_pair_x2_direct(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 qj, float c2,
-                                                       f2& ax, f2& ay, f2& az) {
+                                                       f2& ax, f2& ay, f2& az, float& mn) {
     const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj), dz = f2_sub(zi, zj);
     const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
     float ra, rb;
     f2_unpack(r2, ra, rb);
+    if constexpr (TRACK) mn = fminf(mn, fminf(ra, rb));
     if constexpr (CLAMP) { ra = fmaxf(ra, c2); rb = fmaxf(rb, c2); }
     const f2 ri = f2_pack(rsqrt_ftz(ra), rsqrt_ftz(rb));
     const f2 s = f2_mul(f2_mul(ri, qj), f2_mul(ri, ri));
@@ -223,7 +230,8 @@ struct StepArgs {
 template <int P>
 __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typename Real<P>::T acx,
                                              typename Real<P>::T acy, typename Real<P>::T acz,
-                                             const pdq_sample_params& sp, int& cls, bool& was_alive, bool& dep) {
+                                             const pdq_sample_params& sp, int& cls, bool& was_alive, bool& dep,
+                                             double cx = 0.0, double cy = 0.0, double cz = 0.0) {
     typedef typename Real<P>::T T;
     typedef typename Real<P>::T4 T4;
     const StepConst& K = A.K;
@@ -252,6 +260,7 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
     if (K.forces & PDQ_F_GRAVITY) {
         a[0] += (T)K.grav[0]; a[1] += (T)K.grav[1]; a[2] += (T)K.grav[2];
     }
+    if (K.forces & PDQ_F_CONTACT) { a[0] += (T)cx; a[1] += (T)cy; a[2] += (T)cz; }
     const double r = sqrt(x * x + y * y);
     if (r > 0.0 && (K.forces & (PDQ_F_IMAGE | PDQ_F_VDW))) {
         double aw = 0.0;   // toward the wall
@@ -347,6 +356,132 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
     }
 }
 
+// ---------------------------------------------------------------------------
+// Particle-particle contact (App. A.2 collision force and Eq. vdw between
+// particles) of particle gi with the particles [jb, je) of its sample, in FP64,
+// at the mid-step predicted positions x + v dt/2; accumulated into c[3].
+//  collision (overlap o = (d_i + d_j)/2 - r > 0): m_ij/m_i (K o - H v_n) n,
+//    K = (pi^2 + ln^2 e)/tau_col^2, H = -2 ln e/tau_col, v_n = (v_i - v_j).n,
+//    n = (x_i - x_j)/r, m_ij/m_i = d_j^3/(d_i^3 + d_j^3);
+//  vdW: -zeta A0 d^6 / (6 m_i g^2 (2d+g)^2 (d+g)^3) n with d = 2 d_i d_j/(d_i + d_j),
+//    g = max(surface gap, delta_min), zero when the gap exceeds d/4.
+// Rare: reached only for a thread whose tile pair holds a pair inside the
+// contact range, so it reads the j data straight from global memory.
+// ---------------------------------------------------------------------------
+template <int P>
+__device__ __noinline__ void contact_tile(const StepArgs& A, int64_t gi, int64_t jb, int64_t je, double zeta,
+                                          double c[3]) {
+    typedef typename Real<P>::T4 T4;
+    const StepConst& K = A.K;
+    const T4* pos = (const T4*)A.pos_in;
+    const T4* vel = (const T4*)A.vel_in;
+    const T4 vi = vel[gi];
+    if (!((double)vi.w > 0.5)) return;
+    const double h2 = 0.5 * K.dt;
+    const T4 pi4 = pos[gi];
+    double xi, yi;
+    if (P == PDQ_FP64) { xi = (double)pi4.x; yi = (double)pi4.y; }
+    else { const double2 xy = A.xy_in[gi]; xi = xy.x; yi = xy.y; }
+    const double zi = (double)pi4.z;
+    const ClassK& ci = K.cls[A.tag[gi].y];
+    const double near2 = K.near * K.near;
+    for (int64_t j = jb; j < je; ++j) {
+        if (j == gi) continue;
+        const T4 vj = vel[j];
+        if (!((double)vj.w > 0.5)) continue;
+        const T4 pj = pos[j];
+        double xj, yj;
+        if (P == PDQ_FP64) { xj = (double)pj.x; yj = (double)pj.y; }
+        else { const double2 xy = A.xy_in[j]; xj = xy.x; yj = xy.y; }
+        // separation of nearby particles first (exact by Sterbenz's lemma), then the drift
+        const double dx = (xi - xj) + h2 * ((double)vi.x - (double)vj.x);
+        const double dy = (yi - yj) + h2 * ((double)vi.y - (double)vj.y);
+        double dz = (zi - (double)pj.z) + h2 * ((double)vi.z - (double)vj.z);
+        dz -= K.L * rint(dz * K.invL);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < near2) || !(r2 > 0.0)) continue;
+        const double r = sqrt(r2), inv_r = 1.0 / r;
+        const double nx = dx * inv_r, ny = dy * inv_r, nz = dz * inv_r;
+        const ClassK& cj = K.cls[A.tag[j].y];
+        const double contact = ci.half_d + cj.half_d;
+        double a = 0.0;
+        if ((K.forces & PDQ_F_COLLIDE) && r < contact) {
+            const double vn = ((double)vi.x - (double)vj.x) * nx + ((double)vi.y - (double)vj.y) * ny +
+                              ((double)vi.z - (double)vj.z) * nz;
+            a += cj.d3 / (ci.d3 + cj.d3) * (K.col_k * (contact - r) - K.col_h * vn);
+        }
+        if (K.forces & PDQ_F_VDW_PP) {
+            const double d = 2.0 * ci.d_m * cj.d_m / (ci.d_m + cj.d_m);
+            const double gap = (r - contact) * K.ell;
+            if (gap <= 0.25 * d) {
+                const double gs = fmax(gap, K.delta_min);
+                const double d2 = d * d, e1 = 2.0 * d + gs, e2 = d + gs;
+                a -= zeta * ci.vdw_pp * d2 * d2 * d2 / (gs * gs * e1 * e1 * e2 * e2 * e2);
+            }
+        }
+        c[0] += a * nx; c[1] += a * ny; c[2] += a * nz;
+    }
+}
+
+// Largest speed of the staged j-tile, per warp (0 for padding and removed particles).
+template <int P>
+__device__ __forceinline__ void stage_speed(const StepArgs& A, int64_t j, int64_t end, int lane, int tid, float* s_v) {
+    typedef typename Real<P>::T4 T4;
+    float v = 0.f;
+    if (j < end) {
+        const T4 w = ((const T4*)A.vel_in)[j];
+        if ((double)w.w > 0.5)
+            v = (float)sqrt((double)w.x * (double)w.x + (double)w.y * (double)w.y + (double)w.z * (double)w.z);
+    }
+    for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, d));
+    if (lane == 0) s_v[tid >> 5] = v;
+}
+
+// Start-of-step separation beyond which no pair of the tile pair can come within the contact
+// range by mid-step: range + (largest i speed + largest j speed) dt/2, with margins for the
+// FP32 speeds and positions.
+__device__ __forceinline__ float near_bound(const StepConst& K, const float* s_vi, const float* s_vj, int nw) {
+    float vi = 0.f, vj = 0.f;
+    for (int w = 0; w < nw; ++w) { vi = fmaxf(vi, s_vi[w]); vj = fmaxf(vj, s_vj[w]); }
+    return (float)K.near + 0.5f * (float)K.dt * (vi + vj) * 1.001f + 1e-3f;
+}
+
+// Contact accelerations of this thread's particles from the j-tile starting at j0, added to
+// its own slots of s_ct[3][U][NT].
+template <int P, int NT, int U>
+__device__ __forceinline__ void contact_rows(const StepArgs& A, int64_t base, int64_t end, int64_t j0, double zeta,
+                                             double* s_ct) {
+    const int tid = threadIdx.x;
+    const int64_t je = j0 + NT < end ? j0 + NT : end;
+    for (int u = 0; u < U; ++u) {
+        const int64_t g = base + u * NT + tid;
+        if (g >= end) continue;
+        double c3[3] = {0.0, 0.0, 0.0};
+        contact_tile<P>(A, g, j0, je, zeta, c3);
+        s_ct[(0 * U + u) * NT + tid] += c3[0];
+        s_ct[(1 * U + u) * NT + tid] += c3[1];
+        s_ct[(2 * U + u) * NT + tid] += c3[2];
+    }
+}
+
+// FP64 pair of the contact-force variant: the Coulomb pair plus the smallest r^2 seen.
+__device__ __forceinline__ void coulomb_pair_track(double xi, double yi, double zi, const double4_32a pj, double L,
+                                                   double invL, double c2, double& ax, double& ay, double& az,
+                                                   double& mn) {
+    const double dx = xi - pj.x, dy = yi - pj.y;
+    double dz = zi - pj.z;
+    const double t = __dadd_rn(__fma_rn(dz, invL, 6755399441055744.0), -6755399441055744.0);
+    dz = __fma_rn(-L, t, dz);
+    const double r2u = __fma_rn(dx, dx, __fma_rn(dy, dy, dz * dz));
+    mn = fmin(mn, r2u);
+    const double r2 = fmax(r2u, c2);
+    const double ri = rsqrt(r2);
+    const double s = pj.w * ri * (ri * ri);
+    ax = __fma_rn(s, dx, ax);
+    ay = __fma_rn(s, dy, ay);
+    az = __fma_rn(s, dz, az);
+}
+
 template <int P, int NT, int U, int V>
 __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
     typedef typename Real<P>::T T;
@@ -358,6 +493,11 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
     __shared__ float2 s_zi[NT / 32];      // per-warp z range of this CTA's i-particles
     __shared__ int s_item, s_last;
     __shared__ unsigned int s_alive[PDQ_MAX_CLASSES], s_dep[PDQ_MAX_CLASSES];
+    // contact-force variant (V == 4): per-particle contact accelerations of the item, and the
+    // per-warp largest speeds of the i-particles and of the staged j-tile (near-pair bound)
+    constexpr bool CT = V == 4;
+    __shared__ double s_ct[CT ? 3 * NT * U : 1];
+    __shared__ float s_vi[NT / 32], s_vj[NT / 32];
     const StepConst& K = A.K;
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t step = A.ctl[CTL_STEP];
@@ -388,7 +528,26 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
             else { xi[u] = (T)0; yi[u] = (T)0; zi[u] = (T)0; }
             ax[u] = ay[u] = az[u] = (T)0;
         }
-        if (K.forces & PDQ_F_COULOMB) {
+        double zeta = 0.0;
+        if constexpr (CT) {
+            zeta = A.params[s].zeta;
+            float vmax = 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t g = base + u * NT + tid;
+                s_ct[(0 * U + u) * NT + tid] = 0.0;
+                s_ct[(1 * U + u) * NT + tid] = 0.0;
+                s_ct[(2 * U + u) * NT + tid] = 0.0;
+                if (g < end) {
+                    const T4 v = ((const T4*)A.vel_in)[g];
+                    if ((float)v.w > 0.5f)
+                        vmax = fmaxf(vmax, (float)sqrt((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z));
+                }
+            }
+            for (int d = 16; d > 0; d >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, d));
+            if (lane == 0) s_vi[tid >> 5] = vmax;
+        }
+        if ((K.forces & PDQ_F_COULOMB) || CT) {
             if constexpr (P == PDQ_MIXED) {
                 static_assert(U % 2 == 0, "packed pairs need an even number of i-particles per thread");
                 constexpr int H = U / 2;
@@ -425,6 +584,7 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                         jhi = fmaxf(jhi, __shfl_xor_sync(0xffffffffu, jhi, d));
                     }
                     if (lane == 0) s_zr[tid >> 5] = make_float2(jlo, jhi);
+                    if constexpr (CT) stage_speed<P>(A, j, end, lane, tid, s_vj);
                     sj2[2 * tid] = make_ulonglong2(f2_pack(pj.x, pj.x), f2_pack(pj.y, pj.y));
                     sj2[2 * tid + 1] = make_ulonglong2(f2_pack(pj.z, pj.z), f2_pack(pj.w, pj.w));
                     __syncthreads();
@@ -438,8 +598,13 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                         blo = fminf(blo, s_zr[w].x); bhi = fmaxf(bhi, s_zr[w].y);
                     }
                     const float dlo = alo - bhi, dhi = ahi - blo;
+                    // contact variant: pairs farther apart than thr cannot reach the contact range by
+                    // mid-step (thr adds the largest relative drift over half a step)
+                    float thr = dcz;
+                    if constexpr (CT) thr = fmaxf(dcz, near_bound(K, s_vi, s_vj, NT / 32));
+                    float mn = INFINITY;
                     float shift = 0.f;
-                    bool direct = V == 0;
+                    bool direct = V == 0 || V == 4;
                     if (dlo > -halfL && dhi < halfL) shift = 0.f;
                     else if (dlo > halfL && dhi < 3.f * halfL) shift = Lf;
                     else if (dhi < -halfL && dlo > -3.f * halfL) shift = -Lf;
@@ -451,7 +616,7 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                         for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
                         // z-separated tiles: every |dz| clears the contact distance by a margin far
                         // above the rounding of dz, so the r^2 clamp is dropped for this tile pair
-                        const bool apart = (dlo - shift > dcz) || (dhi - shift < -dcz);
+                        const bool apart = (dlo - shift > thr) || (dhi - shift < -thr);
                         if (apart) {
 #pragma unroll 4
                             for (int k = 0; k < NT; ++k) {
@@ -459,7 +624,7 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
 #pragma unroll
                                 for (int h = 0; h < H; ++h)
                                     coulomb_pair_x2_direct<false>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, (float)c2,
-                                                                  AX[h], AY[h], AZ[h]);
+                                                                  AX[h], AY[h], AZ[h], mn);
                             }
                         } else {
 #pragma unroll 4
@@ -467,8 +632,8 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                                 const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
 #pragma unroll
                                 for (int h = 0; h < H; ++h)
-                                    coulomb_pair_x2_direct<true>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, (float)c2,
-                                                                 AX[h], AY[h], AZ[h]);
+                                    coulomb_pair_x2_direct<true, CT>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y,
+                                                                     (float)c2, AX[h], AY[h], AZ[h], mn);
                             }
                         }
                     } else {
@@ -484,11 +649,14 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                                     coulomb_pair_x2s(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2,
                                                      (float)c2, sx, sy, sz);
                                 } else {
-                                    coulomb_pair_x2(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2,
-                                                    (float)c2, AX[h], AY[h], AZ[h]);
+                                    coulomb_pair_x2<CT>(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2,
+                                                        (float)c2, AX[h], AY[h], AZ[h], mn);
                                 }
                             }
                         }
+                    }
+                    if constexpr (CT) {
+                        if (mn < thr * thr) contact_rows<P, NT, U>(A, base, end, j0, zeta, s_ct);
                     }
                     __syncthreads();
                 }
@@ -515,13 +683,27 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                     if (j < je) pj = pos_in[j];
                     else { pj.x = (T)0; pj.y = (T)0; pj.z = (T)0; pj.w = (T)0; }
                     sj[tid] = pj;
+                    if constexpr (CT) stage_speed<P>(A, j, je, lane, tid, s_vj);
                     __syncthreads();
+                    if constexpr (CT) {
+                        const double thr = (double)near_bound(K, s_vi, s_vj, NT / 32);
+                        double mn = INFINITY;
 #pragma unroll 8
-                    for (int k = 0; k < NT; ++k) {
-                        const T4 p = sj[k];
+                        for (int k = 0; k < NT; ++k) {
+                            const T4 p = sj[k];
 #pragma unroll
-                        for (int u = 0; u < U; ++u)
-                            coulomb_pair(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u]);
+                            for (int u = 0; u < U; ++u)
+                                coulomb_pair_track(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u], mn);
+                        }
+                        if (mn < thr * thr) contact_rows<P, NT, U>(A, base, end, j0, zeta, s_ct);
+                    } else {
+#pragma unroll 8
+                        for (int k = 0; k < NT; ++k) {
+                            const T4 p = sj[k];
+#pragma unroll
+                            for (int u = 0; u < U; ++u)
+                                coulomb_pair(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u]);
+                        }
                     }
                     __syncthreads();
                 }
@@ -569,7 +751,13 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
             const int64_t g = base + u * NT + tid;
             int cls = -1;
             bool was_alive = false, dep = false;
-            if (g < end) local_update<P>(A, g, ax[u], ay[u], az[u], sp, cls, was_alive, dep);
+            if (g < end) {
+                if constexpr (CT)
+                    local_update<P>(A, g, ax[u], ay[u], az[u], sp, cls, was_alive, dep, s_ct[(0 * U + u) * NT + tid],
+                                    s_ct[(1 * U + u) * NT + tid], s_ct[(2 * U + u) * NT + tid]);
+                else
+                    local_update<P>(A, g, ax[u], ay[u], az[u], sp, cls, was_alive, dep);
+            }
             if (counted) {
                 const unsigned live = __ballot_sync(0xffffffffu, was_alive);
                 if (live) {
@@ -840,6 +1028,7 @@ static int tile_threads(const pdq_state* st, const pdq_step_cfg* cfg) {
 // particles per thread: FP64 1; MIXED 4 (two packed pairs), 8 for pair variant 2
 static int tile_ilp(const pdq_state* st, const pdq_step_cfg* cfg = nullptr) {
     if (st->precision == PDQ_FP64) return 1;
+    if (cfg && (cfg->forces & PDQ_F_CONTACT)) return 4;      // contact runs: variant 0 layout
     return (cfg && cfg->variant == 2) ? 8 : 4;
 }
 
@@ -867,7 +1056,21 @@ static int launch_step(const StepArgs& A, cudaStream_t s) {
 
 // variant: MIXED pair math, 0 = all packed f32x2, 1 = packed with scalar accumulation,
 // 2 = as 0 with 8 particles per thread.
-static int dispatch_step(int prec, int NT, int variant, const StepArgs& A, cudaStream_t s) {
+// contact: the particle-particle contact variant (V = 4), whatever the variant.
+static int dispatch_step(int prec, int NT, int variant, bool contact, const StepArgs& A, cudaStream_t s) {
+    if (contact) {
+        if (prec == PDQ_FP64) {
+            if (NT == 32) return launch_step<PDQ_FP64, 32, 1, 4>(A, s);
+            if (NT == 64) return launch_step<PDQ_FP64, 64, 1, 4>(A, s);
+            if (NT == 128) return launch_step<PDQ_FP64, 128, 1, 4>(A, s);
+            if (NT == 256) return launch_step<PDQ_FP64, 256, 1, 4>(A, s);
+        } else {
+            if (NT == 64) return launch_step<PDQ_MIXED, 64, 4, 4>(A, s);
+            if (NT == 128) return launch_step<PDQ_MIXED, 128, 4, 4>(A, s);
+            if (NT == 256) return launch_step<PDQ_MIXED, 256, 4, 4>(A, s);
+        }
+        return PDQ_ERR_INVALID_ARG;
+    }
     if (prec == PDQ_FP64) {
         if (NT == 32) return launch_step<PDQ_FP64, 32, 1, 0>(A, s);
         if (NT == 64) return launch_step<PDQ_FP64, 64, 1, 0>(A, s);
@@ -895,9 +1098,9 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // of an SM, so the step wants about 1024 busy warps (~7 per SM) however few
 // particles there are; when the i-tiles alone give fewer, each tile's pair sum is
 // spread over JS work items (j-chunks of at least one j-tile).  MIXED never splits
-// (its batches have thousands of tiles).
-static int j_split(const pdq_state* st, int TI) {
-    if (st->precision != PDQ_FP64) return 1;
+// (its batches have thousands of tiles); neither do contact runs.
+static int j_split(const pdq_state* st, int TI, bool contact = false) {
+    if (st->precision != PDQ_FP64 || contact) return 1;
     const int64_t cap = st->capacity > 0 ? st->capacity : 1;
     const int64_t tile_warps = (cap + TI - 1) / TI * ((TI + 31) / 32);
     int64_t js = (1024 + tile_warps - 1) / tile_warps;
@@ -910,8 +1113,8 @@ static int j_split(const pdq_state* st, int TI) {
 // Workspace: items | order | MIXED: tag scratch of the z-binning sort;
 // FP64 with JS > 1: tile counters | partial sums [JS][3][capacity].
 static void workspace_layout(const pdq_state* st, int TI, size_t* items_bytes, size_t* total,
-                             size_t* cnt_off = nullptr, size_t* part_off = nullptr) {
-    const int JS = j_split(st, TI);
+                             size_t* cnt_off = nullptr, size_t* part_off = nullptr, bool contact = false) {
+    const int JS = j_split(st, TI, contact);
     const int64_t max_tiles = st->capacity / TI + st->n_samples + 1;
     *items_bytes = align256(sizeof(int2) * (size_t)max_tiles * JS);
     *total = *items_bytes + align256(sizeof(int32_t) * (size_t)st->n_samples);
@@ -989,6 +1192,7 @@ extern "C" int pdq_seed_particles(const pdq_field* field, const pdq_phys* phys, 
     A.offset = st->offset; A.count = st->count; A.ctl = st->ctl; A.params = params;
     A.pos = st->pos[0]; A.vel = st->vel[0]; A.xy = (double2*)st->xy[0]; A.tag = (int2*)st->tag;
     A.capacity = st->capacity; A.S = st->n_samples; A.C = st->n_classes; A.sigma = charge_sigma;
+    A.neg_frac = phys->neg_charge_frac;
     A.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     A.R = K.R; A.L = K.L;
     for (int c = 0; c < st->n_classes; ++c) { A.half_d[c] = K.cls[c].half_d; A.qfac[c] = K.cls[c].qfac; }
@@ -1008,7 +1212,8 @@ extern "C" int pdq_step_workspace_size(const pdq_state* st, const pdq_step_cfg* 
     int rc = validate_state(st);
     if (rc) return rc;
     size_t ib, tot;
-    workspace_layout(st, tile_threads(st, cfg) * tile_ilp(st, cfg), &ib, &tot);
+    workspace_layout(st, tile_threads(st, cfg) * tile_ilp(st, cfg), &ib, &tot, nullptr, nullptr,
+                     cfg && (cfg->forces & PDQ_F_CONTACT));
     *bytes = tot;
     return PDQ_OK;
 }
@@ -1028,15 +1233,18 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
         return PDQ_ERR_INVALID_ARG;
     int rc = validate_state(st);
     if (rc) return rc;
-    if (!(cfg->dt > 0) || (cfg->mode != PDQ_STICK && cfg->mode != PDQ_REBOUND) || (cfg->forces & ~PDQ_F_ALL) ||
-        cfg->compact_every < 0 || cfg->variant < 0 || cfg->variant > 2)
+    if (!(cfg->dt > 0) || (cfg->mode != PDQ_STICK && cfg->mode != PDQ_REBOUND) ||
+        (cfg->forces & ~(PDQ_F_ALL | PDQ_F_CONTACT)) || cfg->compact_every < 0 || cfg->variant < 0 || cfg->variant > 2)
+        return PDQ_ERR_INVALID_ARG;
+    const bool contact = (cfg->forces & PDQ_F_CONTACT) != 0;
+    if (contact && (!(phys->restitution > 0.0 && phys->restitution <= 1.0) || !(phys->tau_col_steps > 0.0)))
         return PDQ_ERR_INVALID_ARG;
     const int NT = tile_threads(st, cfg), U = tile_ilp(st, cfg);
     if (NT != 64 && NT != 128 && NT != 256 && !(NT == 32 && st->precision == PDQ_FP64)) return PDQ_ERR_INVALID_ARG;
     size_t items_bytes, need, cnt_off = 0, part_off = 0;
-    workspace_layout(st, NT * U, &items_bytes, &need, &cnt_off, &part_off);
+    workspace_layout(st, NT * U, &items_bytes, &need, &cnt_off, &part_off, contact);
     if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return PDQ_ERR_WORKSPACE;
-    const int JS = j_split(st, NT * U);
+    const int JS = j_split(st, NT * U, contact);
     if (n_steps == 0) return PDQ_OK;
     StepArgs A;
     memset(&A, 0, sizeof(A));
@@ -1049,6 +1257,11 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
     const double gplus = phys->g * phys->nu / pow(phys->re_tau * phys->nu / phys->radius, 3);
     for (int k = 0; k < 3; ++k) { A.K.grav[k] = gplus * cfg->gravity[k]; A.K.gravf[k] = (float)A.K.grav[k]; }
     A.K.dtf = (float)cfg->dt;
+    if (contact) {   // K = (pi^2 + ln^2 e)/tau_col^2, H = -2 ln e/tau_col (damped oscillator, App. A.2)
+        const double tc = phys->tau_col_steps * cfg->dt, le = log(phys->restitution);
+        A.K.col_k = (kPi * kPi + le * le) / (tc * tc);
+        A.K.col_h = -2.0 * le / tc;
+    }
     A.tag = (const int2*)st->tag; A.offset = st->offset; A.count = st->count; A.params = params;
     A.items = (const int2*)workspace; A.ctl = st->ctl;
     A.n_dep = (unsigned long long*)tally->n_dep; A.n_alive = (unsigned long long*)tally->n_alive;
@@ -1083,7 +1296,7 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
         for (int64_t k = 0; k < n_steps; ++k) {
             A.pos_in = st->pos[cur]; A.vel_in = st->vel[cur]; A.xy_in = (const double2*)st->xy[cur];
             A.pos_out = st->pos[cur ^ 1]; A.vel_out = st->vel[cur ^ 1]; A.xy_out = (double2*)st->xy[cur ^ 1];
-            dispatch_step(st->precision, NT, cfg->variant, A, s);
+            dispatch_step(st->precision, NT, cfg->variant, contact, A, s);
             cur ^= 1;
             ++stepi;
             if (cfg->compact_every > 0 && stepi % cfg->compact_every == 0 && k + 1 < n_steps) {
@@ -1263,7 +1476,7 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
     }
     const int blocks[4] = {64, 128, 256, 32};
     const int n_blk = st->precision == PDQ_FP64 ? 4 : 3;    // 32-thread tiles: FP64 only
-    const int n_var = st->precision == PDQ_MIXED ? 3 : 1;
+    const int n_var = st->precision == PDQ_MIXED && !(cfg->forces & PDQ_F_CONTACT) ? 3 : 1;
     cudaEvent_t e0, e1;
     PDQ_CUDA(cudaEventCreate(&e0));
     PDQ_CUDA(cudaEventCreate(&e1));

@@ -17,6 +17,8 @@ PDQ_OK = 0
 FP64, MIXED = 0, 1
 STICK, REBOUND = 0, 1
 F_DRAG, F_GRAVITY, F_COULOMB, F_IMAGE, F_VDW, F_ALL = 1, 2, 4, 8, 16, 31
+F_COLLIDE, F_VDW_PP = 32, 64        # particle-particle contact (collisions, Eq. vdw between particles)
+F_CONTACT = F_COLLIDE | F_VDW_PP
 MAX_CLASSES = 16
 
 
@@ -29,7 +31,7 @@ class PdqError(RuntimeError):
 class Phys(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "nu", "radius", "re_tau", "u_bulk", "rho_p", "rho_f", "eps0", "q_unit", "hamaker0", "delta_min",
-        "young", "delta_c", "sigma_y0", "g")]
+        "young", "delta_c", "sigma_y0", "g", "restitution", "tau_col_steps", "neg_charge_frac")]
 
 
 class FieldDesc(C.Structure):
