@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--variant", type=int, default=0, help="MIXED pair-math variant")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-vdep-check", action="store_true")
+    ap.add_argument("--contact", action="store_true",
+                    help="half the charges negative, soft-sphere collisions and particle-particle vdW on")
     return ap.parse_args()
 
 
@@ -236,6 +238,8 @@ def run_ours(args):
     params, counts = rank_workload(args.workload, rank, world, args.samples)
     prec = pdq.MIXED if w["precision"] == "mixed" else pdq.FP64
     phys = pdq.phys_default()
+    if args.contact:
+        phys.neg_charge_frac = 0.5
     desc = pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -244,7 +248,7 @@ def run_ours(args):
         prm = pdq.params_tensor(params)
         pdq.seed_particles(field, phys, state, prm, w["particle_seed"], w.get("charge_sigma", 0.0), stream)
         cfg = pdq.step_cfg(w["dt"], window_start=0, compact_every=w.get("compact_every", 0), block=args.block,
-                           variant=args.variant)
+                           variant=args.variant, forces=pdq.F_ALL | (pdq.F_CONTACT if args.contact else 0))
         tally = pdq.Tally(len(counts), len(w["st_plus"]))
         if args.block == 0 and args.variant == 0 and not args.no_autotune:
             pdq.autotune(field, phys, state, prm, cfg, stream)      # project autotuner picks block / variant
@@ -363,7 +367,9 @@ def run_ours(args):
                                "%dx%dx%d field, dt+=%g, compaction every %d steps, %s" % (
                                    args.workload, len(counts), int(np.min(counts)), int(np.max(counts)),
                                    int(np.sum(counts)), len(w["st_plus"]), *w["grid"], w["dt"],
-                                   w.get("compact_every", 0), w["precision"]),
+                                   w.get("compact_every", 0), w["precision"]) + (
+                                   "; half the charges negative, soft-sphere collisions and particle-particle vdW"
+                                   if args.contact else ""),
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (
                        sum(t.numel() * t.element_size() for t in state.current() if t is not None) / 1e9),
                    "parallelism": "samples sharded by rank" if world > 1 else "1 GPU",

@@ -148,7 +148,8 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
 // Two ordered pairs (i_a, j), (i_b, j) of the Coulomb sum in packed form.
 // j = (xj, xj), (yj, yj), (zj, zj), (qj, qj); the minimum image in z uses
 // (dz/L + M) - M = rint(dz/L) with M = 1.5 * 2^23.
-// TRACK: also keep the smallest r^2 seen (contact-force runs look for near pairs).
+// TRACK: also keep the smallest nonzero r^2 seen (contact-force runs look for near pairs; the
+// self pair, r = 0, is left out).
 template <bool TRACK = false>
 __device__ __forceinline__ void coulomb_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 qj, f2 invL2, f2 M2,
                                                 f2 nM2, f2 nL2, float c2, f2& ax, f2& ay, f2& az, float& mn) {
@@ -159,7 +160,7 @@ __device__ __forceinline__ void coulomb_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 y
     const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
     float ra, rb;
     f2_unpack(r2, ra, rb);
-    if constexpr (TRACK) mn = fminf(mn, fminf(ra, rb));
+    if constexpr (TRACK) mn = fminf(mn, fminf(ra > 0.f ? ra : INFINITY, rb > 0.f ? rb : INFINITY));   // not self
     const f2 ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
     const f2 s = f2_mul(f2_mul(ri, qj), f2_mul(ri, ri));
     ax = f2_fma(s, dx, ax);
@@ -178,7 +179,7 @@ __device__ __forceinline__ void coulomb_pair_x2_direct(f2 xi, f2 yi, f2 zi, f2 x
     const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
     float ra, rb;
     f2_unpack(r2, ra, rb);
-    if constexpr (TRACK) mn = fminf(mn, fminf(ra, rb));
+    if constexpr (TRACK) mn = fminf(mn, fminf(ra > 0.f ? ra : INFINITY, rb > 0.f ? rb : INFINITY));   // not self
     if constexpr (CLAMP) { ra = fmaxf(ra, c2); rb = fmaxf(rb, c2); }
     const f2 ri = f2_pack(rsqrt_ftz(ra), rsqrt_ftz(rb));
     const f2 s = f2_mul(f2_mul(ri, qj), f2_mul(ri, ri));
@@ -369,7 +370,7 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
 // contact range, so it reads the j data straight from global memory.
 // ---------------------------------------------------------------------------
 template <int P>
-__device__ __noinline__ void contact_tile(const StepArgs& A, int64_t gi, int64_t jb, int64_t je, double zeta,
+__device__ __forceinline__ void contact_tile(const StepArgs& A, int64_t gi, int64_t jb, int64_t je, double zeta,
                                           double c[3]) {
     typedef typename Real<P>::T4 T4;
     const StepConst& K = A.K;
@@ -464,16 +465,43 @@ __device__ __forceinline__ void contact_rows(const StepArgs& A, int64_t base, in
     }
 }
 
-// FP64 pair of the contact-force variant: the Coulomb pair plus the smallest r^2 seen.
+// End of a j-tile in the contact variant: the closing barrier also ORs the threads' near-pair
+// flags; a flagged tile is appended to the CTA's list (contact_rows runs when the list is full).
+template <int P, int NT, int U, int NF>
+__device__ __forceinline__ void flag_tile(const StepArgs& A, bool near, int64_t j0, int& nflag, long long* s_flag,
+                                          int64_t base, int64_t end, double zeta, double* s_ct) {
+    if (!__syncthreads_or(near)) return;
+    if (nflag == NF) {
+        for (int f = 0; f < NF; ++f) contact_rows<P, NT, U>(A, base, end, s_flag[f], zeta, s_ct);
+        nflag = 0;
+        __syncthreads();           // every thread has read the list before it is overwritten
+    }
+    if (threadIdx.x == 0) s_flag[nflag] = j0;
+    ++nflag;
+}
+
+// Contact accelerations from every flagged j-tile of the item.
+template <int P, int NT, int U>
+__device__ __forceinline__ void flush_flags(const StepArgs& A, int nflag, const long long* s_flag, int64_t base,
+                                            int64_t end, double zeta, double* s_ct) {
+    if (!nflag) return;
+    __syncthreads();               // the last entry is visible
+    for (int f = 0; f < nflag; ++f) contact_rows<P, NT, U>(A, base, end, s_flag[f], zeta, s_ct);
+    __syncthreads();               // the list is free for the next item
+}
+
+// FP64 pair of the contact-force variant: the Coulomb pair plus the smallest high word of r^2
+// seen (for r^2 >= 0 the high word orders like the value; integer ALU work, off the narrow
+// FP64 pipe; the self pair gives 0 and flags its own tile).
 __device__ __forceinline__ void coulomb_pair_track(double xi, double yi, double zi, const double4_32a pj, double L,
                                                    double invL, double c2, double& ax, double& ay, double& az,
-                                                   double& mn) {
+                                                   int& mnh) {
     const double dx = xi - pj.x, dy = yi - pj.y;
     double dz = zi - pj.z;
     const double t = __dadd_rn(__fma_rn(dz, invL, 6755399441055744.0), -6755399441055744.0);
     dz = __fma_rn(-L, t, dz);
     const double r2u = __fma_rn(dx, dx, __fma_rn(dy, dy, dz * dz));
-    mn = fmin(mn, r2u);
+    mnh = min(mnh, __double2hiint(r2u));
     const double r2 = fmax(r2u, c2);
     const double ri = rsqrt(r2);
     const double s = pj.w * ri * (ri * ri);
@@ -482,8 +510,10 @@ __device__ __forceinline__ void coulomb_pair_track(double xi, double yi, double 
     az = __fma_rn(s, dz, az);
 }
 
+// The MIXED contact variant is held to 96 registers (its rare FP64 contact path would
+// otherwise set the register count, and the occupancy, of the whole pair loop).
 template <int P, int NT, int U, int V>
-__global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
+__global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT * 96) : 0) k_step(const StepArgs A) {
     typedef typename Real<P>::T T;
     typedef typename Real<P>::T4 T4;
     // j-tile: FP64 holds double4 (x, y, z, q); MIXED holds each value twice,
@@ -498,6 +528,10 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
     constexpr bool CT = V == 4;
     __shared__ double s_ct[CT ? 3 * NT * U : 1];
     __shared__ float s_vi[NT / 32], s_vj[NT / 32];
+    // j-tiles (first index) flagged as holding a near pair of this item; evaluated after the pair
+    // loop so that the rare contact path stays out of the hot loop (flushed when full)
+    constexpr int kFlags = 64;
+    __shared__ long long s_flag[CT ? kFlags : 1];
     const StepConst& K = A.K;
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t step = A.ctl[CTL_STEP];
@@ -529,6 +563,7 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
             ax[u] = ay[u] = az[u] = (T)0;
         }
         double zeta = 0.0;
+        int nflag = 0;              // flagged j-tiles (uniform across the CTA)
         if constexpr (CT) {
             zeta = A.params[s].zeta;
             float vmax = 0.f;
@@ -655,11 +690,12 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                             }
                         }
                     }
-                    if constexpr (CT) {
-                        if (mn < thr * thr) contact_rows<P, NT, U>(A, base, end, j0, zeta, s_ct);
-                    }
-                    __syncthreads();
+                    if constexpr (CT)
+                        flag_tile<P, NT, U, kFlags>(A, mn < thr * thr, j0, nflag, s_flag, base, end, zeta, s_ct);
+                    else
+                        __syncthreads();
                 }
+                if constexpr (CT) flush_flags<P, NT, U>(A, nflag, s_flag, base, end, zeta, s_ct);
                 if constexpr (V != 1) {
 #pragma unroll
                     for (int h = 0; h < H; ++h) {
@@ -687,15 +723,16 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                     __syncthreads();
                     if constexpr (CT) {
                         const double thr = (double)near_bound(K, s_vi, s_vj, NT / 32);
-                        double mn = INFINITY;
+                        int mnh = 0x7fffffff;
 #pragma unroll 8
                         for (int k = 0; k < NT; ++k) {
                             const T4 p = sj[k];
 #pragma unroll
                             for (int u = 0; u < U; ++u)
-                                coulomb_pair_track(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u], mn);
+                                coulomb_pair_track(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u], mnh);
                         }
-                        if (mn < thr * thr) contact_rows<P, NT, U>(A, base, end, j0, zeta, s_ct);
+                        flag_tile<P, NT, U, kFlags>(A, mnh <= __double2hiint(thr * thr), j0, nflag, s_flag, base, end,
+                                                    zeta, s_ct);
                     } else {
 #pragma unroll 8
                         for (int k = 0; k < NT; ++k) {
@@ -704,9 +741,10 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs A) {
                             for (int u = 0; u < U; ++u)
                                 coulomb_pair(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u]);
                         }
+                        __syncthreads();
                     }
-                    __syncthreads();
                 }
+                if constexpr (CT) flush_flags<P, NT, U>(A, nflag, s_flag, base, end, zeta, s_ct);
             }
         }
         if constexpr (P == PDQ_FP64) {
