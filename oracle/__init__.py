@@ -94,6 +94,9 @@ def lib():
             "orc_boot_indices": (None, [C.c_uint64, C.c_uint32, C.c_int, _I64, _I64]),
             "orc_num_threads": (C.c_int, []),
             "orc_capture_factor": (C.c_double, [P, Fp]),
+            "orc_coulomb_periodic": (None, [C.c_int, _D, _D, _D, _D, _I32, C.c_double, C.c_double, C.c_int, _D]),
+            "orc_run_ext": (C.c_int, [P, Fp, _D, Cp, C.c_int, _D, C.c_int, _I64, _D, C.c_int64, _D,
+                                      _D, _D, _D, _D, _D, _D, _D, _I32, _I32, _I64, _I64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -216,6 +219,33 @@ def run(f, grid, c, st_plus, offset, params, state, n_steps, step0=0, tallies=No
                        state.cls, ndep, nal)
     assert rc == 0
     return ndep, nal
+
+
+def run_ext(f, grid, c, st_plus, offset, params, state, ext, step0=0, tallies=None, p=None):
+    """One step with given Coulomb sums ext [N, 3] instead of the all-pairs loop."""
+    p = p or phys()
+    S, nc = len(offset) - 1, len(st_plus)
+    if tallies is None:
+        tallies = (np.zeros((S, nc), np.int64), np.zeros((S, nc), np.int64))
+    ndep, nal = tallies
+    rc = lib().orc_run_ext(C.byref(p), C.byref(f), np.ascontiguousarray(grid), C.byref(c), nc,
+                           np.ascontiguousarray(st_plus, np.float64), S, np.ascontiguousarray(offset, np.int64),
+                           np.ascontiguousarray(params, np.float64).reshape(-1, 3), step0,
+                           np.ascontiguousarray(ext, np.float64).reshape(-1, 3),
+                           state.x, state.y, state.z, state.vx, state.vy, state.vz, state.q, state.alive,
+                           state.cls, ndep, nal)
+    assert rc == 0
+    return ndep, nal
+
+
+def coulomb_periodic(x, y, z, q, L, contact, n_img=2000, alive=None):
+    """Coulomb sums over all periodic images along z (exact electrostatics of the periodic pipe)."""
+    n = len(x)
+    alive = np.ones(n, np.int32) if alive is None else np.ascontiguousarray(alive, np.int32)
+    s = np.zeros((n, 3))
+    lib().orc_coulomb_periodic(n, *(np.ascontiguousarray(v, np.float64) for v in (x, y, z, q)), alive, L, contact,
+                               n_img, s)
+    return s
 
 
 def vdep(ndep, nalive, dt, r_plus=180.0):

@@ -471,6 +471,7 @@ template <class T>
 struct Run {
     const OrcPhys* p; const OrcField* f; const double* grid; const OrcCfg* cfg;
     Units un; std::vector<ClassProps> cp; double contact;  // Coulomb clamp distance (wall units)
+    const double* ext = nullptr;   // given Coulomb sums [n][3] of this sample (replace the pair loop)
 };
 
 // Non-drag acceleration of particle i (wall units) without the Coulomb sum.
@@ -587,8 +588,13 @@ static void step_sample(const Run<T>& rn, int n, T* x, T* y, T* z, T* vx, T* vy,
     const bool smooth = cfg.smooth_eps > 0;
     std::vector<T> ax(n), ay(n), az(n);
     // 1) Coulomb all-pairs (Eq. coulomb, App. A.2: F_i = sum_{j != i} F_ij n_ij),
-    //    minimum image in z, centre distance clamped at the contact distance.
+    //    minimum image in z, centre distance clamped at the contact distance (or given sums).
     if (cfg.forces & F_COUL) {
+        if (rn.ext) {
+            for (int i = 0; i < n; ++i) {
+                ax[i] = T(rn.ext[3 * i]); ay[i] = T(rn.ext[3 * i + 1]); az[i] = T(rn.ext[3 * i + 2]);
+            }
+        } else {
         #pragma omp parallel for schedule(dynamic, 16)
         for (int i = 0; i < n; ++i) {
             T sx(0.0), sy(0.0), sz(0.0);
@@ -606,6 +612,7 @@ static void step_sample(const Run<T>& rn, int n, T* x, T* y, T* z, T* vx, T* vy,
                 }
             }
             ax[i] = sx; ay[i] = sy; az[i] = sz;
+        }
         }
         // coefficient q_i (q_ref^2 / (4 pi eps0 m_i)) in wall units
         for (int i = 0; i < n; ++i) {
@@ -850,6 +857,61 @@ void orc_coulomb_accel(const OrcPhys* p, const OrcField* f, int n_classes, const
         double coef = p->qmax_coef * p->qmax_coef / (4.0 * M_PI * p->eps0) / c.mass / (rn.un.ell * rn.un.ell) * rn.un.acc;
         for (int k = 0; k < 3; ++k) a[3 * i + k] = q[i] * coef * s[k];
     }
+}
+
+// Coulomb sums s_i = sum_j q_j d / max(|d|, contact)^3 over every periodic image of particle j
+// along z (d = x_i - x_j - k L e_z, |k| <= n_img), j != i, live particles: the electrostatics the
+// paper's P3M approximates (periodic pipe, no images across the wall).  The images beyond n_img
+// are added in their far-field form: pairs (k, -k) contribute 2 d_xy / (kL)^3 across and
+// -4 d_z / (kL)^3 along the axis, summed with sum_{k > K} k^-3 ~ 1 / (2 (K + 1/2)^2).
+void orc_coulomb_periodic(int n, const double* x, const double* y, const double* z, const double* q,
+                          const int32_t* alive, double L, double contact, int n_img, double* s /*[n][3]*/) {
+    const double tail = 1.0 / (2.0 * (n_img + 0.5) * (n_img + 0.5)) / (L * L * L);
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < n; ++i) {
+        double acc[3] = {0, 0, 0};
+        if (alive[i]) {
+            for (int j = 0; j < n; ++j) {
+                if (j == i || !alive[j]) continue;
+                const double dx = x[i] - x[j], dy = y[i] - y[j];
+                const double dz0 = z[i] - z[j];
+                double px = 0, py = 0, pz = 0;
+                for (int k = -n_img; k <= n_img; ++k) {
+                    const double dz = dz0 - k * L;
+                    const double r = std::max(std::sqrt(dx * dx + dy * dy + dz * dz), contact);
+                    const double w = 1.0 / (r * r * r);
+                    px += w * dx; py += w * dy; pz += w * dz;
+                }
+                px += 2.0 * dx * tail; py += 2.0 * dy * tail; pz += -4.0 * dz0 * tail;
+                acc[0] += q[j] * px; acc[1] += q[j] * py; acc[2] += q[j] * pz;
+            }
+        }
+        for (int k = 0; k < 3; ++k) s[3 * i + k] = acc[k];
+    }
+}
+
+// One step of every sample with the Coulomb sums given (ext [N][3], e.g. from a P3M solve of
+// the current state) instead of the all-pairs loop; otherwise as orc_run.
+int orc_run_ext(const OrcPhys* p, const OrcField* f, const double* grid, const OrcCfg* cfg,
+                int n_classes, const double* st_plus, int n_samples, const int64_t* offset,
+                const double* params, int64_t step0, const double* ext,
+                double* x, double* y, double* z, double* vx, double* vy, double* vz, const double* q,
+                int32_t* alive, const int32_t* cls, int64_t* ndep, int64_t* nalive) {
+    if (cfg->smooth_eps > 0) return -1;
+    Run<double> rn;
+    rn.p = p; rn.f = f; rn.grid = grid; rn.cfg = cfg; rn.un = units(*p);
+    for (int c = 0; c < n_classes; ++c) rn.cp.push_back(class_props(*p, st_plus[c]));
+    rn.contact = contact_distance(rn.cp);
+    for (int s = 0; s < n_samples; ++s) {
+        int64_t o = offset[s];
+        int n = (int)(offset[s + 1] - o);
+        SampleParams sp{params[3 * s], params[3 * s + 1], params[3 * s + 2]};
+        rn.ext = ext + 3 * o;
+        step_sample<double>(rn, n, x + o, y + o, z + o, vx + o, vy + o, vz + o, q + o, nullptr,
+                            alive + o, cls + o, sp.zeta, sp.theta, step0 >= cfg->window_start,
+                            ndep + (size_t)s * n_classes, nalive + (size_t)s * n_classes, nullptr, nullptr);
+    }
+    return 0;
 }
 
 // Non-Coulomb, non-drag acceleration (gravity + image + vdW) at given points.
