@@ -42,7 +42,7 @@ enum {
     PDQ_OK = 0,
     PDQ_ERR_INVALID_ARG = -1, /* bad size, NULL pointer, unknown enum value        */
     PDQ_ERR_CUDA = -2,        /* a CUDA runtime call failed                        */
-    PDQ_ERR_OOM = -3,         /* device allocation failed (pdq_field only)         */
+    PDQ_ERR_OOM = -3,         /* device allocation failed (pdq_field, pdq_p3m)      */
     PDQ_ERR_NAN = -4,         /* a kernel saw a non-finite particle state          */
     PDQ_ERR_TIMEOUT = -5,     /* a bounded device wait gave up                     */
     PDQ_ERR_PRECOND = -6,     /* MFMC precondition (Eq. mf-precond) violated       */
@@ -415,6 +415,66 @@ int pdq_mfmc_sobol(int32_t k, const double* const* y, const int64_t* m, const do
  * Errors: INVALID_ARG, CUDA.                                                 */
 int pdq_dgsm_bounds(int32_t S, int32_t C, int32_t d, const double* grad, const double* y, const double* width,
                     double* nu, double* bound, pdq_stream_t stream);
+
+/* ------------------------------------------------------------------ P3M
+ * Electrostatics by P3M (App. A.2: the particle-particle particle-mesh method
+ * the paper uses for ~1e6 particles per sample), for the periodic pipe:
+ * periodic along z with period L, isolated across (no images through the
+ * wall).  It approximates, for every live particle i of a sample,
+ *   s_i = sum_j sum_k q_j d / max(|d|, d_c)^3,  d = x_i - x_j - k L e_z,
+ * over all images k (the all-pairs path uses the nearest image only), d_c the
+ * largest class diameter.  Splitting d/r^3 = K_L + K_S with the Gaussian
+ * screening erf(alpha r)/r: K_L on a mesh of M cells across the diameter
+ * (h = 2R/M; M + 5 nodes from -R - 2h, doubled to Nx = 2(M + 5) so that the
+ * FFT convolution is the open one) and Nz nodes along z; charges assigned and
+ * sums interpolated with TSC weights; the image-summed kernel's transform
+ * divided by the squared TSC window; K_S = d/max(r, d_c)^3 - K_L summed
+ * directly over pairs closer than r_cut via a cell list.  FP64 throughout;
+ * cuFFT for the transforms.  With alpha h = 0.5 and r_cut = 3.3/alpha the
+ * RMS relative error against the exact periodic sum is ~1.4e-4.
+ * A plan owns its device memory (kernel transforms, meshes, cell list; about
+ * 40 Nx^2 Nz bytes).  Pick M with 2(M + 5) a product of small primes (123,
+ * 251) for fast transforms.                                                  */
+typedef struct pdq_p3m_desc {
+    int32_t M;        /* mesh cells across the diameter, >= 4                          */
+    int32_t Nz;       /* mesh nodes along the period L, >= 4                           */
+    double alpha;     /* screening, 1/wall units; 0 = 0.5/h                             */
+    double r_cut;     /* short-range cut-off, wall units, < L/2; 0 = 3.3/alpha          */
+    int32_t n_img;    /* kernel images each way along z before the far-field tail; 0=200 */
+    int32_t pad;
+} pdq_p3m_desc;
+typedef struct pdq_p3m pdq_p3m;
+
+/* Build a plan for `field`'s pipe (R = r_plus, L = l_plus) and up to
+ * max_particles particles per call (the largest sample).  Synchronises
+ * `stream`.  Errors: INVALID_ARG, OOM, CUDA.                                 */
+int pdq_p3m_create(const pdq_field* field, const pdq_p3m_desc* desc, int64_t max_particles, pdq_stream_t stream,
+                   pdq_p3m** out);
+int pdq_p3m_destroy(pdq_p3m* plan);
+/* The effective alpha, r_cut, n_img and the transform size Nx of a plan.   */
+int pdq_p3m_params(const pdq_p3m* plan, double* alpha, double* r_cut, int32_t* n_img, int32_t* nx);
+
+/* P3M Coulomb sums of the current half of `state`: sums device [capacity][3]
+ * (row g = particle g; zero for removed particles and unused rows), in the
+ * units of the all-pairs sum (q in q_unit, lengths in wall units); the
+ * acceleration is coul q_i s_i.  Samples are solved one after another on
+ * `stream`; every sample must have <= max_particles particles.  Reads
+ * count[] to the host (synchronises `stream`).
+ * Errors: INVALID_ARG (state, plan, sizes), CUDA.                            */
+int pdq_p3m_coulomb(pdq_p3m* plan, const pdq_phys* phys, const pdq_state* state, double* sums,
+                    pdq_stream_t stream);
+
+/* pdq_step_particles with the Coulomb acceleration from P3M: each step runs
+ * pdq_p3m_coulomb on the current state, then the step kernel with those sums
+ * in place of its all-pairs loop.  cfg as for pdq_step_particles except:
+ * use_graph = 0, no contact forces (PDQ_F_CONTACT); compaction every
+ * cfg->compact_every steps (unsorted).  workspace as sized by
+ * pdq_step_workspace_size for (state, cfg).  Synchronises `stream` once per
+ * step (sample sizes).  Errors: as pdq_step_particles and pdq_p3m_coulomb.   */
+int pdq_step_particles_p3m(const pdq_field* field, const pdq_phys* phys, pdq_state* state,
+                           const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
+                           pdq_tally* tally, pdq_p3m* plan, void* workspace, size_t workspace_bytes,
+                           pdq_stream_t stream);
 
 #ifdef __cplusplus
 }

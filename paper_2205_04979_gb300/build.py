@@ -61,7 +61,7 @@ def build(force=False, verbose=False):
         objs = list(ex.map(one, sources()))
     tmp = LIB + ".%d.tmp" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
-        "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+        "-lcufft", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stderr)

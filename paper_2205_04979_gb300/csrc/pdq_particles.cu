@@ -30,6 +30,16 @@ enum { ERR_NONFINITE = 1 };
 // ---------------------------------------------------------------------------
 // Host: per-class constants from the physical constants (all SI -> wall units).
 // ---------------------------------------------------------------------------
+// Largest class diameter of a state, wall units (the Coulomb contact distance).
+double contact_distance(const pdq_phys* p, const pdq_state* st) {
+    const double ustar = p->re_tau * p->nu / p->radius;
+    const double ell = p->nu / ustar, tauf = p->nu / (ustar * ustar);
+    double dmax = 0.0;
+    for (int c = 0; c < st->n_classes; ++c)
+        dmax = fmax(dmax, sqrt(18.0 * p->rho_f * p->nu * st->st_plus[c] * tauf / p->rho_p) / ell);
+    return dmax;
+}
+
 int make_step_const(const pdq_field* f, const pdq_phys* p, const pdq_state* st, StepConst* K) {
     memset(K, 0, sizeof(*K));
     const double ustar = p->re_tau * p->nu / p->radius;   // u* = Re_tau nu / R
@@ -224,6 +234,8 @@ struct StepArgs {
     // chunks, one work item each; partial sums go to part[(chunk*3 + k)*cap + g] and
     // the last chunk to finish (tile_cnt) adds them in chunk order and does the update.
     int jsplit; int64_t cap; double* part; int* tile_cnt;
+    // Coulomb sums given per particle ([cap][3], e.g. from P3M): replace the pair loop when set
+    const double* ext;
 };
 
 // Local physics of one particle; returns its class, whether it was alive at the
@@ -582,7 +594,13 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
             for (int d = 16; d > 0; d >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, d));
             if (lane == 0) s_vi[tid >> 5] = vmax;
         }
-        if ((K.forces & PDQ_F_COULOMB) || CT) {
+        if (A.ext) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t g = base + u * NT + tid;
+                if (g < end) { ax[u] = (T)A.ext[3 * g]; ay[u] = (T)A.ext[3 * g + 1]; az[u] = (T)A.ext[3 * g + 2]; }
+            }
+        } else if ((K.forces & PDQ_F_COULOMB) || CT) {
             if constexpr (P == PDQ_MIXED) {
                 static_assert(U % 2 == 0, "packed pairs need an even number of i-particles per thread");
                 constexpr int H = U / 2;
@@ -1264,9 +1282,11 @@ extern "C" int pdq_compact(pdq_state* st, pdq_stream_t stream) {
     return PDQ_OK;
 }
 
-extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, pdq_state* st,
-                                  const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
-                                  pdq_tally* tally, void* workspace, size_t workspace_bytes, pdq_stream_t stream) {
+namespace pdq {
+// The step; ext (optional, device [capacity][3]) replaces the all-pairs Coulomb sums.
+int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const pdq_sample_params* params,
+              const pdq_step_cfg* cfg, int64_t n_steps, pdq_tally* tally, void* workspace, size_t workspace_bytes,
+              pdq_stream_t stream, const double* ext) {
     if (!field || !phys || !params || !cfg || !tally || !tally->n_dep || !tally->n_alive || n_steps < 0)
         return PDQ_ERR_INVALID_ARG;
     int rc = validate_state(st);
@@ -1277,12 +1297,13 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
     const bool contact = (cfg->forces & PDQ_F_CONTACT) != 0;
     if (contact && (!(phys->restitution > 0.0 && phys->restitution <= 1.0) || !(phys->tau_col_steps > 0.0)))
         return PDQ_ERR_INVALID_ARG;
+    if (ext && (contact || cfg->use_graph)) return PDQ_ERR_INVALID_ARG;
     const int NT = tile_threads(st, cfg), U = tile_ilp(st, cfg);
     if (NT != 64 && NT != 128 && NT != 256 && !(NT == 32 && st->precision == PDQ_FP64)) return PDQ_ERR_INVALID_ARG;
     size_t items_bytes, need, cnt_off = 0, part_off = 0;
     workspace_layout(st, NT * U, &items_bytes, &need, &cnt_off, &part_off, contact);
     if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return PDQ_ERR_WORKSPACE;
-    const int JS = j_split(st, NT * U, contact);
+    const int JS = j_split(st, NT * U, contact || ext);
     if (n_steps == 0) return PDQ_OK;
     StepArgs A;
     memset(&A, 0, sizeof(A));
@@ -1305,6 +1326,7 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
     A.n_dep = (unsigned long long*)tally->n_dep; A.n_alive = (unsigned long long*)tally->n_alive;
     A.jsplit = JS;
     A.cap = st->capacity;
+    A.ext = ext;
     if (JS > 1) {
         A.tile_cnt = (int*)((char*)workspace + cnt_off);
         A.part = (double*)((char*)workspace + part_off);
@@ -1402,6 +1424,16 @@ extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, 
     std::lock_guard<std::mutex> lock(g_graph_mu);
     g_graphs[key] = GraphEntry{exec, st->cur};
     return PDQ_OK;
+}
+
+// Compaction entry for the P3M driver (unsorted, stream-ordered).
+int compact_state(pdq_state* st, cudaStream_t s) { return enqueue_compact(st, s); }
+}  // namespace pdq
+
+extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, pdq_state* st,
+                                  const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
+                                  pdq_tally* tally, void* workspace, size_t workspace_bytes, pdq_stream_t stream) {
+    return pdq::step_impl(field, phys, st, params, cfg, n_steps, tally, workspace, workspace_bytes, stream, nullptr);
 }
 
 extern "C" int pdq_release_graphs(void) {

@@ -53,6 +53,11 @@ class StepCfg(C.Structure):
                 ("use_graph", C.c_int32), ("variant", C.c_int32)]
 
 
+class P3MDesc(C.Structure):
+    _fields_ = [("M", C.c_int32), ("Nz", C.c_int32), ("alpha", C.c_double), ("r_cut", C.c_double),
+                ("n_img", C.c_int32), ("pad", C.c_int32)]
+
+
 class BatchStruct(C.Structure):
     _fields_ = [("precision", C.c_int32), ("n_samples", C.c_int32), ("n_classes", C.c_int32), ("pad", C.c_int32),
                 ("st_plus", C.c_double * MAX_CLASSES), ("capacity", C.c_int64), ("offset", C.c_void_p)]
@@ -106,6 +111,13 @@ def lib():
                                           C.c_int32, P, P, P, P, C.c_size_t, P]),
             "pdq_dgsm_bounds": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P]),
             "pdq_capture_efficiency": (C.c_int, [P, C.POINTER(Phys), P, C.c_int64, P, P]),
+            "pdq_p3m_create": (C.c_int, [P, C.POINTER(P3MDesc), C.c_int64, P, C.POINTER(C.c_void_p)]),
+            "pdq_p3m_destroy": (C.c_int, [P]),
+            "pdq_p3m_params": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_int32)]),
+            "pdq_p3m_coulomb": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P, P]),
+            "pdq_step_particles_p3m": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P, C.POINTER(StepCfg),
+                                                 C.c_int64, C.POINTER(TallyStruct), P, P, C.c_size_t, P]),
             "pdq_mfmc_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                                   C.POINTER(C.c_size_t)]),
             "pdq_mfmc_sobol": (C.c_int, [C.c_int32, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
@@ -165,6 +177,39 @@ class Field:
     def close(self):
         if self.handle:
             lib().pdq_destroy_pipe_field(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class P3M:
+    """Owning wrapper of a pdq_p3m plan (P3M electrostatics of the periodic pipe)."""
+
+    def __init__(self, field, M=123, Nz=256, alpha=0.0, r_cut=0.0, n_img=0, max_particles=1, stream=None):
+        d = P3MDesc()
+        d.M, d.Nz, d.alpha, d.r_cut, d.n_img = M, Nz, alpha, r_cut, n_img
+        h = C.c_void_p()
+        _check(lib().pdq_p3m_create(field.handle, C.byref(d), int(max_particles), _stream(stream), C.byref(h)),
+               "p3m_create")
+        self.handle = h
+        a, rc, ni, nx = C.c_double(), C.c_double(), C.c_int32(), C.c_int32()
+        _check(lib().pdq_p3m_params(h, C.byref(a), C.byref(rc), C.byref(ni), C.byref(nx)), "p3m_params")
+        self.alpha, self.r_cut, self.n_img, self.nx = a.value, rc.value, ni.value, nx.value
+
+    def coulomb(self, phys, state, stream=None):
+        """P3M Coulomb sums [capacity, 3] (float64) of the current state."""
+        out = torch.empty((max(state.st.capacity, 1), 3), dtype=torch.float64, device="cuda")
+        _check(lib().pdq_p3m_coulomb(self.handle, C.byref(phys), C.byref(state.st), _ptr(out), _stream(stream)),
+               "p3m_coulomb")
+        return out[: state.st.capacity]
+
+    def close(self):
+        if self.handle:
+            lib().pdq_p3m_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -278,6 +323,13 @@ def step_particles(field, phys, state, params_dev, cfg, n_steps, tally, ws, stre
     _check(lib().pdq_step_particles(field.handle, C.byref(phys), C.byref(state.st), _ptr(params_dev), C.byref(cfg),
                                     int(n_steps), C.byref(tally.t), _ptr(ws), ws.numel(), _stream(stream)),
            "step_particles")
+
+
+def step_particles_p3m(field, phys, state, params_dev, cfg, n_steps, tally, plan, ws, stream=None):
+    """The step with the Coulomb acceleration from a P3M plan (periodic-pipe electrostatics)."""
+    _check(lib().pdq_step_particles_p3m(field.handle, C.byref(phys), C.byref(state.st), _ptr(params_dev),
+                                        C.byref(cfg), int(n_steps), C.byref(tally.t), plan.handle, _ptr(ws),
+                                        ws.numel(), _stream(stream)), "step_particles_p3m")
 
 
 def step_particles_noalloc(field, phys, state, params_dev, cfg, n_steps, tally, stream=None):
