@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--variant", type=int, default=0, help="MIXED pair-math variant")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-vdep-check", action="store_true")
+    ap.add_argument("--particles", type=int, default=100_000, help="P3M workload: particles in the sample")
     ap.add_argument("--contact", action="store_true",
                     help="half the charges negative, soft-sphere collisions and particle-particle vdW on")
     return ap.parse_args()
@@ -470,6 +471,71 @@ def run_sobol(args):
     print(json.dumps(out), flush=True)
 
 
+def run_p3m(args):
+    """Paper-scale single sample (FP64, 10 classes, lognormal charges) with P3M electrostatics,
+    against the all-pairs FP64 step on the same state."""
+    import torch
+    import paper_2205_04979_gb300.pdq as pdq
+    torch.cuda.set_device(0)
+    w = workloads.WORKLOADS["paper_scale_fp64"]
+    n = args.particles
+    phys = pdq.phys_default()
+    desc = pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
+    stream = torch.cuda.Stream()
+    out = {}
+    with torch.cuda.stream(stream):
+        field = pdq.Field(desc, w["field_seed"], stream)
+        plan = pdq.P3M(field, M=123, Nz=256, max_particles=n, stream=stream)
+        prm = pdq.params_tensor([workloads.NOMINAL])
+
+        def fresh():
+            st = pdq.State(pdq.FP64, [n], w["st_plus"])
+            pdq.seed_particles(field, phys, st, prm, w["particle_seed"], w["charge_sigma"], stream)
+            return st
+
+        state = fresh()
+        cfg = pdq.step_cfg(w["dt"], window_start=0)
+        tally = pdq.Tally(1, len(w["st_plus"]))
+        ws = pdq.workspace(state, cfg)
+        pdq.step_particles_p3m(field, phys, state, prm, cfg, args.warmup, tally, plan, ws, stream)
+        stream.synchronize()
+        alive0 = int(tally.n_alive.sum().item())
+        clk = ClockSampler(None)
+        clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pdq.step_particles_p3m(field, phys, state, prm, cfg, args.steps, tally, plan, ws, stream)
+        e1.record(stream)
+        e1.synchronize()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        assert pdq.check_state(state, stream) == 0
+        psteps = int(tally.n_alive.sum().item()) - alive0
+        # the all-pairs FP64 step (nearest image only) on the same initial state, 2 steps
+        ref_ms = None
+        if n <= 200_000:
+            st2 = fresh()
+            t2 = pdq.Tally(1, len(w["st_plus"]))
+            ws2 = pdq.workspace(st2, cfg)
+            pdq.step_particles(field, phys, st2, prm, cfg, 1, t2, ws2, stream)
+            e0.record(stream)
+            pdq.step_particles(field, phys, st2, prm, cfg, 2, t2, ws2, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ref_ms = e0.elapsed_time(e1) / 2
+    out = {"metric": "particle-steps/s, P3M electrostatics (periodic pipe), FP64", "value": psteps / (ms / 1e3),
+           "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "p3m: 1 sample x %d particles, 10 St+ classes, lognormal charges (sigma 0.5), "
+                                  "128x64x128 field, dt+=%g; mesh M=123 across (h=2.93), Nz=256, transform "
+                                  "%dx%dx256, alpha=%.4f, r_cut=%.2f" % (n, w["dt"], plan.nx, plan.nx, plan.alpha,
+                                                                      plan.r_cut)},
+           "all_pairs_fp64_ms_per_step": ref_ms, "clocks": clocks,
+           "gpu_launches": int(args.steps * 16)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -478,6 +544,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "sobol":
         run_sobol(args)
+    elif args.workload == "p3m":
+        run_p3m(args)
     else:
         run_ours(args)
 

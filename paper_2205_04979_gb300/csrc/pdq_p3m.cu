@@ -12,8 +12,8 @@
 //          squared TSC window (sinc^3 per axis) and by the transform size;
 //   solve: TSC charge assignment (atomics) -> FFT -> product with each kernel
 //          component -> inverse FFT -> TSC interpolation; then a cell list
-//          (cells >= r_cut, stable per-cell order) and the direct short-range
-//          sum with the minimum image along z.
+//          (cells >= r_cut, stable per-cell order, particles copied in cell
+//          order) and the direct short-range sum with the minimum image along z.
 // FP64 throughout; cuFFT does the transforms.  One sample at a time.
 #include <cufft.h>
 #include <math.h>
@@ -43,6 +43,8 @@ struct pdq_p3m {
     int* cell_start;            // [ncells + 1]
     int* cell_fill;             // [ncells]
     int* cell_list;             // [max_n]
+    double4_32a* sorted64;          // [max_n] live particles in cell order: x, y, z, q
+    float4* sorted32;           // [max_n] the same positions in FP32 (distance pre-filter)
     double* sums;               // [sums_cap][3], for the step driver
     int64_t sums_cap;
 };
@@ -83,8 +85,9 @@ __device__ __forceinline__ double long_factor(double r2, double alpha) {
     const double r = sqrt(r2), ar = alpha * r;
     const double c = 1.1283791670955126;      // 2 / sqrt(pi)
     if (ar < 1e-2) return c * alpha * alpha * alpha * (2.0 / 3.0) * (1.0 - 0.6 * ar * ar);
-    if (ar > 6.5) return 1.0 / (r2 * r);     // erf = 1, the Gaussian below 1e-18
-    return erf(ar) / (r2 * r) - c * alpha * exp(-ar * ar) / r2;
+    const double ir2 = 1.0 / r2, ir3 = ir2 / r;
+    if (ar > 6.5) return ir3;                 // erf = 1, the Gaussian below 1e-18
+    return erf(ar) * ir3 - c * alpha * exp(-ar * ar) * ir2;
 }
 
 __global__ void k_p3m_kernel(const P3MGeom G, double* gx, double* gy, double* gz) {
@@ -274,47 +277,104 @@ __global__ void k_cell_sort(const int* start, int64_t ncells, int* list) {
     }
 }
 
+// Live particles copied in cell order (FP64 and an FP32 copy of the positions).
+__global__ void k_cell_gather(const P3MPart S, const int* start, int64_t ncells, const int* list, double4_32a* s64,
+                              float4* s32) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= start[ncells]) return;
+    double x, y, z, q;
+    load_particle(S, S.o + list[t], x, y, z, q);
+    s64[t] = make_double4_32a(x, y, z, q);
+    s32[t] = make_float4((float)x, (float)y, (float)z, 0.f);
+}
+
+// One short-range pair: q_j (d / max(r, d_c)^3 - K_L(d)) when r < r_cut (FP64).
+__device__ __forceinline__ void pp_pair(const P3MGeom& G, const double4_32a& pi, const double4_32a& pj, double invL,
+                                        double rc2, double dc2, double& sx, double& sy, double& sz) {
+    const double dx = pi.x - pj.x, dy = pi.y - pj.y;
+    double dz = pi.z - pj.z;
+    dz -= G.L * rint(dz * invL);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 < rc2)) return;
+    const double ic = rsqrt(fmax(r2, dc2));             // 1 / max(r, d_c)
+    const double f = pj.w * (ic * ic * ic - long_factor(r2, G.alpha));
+    sx += f * dx; sy += f * dy; sz += f * dz;
+}
+
 // Short-range part: q_j (d / max(r, d_c)^3 - K_L(d)) over j != i closer than r_cut, added to sums.
-__global__ void k_p3m_pp(const P3MGeom G, const P3MPart S, const int* start, const int* list, double* sums) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= S.n) return;
-    const int64_t gi = S.o + k;
-    double xi, yi, zi, qi;
-    if (!load_particle(S, gi, xi, yi, zi, qi)) return;
-    const int ci = cell_of(G, xi, yi, zi);
-    const int cz = ci % G.ncz, cy = (ci / G.ncz) % G.ncx, cx = ci / (G.ncz * G.ncx);
-    const double rc2 = G.rc * G.rc, dc = G.contact;
-    double sx = 0.0, sy = 0.0, sz = 0.0;
-    const int nz = G.ncz >= 3 ? 3 : G.ncz;      // distinct z-cells around cz
-    for (int a = cx - 1; a <= cx + 1; ++a) {
-        if (a < 0 || a >= G.ncx) continue;
-        for (int b = cy - 1; b <= cy + 1; ++b) {
-            if (b < 0 || b >= G.ncx) continue;
-            for (int t = 0; t < nz; ++t) {
-                int c = G.ncz >= 3 ? cz - 1 + t : t;
-                if (c < 0) c += G.ncz;
-                if (c >= G.ncz) c -= G.ncz;
-                const int cell = (a * G.ncx + b) * G.ncz + c;
-                for (int p = start[cell]; p < start[cell + 1]; ++p) {
-                    const int64_t gj = S.o + list[p];
-                    if (gj == gi) continue;
-                    double xj, yj, zj, qj;
-                    load_particle(S, gj, xj, yj, zj, qj);
-                    const double dx = xi - xj, dy = yi - yj;
-                    double dz = zi - zj;
-                    dz -= G.L * rint(dz / G.L);
-                    const double r2 = dx * dx + dy * dy + dz * dz;
-                    if (!(r2 < rc2)) continue;
-                    const double rr = fmax(sqrt(r2), dc);
-                    const double f = qj * (1.0 / (rr * rr * rr) - long_factor(r2, G.alpha));
-                    sx += f * dx; sy += f * dy; sz += f * dz;
+// One warp per particle i (cell order): the lanes screen 32 candidates of the 27 neighbour cells
+// at a time in FP32 (r^2 < (r_cut + 1e-3)^2 + 1e-3), the survivors go to a per-warp queue in
+// shared memory, and every 32 queued pairs are evaluated in FP64 with all lanes busy; the lanes'
+// partial sums are reduced in a fixed order.
+constexpr int kPPWarps = 8;
+__global__ void __launch_bounds__(32 * kPPWarps) k_p3m_pp(const P3MGeom G, const P3MPart S, const int* start,
+                                                          int64_t ncells, const int* list,
+                                                          const double4_32a* __restrict__ s64,
+                                                          const float4* __restrict__ s32, double* sums) {
+    __shared__ int queue[kPPWarps][64];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int* qw = queue[w];
+    const int n_live = start[ncells];
+    const double rc2 = G.rc * G.rc, dc2 = G.contact * G.contact, invL = 1.0 / G.L;
+    const float rcf = (float)G.rc + 1e-3f, rc2f = rcf * rcf + 1e-3f, Lf = (float)G.L, invLf = 1.0f / Lf;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int t = blockIdx.x * kPPWarps + w; t < n_live; t += gridDim.x * kPPWarps) {
+        const double4_32a pi = s64[t];
+        const float4 fi = s32[t];
+        const int ci = cell_of(G, pi.x, pi.y, pi.z);
+        const int cz = ci % G.ncz, cy = (ci / G.ncz) % G.ncx, cx = ci / (G.ncz * G.ncx);
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        int qn = 0;
+        const int nz = G.ncz >= 3 ? 3 : G.ncz;
+        for (int a = cx - 1; a <= cx + 1; ++a) {
+            if (a < 0 || a >= G.ncx) continue;
+            for (int b = cy - 1; b <= cy + 1; ++b) {
+                if (b < 0 || b >= G.ncx) continue;
+                for (int u = 0; u < nz; ++u) {
+                    int cc = G.ncz >= 3 ? cz - 1 + u : u;
+                    if (cc < 0) cc += G.ncz;
+                    if (cc >= G.ncz) cc -= G.ncz;
+                    const int cell = (a * G.ncx + b) * G.ncz + cc;
+                    const int pe = start[cell + 1];
+                    for (int p0 = start[cell]; p0 < pe; p0 += 32) {
+                        const int p = p0 + lane;
+                        bool pass = false;
+                        if (p < pe && p != t) {
+                            const float4 fj = s32[p];
+                            const float ex = fi.x - fj.x, ey = fi.y - fj.y;
+                            float ez = fi.z - fj.z;
+                            ez -= Lf * rintf(ez * invLf);
+                            pass = ex * ex + ey * ey + ez * ez < rc2f;
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, pass);
+                        if (pass) qw[qn + __popc(m & lt)] = p;
+                        qn += __popc(m);
+                        __syncwarp();
+                        if (qn >= 32) {
+                            pp_pair(G, pi, s64[qw[lane]], invL, rc2, dc2, sx, sy, sz);
+                            __syncwarp();
+                            if (lane < qn - 32) qw[lane] = qw[32 + lane];
+                            qn -= 32;
+                            __syncwarp();
+                        }
+                    }
                 }
             }
         }
+        if (lane < qn) pp_pair(G, pi, s64[qw[lane]], invL, rc2, dc2, sx, sy, sz);
+        __syncwarp();
+        for (int d = 16; d > 0; d >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, d);
+            sy += __shfl_xor_sync(0xffffffffu, sy, d);
+            sz += __shfl_xor_sync(0xffffffffu, sz, d);
+        }
+        if (lane == 0) {
+            const int64_t gi = S.o + list[t];
+            sums[3 * gi] += sx;
+            sums[3 * gi + 1] += sy;
+            sums[3 * gi + 2] += sz;
+        }
     }
-    sums[3 * gi] += sx;
-    sums[3 * gi + 1] += sy;
-    sums[3 * gi + 2] += sz;
 }
 
 unsigned grid_of(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -335,6 +395,7 @@ void free_plan(pdq_p3m* P) {
     if (P->have_inv) cufftDestroy(P->inv);
     cudaFree(P->Gh); cudaFree(P->Q); cudaFree(P->Qh); cudaFree(P->Ah); cudaFree(P->A);
     cudaFree(P->cell_count); cudaFree(P->cell_start); cudaFree(P->cell_fill); cudaFree(P->cell_list);
+    cudaFree(P->sorted64); cudaFree(P->sorted32);
     cudaFree(P->sums);
     delete P;
 }
@@ -387,6 +448,8 @@ extern "C" int pdq_p3m_create(const pdq_field* field, const pdq_p3m_desc* d, int
     alloc((void**)&P->cell_start, (P->ncells + 1) * sizeof(int));
     alloc((void**)&P->cell_fill, P->ncells * sizeof(int));
     alloc((void**)&P->cell_list, P->max_n * sizeof(int));
+    alloc((void**)&P->sorted64, P->max_n * sizeof(double4_32a));
+    alloc((void**)&P->sorted32, P->max_n * sizeof(float4));
     alloc((void**)&Gr, 3 * P->nreal * sizeof(double));
     if (rc == PDQ_OK) rc = cufft_status(cufftPlan3d(&P->fwd, P->Nx, P->Nx, P->Nz, CUFFT_D2Z));
     if (rc == PDQ_OK) P->have_fwd = true;
@@ -467,7 +530,9 @@ extern "C" int pdq_p3m_coulomb(pdq_p3m* P, const pdq_phys* phys, const pdq_state
         k_cell_scan<<<1, 1024, 0, s>>>(P->cell_count, P->ncells, P->cell_start);
         k_cell_fill<<<gp, 256, 0, s>>>(G, S, P->cell_start, P->cell_fill, P->cell_list);
         k_cell_sort<<<grid_of(P->ncells, 128), 128, 0, s>>>(P->cell_start, P->ncells, P->cell_list);
-        k_p3m_pp<<<grid_of(S.n, 128), 128, 0, s>>>(G, S, P->cell_start, P->cell_list, sums);
+        k_cell_gather<<<gp, 256, 0, s>>>(S, P->cell_start, P->ncells, P->cell_list, P->sorted64, P->sorted32);
+        k_p3m_pp<<<(unsigned)std::min<int64_t>(grid_of(S.n, kPPWarps), 16 * 152), 32 * kPPWarps, 0, s>>>(
+            G, S, P->cell_start, P->ncells, P->cell_list, P->sorted64, P->sorted32, sums);
     }
     PDQ_CUDA(cudaGetLastError());
     return PDQ_OK;
