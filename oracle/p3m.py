@@ -56,14 +56,16 @@ class Desc:
 
 
 def kernel_long(dx, dy, dz, alpha):
-    """K_L(d) componentwise; the series 4 alpha^3 / (3 sqrt(pi)) d (1 - 3/5 (alpha r)^2) near r = 0."""
+    """K_L(d) componentwise; near r = 0 (alpha r < 0.05, where the closed form cancels) its Taylor
+    series 4 alpha^3 / (3 sqrt(pi)) d (1 - 3/5 (alpha r)^2 + 3/14 (alpha r)^4)."""
     r2 = dx * dx + dy * dy + dz * dz
     r = np.sqrt(r2)
     ar = alpha * r
-    small = ar < 1e-2
+    small = ar < 0.05
     with np.errstate(divide="ignore", invalid="ignore"):
         f = erf(ar) / (r2 * r) - 2.0 * alpha / math.sqrt(math.pi) * np.exp(-ar * ar) / r2
-    fs = 4.0 * alpha ** 3 / (3.0 * math.sqrt(math.pi)) * (1.0 - 0.6 * ar * ar)
+    u = ar * ar
+    fs = 4.0 * alpha ** 3 / (3.0 * math.sqrt(math.pi)) * (1.0 - 0.6 * u + (3.0 / 14.0) * u * u)
     f = np.where(small, fs, f)
     return f * dx, f * dy, f * dz
 

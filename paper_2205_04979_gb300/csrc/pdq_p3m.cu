@@ -44,6 +44,7 @@ struct pdq_p3m {
     int* cell_fill;             // [ncells]
     int* cell_list;             // [max_n]
     double4_32a* sorted64;          // [max_n] live particles in cell order: x, y, z, q
+    double2* lf_tab;                // [kTab + 1] K_L factor and its u-derivative at u = k (alpha r_cut)^2 / kTab
     float4* sorted32;           // [max_n] the same positions in FP32 (distance pre-filter)
     double* sums;               // [sums_cap][3], for the step driver
     int64_t sums_cap;
@@ -55,7 +56,12 @@ namespace {
 struct P3MGeom {
     double R, L, h, hz, x0, alpha, rc, contact;
     int Mx, Nx, Nz, n_img, ncx, ncz;
+    const double2* lf_tab;
 };
+
+// The short-range pairs read the long-range factor from a cubic Hermite table in
+// u = (alpha r)^2 (relative interpolation error ~1e-13) instead of FP64 erf and exp.
+constexpr int kTab = 4096;
 
 struct P3MPart {                // the particles of one sample, current half of the state
     const void* pos;
@@ -80,11 +86,14 @@ __device__ __forceinline__ bool load_particle(const P3MPart& S, int64_t g, doubl
     return v.w > 0.5f;
 }
 
-// K_L(d) / |d| factor: erf(ar)/r^3 - 2a/sqrt(pi) e^{-a^2 r^2}/r^2; series near 0, 1/r^3 far out.
+// K_L(d) / |d| factor: erf(ar)/r^3 - 2a/sqrt(pi) e^{-a^2 r^2}/r^2; Taylor series near 0, 1/r^3 far out.
 __device__ __forceinline__ double long_factor(double r2, double alpha) {
     const double r = sqrt(r2), ar = alpha * r;
     const double c = 1.1283791670955126;      // 2 / sqrt(pi)
-    if (ar < 1e-2) return c * alpha * alpha * alpha * (2.0 / 3.0) * (1.0 - 0.6 * ar * ar);
+    if (ar < 0.05) {                          // Taylor series where the closed form cancels
+        const double u = ar * ar;
+        return c * alpha * alpha * alpha * (2.0 / 3.0) * (1.0 - 0.6 * u + (3.0 / 14.0) * u * u);
+    }
     const double ir2 = 1.0 / r2, ir3 = ir2 / r;
     if (ar > 6.5) return ir3;                 // erf = 1, the Gaussian below 1e-18
     return erf(ar) * ir3 - c * alpha * exp(-ar * ar) * ir2;
@@ -288,6 +297,35 @@ __global__ void k_cell_gather(const P3MPart S, const int* start, int64_t ncells,
     s32[t] = make_float4((float)x, (float)y, (float)z, 0.f);
 }
 
+// K_L factor and d/du at u = (alpha r)^2, for the table: the series (2 alpha^3 c / 3)
+// (1 - 3u/5 + 3u^2/14) below u = 2.5e-3, the closed form above.
+__device__ __forceinline__ double2 long_factor_u(double u, double alpha) {
+    const double c = 1.1283791670955126, a3 = alpha * alpha * alpha;
+    if (u < 2.5e-3) return make_double2((2.0 / 3.0) * c * a3 * (1.0 - 0.6 * u + (3.0 / 14.0) * u * u),
+                                        (2.0 / 3.0) * c * a3 * (-0.6 + (3.0 / 7.0) * u));
+    const double r = sqrt(u) / alpha, e = exp(-u), er = erf(sqrt(u));
+    const double f = er / (r * r * r) - c * alpha * e / (r * r);
+    const double dfdr = -3.0 * er / (r * r * r * r) + 3.0 * c * alpha * e / (r * r * r) + 2.0 * c * a3 * e / r;
+    return make_double2(f, dfdr / (2.0 * r * alpha * alpha));   // d/du = (d/dr) / (2 r alpha^2)
+}
+
+__global__ void k_lf_table(double alpha, double umax, double2* tab) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > kTab) return;
+    tab[k] = long_factor_u(umax * k / kTab, alpha);
+}
+
+__device__ __forceinline__ double long_factor_tab(const P3MGeom& G, double r2) {
+    const double umax = G.alpha * G.alpha * G.rc * G.rc, hu = umax / kTab;
+    const double x = G.alpha * G.alpha * r2 / hu;
+    int k = (int)x;
+    k = k < 0 ? 0 : (k >= kTab ? kTab - 1 : k);
+    const double t = x - k, t2 = t * t, t3 = t2 * t;
+    const double2 a = G.lf_tab[k], b = G.lf_tab[k + 1];
+    return (2.0 * t3 - 3.0 * t2 + 1.0) * a.x + (t3 - 2.0 * t2 + t) * hu * a.y + (-2.0 * t3 + 3.0 * t2) * b.x +
+           (t3 - t2) * hu * b.y;
+}
+
 // One short-range pair: q_j (d / max(r, d_c)^3 - K_L(d)) when r < r_cut (FP64).
 __device__ __forceinline__ void pp_pair(const P3MGeom& G, const double4_32a& pi, const double4_32a& pj, double invL,
                                         double rc2, double dc2, double& sx, double& sy, double& sz) {
@@ -297,7 +335,7 @@ __device__ __forceinline__ void pp_pair(const P3MGeom& G, const double4_32a& pi,
     const double r2 = dx * dx + dy * dy + dz * dz;
     if (!(r2 < rc2)) return;
     const double ic = rsqrt(fmax(r2, dc2));             // 1 / max(r, d_c)
-    const double f = pj.w * (ic * ic * ic - long_factor(r2, G.alpha));
+    const double f = pj.w * (ic * ic * ic - long_factor_tab(G, r2));
     sx += f * dx; sy += f * dy; sz += f * dz;
 }
 
@@ -386,6 +424,7 @@ P3MGeom geom_of(const pdq_p3m* P, double contact) {
     G.R = P->R; G.L = P->L; G.h = P->h; G.hz = P->hz; G.x0 = P->x0; G.alpha = P->alpha; G.rc = P->rc;
     G.contact = contact; G.Mx = P->Mx; G.Nx = P->Nx; G.Nz = P->Nz; G.n_img = P->n_img;
     G.ncx = P->ncx; G.ncz = P->ncz;
+    G.lf_tab = P->lf_tab;
     return G;
 }
 
@@ -395,7 +434,7 @@ void free_plan(pdq_p3m* P) {
     if (P->have_inv) cufftDestroy(P->inv);
     cudaFree(P->Gh); cudaFree(P->Q); cudaFree(P->Qh); cudaFree(P->Ah); cudaFree(P->A);
     cudaFree(P->cell_count); cudaFree(P->cell_start); cudaFree(P->cell_fill); cudaFree(P->cell_list);
-    cudaFree(P->sorted64); cudaFree(P->sorted32);
+    cudaFree(P->sorted64); cudaFree(P->sorted32); cudaFree(P->lf_tab);
     cudaFree(P->sums);
     delete P;
 }
@@ -450,6 +489,7 @@ extern "C" int pdq_p3m_create(const pdq_field* field, const pdq_p3m_desc* d, int
     alloc((void**)&P->cell_list, P->max_n * sizeof(int));
     alloc((void**)&P->sorted64, P->max_n * sizeof(double4_32a));
     alloc((void**)&P->sorted32, P->max_n * sizeof(float4));
+    alloc((void**)&P->lf_tab, (kTab + 1) * sizeof(double2));
     alloc((void**)&Gr, 3 * P->nreal * sizeof(double));
     if (rc == PDQ_OK) rc = cufft_status(cufftPlan3d(&P->fwd, P->Nx, P->Nx, P->Nz, CUFFT_D2Z));
     if (rc == PDQ_OK) P->have_fwd = true;
@@ -459,6 +499,7 @@ extern "C" int pdq_p3m_create(const pdq_field* field, const pdq_p3m_desc* d, int
     if (rc == PDQ_OK) {
         const P3MGeom G = geom_of(P, 0.0);
         k_p3m_kernel<<<grid_of(P->nreal, 256), 256, 0, s>>>(G, Gr, Gr + P->nreal, Gr + 2 * P->nreal);
+        k_lf_table<<<grid_of(kTab + 1, 256), 256, 0, s>>>(P->alpha, P->alpha * P->alpha * P->rc * P->rc, P->lf_tab);
         for (int c = 0; c < 3 && rc == PDQ_OK; ++c)
             rc = cufft_status(cufftExecD2Z(P->fwd, Gr + c * P->nreal, P->Gh + c * P->ncplx));
         if (rc == PDQ_OK) k_p3m_deconv<<<grid_of(P->ncplx, 256), 256, 0, s>>>(G, P->Gh, (int64_t)P->ncplx);
