@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-vdep-check", action="store_true")
     ap.add_argument("--particles", type=int, default=100_000, help="P3M workload: particles in the sample")
+    ap.add_argument("--p3m-mesh", type=int, nargs=2, default=None, metavar=("M", "NZ"),
+                    help="P3M mesh: cells across the diameter and nodes along z (default by particle count)")
     ap.add_argument("--contact", action="store_true",
                     help="half the charges negative, soft-sphere collisions and particle-particle vdW on")
     return ap.parse_args()
@@ -485,7 +487,8 @@ def run_p3m(args):
     out = {}
     with torch.cuda.stream(stream):
         field = pdq.Field(desc, w["field_seed"], stream)
-        plan = pdq.P3M(field, M=123, Nz=256, max_particles=n, stream=stream)
+        M, Nz = args.p3m_mesh or ((61, 128) if n <= 200_000 else (123, 256))
+        plan = pdq.P3M(field, M=M, Nz=Nz, max_particles=n, stream=stream)
         prm = pdq.params_tensor([workloads.NOMINAL])
 
         def fresh():
@@ -528,9 +531,9 @@ def run_p3m(args):
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
            "config": {"workload": "p3m: 1 sample x %d particles, 10 St+ classes, lognormal charges (sigma 0.5), "
-                                  "128x64x128 field, dt+=%g; mesh M=123 across (h=2.93), Nz=256, transform "
-                                  "%dx%dx256, alpha=%.4f, r_cut=%.2f" % (n, w["dt"], plan.nx, plan.nx, plan.alpha,
-                                                                      plan.r_cut)},
+                                  "128x64x128 field, dt+=%g; mesh M=%d across (h=%.2f), Nz=%d, transform "
+                                  "%dx%dx%d, alpha=%.4f, r_cut=%.2f" % (n, w["dt"], M, 360.0 / M, Nz, plan.nx,
+                                                                      plan.nx, Nz, plan.alpha, plan.r_cut)},
            "all_pairs_fp64_ms_per_step": ref_ms, "clocks": clocks,
            "gpu_launches": int(args.steps * 16)}
     print(json.dumps(out), flush=True)
