@@ -595,6 +595,7 @@ extern "C" int pdq_step_particles_p3m(const pdq_field* field, const pdq_phys* ph
     }
     pdq_step_cfg c1 = *cfg;
     c1.compact_every = 0;
+    c1.variant = 0;
     for (int64_t k = 0; k < n_steps; ++k) {
         int rc = PDQ_OK;
         if (cfg->forces & PDQ_F_COULOMB) {

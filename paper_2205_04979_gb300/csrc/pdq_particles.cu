@@ -14,6 +14,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -240,7 +241,7 @@ struct StepArgs {
 
 // Local physics of one particle; returns its class, whether it was alive at the
 // start of the step, and whether it deposited.
-template <int P>
+template <int P, bool CT = false>
 __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typename Real<P>::T acx,
                                              typename Real<P>::T acy, typename Real<P>::T acz,
                                              const pdq_sample_params& sp, int& cls, bool& was_alive, bool& dep,
@@ -273,7 +274,7 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
     if (K.forces & PDQ_F_GRAVITY) {
         a[0] += (T)K.grav[0]; a[1] += (T)K.grav[1]; a[2] += (T)K.grav[2];
     }
-    if (K.forces & PDQ_F_CONTACT) { a[0] += (T)cx; a[1] += (T)cy; a[2] += (T)cz; }
+    if constexpr (CT) { a[0] += (T)cx; a[1] += (T)cy; a[2] += (T)cz; }
     const double r = sqrt(x * x + y * y);
     if (r > 0.0 && (K.forces & (PDQ_F_IMAGE | PDQ_F_VDW))) {
         double aw = 0.0;   // toward the wall
@@ -594,7 +595,7 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
             for (int d = 16; d > 0; d >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, d));
             if (lane == 0) s_vi[tid >> 5] = vmax;
         }
-        if (A.ext) {
+        if constexpr (V == 5) {      // Coulomb sums given (P3M): no pair loop
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int64_t g = base + u * NT + tid;
@@ -809,7 +810,7 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
             bool was_alive = false, dep = false;
             if (g < end) {
                 if constexpr (CT)
-                    local_update<P>(A, g, ax[u], ay[u], az[u], sp, cls, was_alive, dep, s_ct[(0 * U + u) * NT + tid],
+                    local_update<P, true>(A, g, ax[u], ay[u], az[u], sp, cls, was_alive, dep, s_ct[(0 * U + u) * NT + tid],
                                     s_ct[(1 * U + u) * NT + tid], s_ct[(2 * U + u) * NT + tid]);
                 else
                     local_update<P>(A, g, ax[u], ay[u], az[u], sp, cls, was_alive, dep);
@@ -1112,8 +1113,22 @@ static int launch_step(const StepArgs& A, cudaStream_t s) {
 
 // variant: MIXED pair math, 0 = all packed f32x2, 1 = packed with scalar accumulation,
 // 2 = as 0 with 8 particles per thread.
-// contact: the particle-particle contact variant (V = 4), whatever the variant.
+// contact: the particle-particle contact variant (V = 4), whatever the variant; given
+// Coulomb sums (A.ext, P3M): V = 5, no pair loop.
 static int dispatch_step(int prec, int NT, int variant, bool contact, const StepArgs& A, cudaStream_t s) {
+    if (A.ext) {
+        if (prec == PDQ_FP64) {
+            if (NT == 32) return launch_step<PDQ_FP64, 32, 1, 5>(A, s);
+            if (NT == 64) return launch_step<PDQ_FP64, 64, 1, 5>(A, s);
+            if (NT == 128) return launch_step<PDQ_FP64, 128, 1, 5>(A, s);
+            if (NT == 256) return launch_step<PDQ_FP64, 256, 1, 5>(A, s);
+        } else {
+            if (NT == 64) return launch_step<PDQ_MIXED, 64, 4, 5>(A, s);
+            if (NT == 128) return launch_step<PDQ_MIXED, 128, 4, 5>(A, s);
+            if (NT == 256) return launch_step<PDQ_MIXED, 256, 4, 5>(A, s);
+        }
+        return PDQ_ERR_INVALID_ARG;
+    }
     if (contact) {
         if (prec == PDQ_FP64) {
             if (NT == 32) return launch_step<PDQ_FP64, 32, 1, 4>(A, s);
@@ -1268,7 +1283,9 @@ extern "C" int pdq_step_workspace_size(const pdq_state* st, const pdq_step_cfg* 
     int rc = validate_state(st);
     if (rc) return rc;
     size_t ib, tot;
-    workspace_layout(st, tile_threads(st, cfg) * tile_ilp(st, cfg), &ib, &tot, nullptr, nullptr,
+    // sized for the narrower of the configured tile and 4 particles per thread (the given-sums
+    // step of the P3M driver uses 4), so one workspace serves both step entry points
+    workspace_layout(st, tile_threads(st, cfg) * std::min(tile_ilp(st, cfg), 4), &ib, &tot, nullptr, nullptr,
                      cfg && (cfg->forces & PDQ_F_CONTACT));
     *bytes = tot;
     return PDQ_OK;
@@ -1298,7 +1315,8 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
     if (contact && (!(phys->restitution > 0.0 && phys->restitution <= 1.0) || !(phys->tau_col_steps > 0.0)))
         return PDQ_ERR_INVALID_ARG;
     if (ext && (contact || cfg->use_graph)) return PDQ_ERR_INVALID_ARG;
-    const int NT = tile_threads(st, cfg), U = tile_ilp(st, cfg);
+    const int NT = tile_threads(st, cfg);
+    const int U = ext ? (st->precision == PDQ_FP64 ? 1 : 4) : tile_ilp(st, cfg);   // given sums: 4 per thread
     if (NT != 64 && NT != 128 && NT != 256 && !(NT == 32 && st->precision == PDQ_FP64)) return PDQ_ERR_INVALID_ARG;
     size_t items_bytes, need, cnt_off = 0, part_off = 0;
     workspace_layout(st, NT * U, &items_bytes, &need, &cnt_off, &part_off, contact);
@@ -1470,8 +1488,8 @@ extern "C" int pdq_deposition_tally(const pdq_tally* t, int32_t S, int32_t C, do
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner: times one step of every (block, pair variant) candidate on the
-// caller's state and writes the fastest into cfg.  Each timed step writes the
+// Autotuner: times one step of every (block, pair variant) candidate on the caller's
+// state (best of three after a warm-up) and writes the fastest into cfg.  Each timed step writes the
 // scratch half of the double buffer and a scratch tally, then the state's
 // current half, step counter and control block are restored, so the state is
 // unchanged apart from one z-binned compaction (MIXED with compaction on),
@@ -1561,8 +1579,8 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
             c.variant = v;
             c.compact_every = 0;
             c.use_graph = 0;
-            float ms = 0.f;
-            for (int rep = 0; rep < 2 && rc == PDQ_OK; ++rep) {      // rep 0 warms up
+            float ms = 1e30f;
+            for (int rep = 0; rep < 4 && rc == PDQ_OK; ++rep) {      // rep 0 warms up; best of the other 3
                 cudaEventRecord(e0, s);
                 rc = pdq_step_particles(field, phys, st, params, &c, 1, &scratch, workspace, step_ws, stream);
                 cudaEventRecord(e1, s);
@@ -1570,7 +1588,9 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
                 st->step = step0;
                 cudaMemcpyAsync(st->ctl, &step0, sizeof(int64_t), cudaMemcpyHostToDevice, s);
                 if (cudaEventSynchronize(e1) != cudaSuccess) rc = PDQ_ERR_CUDA;
-                cudaEventElapsedTime(&ms, e0, e1);
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0 && t < ms) ms = t;
             }
             if (rc == PDQ_OK && ms < best) { best = ms; best_b = blocks[bi]; best_v = v; }
         }
