@@ -175,4 +175,46 @@ __device__ __forceinline__ void seed_particle(uint2 key, uint32_t j, double sigm
     qhat = qfac * lam;
 }
 
+// Packed FP32 pairs (sm_100+ f32x2 instructions): one 64-bit register holds the
+// same quantity for two particles, so each FMA-pipe instruction does two lanes' work.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) { f2 d; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) { f2 d; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) { f2 d; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+
+// Two ordered pairs (i_a, j), (i_b, j) of the Coulomb sum in packed form.
+// j = (xj, xj), (yj, yj), (zj, zj), (qj, qj); the minimum image in z uses
+// (dz/L + M) - M = rint(dz/L) with M = 1.5 * 2^23.
+// TRACK: also keep the smallest nonzero r^2 seen (contact-force runs look for near pairs; the
+// self pair, r = 0, is left out).
+template <bool TRACK = false>
+__device__ __forceinline__ void coulomb_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 qj, f2 invL2, f2 M2,
+                                                f2 nM2, f2 nL2, float c2, f2& ax, f2& ay, f2& az, float& mn) {
+    const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj);
+    f2 dz = f2_sub(zi, zj);
+    const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
+    dz = f2_fma(nL2, t, dz);
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    if constexpr (TRACK) mn = fminf(mn, fminf(ra > 0.f ? ra : INFINITY, rb > 0.f ? rb : INFINITY));   // not self
+    const f2 ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
+    const f2 s = f2_mul(f2_mul(ri, qj), f2_mul(ri, ri));
+    ax = f2_fma(s, dx, ax);
+    ay = f2_fma(s, dy, ay);
+    az = f2_fma(s, dz, az);
+}
+
 }  // namespace pdq
