@@ -202,6 +202,7 @@ typedef struct pdq_step_cfg {
     int32_t forces;       /* PDQ_F_* mask                                                    */
     int64_t window_start; /* first global step index counted in the tallies (t+ >= t_w)      */
     int32_t compact_every;/* compact deposited particles out every this many steps; 0 never */
+                          /* (PDQ_MIXED: also re-bins particles by z, at least every 10 steps) */
     int32_t block;        /* threads per CTA of the step kernel: 0 (auto), 64, 128, 256      */
                           /* (and 32 for PDQ_FP64)                                           */
     int32_t use_graph;    /* 1: capture the call as a CUDA graph (first call with a given      */
