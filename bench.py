@@ -371,6 +371,8 @@ def run_ours(args):
                                    args.workload, len(counts), int(np.min(counts)), int(np.max(counts)),
                                    int(np.sum(counts)), len(w["st_plus"]), *w["grid"], w["dt"],
                                    w.get("compact_every", 0), w["precision"]) + (
+                                   " (z-binned, re-binned and compacted every 10 steps)"
+                                   if w["precision"] == "mixed" and w.get("compact_every", 0) > 0 else "") + (
                                    "; half the charges negative, soft-sphere collisions and particle-particle vdW"
                                    if args.contact else ""),
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (
