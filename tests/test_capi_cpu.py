@@ -94,3 +94,28 @@ def test_mfmc_allocate_host_logic(pdq):
                                  C.c_void_p(w.ctypes.data), 10.0, 0, C.c_void_p(mo.ctypes.data),
                                  C.c_void_p(ao.ctypes.data), None, None)
         assert rc == -6
+
+
+def test_contact_and_p3m_arguments_rejected_on_host(pdq):
+    L = pdq.lib()
+    p = pdq.phys_default()
+    assert p.restitution == 0.9 and p.tau_col_steps == 15.0 and p.neg_charge_frac == 0.0
+    # capture efficiency, P3M plan and solve: NULL / out-of-range arguments fail before any CUDA call
+    assert L.pdq_capture_efficiency(None, C.byref(p), None, 1, None, None) == -1
+    d = pdq.P3MDesc()
+    d.M, d.Nz = 2, 64
+    h = C.c_void_p()
+    assert L.pdq_p3m_create(None, C.byref(d), 100, None, C.byref(h)) == -1
+    assert L.pdq_p3m_coulomb(None, C.byref(p), None, None, None) == -1
+    assert L.pdq_p3m_params(None, None, None, None, None) == -1
+    assert L.pdq_p3m_destroy(None) == 0
+    # the P3M step refuses graph mode and contact forces before touching the plan or the GPU
+    cfg = pdq.step_cfg(0.05, use_graph=True)
+    s = pdq.StateStruct()
+    t = pdq.TallyStruct()
+    fake = C.c_void_p(1)
+    assert L.pdq_step_particles_p3m(None, C.byref(p), C.byref(s), None, C.byref(cfg), 1, C.byref(t), fake, None, 0,
+                                    None) == -1
+    cfg = pdq.step_cfg(0.05, forces=pdq.F_ALL | pdq.F_CONTACT)
+    assert L.pdq_step_particles_p3m(None, C.byref(p), C.byref(s), None, C.byref(cfg), 1, C.byref(t), fake, None, 0,
+                                    None) == -1
