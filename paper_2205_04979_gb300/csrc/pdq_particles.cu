@@ -198,6 +198,9 @@ struct StepArgs {
     int jsplit; int64_t cap; double* part; int* tile_cnt;
     // Coulomb sums given per particle ([cap][3], e.g. from P3M): replace the pair loop when set
     const double* ext;
+    // host only: upper bound on the work items of a launch (the persistent grid is capped by it,
+    // so that few items spread one per CTA over the SMs instead of piling onto the first CTAs)
+    int64_t max_items;
 };
 
 // Local physics of one particle; returns its class, whether it was alive at the
@@ -1068,7 +1071,9 @@ static int launch_step(const StepArgs& A, cudaStream_t s) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<P, NT, U, V>, NT, 0);
         if (per_sm <= 0) per_sm = 1;
     }
-    k_step<P, NT, U, V><<<sm_count() * per_sm, NT, 0, s>>>(A);
+    const int64_t full = (int64_t)sm_count() * per_sm;
+    k_step<P, NT, U, V><<<(unsigned)std::max<int64_t>(1, std::min(full, A.max_items > 0 ? A.max_items : full)), NT, 0,
+                          s>>>(A);
     return PDQ_OK;
 }
 
@@ -1317,6 +1322,7 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
     A.jsplit = JS;
     A.cap = st->capacity;
     A.ext = ext;
+    A.max_items = (st->capacity / (NT * U) + st->n_samples + 1) * JS;
     if (JS > 1) {
         A.tile_cnt = (int*)((char*)workspace + cnt_off);
         A.part = (double*)((char*)workspace + part_off);
