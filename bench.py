@@ -286,8 +286,11 @@ def run_ours(args):
         psteps = int(tally.n_alive.sum().item()) - alive0
         pairs = 0.5 * (np.sum(cnt0 ** 2) + np.sum(cnt1 ** 2)) * args.steps
         s0 = state.step_index - args.steps
-        n_compact = sum(1 for k in range(args.steps - 1) if cfg.compact_every and (s0 + k + 1) % cfg.compact_every == 0)
-        launches = 1 + args.steps + 2 * n_compact        # build_items, k_step per step, compact + build_items
+        # the MIXED step re-bins (sorts and compacts) at least every 10 steps and once at the start of a call
+        binned = prec == pdq.MIXED and cfg.compact_every > 0
+        ci = min(cfg.compact_every, 10) if binned else cfg.compact_every
+        n_compact = sum(1 for k in range(args.steps - 1) if ci and (s0 + k + 1) % ci == 0)
+        launches = int(binned) + 1 + args.steps + 2 * n_compact   # sort, build_items, k_step per step, re-bin + items
 
         # e2e: state in pinned host memory; upload, one step, download state + tallies
         e2e = None
