@@ -434,7 +434,8 @@ int pdq_dgsm_bounds(int32_t S, int32_t C, int32_t d, const double* grad, const d
  * cuFFT for the transforms.  With alpha h = 0.5 and r_cut = 3.3/alpha the
  * RMS relative error against the exact periodic sum is ~1.4e-4.
  * A plan owns its device memory (kernel transforms, meshes, cell list; about
- * 40 Nx^2 Nz bytes).  Pick M with 2(M + 5) a product of small primes (123,
+ * 40 Nx^2 Nz bytes, plus a [capacity][3] FP64 buffer that
+ * pdq_step_particles_p3m allocates the first time it meets a state that large).  Pick M with 2(M + 5) a product of small primes (123,
  * 251) for fast transforms.                                                  */
 typedef struct pdq_p3m_desc {
     int32_t M;        /* mesh cells across the diameter, >= 4                          */
