@@ -314,6 +314,20 @@ def test_mixed_binned_compaction_parity(pdq, fields, variant):
         assert np.mean(np.diff(b) >= -2) > 0.95
 
 
+def test_mixed_rebinning_between_compactions(pdq, fields):
+    # compact_every = 100: the MIXED step still re-bins (and compacts) every 10 steps, so after 25
+    # steps the state was last binned at step 20; parity with the oracle is unchanged
+    counts = [1000, 333, 129]
+    st, tally, ost, nd, na = _run_both(pdq, fields, 1, counts, ST3, PRM3, 25, {"compact_every": 100})
+    n_live = _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 2e-6, 2e-5, max_flip=0.005)
+    assert n_live > 0
+    z = st.current()[0][:, 2].cpu().numpy()
+    cnt, offs = st.count.cpu().numpy(), st.offset.cpu().numpy()
+    for s in range(3):
+        b = np.floor(z[offs[s]:offs[s] + cnt[s]] * 256 / 720.0)
+        assert np.mean(np.diff(b) >= -2) > 0.95
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_nonfinite_state_reported(pdq, fields, precision):
     # failure made on the host: one particle's velocity is set to NaN; the step runs to the end,
