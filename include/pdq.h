@@ -201,8 +201,8 @@ typedef struct pdq_step_cfg {
     int32_t mode;         /* PDQ_STICK (removal on wall contact, App. A) or PDQ_REBOUND      */
     int32_t forces;       /* PDQ_F_* mask                                                    */
     int64_t window_start; /* first global step index counted in the tallies (t+ >= t_w)      */
-    int32_t compact_every;/* compact deposited particles out every this many steps; 0 never */
-                          /* (PDQ_MIXED: also re-bins particles by z, at least every 10 steps) */
+    int32_t compact_every;/* compact deposited particles out every this many steps (done     */
+                          /* with the z-binning pass, so at least every 10 steps); 0 never   */
     int32_t block;        /* threads per CTA of the step kernel: 0 (auto), 64, 128, 256      */
                           /* (and 32 for PDQ_FP64)                                           */
     int32_t use_graph;    /* 1: capture the call as a CUDA graph (first call with a given      */
@@ -240,9 +240,13 @@ int pdq_step_workspace_size(const pdq_state* state, const pdq_step_cfg* cfg, siz
  * FP64 runs everything in double; MIXED keeps x, y, the wall gap, the vdW
  * term and the tallies in double and runs the pair sum, interpolation, drag
  * and velocities in float.  `workspace` (>= pdq_step_workspace_size bytes,
- * device, 256-byte aligned) holds the work queue.  Compaction runs after every
- * step whose index + 1 is a multiple of compact_every.  The first call for a
- * state reads offset[] to the host (synchronises `stream`).
+ * device, 256-byte aligned) holds the work queue.  The particles of each
+ * sample are grouped by z (a stable binning; `tag` moves with them, so
+ * identify particles by tag, not by row) at the start of the call and every
+ * min(compact_every, 10) steps (every 10 when compact_every = 0); when
+ * compact_every > 0 the same pass compacts deposited particles out, updating
+ * count[].  The first call for a state reads offset[] to the host
+ * (synchronises `stream`).
  * Errors: INVALID_ARG, WORKSPACE, CUDA.  Non-finite states set the error word
  * read by pdq_check_state.                                                   */
 int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, pdq_state* state,

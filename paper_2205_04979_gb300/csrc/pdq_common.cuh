@@ -96,10 +96,10 @@ struct StepConst {
 int make_step_const(const pdq_field* f, const pdq_phys* p, const pdq_state* st, StepConst* K);
 
 // The particle step with optional given Coulomb sums ext (device [capacity][3]) in place of
-// the all-pairs loop, and an unsorted compaction (pdq_particles.cu).
+// the all-pairs loop (bin = false: no z-binning), and an unsorted compaction (pdq_particles.cu).
 int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const pdq_sample_params* params,
               const pdq_step_cfg* cfg, int64_t n_steps, pdq_tally* tally, void* workspace, size_t workspace_bytes,
-              pdq_stream_t stream, const double* ext);
+              pdq_stream_t stream, const double* ext, bool bin);
 int compact_state(pdq_state* st, cudaStream_t s);
 // Largest class diameter of a state in wall units (pdq_particles.cu).
 double contact_distance(const pdq_phys* p, const pdq_state* st);

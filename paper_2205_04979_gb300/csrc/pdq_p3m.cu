@@ -603,7 +603,7 @@ extern "C" int pdq_step_particles_p3m(const pdq_field* field, const pdq_phys* ph
             if (rc) return rc;
         }
         rc = step_impl(field, phys, st, params, &c1, 1, tally, workspace, workspace_bytes, stream,
-                       (cfg->forces & PDQ_F_COULOMB) ? P->sums : nullptr);
+                       (cfg->forces & PDQ_F_COULOMB) ? P->sums : nullptr, false);
         if (rc) return rc;
         if (cfg->compact_every > 0 && st->step % cfg->compact_every == 0 && k + 1 < n_steps) {
             rc = compact_state(st, (cudaStream_t)stream);

@@ -467,6 +467,21 @@ __device__ __forceinline__ void flush_flags(const StepArgs& A, int nflag, const 
     __syncthreads();               // the list is free for the next item
 }
 
+// FP64 pair of a tile pair that needs no periodic image (the shift is folded into zi); without
+// CLAMP every |dz| of the tile pair exceeds the contact distance, so r^2 > c2 (self pair excluded).
+template <bool CLAMP>
+__device__ __forceinline__ void coulomb_pair_direct64(double xi, double yi, double zi, const double4_32a pj,
+                                                      double c2, double& ax, double& ay, double& az) {
+    const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+    double r2 = __fma_rn(dx, dx, __fma_rn(dy, dy, dz * dz));
+    if constexpr (CLAMP) r2 = fmax(r2, c2);
+    const double ri = rsqrt(r2);
+    const double s = pj.w * ri * (ri * ri);
+    ax = __fma_rn(s, dx, ax);
+    ay = __fma_rn(s, dy, ay);
+    az = __fma_rn(s, dz, az);
+}
+
 // FP64 pair of the contact-force variant: the Coulomb pair plus the smallest high word of r^2
 // seen (for r^2 >= 0 the high word orders like the value; integer ALU work, off the narrow
 // FP64 pipe; the self pair gives 0 and flags its own tile).
@@ -498,6 +513,7 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
     __shared__ __align__(32) unsigned char smem_raw[NT * 32];
     __shared__ float2 s_zr[NT / 32];      // per-warp z range of the staged j-tile
     __shared__ float2 s_zi[NT / 32];      // per-warp z range of this CTA's i-particles
+    __shared__ double2 s_z64[P == PDQ_FP64 ? 2 * (NT / 32) : 1];   // FP64: i ranges, then j ranges
     __shared__ int s_item, s_last;
     __shared__ unsigned int s_alive[PDQ_MAX_CLASSES], s_dep[PDQ_MAX_CLASSES];
     // contact-force variant (V == 4): per-particle contact accelerations of the item, and the
@@ -690,6 +706,19 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
                 }
             } else {
                 T4* sj = reinterpret_cast<T4*>(smem_raw);
+                // z range of this CTA's i-particles, in FP64 (the tiles of a z-binned sample are narrow)
+                {
+                    double lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (base + u * NT + tid < end) { lo = fmin(lo, (double)zi[u]); hi = fmax(hi, (double)zi[u]); }
+                    for (int d = 16; d > 0; d >>= 1) {
+                        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+                        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+                    }
+                    if (lane == 0) s_z64[tid >> 5] = make_double2(lo, hi);
+                }
+                const double dcz64 = sqrt((double)c2) + 1e-9;    // contact distance + rounding margin
                 int64_t jb = o, je = end;
                 if (JS > 1) {      // chunk jc of the sample's j range, a whole number of j-tiles long
                     const int64_t ch = ((end - o + JS - 1) / JS + NT - 1) / NT * NT;
@@ -703,6 +732,14 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
                     else { pj.x = (T)0; pj.y = (T)0; pj.z = (T)0; pj.w = (T)0; }
                     sj[tid] = pj;
                     if constexpr (CT) stage_speed<P>(A, j, je, lane, tid, s_vj);
+                    if constexpr (!CT) {
+                        double lo = j < je ? (double)pj.z : INFINITY, hi = j < je ? (double)pj.z : -INFINITY;
+                        for (int d = 16; d > 0; d >>= 1) {
+                            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+                            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+                        }
+                        if (lane == 0) s_z64[NT / 32 + (tid >> 5)] = make_double2(lo, hi);
+                    }
                     __syncthreads();
                     if constexpr (CT) {
                         const double thr = (double)near_bound(K, s_vi, s_vj, NT / 32);
@@ -717,12 +754,51 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
                         flag_tile<P, NT, U, kFlags>(A, mnh <= __double2hiint(thr * thr), j0, nflag, s_flag, base, end,
                                                     zeta, s_ct);
                     } else {
-#pragma unroll 8
-                        for (int k = 0; k < NT; ++k) {
-                            const T4 p = sj[k];
+                        // as the MIXED path: a tile pair inside one period window takes a uniform
+                        // shift instead of the per-pair minimum image, and z-separated tile pairs
+                        // (every |dz| beyond the contact distance) skip the clamp
+                        double alo = INFINITY, ahi = -INFINITY, blo = INFINITY, bhi = -INFINITY;
 #pragma unroll
-                            for (int u = 0; u < U; ++u)
-                                coulomb_pair(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u]);
+                        for (int w = 0; w < NT / 32; ++w) {
+                            alo = fmin(alo, s_z64[w].x); ahi = fmax(ahi, s_z64[w].y);
+                            blo = fmin(blo, s_z64[NT / 32 + w].x); bhi = fmax(bhi, s_z64[NT / 32 + w].y);
+                        }
+                        const double dlo = alo - bhi, dhi = ahi - blo, halfL = 0.5 * (double)L;
+                        double shift = 0.0;
+                        bool direct = true;
+                        if (dlo > -halfL && dhi < halfL) shift = 0.0;
+                        else if (dlo > halfL && dhi < 3.0 * halfL) shift = (double)L;
+                        else if (dhi < -halfL && dlo > -3.0 * halfL) shift = -(double)L;
+                        else direct = false;
+                        if (direct) {
+                            T zs[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) zs[u] = zi[u] - (T)shift;
+                            if ((dlo - shift > dcz64) || (dhi - shift < -dcz64)) {
+#pragma unroll 8
+                                for (int k = 0; k < NT; ++k) {
+                                    const T4 p = sj[k];
+#pragma unroll
+                                    for (int u = 0; u < U; ++u)
+                                        coulomb_pair_direct64<false>(xi[u], yi[u], zs[u], p, c2, ax[u], ay[u], az[u]);
+                                }
+                            } else {
+#pragma unroll 8
+                                for (int k = 0; k < NT; ++k) {
+                                    const T4 p = sj[k];
+#pragma unroll
+                                    for (int u = 0; u < U; ++u)
+                                        coulomb_pair_direct64<true>(xi[u], yi[u], zs[u], p, c2, ax[u], ay[u], az[u]);
+                                }
+                            }
+                        } else {
+#pragma unroll 8
+                            for (int k = 0; k < NT; ++k) {
+                                const T4 p = sj[k];
+#pragma unroll
+                                for (int u = 0; u < U; ++u)
+                                    coulomb_pair(xi[u], yi[u], zi[u], p, L, invL, c2, ax[u], ay[u], az[u]);
+                            }
                         }
                         __syncthreads();
                     }
@@ -897,7 +973,7 @@ __global__ void __launch_bounds__(1024) k_compact(void* pos, void* vel, double2*
     int out = 0;
     for (int c0 = 0; c0 < n; c0 += blockDim.x) {
         const int i = c0 + threadIdx.x;
-        T4 p, v;
+        T4 p = {}, v = {};
         double2 w = make_double2(0.0, 0.0);
         int2 tg = make_int2(0, 0);
         bool alive = false;
@@ -923,35 +999,45 @@ __global__ void __launch_bounds__(1024) k_compact(void* pos, void* vel, double2*
 }
 
 // ---------------------------------------------------------------------------
-// Compaction with z-binning (MIXED): one CTA per sample copies the live
-// particles of the current half into the other half, grouped by 256 bins of z
-// and in their previous order inside a bin (a stable counting sort: histogram,
-// bin bases, then chunks in order with ranks from __match_any_sync).  Tiles of
-// a binned sample cover short z-intervals, which lets the step skip the
-// per-pair minimum image for most tile pairs.  Tags go to `tag_out` (scratch).
+// z-binning: one CTA per sample copies the particles of the current half into
+// the other half, grouped by 256 bins of z and in their previous order inside a
+// bin (a stable counting sort: histogram, bin bases, then chunks in order with
+// ranks from __match_any_sync).  With `compact` the removed particles are left
+// out (a compaction); without, they are binned like the others and the count is
+// unchanged.  Tiles of a binned sample cover short z-intervals, which lets the
+// step skip the per-pair minimum image for most tile pairs.  Tags go to
+// `tag_out` (scratch).
 // ---------------------------------------------------------------------------
 constexpr int kZBins = 256;
 
-__global__ void __launch_bounds__(1024) k_sort_compact(const float4* __restrict__ pos_in, const float4* __restrict__ vel_in,
+template <int P>
+__global__ void __launch_bounds__(1024) k_sort_compact(const void* __restrict__ pos_in_, const void* __restrict__ vel_in_,
                                                        const double2* __restrict__ xy_in, const int2* __restrict__ tag_in,
-                                                       float4* __restrict__ pos_out, float4* __restrict__ vel_out,
+                                                       void* __restrict__ pos_out_, void* __restrict__ vel_out_,
                                                        double2* __restrict__ xy_out, int2* __restrict__ tag_out,
                                                        const int64_t* __restrict__ offset, int32_t* __restrict__ count,
-                                                       float bins_per_length) {
+                                                       float bins_per_length, int compact) {
+    typedef typename Real<P>::T4 T4;
+    const T4* pos_in = (const T4*)pos_in_;
+    const T4* vel_in = (const T4*)vel_in_;
+    T4* pos_out = (T4*)pos_out_;
+    T4* vel_out = (T4*)vel_out_;
     __shared__ int base[kZBins];
     __shared__ int running[kZBins];
     __shared__ int wcnt[32][kZBins];
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t o = offset[s];
     const int n = count[s];
+    auto bin_of = [&](const T4& p, const T4& v) -> int {
+        if (compact && !((double)v.w > 0.5)) return -1;
+        const float zb = (float)p.z * bins_per_length;
+        return isfinite(zb) ? min(kZBins - 1, max(0, (int)zb)) : 0;
+    };
     for (int b = tid; b < kZBins; b += blockDim.x) { base[b] = 0; running[b] = 0; }
     __syncthreads();
     for (int i = tid; i < n; i += blockDim.x) {
-        if (vel_in[o + i].w > 0.5f) {
-            const float zb = pos_in[o + i].z * bins_per_length;
-            const int b = isfinite(zb) ? min(kZBins - 1, max(0, (int)zb)) : 0;
-            atomicAdd(&base[b], 1);
-        }
+        const int b = bin_of(pos_in[o + i], vel_in[o + i]);
+        if (b >= 0) atomicAdd(&base[b], 1);
     }
     __syncthreads();
     if (tid == 0) {
@@ -962,19 +1048,16 @@ __global__ void __launch_bounds__(1024) k_sort_compact(const float4* __restrict_
     for (int c0 = 0; c0 < n; c0 += blockDim.x) {
         for (int q = tid; q < 32 * kZBins; q += blockDim.x) (&wcnt[0][0])[q] = 0;
         const int i = c0 + tid;
-        float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
+        T4 p = {}, v = {};
         double2 w = make_double2(0.0, 0.0);
         int2 tg = make_int2(0, 0);
         int b = -1;
         if (i < n) {
             p = pos_in[o + i];
             v = vel_in[o + i];
-            w = xy_in[o + i];
+            if (P == PDQ_MIXED) w = xy_in[o + i];
             tg = tag_in[o + i];
-            if (v.w > 0.5f) {
-                const float zb = p.z * bins_per_length;
-                b = isfinite(zb) ? min(kZBins - 1, max(0, (int)zb)) : 0;
-            }
+            b = bin_of(p, v);
         }
         const unsigned peers = __match_any_sync(0xffffffffu, b);
         const int rank = __popc(peers & ((1u << lane) - 1u));
@@ -991,7 +1074,7 @@ __global__ void __launch_bounds__(1024) k_sort_compact(const float4* __restrict_
             const int64_t d = o + base[b] + wcnt[warp][b] + rank;
             pos_out[d] = p;
             vel_out[d] = v;
-            xy_out[d] = w;
+            if (P == PDQ_MIXED) xy_out[d] = w;
             tag_out[d] = tg;
         }
         __syncthreads();
@@ -1147,7 +1230,7 @@ static int j_split(const pdq_state* st, int TI, bool contact = false) {
     return js < 1 ? 1 : (int)js;
 }
 
-// Workspace: items | order | MIXED: tag scratch of the z-binning sort;
+// Workspace: items | order | tag scratch of the z-binning sort;
 // FP64 with JS > 1: tile counters | partial sums [JS][3][capacity].
 static void workspace_layout(const pdq_state* st, int TI, size_t* items_bytes, size_t* total,
                              size_t* cnt_off = nullptr, size_t* part_off = nullptr, bool contact = false) {
@@ -1155,7 +1238,7 @@ static void workspace_layout(const pdq_state* st, int TI, size_t* items_bytes, s
     const int64_t max_tiles = st->capacity / TI + st->n_samples + 1;
     *items_bytes = align256(sizeof(int2) * (size_t)max_tiles * JS);
     *total = *items_bytes + align256(sizeof(int32_t) * (size_t)st->n_samples);
-    if (st->precision == PDQ_MIXED) *total += align256(sizeof(int2) * (size_t)(st->capacity > 0 ? st->capacity : 1));
+    *total += align256(sizeof(int2) * (size_t)(st->capacity > 0 ? st->capacity : 1));   // tag scratch of the z-binning
     if (JS > 1) {
         if (cnt_off) *cnt_off = *total;
         *total += align256(sizeof(int) * (size_t)max_tiles);
@@ -1164,15 +1247,19 @@ static void workspace_layout(const pdq_state* st, int TI, size_t* items_bytes, s
     }
 }
 
-// MIXED: z-binned compaction from the current half into the other half, tags
+// z-binning (with or without compaction) from the current half into the other half, tags
 // through the workspace scratch, then flip the current half.
-static int enqueue_sort_compact(pdq_state* st, int2* tag_scratch, float bins_per_length, cudaStream_t s) {
+static int enqueue_sort_compact(pdq_state* st, int2* tag_scratch, float bins_per_length, bool compact,
+                                cudaStream_t s) {
     const int h = st->cur;
-    k_sort_compact<<<st->n_samples, 1024, 0, s>>>((const float4*)st->pos[h], (const float4*)st->vel[h],
-                                                  (const double2*)st->xy[h], (const int2*)st->tag,
-                                                  (float4*)st->pos[h ^ 1], (float4*)st->vel[h ^ 1],
-                                                  (double2*)st->xy[h ^ 1], tag_scratch, st->offset, st->count,
-                                                  bins_per_length);
+    if (st->precision == PDQ_FP64)
+        k_sort_compact<PDQ_FP64><<<st->n_samples, 1024, 0, s>>>(st->pos[h], st->vel[h], nullptr, (const int2*)st->tag,
+                                                                st->pos[h ^ 1], st->vel[h ^ 1], nullptr, tag_scratch,
+                                                                st->offset, st->count, bins_per_length, (int)compact);
+    else
+        k_sort_compact<PDQ_MIXED><<<st->n_samples, 1024, 0, s>>>(
+            st->pos[h], st->vel[h], (const double2*)st->xy[h], (const int2*)st->tag, st->pos[h ^ 1], st->vel[h ^ 1],
+            (double2*)st->xy[h ^ 1], tag_scratch, st->offset, st->count, bins_per_length, (int)compact);
     PDQ_CUDA(cudaMemcpyAsync(st->tag, tag_scratch, sizeof(int2) * (size_t)st->capacity, cudaMemcpyDeviceToDevice, s));
     st->cur = h ^ 1;
     return PDQ_OK;
@@ -1199,22 +1286,21 @@ struct GraphEntry {
 static std::mutex g_graph_mu;
 static std::map<std::string, GraphEntry> g_graphs;
 
-// Steps between compactions: cfg->compact_every, and for MIXED (z-binned, re-binned at each
-// compaction) at most kRebinSteps, since the bins widen as particles stream along z (over a
-// 100-step cycle of the batched workload: 180.8 ms/step re-binned every 100 steps, 173.0
-// every 10; the fused re-bin and compaction costs ~0.6 ms).
+// z-binning schedule of the step: the state is binned by z at the start of a call and
+// re-binned every rebin_interval steps, compacting at the same time when compaction is on
+// (compact_every > 0; then at most every compact_every steps).  The bins widen as particles
+// stream along z: over a 100-step cycle of the batched workload the step averaged 180.8 ms
+// re-binned every 100 steps and 173.0 ms every 10; each pass costs ~0.6 ms there.
 constexpr int kRebinSteps = 10;
-static int64_t compaction_interval(const pdq_state* st, const pdq_step_cfg* cfg) {
-    if (cfg->compact_every <= 0) return 0;
-    return st->precision == PDQ_MIXED ? std::min<int64_t>(cfg->compact_every, kRebinSteps) : cfg->compact_every;
+static int64_t rebin_interval(const pdq_step_cfg* cfg) {
+    return cfg->compact_every > 0 ? std::min<int64_t>(cfg->compact_every, kRebinSteps) : kRebinSteps;
 }
 
 static std::string graph_key(const pdq_field* field, const pdq_phys* phys, const pdq_state* st,
                              const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
                              const pdq_tally* tally, const void* ws, size_t ws_bytes, cudaStream_t s) {
     pdq_state k = *st;
-    const int64_t ci = compaction_interval(st, cfg);
-    k.step = ci > 0 ? st->step % ci : 0;
+    k.step = st->step % rebin_interval(cfg);
     std::string key;
     auto put = [&](const void* p, size_t n) { key.append((const char*)p, n); };
     put(&field, sizeof(field)); put(phys, sizeof(*phys)); put(&k, sizeof(k)); put(&params, sizeof(params));
@@ -1280,7 +1366,7 @@ namespace pdq {
 // The step; ext (optional, device [capacity][3]) replaces the all-pairs Coulomb sums.
 int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const pdq_sample_params* params,
               const pdq_step_cfg* cfg, int64_t n_steps, pdq_tally* tally, void* workspace, size_t workspace_bytes,
-              pdq_stream_t stream, const double* ext) {
+              pdq_stream_t stream, const double* ext, bool bin) {
     if (!field || !phys || !params || !cfg || !tally || !tally->n_dep || !tally->n_alive || n_steps < 0)
         return PDQ_ERR_INVALID_ARG;
     int rc = validate_state(st);
@@ -1331,16 +1417,17 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
     int32_t* order = (int32_t*)((char*)workspace + items_bytes);
     cudaStream_t s = (cudaStream_t)stream;
 
-    // MIXED with compaction enabled: particles are z-binned (at the start of the call and at
-    // every compaction, at least every kRebinSteps steps) so that most tile pairs skip the
-    // per-pair minimum image.
-    const bool binned = st->precision == PDQ_MIXED && cfg->compact_every > 0;
-    const int64_t compact_interval = compaction_interval(st, cfg);
+    // Particles are z-binned at the start of the call and every rebin_interval steps (compacted
+    // at the same time when compaction is on) so that most tile pairs skip the per-pair minimum
+    // image.  Not with given Coulomb sums: the P3M driver has its own cell list.
+    const bool binned = bin && !ext;
+    const bool compact = cfg->compact_every > 0;
+    const int64_t rebin = binned ? rebin_interval(cfg) : cfg->compact_every;
     int2* tag_scratch = (int2*)((char*)workspace + items_bytes + align256(sizeof(int32_t) * (size_t)st->n_samples));
     const float bins_per_length = (float)(kZBins / A.K.L);
     auto enqueue = [&]() -> int {
         if (binned) {
-            const int r = enqueue_sort_compact(st, tag_scratch, bins_per_length, s);
+            const int r = enqueue_sort_compact(st, tag_scratch, bins_per_length, compact, s);
             if (r) return r;
         }
         int cur = st->cur;
@@ -1357,10 +1444,10 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
             dispatch_step(st->precision, NT, cfg->variant, contact, A, s);
             cur ^= 1;
             ++stepi;
-            if (compact_interval > 0 && stepi % compact_interval == 0 && k + 1 < n_steps) {
+            if (rebin > 0 && stepi % rebin == 0 && k + 1 < n_steps) {
                 st->cur = cur;
                 if (binned) {
-                    const int r = enqueue_sort_compact(st, tag_scratch, bins_per_length, s);
+                    const int r = enqueue_sort_compact(st, tag_scratch, bins_per_length, compact, s);
                     if (r) return r;
                     cur = st->cur;
                 } else {
@@ -1431,7 +1518,8 @@ int compact_state(pdq_state* st, cudaStream_t s) { return enqueue_compact(st, s)
 extern "C" int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, pdq_state* st,
                                   const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
                                   pdq_tally* tally, void* workspace, size_t workspace_bytes, pdq_stream_t stream) {
-    return pdq::step_impl(field, phys, st, params, cfg, n_steps, tally, workspace, workspace_bytes, stream, nullptr);
+    return pdq::step_impl(field, phys, st, params, cfg, n_steps, tally, workspace, workspace_bytes, stream, nullptr,
+                          true);
 }
 
 extern "C" int pdq_release_graphs(void) {
@@ -1472,7 +1560,7 @@ extern "C" int pdq_deposition_tally(const pdq_tally* t, int32_t S, int32_t C, do
 // state (best of three after a warm-up) and writes the fastest into cfg.  Each timed step writes the
 // scratch half of the double buffer and a scratch tally, then the state's
 // current half, step counter and control block are restored, so the state is
-// unchanged apart from one z-binned compaction (MIXED with compaction on),
+// unchanged apart from one z-binning (a compaction too when compaction is on),
 // which only reorders live particles.  Results are cached per (precision,
 // log2 capacity, log2 samples, forces) for the process lifetime.
 // ---------------------------------------------------------------------------
@@ -1532,14 +1620,14 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
     pdq_tally scratch;
     scratch.n_dep = (int64_t*)((char*)workspace + step_ws);
     scratch.n_alive = (int64_t*)((char*)workspace + step_ws + tb);
-    if (st->precision == PDQ_MIXED && cfg->compact_every > 0) {
+    {   // bin the state once (as a step call would), then time unbinned single steps on it
         StepConst K;
         rc = make_step_const(field, phys, st, &K);
         if (rc) return rc;
         size_t ib, tot;
         workspace_layout(st, min_tile(st), &ib, &tot);
         int2* tag_scratch = (int2*)((char*)workspace + ib + align256(sizeof(int32_t) * (size_t)st->n_samples));
-        rc = enqueue_sort_compact(st, tag_scratch, (float)(kZBins / K.L), s);
+        rc = enqueue_sort_compact(st, tag_scratch, (float)(kZBins / K.L), cfg->compact_every > 0, s);
         if (rc) return rc;
     }
     const int blocks[4] = {64, 128, 256, 32};
@@ -1562,7 +1650,7 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
             float ms = 1e30f;
             for (int rep = 0; rep < 4 && rc == PDQ_OK; ++rep) {      // rep 0 warms up; best of the other 3
                 cudaEventRecord(e0, s);
-                rc = pdq_step_particles(field, phys, st, params, &c, 1, &scratch, workspace, step_ws, stream);
+                rc = step_impl(field, phys, st, params, &c, 1, &scratch, workspace, step_ws, stream, nullptr, false);
                 cudaEventRecord(e1, s);
                 st->cur = cur0;
                 st->step = step0;
