@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "pdq_common.cuh"
@@ -349,6 +350,99 @@ __global__ void k_adj_seed(const AdjArgs A) {
     ((double*)A.qhat)[g] = qh;
 }
 
+// z-binning of the adjoint state at a checkpoint: one CTA per sample copies the state slot
+// `src` (and the per-particle qhat, class) into `dst` grouped by 256 bins of z, stable inside
+// a bin (histogram, bin bases, chunks ranked with __match_any_sync), and records
+// perm[new] = old index within the sample.  No particle is removed in the smoothed
+// functional, so this is a permutation; the reverse sweep undoes it on the cotangents.
+constexpr int kAdjBins = 256;
+__global__ void __launch_bounds__(1024) k_adj_sort(const int64_t* __restrict__ offset, Slot src,
+                                                   const double* __restrict__ qh_in, const int32_t* __restrict__ cl_in,
+                                                   Slot dst, double* __restrict__ qh_out, int32_t* __restrict__ cl_out,
+                                                   int32_t* __restrict__ perm, float bins_per_length) {
+    __shared__ int base[kAdjBins];
+    __shared__ int running[kAdjBins];
+    __shared__ int wcnt[32][kAdjBins];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t o = offset[s];
+    const int n = (int)(offset[s + 1] - o);
+    auto bin_of = [&](double z) -> int {
+        const float zb = (float)z * bins_per_length;
+        return isfinite(zb) ? min(kAdjBins - 1, max(0, (int)zb)) : 0;
+    };
+    for (int b = tid; b < kAdjBins; b += blockDim.x) { base[b] = 0; running[b] = 0; }
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) atomicAdd(&base[bin_of(src.z[o + i])], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int b = 0; b < kAdjBins; ++b) { const int h = base[b]; base[b] = acc; acc += h; }
+    }
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        for (int q = tid; q < 32 * kAdjBins; q += blockDim.x) (&wcnt[0][0])[q] = 0;
+        const int i = c0 + tid;
+        const int b = i < n ? bin_of(src.z[o + i]) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        __syncthreads();
+        if (b >= 0 && rank == 0) wcnt[warp][b] = __popc(peers);
+        __syncthreads();
+        if (tid < kAdjBins) {
+            int acc = running[tid];
+            for (int q = 0; q < 32; ++q) { const int cc = wcnt[q][tid]; wcnt[q][tid] = acc; acc += cc; }
+            running[tid] = acc;
+        }
+        __syncthreads();
+        if (b >= 0) {
+            const int64_t g = o + i, d = o + base[b] + wcnt[warp][b] + rank;
+            dst.x[d] = src.x[g]; dst.y[d] = src.y[g]; dst.z[d] = src.z[g];
+            dst.vx[d] = src.vx[g]; dst.vy[d] = src.vy[g]; dst.vz[d] = src.vz[g]; dst.w[d] = src.w[g];
+            qh_out[d] = qh_in[g];
+            cl_out[d] = cl_in[g];
+            perm[d] = i;
+        }
+        __syncthreads();
+    }
+}
+
+// Cotangents of a binned state back to the order before the binning: out[o + perm[i]] = in[o + i].
+__global__ void k_adj_unperm(const int64_t* __restrict__ offset, const int32_t* __restrict__ perm,
+                             const double* __restrict__ in, double* __restrict__ out) {
+    const int s = blockIdx.y;
+    const int64_t o = offset[s], n = offset[s + 1] - o;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[o + perm[o + i]] = in[o + i];
+}
+
+// Tile pairs of a z-binned sample (MIXED pair loops): the dz of an (i-tile, j-tile) pair lies in
+// [a_lo - b_hi, a_hi - b_lo]; inside one period window the minimum image is a uniform shift
+// (0 or +-L, folded into z_i), and when every |dz| also exceeds the contact distance the clamp
+// goes too (as in the step kernel).
+struct TileClass { bool direct, apart; float shift; };
+__device__ __forceinline__ float2 warp_range(float lo, float hi) {
+    for (int d = 16; d > 0; d >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    return make_float2(lo, hi);
+}
+__device__ __forceinline__ TileClass classify_tiles(const float2* s_zi, const float2* s_zr, int nw, float L,
+                                                    float dcz) {
+    float alo = INFINITY, ahi = -INFINITY, blo = INFINITY, bhi = -INFINITY;
+    for (int w = 0; w < nw; ++w) {
+        alo = fminf(alo, s_zi[w].x); ahi = fmaxf(ahi, s_zi[w].y);
+        blo = fminf(blo, s_zr[w].x); bhi = fmaxf(bhi, s_zr[w].y);
+    }
+    const float dlo = alo - bhi, dhi = ahi - blo, halfL = 0.5f * L;
+    TileClass t{true, false, 0.f};
+    if (dlo > -halfL && dhi < halfL) t.shift = 0.f;
+    else if (dlo > halfL && dhi < 3.f * halfL) t.shift = L;
+    else if (dhi < -halfL && dlo > -3.f * halfL) t.shift = -L;
+    else t.direct = false;
+    t.apart = t.direct && ((dlo - t.shift > dcz) || (dhi - t.shift < -dcz));
+    return t;
+}
+
 // Particles per thread of the forward and pair-VJP kernels: MIXED packs two i-particles
 // per f32x2 instruction (4 per thread), FP64 keeps 2 for ILP.
 template <int P> __host__ __device__ constexpr int adj_ilp() { return P == PDQ_MIXED ? 4 : 2; }
@@ -359,6 +453,7 @@ __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
     typedef typename Real<P>::T4 T4;
     constexpr int U = adj_ilp<P>();          // particles per thread (ILP over the shared j-tile)
     __shared__ __align__(32) unsigned char smem_raw[NT * 32];
+    __shared__ float2 s_zi[NT / 32], s_zr[NT / 32];
     T4* sj = reinterpret_cast<T4*>(smem_raw);
     const int s = blockIdx.y, tid = threadIdx.x;
     const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
@@ -393,6 +488,15 @@ __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
             Z[h] = f2_pack((float)zi[2 * h], (float)zi[2 * h + 1]);
             AX[h] = AY[h] = AZ[h] = 0ull;
         }
+        {
+            float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if ((int64_t)blockIdx.x * NT * U + u * NT + tid < n) { lo = fminf(lo, (float)zi[u]); hi = fmaxf(hi, (float)zi[u]); }
+            const float2 r = warp_range(lo, hi);
+            if ((tid & 31) == 0) s_zi[tid >> 5] = r;
+        }
+        const float dcz = sqrtf(c2) + 1e-3f;
         for (int64_t j0 = 0; j0 < n; j0 += NT) {
             const int64_t j = j0 + tid;
             float px = 0.f, py = 0.f, pz = 0.f, pq = 0.f;
@@ -401,16 +505,45 @@ __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
                 px = (float)A.in.x[gj]; py = (float)A.in.y[gj]; pz = (float)A.in.z[gj];
                 pq = (float)(A.in.w[gj] * sp.xi * A.qhat[gj]);
             }
+            const float2 r = warp_range(j < n ? pz : INFINITY, j < n ? pz : -INFINITY);
+            if ((tid & 31) == 0) s_zr[tid >> 5] = r;
             sj2[2 * tid] = make_ulonglong2(f2_pack(px, px), f2_pack(py, py));
             sj2[2 * tid + 1] = make_ulonglong2(f2_pack(pz, pz), f2_pack(pq, pq));
             __syncthreads();
-#pragma unroll 4
-            for (int k = 0; k < NT; ++k) {
-                const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+            const TileClass tc = classify_tiles(s_zi, s_zr, NT / 32, L, dcz);
+            if (tc.direct) {
+                const f2 sh = f2_pack(tc.shift, tc.shift);
+                f2 Zs[H];
 #pragma unroll
-                for (int h = 0; h < H; ++h)
-                    coulomb_pair_x2<false>(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2, AX[h],
-                                           AY[h], AZ[h], unused);
+                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+                if (tc.apart) {
+#pragma unroll 4
+                    for (int k = 0; k < NT; ++k) {
+                        const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+#pragma unroll
+                        for (int h = 0; h < H; ++h)
+                            coulomb_pair_x2_direct<false>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, c2, AX[h], AY[h],
+                                                          AZ[h], unused);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int k = 0; k < NT; ++k) {
+                        const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+#pragma unroll
+                        for (int h = 0; h < H; ++h)
+                            coulomb_pair_x2_direct<true>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, c2, AX[h], AY[h],
+                                                         AZ[h], unused);
+                    }
+                }
+            } else {
+#pragma unroll 4
+                for (int k = 0; k < NT; ++k) {
+                    const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        coulomb_pair_x2<false>(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2, AX[h],
+                                               AY[h], AZ[h], unused);
+                }
             }
             __syncthreads();
         }
@@ -613,20 +746,30 @@ __global__ void __launch_bounds__(128) k_adj_local(const AdjArgs A) {
 // One j against two m-particles of the pair VJP, packed f32x2 (the scalar loop below, two
 // lanes per instruction).  nQm = -Q_m; mask3 = -3 where r^2 exceeds the clamp, 0 inside it.
 // Accumulates A1 += Q_j/r^3, A2 += c_j/r^3, A3 += k d with k = -3 (Q_j d.c_m - Q_m d.c_j)/r^5,
-// Qp += (d.c_j)/r^3 (the caller negates it).
+// Qp += (d.c_j)/r^3 (the caller negates it).  MINIMG: fold dz to the minimum image (else zm
+// carries the tile pair's uniform shift); CLAMP: some pair of the tiles may be closer than d_c.
 struct VjpJ { f2 x, y, z, Q, cx, cy, cz; };
+template <bool MINIMG, bool CLAMP>
 __device__ __forceinline__ void vjp_pair_x2(f2 xm, f2 ym, f2 zm, f2 nQm, f2 cmx, f2 cmy, f2 cmz, const VjpJ& J,
                                             f2 invL2, f2 M2, f2 nM2, f2 nL2, float c2, f2& A1, f2& A2x, f2& A2y,
                                             f2& A2z, f2& A3x, f2& A3y, f2& A3z, f2& Qp) {
     const f2 dx = f2_sub(xm, J.x), dy = f2_sub(ym, J.y);
     f2 dz = f2_sub(zm, J.z);
-    const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
-    dz = f2_fma(nL2, t, dz);
+    if constexpr (MINIMG) {
+        const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
+        dz = f2_fma(nL2, t, dz);
+    }
     const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
     float ra, rb;
     f2_unpack(r2, ra, rb);
-    const f2 ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
-    const f2 mask3 = f2_pack(ra > c2 ? -3.f : 0.f, rb > c2 ? -3.f : 0.f);
+    f2 ri, mask3;
+    if constexpr (CLAMP) {
+        ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
+        mask3 = f2_pack(ra > c2 ? -3.f : 0.f, rb > c2 ? -3.f : 0.f);
+    } else {
+        ri = f2_pack(rsqrt_ftz(ra), rsqrt_ftz(rb));
+        mask3 = f2_pack(-3.f, -3.f);
+    }
     const f2 ri2 = f2_mul(ri, ri), ri3 = f2_mul(ri2, ri);
     const f2 dcj = f2_fma(dx, J.cx, f2_fma(dy, J.cy, f2_mul(dz, J.cz)));
     const f2 dcm = f2_fma(dx, cmx, f2_fma(dy, cmy, f2_mul(dz, cmz)));
@@ -647,6 +790,7 @@ __global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
     typedef typename Real<P>::T T;
     constexpr int U = adj_ilp<P>();          // particles m per thread
     __shared__ __align__(16) unsigned char smem_raw[P == PDQ_MIXED ? NT * 64 : 7 * NT * sizeof(T)];
+    __shared__ float2 s_zi[NT / 32], s_zr[NT / 32];
     T (*sj)[NT] = reinterpret_cast<T (*)[NT]>(smem_raw);
     const int s = blockIdx.y, tid = threadIdx.x;
     const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
@@ -690,6 +834,15 @@ __global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
             CZ[h] = f2_pack(cmz[2 * h], cmz[2 * h + 1]);
             A1[h] = A2x[h] = A2y[h] = A2z[h] = A3x[h] = A3y[h] = A3z[h] = Qp[h] = 0ull;
         }
+        {
+            float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if ((int64_t)blockIdx.x * NT * U + u * NT + tid < n) { lo = fminf(lo, zm[u]); hi = fmaxf(hi, zm[u]); }
+            const float2 r = warp_range(lo, hi);
+            if ((tid & 31) == 0) s_zi[tid >> 5] = r;
+        }
+        const float dcz = sqrtf(c2) + 1e-3f;
         for (int64_t j0 = 0; j0 < n; j0 += NT) {
             const int64_t j = j0 + tid;
             float v[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -703,15 +856,31 @@ __global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
             sj2[4 * tid + 1] = make_ulonglong2(f2_pack(v[2], v[2]), f2_pack(v[3], v[3]));
             sj2[4 * tid + 2] = make_ulonglong2(f2_pack(v[4], v[4]), f2_pack(v[5], v[5]));
             sj2[4 * tid + 3] = make_ulonglong2(f2_pack(v[6], v[6]), 0ull);
+            const float2 r = warp_range(j < n ? v[2] : INFINITY, j < n ? v[2] : -INFINITY);
+            if ((tid & 31) == 0) s_zr[tid >> 5] = r;
             __syncthreads();
+            const TileClass tc = classify_tiles(s_zi, s_zr, NT / 32, L, dcz);
+            auto tile = [&](auto minimg, auto clamp, const f2* Zt) {
 #pragma unroll 2
-            for (int k = 0; k < NT; ++k) {
-                const ulonglong2 a = sj2[4 * k], b = sj2[4 * k + 1], cc = sj2[4 * k + 2], d = sj2[4 * k + 3];
-                const VjpJ J{a.x, a.y, b.x, b.y, cc.x, cc.y, d.x};
+                for (int k = 0; k < NT; ++k) {
+                    const ulonglong2 a = sj2[4 * k], b = sj2[4 * k + 1], cc = sj2[4 * k + 2], d = sj2[4 * k + 3];
+                    const VjpJ J{a.x, a.y, b.x, b.y, cc.x, cc.y, d.x};
 #pragma unroll
-                for (int h = 0; h < H; ++h)
-                    vjp_pair_x2(X[h], Y[h], Z[h], NQ[h], CX[h], CY[h], CZ[h], J, invL2, M2, nM2, nL2, c2, A1[h],
-                                A2x[h], A2y[h], A2z[h], A3x[h], A3y[h], A3z[h], Qp[h]);
+                    for (int h = 0; h < H; ++h)
+                        vjp_pair_x2<decltype(minimg)::value, decltype(clamp)::value>(
+                            X[h], Y[h], Zt[h], NQ[h], CX[h], CY[h], CZ[h], J, invL2, M2, nM2, nL2, c2, A1[h], A2x[h],
+                            A2y[h], A2z[h], A3x[h], A3y[h], A3z[h], Qp[h]);
+                }
+            };
+            if (tc.direct) {
+                const f2 sh = f2_pack(tc.shift, tc.shift);
+                f2 Zs[H];
+#pragma unroll
+                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+                if (tc.apart) tile(std::false_type{}, std::false_type{}, Zs);
+                else tile(std::false_type{}, std::true_type{}, Zs);
+            } else {
+                tile(std::true_type{}, std::true_type{}, Z);
             }
             __syncthreads();
         }
@@ -862,6 +1031,9 @@ static AdjLayout adj_layout(int64_t N, int32_t S, int32_t C, int64_t n_steps, in
     b += vec * 11;                                 // cotangents, c
     b += vec;                                      // qhat
     b += a256(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));   // classes
+    // per checkpoint, the z-binned order's qhat, classes and permutation; 7 scratch cotangents
+    b += (vec + 2 * a256(sizeof(int32_t) * (size_t)(N > 0 ? N : 1))) * (size_t)L.n_ck;
+    b += vec * 7;
     b += a256(sizeof(double) * (size_t)S * C) * 4; // num, den, nbar, dbar
     L.bytes = b;
     return L;
@@ -944,7 +1116,18 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
     A.wb = (double*)take(vec); A.qb = (double*)take(vec);
     A.cx = (double*)take(vec); A.cy = (double*)take(vec); A.cz = (double*)take(vec);
     A.qhat = (double*)take(vec);
-    A.cls = (int32_t*)take(a256(sizeof(int32_t) * (size_t)(N > 0 ? N : 1)));
+    const size_t ivec = a256(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    A.cls = (int32_t*)take(ivec);
+    // z-binned order of each checkpoint: its qhat, classes and permutation; scratch cotangents
+    std::vector<double*> ck_qh(Ly.n_ck);
+    std::vector<int32_t*> ck_cl(Ly.n_ck), ck_perm(Ly.n_ck);
+    for (int64_t k = 0; k < Ly.n_ck; ++k) {
+        ck_qh[k] = (double*)take(vec);
+        ck_cl[k] = (int32_t*)take(ivec);
+        ck_perm[k] = (int32_t*)take(ivec);
+    }
+    double* scratch[7];
+    for (auto& q : scratch) q = (double*)take(vec);
     const size_t sc = a256(sizeof(double) * (size_t)A.S * A.C);
     A.num = (double*)take(sc); A.den = (double*)take(sc);
     double* nbar = (double*)take(sc);
@@ -981,16 +1164,30 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
         return cudaSuccess;
     };
 
+    // Checkpoint k holds the state z-binned (the pair loops then see tiles of nearby z, see
+    // k_adj_forward); the steps of segment k run in that order with its qhat and classes.
+    const float bpl = (float)(kAdjBins / A.K.L);
+    const double* qh_cur = A.qhat;
+    const int32_t* cl_cur = A.cls;
+    auto checkpoint = [&](int64_t k, const Slot& from) -> cudaError_t {
+        k_adj_sort<<<(unsigned)A.S, 1024, 0, s>>>(batch->offset, from, qh_cur, cl_cur, ck[k], ck_qh[k], ck_cl[k],
+                                                  ck_perm[k], bpl);
+        qh_cur = ck_qh[k];
+        cl_cur = ck_cl[k];
+        A.qhat = ck_qh[k];
+        A.cls = ck_cl[k];
+        return copy_state(from, ck[k]);
+    };
     // seed into segment slot 0, save as checkpoint 0
     A.out = seg[0];
     k_adj_seed<<<dim3((unsigned)((nmax + NT - 1) / NT), (unsigned)A.S), NT, 0, s>>>(A);
     PDQ_CUDA(cudaMemsetAsync(A.num, 0, sc, s));
     PDQ_CUDA(cudaMemsetAsync(A.den, 0, sc, s));
-    PDQ_CUDA(copy_state(ck[0], seg[0]));
+    PDQ_CUDA(checkpoint(0, seg[0]));
     // forward sweep: ping-pong between segment slots 0 and 1, checkpoint every K steps
     for (int64_t n = 0; n < n_steps; ++n) {
         fwd(seg[n & 1], seg[(n + 1) & 1], n, 1);
-        if ((n + 1) % K == 0 && (n + 1) < n_steps) PDQ_CUDA(copy_state(ck[(n + 1) / K], seg[(n + 1) & 1]));
+        if ((n + 1) % K == 0 && (n + 1) < n_steps) PDQ_CUDA(checkpoint((n + 1) / K, seg[(n + 1) & 1]));
     }
     const int nsc = A.S * A.C;
     k_adj_finish<<<(nsc + 255) / 256, 256, 0, s>>>(A.num, A.den, nullptr, nsc, A.K.R, A.K.dt, J, nullptr, nullptr);
@@ -1006,6 +1203,8 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
         for (int64_t kseg = Ly.n_ck - 1; kseg >= 0; --kseg) {
             const int64_t n0 = kseg * K;
             const int64_t len = std::min<int64_t>(K, n_steps - n0);
+            A.qhat = ck_qh[kseg];
+            A.cls = ck_cl[kseg];
             PDQ_CUDA(copy_state(seg[0], ck[kseg]));
             for (int64_t t = 0; t < len; ++t) fwd(seg[t], seg[t + 1], n0 + t, 0);
             for (int64_t t = len - 1; t >= 0; --t) {
@@ -1017,6 +1216,15 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
                 } else {
                     k_adj_local<PDQ_FP64><<<dim3((unsigned)((nmax + 127) / 128), (unsigned)A.S), 128, 0, s>>>(A);
                     k_adj_pairs<PDQ_FP64, NT><<<grid, NT, 0, s>>>(A);
+                }
+            }
+            if (kseg > 0) {
+                // cotangents of checkpoint kseg's binned state -> the order segment kseg-1 ends in
+                double** bars[7] = {&A.xb, &A.yb, &A.zb, &A.vxb, &A.vyb, &A.vzb, &A.wb};
+                for (int q = 0; q < 7; ++q) {
+                    k_adj_unperm<<<dim3((unsigned)((nmax + 255) / 256), (unsigned)A.S), 256, 0, s>>>(
+                        batch->offset, ck_perm[kseg], *bars[q], scratch[q]);
+                    std::swap(*bars[q], scratch[q]);
                 }
             }
             PDQ_CUDA(cudaGetLastError());

@@ -217,4 +217,24 @@ __device__ __forceinline__ void coulomb_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 y
     az = f2_fma(s, dz, az);
 }
 
+// Same pairs when no pair of the (i-tile, j-tile) combination needs the
+// periodic image: dz = (z_i - shift) - z_j directly (the shift is folded into zi).
+// CLAMP = false when every |dz| of the tile pair exceeds the contact distance, so
+// r^2 > c2 and the clamp could not change a result.
+template <bool CLAMP, bool TRACK = false>
+__device__ __forceinline__ void coulomb_pair_x2_direct(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 qj, float c2,
+                                                       f2& ax, f2& ay, f2& az, float& mn) {
+    const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj), dz = f2_sub(zi, zj);
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    if constexpr (TRACK) mn = fminf(mn, fminf(ra > 0.f ? ra : INFINITY, rb > 0.f ? rb : INFINITY));   // not self
+    if constexpr (CLAMP) { ra = fmaxf(ra, c2); rb = fmaxf(rb, c2); }
+    const f2 ri = f2_pack(rsqrt_ftz(ra), rsqrt_ftz(rb));
+    const f2 s = f2_mul(f2_mul(ri, qj), f2_mul(ri, ri));
+    ax = f2_fma(s, dx, ax);
+    ay = f2_fma(s, dy, ay);
+    az = f2_fma(s, dz, az);
+}
+
 }  // namespace pdq
