@@ -35,6 +35,10 @@ import workloads  # noqa: E402
 
 METRIC = "particle-steps/s, batched mixed vs plain FP64 on GB300 at ≤1e-3 rel V_dep error"
 FLOPS_PER_PAIR = 21          # 3 sub, 4 minimum image, 5 r^2, 3 r^-3 q, 6 accumulate (FMA = 2); + 1 rsqrt
+# pair variant 3 (Newton pairs, each unordered pair once): 3 sub, 5 r^2, 2 r^-3, 2 charge products and
+# 12 for the six accumulating FMAs = 24 flops from 16 FP32-pipe lane-operations per unordered pair
+NEWTON_FLOPS_PER_PAIR = 12   # per ordered pair
+NEWTON_FLOPS_PER_LANE_OP = 24.0 / 16.0
 KSTEP_DRAM_BYTES = {2: 495.4e6}   # per k_step launch on 4,557,792 particles (ncu, current kernel)
 SM_COUNT, FP32_LANES = 152, 128
 FP64_NOMINAL_TFLOPS = 1.25
@@ -290,7 +294,9 @@ def run_ours(args):
         binned = prec == pdq.MIXED and cfg.compact_every > 0
         ci = min(cfg.compact_every, 10) if binned else cfg.compact_every
         n_compact = sum(1 for k in range(args.steps - 1) if ci and (s0 + k + 1) % ci == 0)
-        launches = int(binned) + 1 + args.steps + 2 * n_compact   # sort, build_items, k_step per step, re-bin + items
+        # sort, build_items, the step kernel(s) per step (Newton pairs: pair sums + update), re-bin + items
+        per_step = 2 if prec == pdq.MIXED and cfg.variant == 3 and not args.contact else 1
+        launches = int(binned) + 1 + per_step * args.steps + 2 * n_compact
 
         # e2e: state in pinned host memory; upload, one step, download state + tallies
         e2e = None
@@ -356,13 +362,19 @@ def run_ours(args):
         return
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if prec == pdq.MIXED:
+    newton = prec == pdq.MIXED and cfg.variant == 3 and not args.contact
+    flops_per_pair = NEWTON_FLOPS_PER_PAIR if newton else FLOPS_PER_PAIR
+    if newton:
+        peak_tflops = SM_COUNT * FP32_LANES * NEWTON_FLOPS_PER_LANE_OP * sm_max * 1e6 / 1e12
+        peak_note = ("FP32 pipe peak for the Newton-pair instruction mix = 152 SMs x 128 lanes x %.0f MHz "
+                     "(max SM clock) x 24 flops / 16 lane-ops" % sm_max)
+    elif prec == pdq.MIXED:
         peak_tflops = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
         peak_note = "FP32 pipe peak = 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % sm_max
     else:
         peak_tflops = FP64_NOMINAL_TFLOPS
         peak_note = "FP64 nominal dense peak of the GB300 (1.25 TFLOP/s)"
-    achieved = FLOPS_PER_PAIR * pairs / (ms / 1e3) / 1e12
+    achieved = flops_per_pair * pairs / (ms / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": psteps_all / (ms_max / 1e3), "unit": "particle-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -381,7 +393,9 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (
                        sum(t.numel() * t.element_size() for t in state.current() if t is not None) / 1e9),
                    "parallelism": "samples sharded by rank" if world > 1 else "1 GPU",
-                   "tile": {"block": cfg.block, "i_per_thread": (8 if cfg.variant == 2 else 4) if prec == pdq.MIXED else 1,
+                   "tile": {"block": cfg.block,
+                            "i_per_thread": (8 if cfg.variant in (2, 3) and not args.contact else 4)
+                            if prec == pdq.MIXED else 1,
                             "variant": cfg.variant, "autotuned": args.block == 0 and not args.no_autotune}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
@@ -391,9 +405,12 @@ def run_ours(args):
                      # count of this launch; null for a variant without a capture of this kernel
                      "traffic": KSTEP_DRAM_BYTES[cfg.variant] / 4557792 * float(np.sum(counts))
                      if prec == pdq.MIXED and cfg.variant in KSTEP_DRAM_BYTES else None,
-                     "kernel": "k_step (all-pairs Coulomb + local step)",
+                     "kernel": "k_pairs_sym (Newton-pair Coulomb sums), then the given-sums k_step update"
+                               if newton else "k_step (all-pairs Coulomb + local step)",
                      "note": "%s; %d flops per ordered pair; time per step from CUDA events over the timed "
-                             "region" % (peak_note, FLOPS_PER_PAIR)},
+                             "region%s" % (peak_note, flops_per_pair,
+                                           " (both kernels and the zeroing of the sums: a lower bound on the "
+                                           "pair kernel's own rate)" if newton else "")},
         "clocks": clocks,
         "gpu_launches": int(launches),
         "e2e": e2e,

@@ -24,7 +24,8 @@
 
 namespace pdq {
 
-enum { CTL_STEP = 0, CTL_QUEUE = 1, CTL_DONE = 2, CTL_ERROR = 3, CTL_NITEMS = 4 };
+// CTL_QUEUE2 / CTL_DONE2: work queue and done counter of the Newton-pair sum kernel (pair variant 3)
+enum { CTL_STEP = 0, CTL_QUEUE = 1, CTL_DONE = 2, CTL_ERROR = 3, CTL_NITEMS = 4, CTL_QUEUE2 = 5, CTL_DONE2 = 6 };
 enum { ERR_NONFINITE = 1 };
 
 
@@ -178,6 +179,9 @@ struct StepArgs {
     int jsplit; int64_t cap; double* part; int* tile_cnt;
     // Coulomb sums given per particle ([cap][3], e.g. from P3M): replace the pair loop when set
     const double* ext;
+    // pair variant 3: FP32 Coulomb sums [cap] (x, y, z, unused) accumulated by k_pairs_sym; the
+    // given-sums step (V = 5) reads them instead of ext when set
+    float4* acc4;
     // host only: upper bound on the work items of a launch (the persistent grid is capped by it,
     // so that few items spread one per CTA over the SMs instead of piling onto the first CTAs)
     int64_t max_items;
@@ -555,11 +559,14 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
             for (int d = 16; d > 0; d >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, d));
             if (lane == 0) s_vi[tid >> 5] = vmax;
         }
-        if constexpr (V == 5) {      // Coulomb sums given (P3M): no pair loop
+        if constexpr (V == 5) {      // Coulomb sums given (P3M, or the Newton-pair kernel): no pair loop
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int64_t g = base + u * NT + tid;
-                if (g < end) { ax[u] = (T)A.ext[3 * g]; ay[u] = (T)A.ext[3 * g + 1]; az[u] = (T)A.ext[3 * g + 2]; }
+                if (g < end) {
+                    if (A.acc4) { const float4 a = A.acc4[g]; ax[u] = (T)a.x; ay[u] = (T)a.y; az[u] = (T)a.z; }
+                    else { ax[u] = (T)A.ext[3 * g]; ay[u] = (T)A.ext[3 * g + 1]; az[u] = (T)A.ext[3 * g + 2]; }
+                }
             }
         } else if ((K.forces & PDQ_F_COULOMB) || CT) {
             if constexpr (P == PDQ_MIXED) {
@@ -869,6 +876,237 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
 }
 
 // ---------------------------------------------------------------------------
+// Pair variant 3 (MIXED): the Coulomb sums with each unordered pair evaluated once
+// (Newton's third law, G(-d) = -G(d)): a_i += q_j G(d) and a_j -= q_i G(d), d = x_i - x_j,
+// G(d) = d / max(|d|, d_c)^3.  Per packed pair (two i-particles, one j) 16 f32x2
+// operations and 2 rsqrt give four ordered pairs, against 12 and 2 for two ordered pairs
+// in the one-sided loop.  MINIMG: per-pair minimum image in z (else the tile pair's uniform
+// shift is folded into zi); CLAMP: some pair of the tiles may come closer than d_c.
+// nqi = -q_i; the j-side sums of the two lanes land in (jx, jy, jz).
+// ---------------------------------------------------------------------------
+template <bool MINIMG, bool CLAMP>
+__device__ __forceinline__ void coulomb_pair_x2_sym(f2 xi, f2 yi, f2 zi, f2 nqi, f2 xj, f2 yj, f2 zj, f2 qj,
+                                                    f2 invL2, f2 M2, f2 nM2, f2 nL2, float c2, f2& ax, f2& ay,
+                                                    f2& az, f2& jx, f2& jy, f2& jz) {
+    const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj);
+    f2 dz = f2_sub(zi, zj);
+    if constexpr (MINIMG) {
+        const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
+        dz = f2_fma(nL2, t, dz);
+    }
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    if constexpr (CLAMP) { ra = fmaxf(ra, c2); rb = fmaxf(rb, c2); }
+    const f2 ri = f2_pack(rsqrt_ftz(ra), rsqrt_ftz(rb));
+    const f2 ri3 = f2_mul(f2_mul(ri, ri), ri);
+    const f2 si = f2_mul(ri3, qj), sj = f2_mul(ri3, nqi);
+    ax = f2_fma(si, dx, ax);
+    ay = f2_fma(si, dy, ay);
+    az = f2_fma(si, dz, az);
+    jx = f2_fma(sj, dx, jx);
+    jy = f2_fma(sj, dy, jy);
+    jz = f2_fma(sj, dz, jz);
+}
+
+// z-range classification of an i-range [alo, ahi] against a j-range [blo, bhi] (as in k_step):
+// inside one period window the minimum image is a uniform shift; z-separated by more than
+// dcz the clamp is dropped too.
+struct ZClass { bool direct, apart; float shift; };
+__device__ __forceinline__ ZClass zclass(float alo, float ahi, float blo, float bhi, float Lf, float dcz) {
+    const float dlo = alo - bhi, dhi = ahi - blo, halfL = 0.5f * Lf;
+    ZClass t{true, false, 0.f};
+    if (dlo > -halfL && dhi < halfL) t.shift = 0.f;
+    else if (dlo > halfL && dhi < 3.f * halfL) t.shift = Lf;
+    else if (dhi < -halfL && dlo > -3.f * halfL) t.shift = -Lf;
+    else t.direct = false;
+    t.apart = t.direct && ((dlo - t.shift > dcz) || (dhi - t.shift < -dcz));
+    return t;
+}
+
+// Coulomb sums of pair variant 3 into A.acc4 (zeroed before the launch); the given-sums step
+// then does the local update.  Persistent CTAs take (sample, i-tile) items from CTL_QUEUE2; an
+// item covers the pairs of its NT*U i-particles with every particle of the sample from the
+// tile's first index on:
+//   - its own tile (the diagonal block): one-sided, each i against every j of the tile;
+//   - the later particles: Newton pairs.  A j-tile of NT particles is staged in shared memory;
+//     each warp takes it in groups of 32 j, lane l holding j = (l + k) mod 32 at step k and
+//     passing that j's running sum to lane l - 1 after the step, so that within a warp no two
+//     lanes touch the same j and after 32 steps every sum is back at its own lane.  The per-warp
+//     sums of the tile are added in shared memory and leave with one float4 atomic per j.
+// The earlier particles of the sample reach this tile as the j side of earlier tiles' items.
+// Padding particles sit far off the axis (x = +-1e15) with zero charge, so they add nothing.
+template <int NT, int U>
+__global__ void __launch_bounds__(NT) k_pairs_sym(const StepArgs A) {
+    constexpr int W = NT / 32, H = U / 2;
+    static_assert(U % 2 == 0 && NT % 32 == 0, "packed pairs over whole warps");
+    // j-tile, pre-duplicated: (x,x,y,y) at sj2[j], (z,z,q,q) at sj2[NT + j] (16-byte stride, so the
+    // skewed per-lane reads of the Newton loop are free of bank conflicts)
+    __shared__ __align__(32) ulonglong2 sj2[2 * NT];
+    __shared__ float s_jacc[W][3][NT];                    // per-warp j-side sums of the staged tile
+    __shared__ float2 s_zr[W];                            // z range of each 32-j group of the tile
+    __shared__ int s_item;
+    const StepConst& K = A.K;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n_items = A.ctl[CTL_NITEMS];
+    const float4* __restrict__ pos_in = (const float4*)A.pos_in;
+    const float Lf = (float)K.L, M = 12582912.0f;
+    const f2 invL2 = f2_pack((float)K.invL, (float)K.invL), M2 = f2_pack(M, M), nM2 = f2_pack(-M, -M);
+    const f2 nL2 = f2_pack(-Lf, -Lf);
+    const float c2 = (float)K.contact2f;
+    const float dcz = sqrtf(c2) + 1e-3f;     // contact distance + rounding margin
+    const float kPadI = 1e15f, kPadJ = -1e15f;
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd((unsigned long long*)&A.ctl[CTL_QUEUE2], 1ull);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;
+        const int2 it = A.items[item];
+        const int64_t o = A.offset[it.x];
+        const int64_t end = o + A.count[it.x];
+        const int64_t base = o + (int64_t)it.y * (NT * U);
+        const int64_t dend = base + NT * U < end ? base + NT * U : end;
+        f2 X[H], Y[H], Z[H], NQ[H], AX[H], AY[H], AZ[H];
+        float ilo = INFINITY, ihi = -INFINITY;
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            float4 p[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int64_t g = base + (2 * h + e) * NT + tid;
+                if (g < end) {
+                    p[e] = pos_in[g];
+                    ilo = fminf(ilo, p[e].z);
+                    ihi = fmaxf(ihi, p[e].z);
+                } else {
+                    p[e] = make_float4(kPadI, 0.f, 0.f, 0.f);
+                }
+            }
+            X[h] = f2_pack(p[0].x, p[1].x);
+            Y[h] = f2_pack(p[0].y, p[1].y);
+            Z[h] = f2_pack(p[0].z, p[1].z);
+            NQ[h] = f2_pack(-p[0].w, -p[1].w);
+            AX[h] = AY[h] = AZ[h] = 0ull;
+        }
+        for (int d = 16; d > 0; d >>= 1) {     // this warp's i range
+            ilo = fminf(ilo, __shfl_xor_sync(0xffffffffu, ilo, d));
+            ihi = fmaxf(ihi, __shfl_xor_sync(0xffffffffu, ihi, d));
+        }
+        for (int64_t j0 = base; j0 < end; j0 += NT) {
+            const bool diag = j0 < dend;
+            const int64_t jlim = diag ? dend : end;
+            const int64_t j = j0 + tid;
+            const float4 pj = j < jlim ? pos_in[j] : make_float4(kPadJ, 0.f, 0.f, 0.f);
+            float jlo = j < jlim ? pj.z : INFINITY, jhi = j < jlim ? pj.z : -INFINITY;
+            for (int d = 16; d > 0; d >>= 1) {
+                jlo = fminf(jlo, __shfl_xor_sync(0xffffffffu, jlo, d));
+                jhi = fmaxf(jhi, __shfl_xor_sync(0xffffffffu, jhi, d));
+            }
+            if (lane == 0) s_zr[warp] = make_float2(jlo, jhi);
+            sj2[tid] = make_ulonglong2(f2_pack(pj.x, pj.x), f2_pack(pj.y, pj.y));
+            sj2[NT + tid] = make_ulonglong2(f2_pack(pj.z, pj.z), f2_pack(pj.w, pj.w));
+            __syncthreads();
+            if (diag) {
+                // one-sided over the tile's own particles (self pair: d = 0 adds nothing)
+                float blo = INFINITY, bhi = -INFINITY;
+#pragma unroll
+                for (int w = 0; w < W; ++w) { blo = fminf(blo, s_zr[w].x); bhi = fmaxf(bhi, s_zr[w].y); }
+                const ZClass zc = zclass(ilo, ihi, blo, bhi, Lf, dcz);
+                float mn = 0.f;
+                if (zc.direct) {
+                    const f2 sh = f2_pack(zc.shift, zc.shift);
+                    f2 Zs[H];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+#pragma unroll 4
+                    for (int k = 0; k < NT; ++k) {
+                        const ulonglong2 a = sj2[k], b = sj2[NT + k];
+#pragma unroll
+                        for (int h = 0; h < H; ++h)
+                            coulomb_pair_x2_direct<true>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, c2, AX[h], AY[h],
+                                                         AZ[h], mn);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int k = 0; k < NT; ++k) {
+                        const ulonglong2 a = sj2[k], b = sj2[NT + k];
+#pragma unroll
+                        for (int h = 0; h < H; ++h)
+                            coulomb_pair_x2<false>(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2,
+                                                   AX[h], AY[h], AZ[h], mn);
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
+            // Newton pairs with the later particles, one 32-j group at a time
+#pragma unroll 1
+            for (int g = 0; g < W; ++g) {
+                const float2 zr = s_zr[g];
+                const ZClass zc = zclass(ilo, ihi, zr.x, zr.y, Lf, dcz);
+                float jx = 0.f, jy = 0.f, jz = 0.f;
+                auto group = [&](auto minimg, auto clamp, const f2* Zt) {
+#pragma unroll 2
+                    for (int k = 0; k < 32; ++k) {
+                        const int jj = g * 32 + ((lane + k) & 31);
+                        const ulonglong2 a = sj2[jj], b = sj2[NT + jj];
+                        f2 JX = f2_pack(jx, 0.f), JY = f2_pack(jy, 0.f), JZ = f2_pack(jz, 0.f);
+#pragma unroll
+                        for (int h = 0; h < H; ++h)
+                            coulomb_pair_x2_sym<decltype(minimg)::value, decltype(clamp)::value>(
+                                X[h], Y[h], Zt[h], NQ[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2, AX[h], AY[h],
+                                AZ[h], JX, JY, JZ);
+                        float l0, l1;
+                        f2_unpack(JX, l0, l1); jx = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                        f2_unpack(JY, l0, l1); jy = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                        f2_unpack(JZ, l0, l1); jz = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                    }
+                };
+                if (zc.direct) {
+                    const f2 sh = f2_pack(zc.shift, zc.shift);
+                    f2 Zs[H];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+                    if (zc.apart) group(std::false_type{}, std::false_type{}, Zs);
+                    else group(std::false_type{}, std::true_type{}, Zs);
+                } else {
+                    group(std::true_type{}, std::true_type{}, Z);
+                }
+                s_jacc[warp][0][g * 32 + lane] = jx;
+                s_jacc[warp][1][g * 32 + lane] = jy;
+                s_jacc[warp][2][g * 32 + lane] = jz;
+            }
+            __syncthreads();
+            if (j < end) {
+                float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+                for (int w = 0; w < W; ++w) { sx += s_jacc[w][0][tid]; sy += s_jacc[w][1][tid]; sz += s_jacc[w][2][tid]; }
+                atomicAdd(&A.acc4[j], make_float4(sx, sy, sz, 0.f));
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            float a0[3], a1[3];
+            f2_unpack(AX[h], a0[0], a1[0]);
+            f2_unpack(AY[h], a0[1], a1[1]);
+            f2_unpack(AZ[h], a0[2], a1[2]);
+            const int64_t g0 = base + (2 * h) * NT + tid, g1 = g0 + NT;
+            if (g0 < end) atomicAdd(&A.acc4[g0], make_float4(a0[0], a0[1], a0[2], 0.f));
+            if (g1 < end) atomicAdd(&A.acc4[g1], make_float4(a1[0], a1[1], a1[2], 0.f));
+        }
+    }
+    if (tid == 0) {
+        __threadfence();
+        const unsigned long long prev = atomicAdd((unsigned long long*)&A.ctl[CTL_DONE2], 1ull);
+        if (prev == gridDim.x - 1) {   // last CTA: reset the queue for the next step
+            A.ctl[CTL_QUEUE2] = 0;
+            A.ctl[CTL_DONE2] = 0;
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Work items: samples ordered by live count (largest first), JS items per i-tile
 // (one per j-chunk; JS = 1 unless the FP64 j-split is on), item.y = tile * JS + chunk.
 // Single CTA of 1024 threads; order[] and items[] live in the caller workspace.
@@ -934,6 +1172,8 @@ __global__ void __launch_bounds__(1024) k_build_items(const int32_t* __restrict_
         ctl[CTL_NITEMS] = running;
         ctl[CTL_QUEUE] = 0;
         ctl[CTL_DONE] = 0;
+        ctl[CTL_QUEUE2] = 0;
+        ctl[CTL_DONE2] = 0;
     }
 }
 
@@ -1109,11 +1349,15 @@ static int tile_threads(const pdq_state* st, const pdq_step_cfg* cfg) {
     if (cfg && cfg->block) return cfg->block;
     return st->precision == PDQ_FP64 ? 128 : 128;
 }
-// particles per thread: FP64 1; MIXED 4 (two packed pairs), 8 for pair variant 2
+// Pair variant 3 (Newton pairs) applies to MIXED runs without contact forces.
+static bool newton_pairs(const pdq_state* st, const pdq_step_cfg* cfg) {
+    return cfg && cfg->variant == 3 && st->precision == PDQ_MIXED && !(cfg->forces & PDQ_F_CONTACT);
+}
+// particles per thread: FP64 1; MIXED 4 (two packed pairs), 8 for pair variants 2 and 3
 static int tile_ilp(const pdq_state* st, const pdq_step_cfg* cfg = nullptr) {
     if (st->precision == PDQ_FP64) return 1;
     if (cfg && (cfg->forces & PDQ_F_CONTACT)) return 4;      // contact runs: variant 0 layout
-    return (cfg && cfg->variant == 2) ? 8 : 4;
+    return (cfg && (cfg->variant == 2 || cfg->variant == 3)) ? 8 : 4;
 }
 
 static int sm_count() {
@@ -1140,11 +1384,32 @@ static int launch_step(const StepArgs& A, cudaStream_t s) {
     return PDQ_OK;
 }
 
+// Pair variant 3: the Newton-pair sums (NT threads, 8 particles per thread) into A.acc4, then
+// the given-sums step over the same tiles (2 NT threads, 4 particles per thread).
+template <int NT>
+static int launch_newton(const StepArgs& A, cudaStream_t s) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_sym<NT, 8>, NT, 0);
+        if (per_sm <= 0) per_sm = 1;
+    }
+    const int64_t full = (int64_t)sm_count() * per_sm;
+    PDQ_CUDA(cudaMemsetAsync(A.acc4, 0, sizeof(float4) * (size_t)(A.cap > 0 ? A.cap : 1), s));
+    k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, std::min(full, A.max_items > 0 ? A.max_items : full)), NT, 0,
+                         s>>>(A);
+    return launch_step<PDQ_MIXED, 2 * NT, 4, 5>(A, s);
+}
+
 // variant: MIXED pair math, 0 = all packed f32x2, 1 = packed with scalar accumulation,
-// 2 = as 0 with 8 particles per thread.
+// 2 = as 0 with 8 particles per thread, 3 = Newton pairs (A.acc4 set; not with contact).
 // contact: the particle-particle contact variant (V = 4), whatever the variant; given
 // Coulomb sums (A.ext, P3M): V = 5, no pair loop.
 static int dispatch_step(int prec, int NT, int variant, bool contact, const StepArgs& A, cudaStream_t s) {
+    if (A.acc4) {
+        if (NT == 64) return launch_newton<64>(A, s);
+        if (NT == 128) return launch_newton<128>(A, s);
+        return PDQ_ERR_INVALID_ARG;
+    }
     if (A.ext) {
         if (prec == PDQ_FP64) {
             if (NT == 32) return launch_step<PDQ_FP64, 32, 1, 5>(A, s);
@@ -1211,14 +1476,20 @@ static int j_split(const pdq_state* st, int TI, bool contact = false) {
 }
 
 // Workspace: items | order | tag scratch of the z-binning sort;
-// FP64 with JS > 1: tile counters | partial sums [JS][3][capacity].
+// FP64 with JS > 1: tile counters | partial sums [JS][3][capacity];
+// pair variant 3: FP32 sums float4 [capacity].
 static void workspace_layout(const pdq_state* st, int TI, size_t* items_bytes, size_t* total,
-                             size_t* cnt_off = nullptr, size_t* part_off = nullptr, bool contact = false) {
+                             size_t* cnt_off = nullptr, size_t* part_off = nullptr, bool contact = false,
+                             size_t* acc_off = nullptr, bool newton = false) {
     const int JS = j_split(st, TI, contact);
     const int64_t max_tiles = st->capacity / TI + st->n_samples + 1;
     *items_bytes = align256(sizeof(int2) * (size_t)max_tiles * JS);
     *total = *items_bytes + align256(sizeof(int32_t) * (size_t)st->n_samples);
     *total += align256(sizeof(int2) * (size_t)(st->capacity > 0 ? st->capacity : 1));   // tag scratch of the z-binning
+    if (newton) {
+        if (acc_off) *acc_off = *total;
+        *total += align256(sizeof(float4) * (size_t)(st->capacity > 0 ? st->capacity : 1));
+    }
     if (JS > 1) {
         if (cnt_off) *cnt_off = *total;
         *total += align256(sizeof(int) * (size_t)max_tiles);
@@ -1329,7 +1600,7 @@ extern "C" int pdq_step_workspace_size(const pdq_state* st, const pdq_step_cfg* 
     // sized for the narrower of the configured tile and 4 particles per thread (the given-sums
     // step of the P3M driver uses 4), so one workspace serves both step entry points
     workspace_layout(st, tile_threads(st, cfg) * std::min(tile_ilp(st, cfg), 4), &ib, &tot, nullptr, nullptr,
-                     cfg && (cfg->forces & PDQ_F_CONTACT));
+                     cfg && (cfg->forces & PDQ_F_CONTACT), nullptr, newton_pairs(st, cfg));
     *bytes = tot;
     return PDQ_OK;
 }
@@ -1352,7 +1623,7 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
     int rc = validate_state(st);
     if (rc) return rc;
     if (!(cfg->dt > 0) || (cfg->mode != PDQ_STICK && cfg->mode != PDQ_REBOUND) ||
-        (cfg->forces & ~(PDQ_F_ALL | PDQ_F_CONTACT)) || cfg->compact_every < 0 || cfg->variant < 0 || cfg->variant > 2)
+        (cfg->forces & ~(PDQ_F_ALL | PDQ_F_CONTACT)) || cfg->compact_every < 0 || cfg->variant < 0 || cfg->variant > 3)
         return PDQ_ERR_INVALID_ARG;
     const bool contact = (cfg->forces & PDQ_F_CONTACT) != 0;
     if (contact && (!(phys->restitution > 0.0 && phys->restitution <= 1.0) || !(phys->tau_col_steps > 0.0)))
@@ -1361,8 +1632,10 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
     const int NT = tile_threads(st, cfg);
     const int U = ext ? (st->precision == PDQ_FP64 ? 1 : 4) : tile_ilp(st, cfg);   // given sums: 4 per thread
     if (NT != 64 && NT != 128 && NT != 256 && !(NT == 32 && st->precision == PDQ_FP64)) return PDQ_ERR_INVALID_ARG;
-    size_t items_bytes, need, cnt_off = 0, part_off = 0;
-    workspace_layout(st, NT * U, &items_bytes, &need, &cnt_off, &part_off, contact);
+    const bool newton = !ext && newton_pairs(st, cfg);
+    if (newton && NT == 256) return PDQ_ERR_INVALID_ARG;      // its update step would need 512 threads
+    size_t items_bytes, need, cnt_off = 0, part_off = 0, acc_off = 0;
+    workspace_layout(st, NT * U, &items_bytes, &need, &cnt_off, &part_off, contact, &acc_off, newton);
     if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return PDQ_ERR_WORKSPACE;
     const int JS = j_split(st, NT * U, contact || ext);
     if (n_steps == 0) return PDQ_OK;
@@ -1388,6 +1661,7 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
     A.jsplit = JS;
     A.cap = st->capacity;
     A.ext = ext;
+    if (newton) A.acc4 = (float4*)((char*)workspace + acc_off);
     A.max_items = (st->capacity / (NT * U) + st->n_samples + 1) * JS;
     if (JS > 1) {
         A.tile_cnt = (int*)((char*)workspace + cnt_off);
@@ -1421,7 +1695,8 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
         for (int64_t k = 0; k < n_steps; ++k) {
             A.pos_in = st->pos[cur]; A.vel_in = st->vel[cur]; A.xy_in = (const double2*)st->xy[cur];
             A.pos_out = st->pos[cur ^ 1]; A.vel_out = st->vel[cur ^ 1]; A.xy_out = (double2*)st->xy[cur ^ 1];
-            dispatch_step(st->precision, NT, cfg->variant, contact, A, s);
+            const int r = dispatch_step(st->precision, NT, cfg->variant, contact, A, s);
+            if (r) return r;
             cur ^= 1;
             ++stepi;
             if (rebin > 0 && stepi % rebin == 0 && k + 1 < n_steps) {
@@ -1561,7 +1836,7 @@ static size_t autotune_scratch_offset(const pdq_state* st) {
     size_t best = 0;
     for (int k = 0; k < (f64 ? 4 : 6); ++k) {
         size_t ib, tot;
-        workspace_layout(st, f64 ? tiles_f64[k] : tiles_mixed[k], &ib, &tot);
+        workspace_layout(st, f64 ? tiles_f64[k] : tiles_mixed[k], &ib, &tot, nullptr, nullptr, false, nullptr, !f64);
         if (tot > best) best = tot;
     }
     return best;
@@ -1612,7 +1887,7 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
     }
     const int blocks[4] = {64, 128, 256, 32};
     const int n_blk = st->precision == PDQ_FP64 ? 4 : 3;    // 32-thread tiles: FP64 only
-    const int n_var = st->precision == PDQ_MIXED && !(cfg->forces & PDQ_F_CONTACT) ? 3 : 1;
+    const int n_var = st->precision == PDQ_MIXED && !(cfg->forces & PDQ_F_CONTACT) ? 4 : 1;
     cudaEvent_t e0, e1;
     PDQ_CUDA(cudaEventCreate(&e0));
     PDQ_CUDA(cudaEventCreate(&e1));
@@ -1622,6 +1897,7 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
     const int64_t step0 = st->step;
     for (int bi = 0; bi < n_blk && rc == PDQ_OK; ++bi) {
         for (int v = 0; v < n_var && rc == PDQ_OK; ++v) {
+            if (v == 3 && blocks[bi] == 256) continue;       // Newton pairs: 64 or 128 threads
             pdq_step_cfg c = *cfg;
             c.block = blocks[bi];
             c.variant = v;

@@ -119,3 +119,35 @@ def test_contact_and_p3m_arguments_rejected_on_host(pdq):
     cfg = pdq.step_cfg(0.05, forces=pdq.F_ALL | pdq.F_CONTACT)
     assert L.pdq_step_particles_p3m(None, C.byref(p), C.byref(s), None, C.byref(cfg), 1, C.byref(t), fake, None, 0,
                                     None) == -1
+
+
+def _fake_mixed_state(pdq, capacity):
+    s = pdq.StateStruct()
+    s.precision, s.n_samples, s.n_classes, s.capacity = 1, 2, 1, capacity
+    s.st_plus[0] = 1.0
+    s.offset = s.count = s.tag = s.ctl = 16
+    for h in range(2):
+        s.pos[h] = s.vel[h] = s.xy[h] = 16
+    return s
+
+
+def test_newton_pair_variant_host_logic(pdq):
+    # pair variant 3 keeps FP32 sums float4 [capacity] in the workspace; it runs at 64 or 128
+    # threads (its update step uses twice as many), and variants above 3 are rejected
+    L = pdq.lib()
+    s = _fake_mixed_state(pdq, 100_000)
+    sizes = {}
+    for v in (2, 3):
+        cfg = pdq.step_cfg(0.05, block=128, variant=v)
+        n = C.c_size_t()
+        assert L.pdq_step_workspace_size(C.byref(s), C.byref(cfg), C.byref(n)) == 0
+        sizes[v] = n.value
+    assert sizes[3] - sizes[2] >= 16 * 100_000
+    t = pdq.TallyStruct()
+    t.n_dep = t.n_alive = 16
+    fake = C.c_void_p(16)
+    for block, variant in ((256, 3), (128, 4)):
+        cfg = pdq.step_cfg(0.05, block=block, variant=variant)
+        rc = L.pdq_step_particles(fake, C.byref(pdq.phys_default()), C.byref(s), fake, C.byref(cfg), 1, C.byref(t),
+                                  C.c_void_p(256), 1 << 40, None)
+        assert rc == -1, (block, variant)

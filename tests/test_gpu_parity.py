@@ -254,10 +254,12 @@ def test_fp64_lognormal_charge_parity(pdq, fields):
     _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 1e-9, 1e-9)
 
 
-def test_mixed_parity(pdq, fields):
-    # FP32 pair sum / interpolation / velocities, FP64 wall-normal position
+@pytest.mark.parametrize("variant,block", [(0, 0), (3, 64), (3, 128)])
+def test_mixed_parity(pdq, fields, variant, block):
+    # FP32 pair sum / interpolation / velocities, FP64 wall-normal position; variant 3 evaluates
+    # each pair once (Newton pairs) and sums through FP32 atomics
     counts = [1000, 333, 129]
-    st, tally, ost, nd, na = _run_both(pdq, fields, 1, counts, ST3, PRM3, 20, {})
+    st, tally, ost, nd, na = _run_both(pdq, fields, 1, counts, ST3, PRM3, 20, {"variant": variant}, block=block)
     _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 2e-6, 2e-5, max_flip=0.005)
 
 
@@ -294,7 +296,7 @@ def test_edge_cases(pdq, fields):
         pdq.step_particles(f, phys, st, prm, cfg, 1, tally, ws[:16])
 
 
-@pytest.mark.parametrize("variant", [0, 2])
+@pytest.mark.parametrize("variant", [0, 2, 3])
 def test_mixed_binned_compaction_parity(pdq, fields, variant):
     # MIXED with compaction: particles are z-binned at the start of the call and at every
     # compaction, and most tile pairs skip the per-pair minimum image (uniform shift of 0 or
