@@ -39,7 +39,9 @@ FLOPS_PER_PAIR = 21          # 3 sub, 4 minimum image, 5 r^2, 3 r^-3 q, 6 accumu
 # 12 for the six accumulating FMAs = 24 flops from 16 FP32-pipe lane-operations per unordered pair
 NEWTON_FLOPS_PER_PAIR = 12   # per ordered pair
 NEWTON_FLOPS_PER_LANE_OP = 24.0 / 16.0
-KSTEP_DRAM_BYTES = {2: 495.4e6}   # per k_step launch on 4,557,792 particles (ncu, current kernel)
+# DRAM bytes per launch of the dominant kernel on 4,557,792 particles (ncu): k_step for pair variant 2,
+# k_pairs_sym for pair variant 3
+KSTEP_DRAM_BYTES = {2: 495.4e6, 3: 178.8e6}
 SM_COUNT, FP32_LANES = 152, 128
 FP64_NOMINAL_TFLOPS = 1.25
 
@@ -399,12 +401,13 @@ def run_ours(args):
                             "variant": cfg.variant, "autotuned": args.block == 0 and not args.no_autotune}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
-                     # dram bytes read + written per launch from the ncu capture in
-                     # profiles/k_step_mixed_batched.md (4,557,792 particles, z-binned kernel with
-                     # clamp-free tile pairs, pair variant 2: 495.4 MB), scaled by the particle
-                     # count of this launch; null for a variant without a capture of this kernel
+                     # dram bytes read + written per launch from the ncu captures in
+                     # profiles/k_step_mixed_batched.md (pair variant 2: 495.4 MB) and
+                     # profiles/k_pairs_sym_batched.md (variant 3: 178.8 MB), both on 4,557,792
+                     # particles, scaled by the particle count of this launch; null for a
+                     # variant without a capture of its kernel
                      "traffic": KSTEP_DRAM_BYTES[cfg.variant] / 4557792 * float(np.sum(counts))
-                     if prec == pdq.MIXED and cfg.variant in KSTEP_DRAM_BYTES else None,
+                     if prec == pdq.MIXED and cfg.variant in KSTEP_DRAM_BYTES and not args.contact else None,
                      "kernel": "k_pairs_sym (Newton-pair Coulomb sums), then the given-sums k_step update"
                                if newton else "k_step (all-pairs Coulomb + local step)",
                      "note": "%s; %d flops per ordered pair; time per step from CUDA events over the timed "
