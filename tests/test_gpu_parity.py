@@ -361,3 +361,43 @@ def test_capture_efficiency(pdq, fields):
     v = torch.tensor([[1e-3, 2e-2], [0.0, 5e-1]], dtype=torch.float64, device="cuda")
     ce = pdq.capture_efficiency(f, pdq.phys_default(), v)
     assert torch.allclose(ce.cpu(), v.cpu() * oracle.capture_factor(of), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("counts", [[0, 5, 1, 0], [1024, 1025, 1023, 2049]])
+def test_mixed_newton_pairs_edge_sizes(pdq, fields, counts):
+    # pair variant 3 at 128 threads x 8 particles: 1,024-particle tiles; empty and one-particle
+    # samples, samples of exactly one tile, one tile +-1 and two tiles + 1 (the boundary between a
+    # tile's own block and the later particles), with compaction every step
+    prm = np.tile(PRM3[:1], (len(counts), 1))
+    st, tally, ost, nd, na = _run_both(pdq, fields, 1, counts, ST3, prm, 5, {"variant": 3, "compact_every": 1},
+                                       block=128)
+    _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 2e-6, 2e-5, max_flip=0.005)
+    assert np.array_equal(tally.n_alive.cpu().numpy(), na)
+
+
+def test_mixed_newton_pairs_graph_replay(pdq, fields):
+    # graph mode (three replays of a captured 2-step call) against direct launches: the float
+    # atomics of variant 3 sum in a run-dependent order, so the bar is the MIXED one
+    f, of, grid, _ = fields
+    counts = [1500, 700]
+    prm = PRM3[:2]
+    stream = torch.cuda.Stream()
+    runs = []
+    for graph in (True, False):
+        phys, st, p, ost, off = _setup(pdq, fields, 1, counts, ST3, prm)
+        cfg = pdq.step_cfg(0.1, block=128, variant=3, use_graph=graph)
+        tally = pdq.Tally(2, 3)
+        ws = pdq.workspace(st, cfg)
+        torch.cuda.synchronize()          # seeding and allocation ran on the default stream
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                pdq.step_particles(f, phys, st, p, cfg, 2, tally, ws, stream)
+        stream.synchronize()
+        assert st.step_index == 6 and int(st.ctl[0]) == 6
+        runs.append((st, tally))
+    pdq.release_graphs()
+    oracle.run(of, grid, oracle.cfg(0.1), ST3, off, prm, ost, 6)
+    for st, tally in runs:
+        _compare_by_id(st, ost, off, 2e-6, 2e-5, max_flip=0.005)
+    a, b = (r[1].n_alive.cpu().numpy() for r in runs)
+    assert np.abs(a - b).max() <= 2           # a deposition decision may flip on last-bit differences
