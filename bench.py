@@ -292,13 +292,13 @@ def run_ours(args):
         psteps = int(tally.n_alive.sum().item()) - alive0
         pairs = 0.5 * (np.sum(cnt0 ** 2) + np.sum(cnt1 ** 2)) * args.steps
         s0 = state.step_index - args.steps
-        # the MIXED step re-bins (sorts and compacts) at least every 10 steps and once at the start of a call
-        binned = prec == pdq.MIXED and cfg.compact_every > 0
-        ci = min(cfg.compact_every, 10) if binned else cfg.compact_every
-        n_compact = sum(1 for k in range(args.steps - 1) if ci and (s0 + k + 1) % ci == 0)
+        # the step z-bins (and compacts, when compaction is on) at the start of a call and every
+        # min(compact_every, 10) steps, 10 without compaction; both precisions
+        ci = min(cfg.compact_every, 10) if cfg.compact_every > 0 else 10
+        n_rebin = sum(1 for k in range(args.steps - 1) if (s0 + k + 1) % ci == 0)
         # sort, build_items, the step kernel(s) per step (Newton pairs: pair sums + update), re-bin + items
-        per_step = 2 if prec == pdq.MIXED and cfg.variant == 3 and not args.contact else 1
-        launches = int(binned) + 1 + per_step * args.steps + 2 * n_compact
+        per_step = 2 if cfg.variant == 3 and not args.contact else 1
+        launches = 1 + 1 + per_step * args.steps + 2 * n_rebin
 
         # e2e: state in pinned host memory; upload, one step, download state + tallies
         e2e = None
@@ -364,12 +364,17 @@ def run_ours(args):
         return
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    newton = prec == pdq.MIXED and cfg.variant == 3 and not args.contact
+    newton = cfg.variant == 3 and not args.contact
     flops_per_pair = NEWTON_FLOPS_PER_PAIR if newton else FLOPS_PER_PAIR
-    if newton:
+    if newton and prec == pdq.MIXED:
         peak_tflops = SM_COUNT * FP32_LANES * NEWTON_FLOPS_PER_LANE_OP * sm_max * 1e6 / 1e12
         peak_note = ("FP32 pipe peak for the Newton-pair instruction mix = 152 SMs x 128 lanes x %.0f MHz "
                      "(max SM clock) x 24 flops / 16 lane-ops" % sm_max)
+    elif newton:
+        peak_tflops = FP64_NOMINAL_TFLOPS * NEWTON_FLOPS_PER_LANE_OP / 2
+        peak_note = ("FP64 pipe peak for the Newton-pair instruction mix = the nominal 1.25 TFLOP/s (FMA = 2) "
+                     "x (24 flops / 16 operations) / 2; the FP64 rsqrt's refinement steps run on the same pipe "
+                     "and are not counted")
     elif prec == pdq.MIXED:
         peak_tflops = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
         peak_note = "FP32 pipe peak = 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % sm_max
@@ -397,7 +402,7 @@ def run_ours(args):
                    "parallelism": "samples sharded by rank" if world > 1 else "1 GPU",
                    "tile": {"block": cfg.block,
                             "i_per_thread": (8 if cfg.variant in (2, 3) and not args.contact else 4)
-                            if prec == pdq.MIXED else 1,
+                            if prec == pdq.MIXED else (2 if newton else 1),
                             "variant": cfg.variant, "autotuned": args.block == 0 and not args.no_autotune}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
@@ -408,7 +413,9 @@ def run_ours(args):
                      # variant without a capture of its kernel
                      "traffic": KSTEP_DRAM_BYTES[cfg.variant] / 4557792 * float(np.sum(counts))
                      if prec == pdq.MIXED and cfg.variant in KSTEP_DRAM_BYTES and not args.contact else None,
-                     "kernel": "k_pairs_sym (Newton-pair Coulomb sums), then the given-sums k_step update"
+                     "kernel": ("k_pairs_sym (Newton-pair Coulomb sums), then the given-sums k_step update"
+                                if prec == pdq.MIXED else
+                                "k_pairs_sym64 (FP64 Newton-pair Coulomb sums), then the given-sums k_step update")
                                if newton else "k_step (all-pairs Coulomb + local step)",
                      "note": "%s; %d flops per ordered pair; time per step from CUDA events over the timed "
                              "region%s" % (peak_note, flops_per_pair,

@@ -211,10 +211,11 @@ typedef struct pdq_step_cfg {
     int32_t variant;      /* MIXED pair math: 0 packed f32x2 (4 particles per thread),      */
                           /* 1 packed with scalar sums, 2 packed with 8 particles per thread, */
                           /* 3 Newton pairs: each pair evaluated once for both particles     */
-                          /*   (Eq. coulomb is odd in x_i - x_j), summed in float through    */
-                          /*   atomics (not bit-reproducible from run to run), then the      */
-                          /*   local update; block 64 or 128 only.  Ignored by PDQ_FP64 and  */
-                          /*   by contact runs                                                */
+                          /*   (Eq. coulomb is odd in x_i - x_j), summed through atomics     */
+                          /*   (float for MIXED, double for PDQ_FP64; not bit-reproducible   */
+                          /*   from run to run), then the local update; block 64 or 128      */
+                          /*   only.  Ignored by contact runs; for PDQ_FP64 the only other   */
+                          /*   value read is 0                                                */
 } pdq_step_cfg;
 
 /* Caller-owned tallies, device int64 [S][C], accumulated across calls:
@@ -227,9 +228,10 @@ typedef struct pdq_tally {
 
 /* Workspace bytes pdq_step_particles needs for this state and configuration
  * (the work-item table; MIXED: the z-binning sort's scratch; pair variant 3:
- * 16 B x capacity of float sums; PDQ_FP64 with few i-tiles: per-chunk partial
- * pair sums, 24 B x particles x chunks, chunks <= 16, chosen from the
- * capacity, the tile and the device's SM count).                             */
+ * 16 B (MIXED) or 24 B (PDQ_FP64) x capacity of sums; PDQ_FP64 with few
+ * i-tiles, one-sided: per-chunk partial pair sums, 24 B x particles x chunks,
+ * chunks <= 64, chosen from the capacity, the tile and the device's SM
+ * count).                                                                    */
 int pdq_step_workspace_size(const pdq_state* state, const pdq_step_cfg* cfg, size_t* bytes);
 
 /* Advance all samples n_steps steps (App. A.2).  One step of particle i:

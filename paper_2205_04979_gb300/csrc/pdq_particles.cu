@@ -180,8 +180,10 @@ struct StepArgs {
     // Coulomb sums given per particle ([cap][3], e.g. from P3M): replace the pair loop when set
     const double* ext;
     // pair variant 3: FP32 Coulomb sums [cap] (x, y, z, unused) accumulated by k_pairs_sym; the
-    // given-sums step (V = 5) reads them instead of ext when set
+    // given-sums step (V = 5) reads them instead of ext when set.  FP64: acc64 [cap][3], summed by
+    // k_pairs_sym64 and passed to the given-sums step as ext
     float4* acc4;
+    double* acc64;
     // host only: upper bound on the work items of a launch (the persistent grid is capped by it,
     // so that few items spread one per CTA over the SMs instead of piling onto the first CTAs)
     int64_t max_items;
@@ -531,6 +533,12 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
         const int JS = P == PDQ_FP64 ? A.jsplit : 1;
         const int tile = it.y / JS, jc = it.y - tile * JS;
         const int64_t base = o + (int64_t)tile * (NT * U);
+        if constexpr (V == 5) {      // FP64 Newton pairs: one update per tile, from its chunk-0 item
+            if (jc != 0) {
+                __syncthreads();
+                continue;
+            }
+        }
         T xi[U], yi[U], zi[U], ax[U], ay[U], az[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -793,7 +801,7 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
                 if constexpr (CT) flush_flags<P, NT, U>(A, nflag, s_flag, base, end, zeta, s_ct);
             }
         }
-        if constexpr (P == PDQ_FP64) {
+        if constexpr (P == PDQ_FP64 && V != 5) {
             if (JS > 1) {
                 double* part = A.part;
                 const int64_t cap = A.cap;
@@ -1106,6 +1114,221 @@ __global__ void __launch_bounds__(NT) k_pairs_sym(const StepArgs A) {
     }
 }
 
+// FP64 Newton pair: coulomb_pair_x2_sym for one i-particle in double (minimum image by the
+// 1.5 * 2^52 rounding constant, as the one-sided FP64 pair).
+template <bool MINIMG, bool CLAMP>
+__device__ __forceinline__ void coulomb_pair_sym64(double xi, double yi, double zi, double nqi, double2 xyj,
+                                                   double2 zqj, double L, double invL, double c2, double& ax,
+                                                   double& ay, double& az, double& jx, double& jy, double& jz) {
+    const double dx = xi - xyj.x, dy = yi - xyj.y;
+    double dz = zi - zqj.x;
+    if constexpr (MINIMG) {
+        const double t = __dadd_rn(__fma_rn(dz, invL, 6755399441055744.0), -6755399441055744.0);
+        dz = __fma_rn(-L, t, dz);
+    }
+    double r2 = __fma_rn(dx, dx, __fma_rn(dy, dy, dz * dz));
+    if constexpr (CLAMP) r2 = fmax(r2, c2);
+    const double ri = rsqrt(r2);
+    const double ri3 = ri * (ri * ri);
+    const double si = zqj.y * ri3, sj = nqi * ri3;
+    ax = __fma_rn(si, dx, ax);
+    ay = __fma_rn(si, dy, ay);
+    az = __fma_rn(si, dz, az);
+    jx = __fma_rn(sj, dx, jx);
+    jy = __fma_rn(sj, dy, jy);
+    jz = __fma_rn(sj, dz, jz);
+}
+
+// Pair variant 3 in FP64: k_pairs_sym's scheme with U particles per thread (no packing) and the
+// sums in double through atomics into A.acc64 [cap][3] (zeroed before the launch).  A single
+// large sample gives few i-tiles with triangular work, so each tile's j range is cut into
+// A.jsplit chunks of whole j-tiles, one work item each (item.y = tile * JS + chunk; chunks that
+// end before the tile are empty items).
+template <int NT, int U>
+__global__ void __launch_bounds__(NT) k_pairs_sym64(const StepArgs A) {
+    constexpr int W = NT / 32;
+    static_assert(NT % 32 == 0, "whole warps");
+    __shared__ __align__(16) double2 s_xy[NT];     // staged j: (x, y) and (z, q) apart, 16-byte strides
+    __shared__ __align__(16) double2 s_zq[NT];
+    __shared__ double s_jacc[W][3][NT];
+    __shared__ double2 s_zr[W];
+    __shared__ int s_item;
+    const StepConst& K = A.K;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n_items = A.ctl[CTL_NITEMS];
+    const double4_32a* __restrict__ pos_in = (const double4_32a*)A.pos_in;
+    const double L = K.L, invL = K.invL, c2 = K.contact2;
+    const double dcz = sqrt(c2) + 1e-9;        // contact distance + rounding margin
+    const int JS = A.jsplit;
+    double* __restrict__ acc = A.acc64;
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd((unsigned long long*)&A.ctl[CTL_QUEUE2], 1ull);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;
+        const int2 it = A.items[item];
+        const int64_t o = A.offset[it.x];
+        const int64_t end = o + A.count[it.x];
+        const int tile = it.y / JS, jc = it.y - tile * JS;
+        const int64_t base = o + (int64_t)tile * (NT * U);
+        const int64_t dend = base + NT * U < end ? base + NT * U : end;
+        int64_t jb = base, je = end;
+        if (JS > 1) {      // chunk jc of the sample, a whole number of j-tiles long, from this tile on
+            const int64_t ch = ((end - o + JS - 1) / JS + NT - 1) / NT * NT;
+            const int64_t cb = o + jc * ch, ce = cb + ch < end ? cb + ch : end;
+            jb = cb > base ? cb : base;
+            je = ce;
+        }
+        if (jb >= je) {    // the chunk lies before this tile (uniform across the CTA)
+            __syncthreads();
+            continue;
+        }
+        double xi[U], yi[U], zi[U], nq[U], ax[U], ay[U], az[U];
+        double ilo = INFINITY, ihi = -INFINITY;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t g = base + u * NT + tid;
+            if (g < end) {
+                const double4_32a p = pos_in[g];
+                xi[u] = p.x; yi[u] = p.y; zi[u] = p.z; nq[u] = -p.w;
+                ilo = fmin(ilo, p.z);
+                ihi = fmax(ihi, p.z);
+            } else {
+                xi[u] = 1e15; yi[u] = 0.0; zi[u] = 0.0; nq[u] = 0.0;
+            }
+            ax[u] = ay[u] = az[u] = 0.0;
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            ilo = fmin(ilo, __shfl_xor_sync(0xffffffffu, ilo, d));
+            ihi = fmax(ihi, __shfl_xor_sync(0xffffffffu, ihi, d));
+        }
+        for (int64_t j0 = jb; j0 < je; j0 += NT) {
+            const bool diag = j0 < dend;
+            const int64_t jlim = diag ? (dend < je ? dend : je) : je;
+            const int64_t j = j0 + tid;
+            double2 xy = make_double2(-1e15, 0.0), zq = make_double2(0.0, 0.0);
+            if (j < jlim) {
+                const double4_32a p = pos_in[j];
+                xy = make_double2(p.x, p.y);
+                zq = make_double2(p.z, p.w);
+            }
+            double jlo = j < jlim ? zq.x : INFINITY, jhi = j < jlim ? zq.x : -INFINITY;
+            for (int d = 16; d > 0; d >>= 1) {
+                jlo = fmin(jlo, __shfl_xor_sync(0xffffffffu, jlo, d));
+                jhi = fmax(jhi, __shfl_xor_sync(0xffffffffu, jhi, d));
+            }
+            if (lane == 0) s_zr[warp] = make_double2(jlo, jhi);
+            s_xy[tid] = xy;
+            s_zq[tid] = zq;
+            __syncthreads();
+            const double halfL = 0.5 * L;
+            auto classify = [&](double blo, double bhi, bool& direct, bool& apart, double& shift) {
+                const double dlo = ilo - bhi, dhi = ihi - blo;
+                direct = true;
+                shift = 0.0;
+                if (dlo > -halfL && dhi < halfL) shift = 0.0;
+                else if (dlo > halfL && dhi < 3.0 * halfL) shift = L;
+                else if (dhi < -halfL && dlo > -3.0 * halfL) shift = -L;
+                else direct = false;
+                apart = direct && ((dlo - shift > dcz) || (dhi - shift < -dcz));
+            };
+            if (diag) {
+                // one-sided over the tile's own particles (self pair: d = 0 adds nothing)
+                double blo = INFINITY, bhi = -INFINITY;
+#pragma unroll
+                for (int w = 0; w < W; ++w) { blo = fmin(blo, s_zr[w].x); bhi = fmax(bhi, s_zr[w].y); }
+                bool direct, apart;
+                double shift;
+                classify(blo, bhi, direct, apart, shift);
+                if (direct) {
+                    double zs[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) zs[u] = zi[u] - shift;
+#pragma unroll 4
+                    for (int k = 0; k < NT; ++k) {
+                        const double2 a = s_xy[k], b = s_zq[k];
+                        const double4_32a pj = make_double4_32a(a.x, a.y, b.x, b.y);
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            coulomb_pair_direct64<true>(xi[u], yi[u], zs[u], pj, c2, ax[u], ay[u], az[u]);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int k = 0; k < NT; ++k) {
+                        const double2 a = s_xy[k], b = s_zq[k];
+                        const double4_32a pj = make_double4_32a(a.x, a.y, b.x, b.y);
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            coulomb_pair(xi[u], yi[u], zi[u], pj, L, invL, c2, ax[u], ay[u], az[u]);
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
+#pragma unroll 1
+            for (int g = 0; g < W; ++g) {
+                bool direct, apart;
+                double shift;
+                classify(s_zr[g].x, s_zr[g].y, direct, apart, shift);
+                double jx = 0.0, jy = 0.0, jz = 0.0;
+                auto group = [&](auto minimg, auto clamp, const double* zt) {
+#pragma unroll 2
+                    for (int k = 0; k < 32; ++k) {
+                        const int jj = g * 32 + ((lane + k) & 31);
+                        const double2 a = s_xy[jj], b = s_zq[jj];
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            coulomb_pair_sym64<decltype(minimg)::value, decltype(clamp)::value>(
+                                xi[u], yi[u], zt[u], nq[u], a, b, L, invL, c2, ax[u], ay[u], az[u], jx, jy, jz);
+                        jx = __shfl_sync(0xffffffffu, jx, (lane + 1) & 31);
+                        jy = __shfl_sync(0xffffffffu, jy, (lane + 1) & 31);
+                        jz = __shfl_sync(0xffffffffu, jz, (lane + 1) & 31);
+                    }
+                };
+                if (direct) {
+                    double zs[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) zs[u] = zi[u] - shift;
+                    if (apart) group(std::false_type{}, std::false_type{}, zs);
+                    else group(std::false_type{}, std::true_type{}, zs);
+                } else {
+                    group(std::true_type{}, std::true_type{}, zi);
+                }
+                s_jacc[warp][0][g * 32 + lane] = jx;
+                s_jacc[warp][1][g * 32 + lane] = jy;
+                s_jacc[warp][2][g * 32 + lane] = jz;
+            }
+            __syncthreads();
+            if (j < je) {
+                double sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) { sx += s_jacc[w][0][tid]; sy += s_jacc[w][1][tid]; sz += s_jacc[w][2][tid]; }
+                atomicAdd(&acc[3 * j], sx);
+                atomicAdd(&acc[3 * j + 1], sy);
+                atomicAdd(&acc[3 * j + 2], sz);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t g = base + u * NT + tid;
+            if (g < end) {
+                atomicAdd(&acc[3 * g], ax[u]);
+                atomicAdd(&acc[3 * g + 1], ay[u]);
+                atomicAdd(&acc[3 * g + 2], az[u]);
+            }
+        }
+    }
+    if (tid == 0) {
+        __threadfence();
+        const unsigned long long prev = atomicAdd((unsigned long long*)&A.ctl[CTL_DONE2], 1ull);
+        if (prev == gridDim.x - 1) {
+            A.ctl[CTL_QUEUE2] = 0;
+            A.ctl[CTL_DONE2] = 0;
+            __threadfence();
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Work items: samples ordered by live count (largest first), JS items per i-tile
 // (one per j-chunk; JS = 1 unless the FP64 j-split is on), item.y = tile * JS + chunk.
@@ -1349,13 +1572,14 @@ static int tile_threads(const pdq_state* st, const pdq_step_cfg* cfg) {
     if (cfg && cfg->block) return cfg->block;
     return st->precision == PDQ_FP64 ? 128 : 128;
 }
-// Pair variant 3 (Newton pairs) applies to MIXED runs without contact forces.
+// Pair variant 3 (Newton pairs) applies to runs without contact forces, both precisions.
 static bool newton_pairs(const pdq_state* st, const pdq_step_cfg* cfg) {
-    return cfg && cfg->variant == 3 && st->precision == PDQ_MIXED && !(cfg->forces & PDQ_F_CONTACT);
+    return cfg && cfg->variant == 3 && !(cfg->forces & PDQ_F_CONTACT);
 }
-// particles per thread: FP64 1; MIXED 4 (two packed pairs), 8 for pair variants 2 and 3
+// particles per thread: FP64 1 (2 for its Newton-pair kernel); MIXED 4 (two packed pairs), 8 for
+// pair variants 2 and 3
 static int tile_ilp(const pdq_state* st, const pdq_step_cfg* cfg = nullptr) {
-    if (st->precision == PDQ_FP64) return 1;
+    if (st->precision == PDQ_FP64) return newton_pairs(st, cfg) ? 2 : 1;
     if (cfg && (cfg->forces & PDQ_F_CONTACT)) return 4;      // contact runs: variant 0 layout
     return (cfg && (cfg->variant == 2 || cfg->variant == 3)) ? 8 : 4;
 }
@@ -1387,6 +1611,21 @@ static int launch_step(const StepArgs& A, cudaStream_t s) {
 // Pair variant 3: the Newton-pair sums (NT threads, 8 particles per thread) into A.acc4, then
 // the given-sums step over the same tiles (2 NT threads, 4 particles per thread).
 template <int NT>
+static int launch_newton64(const StepArgs& A, cudaStream_t s) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_sym64<NT, 2>, NT, 0);
+        if (per_sm <= 0) per_sm = 1;
+    }
+    const int64_t full = (int64_t)sm_count() * per_sm;
+    PDQ_CUDA(cudaMemsetAsync(A.acc64, 0, 3 * sizeof(double) * (size_t)(A.cap > 0 ? A.cap : 1), s));
+    k_pairs_sym64<NT, 2><<<(unsigned)std::max<int64_t>(1, std::min(full, A.max_items > 0 ? A.max_items : full)), NT,
+                           0, s>>>(A);
+    StepArgs B = A;
+    B.ext = A.acc64;
+    return launch_step<PDQ_FP64, 2 * NT, 1, 5>(B, s);
+}
+template <int NT>
 static int launch_newton(const StepArgs& A, cudaStream_t s) {
     static int per_sm = 0;
     if (!per_sm) {
@@ -1408,6 +1647,11 @@ static int dispatch_step(int prec, int NT, int variant, bool contact, const Step
     if (A.acc4) {
         if (NT == 64) return launch_newton<64>(A, s);
         if (NT == 128) return launch_newton<128>(A, s);
+        return PDQ_ERR_INVALID_ARG;
+    }
+    if (A.acc64) {
+        if (NT == 64) return launch_newton64<64>(A, s);
+        if (NT == 128) return launch_newton64<128>(A, s);
         return PDQ_ERR_INVALID_ARG;
     }
     if (A.ext) {
@@ -1475,22 +1719,33 @@ static int j_split(const pdq_state* st, int TI, bool contact = false) {
     return js < 1 ? 1 : (int)js;
 }
 
+// FP64 Newton pairs: j-chunks per tile so that the triangular work of few large samples spreads
+// evenly (about 8 i-tiles of j per chunk, at most 64 chunks).
+static int newton_chunks(const pdq_state* st, int TI) {
+    if (st->precision != PDQ_FP64) return 1;
+    const int64_t cap = st->capacity > 0 ? st->capacity : 1;
+    int64_t js = (cap + 8 * (int64_t)TI - 1) / (8 * (int64_t)TI);
+    if (js > 64) js = 64;
+    return js < 1 ? 1 : (int)js;
+}
+
 // Workspace: items | order | tag scratch of the z-binning sort;
-// FP64 with JS > 1: tile counters | partial sums [JS][3][capacity];
-// pair variant 3: FP32 sums float4 [capacity].
+// FP64 with JS > 1 (one-sided): tile counters | partial sums [JS][3][capacity];
+// pair variant 3: the sums, float4 [capacity] (MIXED) or double [capacity][3] (FP64).
 static void workspace_layout(const pdq_state* st, int TI, size_t* items_bytes, size_t* total,
                              size_t* cnt_off = nullptr, size_t* part_off = nullptr, bool contact = false,
                              size_t* acc_off = nullptr, bool newton = false) {
-    const int JS = j_split(st, TI, contact);
+    const int JS = newton ? newton_chunks(st, TI) : j_split(st, TI, contact);
     const int64_t max_tiles = st->capacity / TI + st->n_samples + 1;
     *items_bytes = align256(sizeof(int2) * (size_t)max_tiles * JS);
     *total = *items_bytes + align256(sizeof(int32_t) * (size_t)st->n_samples);
     *total += align256(sizeof(int2) * (size_t)(st->capacity > 0 ? st->capacity : 1));   // tag scratch of the z-binning
     if (newton) {
         if (acc_off) *acc_off = *total;
-        *total += align256(sizeof(float4) * (size_t)(st->capacity > 0 ? st->capacity : 1));
+        const size_t per = st->precision == PDQ_FP64 ? 3 * sizeof(double) : sizeof(float4);
+        *total += align256(per * (size_t)(st->capacity > 0 ? st->capacity : 1));
     }
-    if (JS > 1) {
+    if (JS > 1 && !newton) {
         if (cnt_off) *cnt_off = *total;
         *total += align256(sizeof(int) * (size_t)max_tiles);
         if (part_off) *part_off = *total;
@@ -1633,11 +1888,11 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
     const int U = ext ? (st->precision == PDQ_FP64 ? 1 : 4) : tile_ilp(st, cfg);   // given sums: 4 per thread
     if (NT != 64 && NT != 128 && NT != 256 && !(NT == 32 && st->precision == PDQ_FP64)) return PDQ_ERR_INVALID_ARG;
     const bool newton = !ext && newton_pairs(st, cfg);
-    if (newton && NT == 256) return PDQ_ERR_INVALID_ARG;      // its update step would need 512 threads
+    if (newton && NT != 64 && NT != 128) return PDQ_ERR_INVALID_ARG;   // its update step runs 2 NT threads
     size_t items_bytes, need, cnt_off = 0, part_off = 0, acc_off = 0;
     workspace_layout(st, NT * U, &items_bytes, &need, &cnt_off, &part_off, contact, &acc_off, newton);
     if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return PDQ_ERR_WORKSPACE;
-    const int JS = j_split(st, NT * U, contact || ext);
+    const int JS = newton ? newton_chunks(st, NT * U) : j_split(st, NT * U, contact || ext);
     if (n_steps == 0) return PDQ_OK;
     StepArgs A;
     memset(&A, 0, sizeof(A));
@@ -1661,9 +1916,10 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
     A.jsplit = JS;
     A.cap = st->capacity;
     A.ext = ext;
-    if (newton) A.acc4 = (float4*)((char*)workspace + acc_off);
+    if (newton && st->precision == PDQ_MIXED) A.acc4 = (float4*)((char*)workspace + acc_off);
+    if (newton && st->precision == PDQ_FP64) A.acc64 = (double*)((char*)workspace + acc_off);
     A.max_items = (st->capacity / (NT * U) + st->n_samples + 1) * JS;
-    if (JS > 1) {
+    if (JS > 1 && !newton) {
         A.tile_cnt = (int*)((char*)workspace + cnt_off);
         A.part = (double*)((char*)workspace + part_off);
     }
@@ -1686,7 +1942,7 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
         }
         int cur = st->cur;
         int64_t stepi = st->step;
-        if (JS > 1) {   // each tile's last chunk resets its counter, so zeroing once per call suffices
+        if (JS > 1 && !newton) {   // each tile's last chunk resets its counter, so zeroing once per call suffices
             const cudaError_t e = cudaMemsetAsync(A.tile_cnt, 0, sizeof(int) * (size_t)(st->capacity / (NT * U) +
                                                                                           st->n_samples + 1), s);
             if (e != cudaSuccess) return cuda_status(e);
@@ -1835,9 +2091,12 @@ static size_t autotune_scratch_offset(const pdq_state* st) {
     const int tiles_mixed[6] = {64 * 4, 128 * 4, 256 * 4, 64 * 8, 128 * 8, 256 * 8};
     size_t best = 0;
     for (int k = 0; k < (f64 ? 4 : 6); ++k) {
-        size_t ib, tot;
-        workspace_layout(st, f64 ? tiles_f64[k] : tiles_mixed[k], &ib, &tot, nullptr, nullptr, false, nullptr, !f64);
-        if (tot > best) best = tot;
+        for (int nw = 0; nw < 2; ++nw) {      // one-sided and Newton-pair layouts
+            size_t ib, tot;
+            const int TI = f64 ? tiles_f64[k] * (nw ? 2 : 1) : tiles_mixed[k];
+            workspace_layout(st, TI, &ib, &tot, nullptr, nullptr, false, nullptr, nw == 1);
+            if (tot > best) best = tot;
+        }
     }
     return best;
 }
@@ -1887,7 +2146,11 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
     }
     const int blocks[4] = {64, 128, 256, 32};
     const int n_blk = st->precision == PDQ_FP64 ? 4 : 3;    // 32-thread tiles: FP64 only
-    const int n_var = st->precision == PDQ_MIXED && !(cfg->forces & PDQ_F_CONTACT) ? 4 : 1;
+    // candidate pair variants: MIXED 0-3, FP64 0 and 3 (Newton pairs); contact runs 0 only
+    const bool contact_run = (cfg->forces & PDQ_F_CONTACT) != 0;
+    const int vars_mixed[4] = {0, 1, 2, 3}, vars_f64[2] = {0, 3};
+    const int* vars = st->precision == PDQ_MIXED ? vars_mixed : vars_f64;
+    const int n_var = contact_run ? 1 : (st->precision == PDQ_MIXED ? 4 : 2);
     cudaEvent_t e0, e1;
     PDQ_CUDA(cudaEventCreate(&e0));
     PDQ_CUDA(cudaEventCreate(&e1));
@@ -1896,8 +2159,9 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
     const int cur0 = st->cur;
     const int64_t step0 = st->step;
     for (int bi = 0; bi < n_blk && rc == PDQ_OK; ++bi) {
-        for (int v = 0; v < n_var && rc == PDQ_OK; ++v) {
-            if (v == 3 && blocks[bi] == 256) continue;       // Newton pairs: 64 or 128 threads
+        for (int vi = 0; vi < n_var && rc == PDQ_OK; ++vi) {
+            const int v = vars[vi];
+            if (v == 3 && blocks[bi] != 64 && blocks[bi] != 128) continue;       // Newton pairs: 64 or 128 threads
             pdq_step_cfg c = *cfg;
             c.block = blocks[bi];
             c.variant = v;

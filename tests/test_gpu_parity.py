@@ -174,10 +174,11 @@ def test_fp64_single_sample_jsplit_parity(pdq, fields, block):
     assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
 
 
-def test_fp64_compaction_parity(pdq, fields):
+@pytest.mark.parametrize("variant", [0, 3])
+def test_fp64_compaction_parity(pdq, fields, variant):
     counts = [1000, 333, 129]
     st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3, 50,
-                                       {"window_start": 0, "compact_every": 7})
+                                       {"window_start": 0, "compact_every": 7, "variant": variant})
     n_live = _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 1e-9, 1e-9)
     assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
     # compaction kept exactly the live particles, each once, grouped by z bin (binned at the
@@ -192,6 +193,31 @@ def test_fp64_compaction_parity(pdq, fields):
         assert len(np.unique(ids)) == len(ids)
         b = np.floor(z[offs[s]:offs[s] + cnt[s]] * 256 / 720.0)
         assert np.mean(np.diff(b) >= -2) > 0.95
+
+
+@pytest.mark.parametrize("block", [64, 128])
+def test_fp64_newton_pairs_parity(pdq, fields, block):
+    # pair variant 3 in FP64: each pair evaluated once, sums in double through atomics (the
+    # order of the additions differs from the oracle's, within the FP64 bars)
+    counts = [1000, 333, 129]
+    off = np.r_[0, np.cumsum(counts)]
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3, 1, {"variant": 3}, block=block)
+    assert _compare_by_id(st, ost, off, 1e-12, 1e-12) > 0
+    assert np.array_equal(tally.n_alive.cpu().numpy(), na)
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3, 50, {"variant": 3, "window_start": 10},
+                                       block=block)
+    assert _compare_by_id(st, ost, off, 1e-9, 1e-9) > 0
+    assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
+
+
+def test_fp64_newton_pairs_chunked_single_sample(pdq, fields):
+    # one 6,000-particle sample at 128 threads x 2: 24 tiles of 256, each tile's j range in 3
+    # chunks of 2,048 (one work item each, the earlier chunks of late tiles empty)
+    counts = [6000]
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, [10.0], PRM3[:1], 10,
+                                       {"variant": 3, "window_start": 2}, block=128)
+    assert _compare_by_id(st, ost, np.r_[0, 6000], 1e-10, 1e-10) > 0
+    assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
 
 
 def test_fp64_rebound_parity(pdq, fields):
