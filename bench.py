@@ -41,7 +41,7 @@ NEWTON_FLOPS_PER_PAIR = 12   # per ordered pair
 NEWTON_FLOPS_PER_LANE_OP = 24.0 / 16.0
 # DRAM bytes per launch of the dominant kernel on 4,557,792 particles (ncu): k_step for pair variant 2,
 # k_pairs_sym for pair variant 3
-KSTEP_DRAM_BYTES = {2: 495.4e6, 3: 178.8e6}
+KSTEP_DRAM_BYTES = {2: 495.4e6, 3: 178.7e6}
 SM_COUNT, FP32_LANES = 152, 128
 FP64_NOMINAL_TFLOPS = 1.25
 
@@ -408,7 +408,7 @@ def run_ours(args):
                      "frac": achieved / peak_tflops,
                      # dram bytes read + written per launch from the ncu captures in
                      # profiles/k_step_mixed_batched.md (pair variant 2: 495.4 MB) and
-                     # profiles/k_pairs_sym_batched.md (variant 3: 178.8 MB), both on 4,557,792
+                     # profiles/k_pairs_sym_batched.md (variant 3: 178.7 MB), both on 4,557,792
                      # particles, scaled by the particle count of this launch; null for a
                      # variant without a capture of its kernel
                      "traffic": KSTEP_DRAM_BYTES[cfg.variant] / 4557792 * float(np.sum(counts))

@@ -944,8 +944,11 @@ __device__ __forceinline__ ZClass zclass(float alo, float ahi, float blo, float 
 //     sums of the tile are added in shared memory and leave with one float4 atomic per j.
 // The earlier particles of the sample reach this tile as the j side of earlier tiles' items.
 // Padding particles sit far off the axis (x = +-1e15) with zero charge, so they add nothing.
+// Register budget: 3 CTAs of 128 threads per SM (up to 168 registers), so that the 32-step loop
+// unrolled by 4 keeps more independent pair chains in flight (measured 2.6 % faster than 4 CTAs
+// at 128 registers).
 template <int NT, int U>
-__global__ void __launch_bounds__(NT) k_pairs_sym(const StepArgs A) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_pairs_sym(const StepArgs A) {
     constexpr int W = NT / 32, H = U / 2;
     static_assert(U % 2 == 0 && NT % 32 == 0, "packed pairs over whole warps");
     // j-tile, pre-duplicated: (x,x,y,y) at sj2[j], (z,z,q,q) at sj2[NT + j] (16-byte stride, so the
@@ -1054,7 +1057,7 @@ __global__ void __launch_bounds__(NT) k_pairs_sym(const StepArgs A) {
                 const ZClass zc = zclass(ilo, ihi, zr.x, zr.y, Lf, dcz);
                 float jx = 0.f, jy = 0.f, jz = 0.f;
                 auto group = [&](auto minimg, auto clamp, const f2* Zt) {
-#pragma unroll 2
+#pragma unroll 4
                     for (int k = 0; k < 32; ++k) {
                         const int jj = g * 32 + ((lane + k) & 31);
                         const ulonglong2 a = sj2[jj], b = sj2[NT + jj];
