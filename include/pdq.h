@@ -351,8 +351,8 @@ typedef struct pdq_batch {
 /* Workspace bytes of pdq_adjoint_run: FP64 storage of 8 arrays per particle
  * and 2 int32 ones per checkpoint (ceil(n_steps/K) of them: the state
  * z-binned, its charges, classes and binning permutation), 10 per step of one
- * segment (K + 1 levels), 19 for cotangents and charges, plus 4 [S][C]
- * tallies.                                                                   */
+ * segment (K + 1 levels), 19 for cotangents and charges, 16 B per particle of
+ * float sums (the MIXED Newton-pair kernels), plus 4 [S][C] tallies.         */
 int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_steps, int32_t K, size_t* bytes);
 
 /* Smoothed deposition functional and its hand-written reverse-mode adjoint.

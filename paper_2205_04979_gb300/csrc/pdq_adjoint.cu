@@ -32,6 +32,7 @@
 
 #include "pdq_common.cuh"
 #include "pdq_device.cuh"
+#include "pdq_newton.cuh"
 
 namespace pdq {
 
@@ -57,6 +58,8 @@ struct AdjArgs {
     double *cx, *cy, *cz;               // c = coul q abar [N]
     const double *nbar, *dbar;          // cotangents of num and den [S][C]
     double* pbar;                       // [S][3]
+    float4* acc4;                       // MIXED Newton-pair sums [N]: forward Coulomb sums (x, y, z),
+                                        // reverse pair-VJP sums (x-bar x, y, z; charge term w)
     // seeding
     uint2 key;
     double sigma, neg_frac;
@@ -418,7 +421,6 @@ __global__ void k_adj_unperm(const int64_t* __restrict__ offset, const int32_t* 
 // [a_lo - b_hi, a_hi - b_lo]; inside one period window the minimum image is a uniform shift
 // (0 or +-L, folded into z_i), and when every |dz| also exceeds the contact distance the clamp
 // goes too (as in the step kernel).
-struct TileClass { bool direct, apart; float shift; };
 __device__ __forceinline__ float2 warp_range(float lo, float hi) {
     for (int d = 16; d > 0; d >>= 1) {
         lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, d));
@@ -426,28 +428,22 @@ __device__ __forceinline__ float2 warp_range(float lo, float hi) {
     }
     return make_float2(lo, hi);
 }
-__device__ __forceinline__ TileClass classify_tiles(const float2* s_zi, const float2* s_zr, int nw, float L,
-                                                    float dcz) {
+__device__ __forceinline__ ZClass classify_tiles(const float2* s_zi, const float2* s_zr, int nw, float L, float dcz) {
     float alo = INFINITY, ahi = -INFINITY, blo = INFINITY, bhi = -INFINITY;
     for (int w = 0; w < nw; ++w) {
         alo = fminf(alo, s_zi[w].x); ahi = fmaxf(ahi, s_zi[w].y);
         blo = fminf(blo, s_zr[w].x); bhi = fmaxf(bhi, s_zr[w].y);
     }
-    const float dlo = alo - bhi, dhi = ahi - blo, halfL = 0.5f * L;
-    TileClass t{true, false, 0.f};
-    if (dlo > -halfL && dhi < halfL) t.shift = 0.f;
-    else if (dlo > halfL && dhi < 3.f * halfL) t.shift = L;
-    else if (dhi < -halfL && dlo > -3.f * halfL) t.shift = -L;
-    else t.direct = false;
-    t.apart = t.direct && ((dlo - t.shift > dcz) || (dhi - t.shift < -dcz));
-    return t;
+    return zclass(alo, ahi, blo, bhi, L, dcz);
 }
 
 // Particles per thread of the forward and pair-VJP kernels: MIXED packs two i-particles
 // per f32x2 instruction (4 per thread), FP64 keeps 2 for ILP.
 template <int P> __host__ __device__ constexpr int adj_ilp() { return P == PDQ_MIXED ? 4 : 2; }
 
-template <int P, int NT>
+// SUMS: the Coulomb sums come from A.acc4 (the Newton-pair kernel k_adj_sums_sym) instead of the
+// pair loop below.
+template <int P, int NT, bool SUMS = false>
 __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
     typedef typename Real<P>::T T;
     typedef typename Real<P>::T4 T4;
@@ -471,7 +467,16 @@ __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
         zi[u] = valid ? (T)A.in.z[g] : (T)0;
         ax[u] = ay[u] = az[u] = (T)0;
     }
-    if ((K.forces & PDQ_F_COULOMB) && P == PDQ_MIXED) {
+    if constexpr (SUMS) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = (int64_t)blockIdx.x * NT * U + u * NT + tid;
+            if (i < n) {
+                const float4 a = A.acc4[o + i];
+                ax[u] = (T)a.x; ay[u] = (T)a.y; az[u] = (T)a.z;
+            }
+        }
+    } else if ((K.forces & PDQ_F_COULOMB) && P == PDQ_MIXED) {
         // packed: j-tile staged pre-duplicated (x, x, y, y), (z, z, qw, qw); two i-particles per lane op
         constexpr int H = U / 2;
         ulonglong2* sj2 = reinterpret_cast<ulonglong2*>(smem_raw);
@@ -510,7 +515,7 @@ __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
             sj2[2 * tid] = make_ulonglong2(f2_pack(px, px), f2_pack(py, py));
             sj2[2 * tid + 1] = make_ulonglong2(f2_pack(pz, pz), f2_pack(pq, pq));
             __syncthreads();
-            const TileClass tc = classify_tiles(s_zi, s_zr, NT / 32, L, dcz);
+            const ZClass tc = classify_tiles(s_zi, s_zr, NT / 32, L, dcz);
             if (tc.direct) {
                 const f2 sh = f2_pack(tc.shift, tc.shift);
                 f2 Zs[H];
@@ -859,7 +864,7 @@ __global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
             const float2 r = warp_range(j < n ? v[2] : INFINITY, j < n ? v[2] : -INFINITY);
             if ((tid & 31) == 0) s_zr[tid >> 5] = r;
             __syncthreads();
-            const TileClass tc = classify_tiles(s_zi, s_zr, NT / 32, L, dcz);
+            const ZClass tc = classify_tiles(s_zi, s_zr, NT / 32, L, dcz);
             auto tile = [&](auto minimg, auto clamp, const f2* Zt) {
 #pragma unroll 2
                 for (int k = 0; k < NT; ++k) {
@@ -992,6 +997,256 @@ __global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
     warp_add(xs, A.pbar + (int64_t)s * 3 + 0);
 }
 
+// ---------------------------------------------------------------------------
+// Newton pairs (MIXED): each unordered pair evaluated once for both particles.
+// ---------------------------------------------------------------------------
+// Forward Coulomb sums S_i = sum_j Q_j G(x_i - x_j), Q = w xi qhat, into A.acc4 (zeroed before
+// the launch) with the step's newton_tile; grid (i-tiles of NT*U, samples).  k_adj_forward
+// with SUMS then does the local part.
+template <int NT, int U>
+__global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_sums_sym(const AdjArgs A) {
+    const int s = blockIdx.y;
+    const int64_t o = A.offset[s], end = A.offset[s + 1];
+    const int64_t base = o + (int64_t)blockIdx.x * NT * U;
+    if (base >= end) return;
+    const double xi = A.params[s].xi;
+    const auto load = [&](int64_t g) {
+        return make_float4((float)A.in.x[g], (float)A.in.y[g], (float)A.in.z[g], (float)(A.in.w[g] * xi * A.qhat[g]));
+    };
+    newton_tile<NT, U>(load, base, end, (float)A.K.L, (float)A.K.invL, (float)A.K.contact2f, A.acc4);
+}
+
+// Pair-VJP term of pair (m, j) in x-bar_m, d = x_m - x_j:
+//   T = J(d)(Q_j c_m - Q_m c_j) = u / r^3 - 3 d (d.u) / r^5,  u = Q_j c_m - Q_m c_j
+// (u / d_c^3 inside the clamp).  J is even in d and u odd under m <-> j, so T enters x-bar_j
+// with the opposite sign.  The charge term Qp_m = sum_j (d.c_j)/r^3 (Q-bar_m = -Qp_m) gets
+// -(d.c_m)/r^3 for j.  One j against two m-particles, packed: T is added to (tx, ty, tz) and
+// (jx, jy, jz), (d.c_j)/r^3 to qp and (d.c_m)/r^3 to jq; the caller negates the j sums.
+// nQm = -Q_m; MINIMG / CLAMP as in vjp_pair_x2.
+template <bool MINIMG, bool CLAMP>
+__device__ __forceinline__ void vjp_pair_x2_sym(f2 xm, f2 ym, f2 zm, f2 nQm, f2 cmx, f2 cmy, f2 cmz, const VjpJ& J,
+                                                f2 invL2, f2 M2, f2 nM2, f2 nL2, float c2, f2& tx, f2& ty, f2& tz,
+                                                f2& qp, f2& jx, f2& jy, f2& jz, f2& jq) {
+    const f2 dx = f2_sub(xm, J.x), dy = f2_sub(ym, J.y);
+    f2 dz = f2_sub(zm, J.z);
+    if constexpr (MINIMG) {
+        const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
+        dz = f2_fma(nL2, t, dz);
+    }
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    f2 ri, mask3;
+    if constexpr (CLAMP) {
+        ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
+        mask3 = f2_pack(ra > c2 ? -3.f : 0.f, rb > c2 ? -3.f : 0.f);
+    } else {
+        ri = f2_pack(rsqrt_ftz(ra), rsqrt_ftz(rb));
+        mask3 = f2_pack(-3.f, -3.f);
+    }
+    const f2 ri2 = f2_mul(ri, ri), ri3 = f2_mul(ri2, ri);
+    const f2 ux = f2_fma(J.Q, cmx, f2_mul(nQm, J.cx));
+    const f2 uy = f2_fma(J.Q, cmy, f2_mul(nQm, J.cy));
+    const f2 uz = f2_fma(J.Q, cmz, f2_mul(nQm, J.cz));
+    const f2 du = f2_fma(dx, ux, f2_fma(dy, uy, f2_mul(dz, uz)));
+    const f2 kk = f2_mul(f2_mul(f2_mul(ri3, ri2), mask3), du);
+    const f2 Tx = f2_fma(kk, dx, f2_mul(ux, ri3));
+    const f2 Ty = f2_fma(kk, dy, f2_mul(uy, ri3));
+    const f2 Tz = f2_fma(kk, dz, f2_mul(uz, ri3));
+    tx = f2_add(tx, Tx);
+    ty = f2_add(ty, Ty);
+    tz = f2_add(tz, Tz);
+    jx = f2_add(jx, Tx);
+    jy = f2_add(jy, Ty);
+    jz = f2_add(jz, Tz);
+    const f2 dcj = f2_fma(dx, J.cx, f2_fma(dy, J.cy, f2_mul(dz, J.cz)));
+    const f2 dcm = f2_fma(dx, cmx, f2_fma(dy, cmy, f2_mul(dz, cmz)));
+    qp = f2_fma(ri3, dcj, qp);
+    jq = f2_fma(ri3, dcm, jq);
+}
+
+// Pair VJP with Newton pairs (MIXED), the scheme of newton_tile: grid (m-tiles of NT*U,
+// samples); the tile's own block one-sided (the j sums of vjp_pair_x2_sym left unused), every
+// later particle of the sample as a Newton pair with 32-j groups walked by skewed lanes.  Sums
+// (x-bar x, y, z, Qp) go to A.acc4 by float4 atomics; k_adj_pairs_finish applies them.
+template <int NT, int U>
+__global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_pairs_sym(const AdjArgs A) {
+    constexpr int W = NT / 32, H = U / 2;
+    static_assert(U % 2 == 0 && NT % 32 == 0, "packed pairs over whole warps");
+    // staged j: (x,x,y,y), (z,z,Q,Q), (cx,cx,cy,cy), (cz,cz,-,-), each array at a 16-byte stride
+    __shared__ __align__(16) ulonglong2 sA[NT], sB[NT], sC[NT], sD[NT];
+    __shared__ float s_jacc[W][4][NT];
+    __shared__ float2 s_zr[W];
+    const int s = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t o = A.offset[s], end = A.offset[s + 1];
+    const int64_t base = o + (int64_t)blockIdx.x * NT * U;
+    if (base >= end) return;
+    const int64_t dend = base + NT * U < end ? base + NT * U : end;
+    const double xi = A.params[s].xi;
+    const StepConst& K = A.K;
+    const float L = (float)K.L, M = 12582912.0f;
+    const f2 invL2 = f2_pack((float)K.invL, (float)K.invL), M2 = f2_pack(M, M), nM2 = f2_pack(-M, -M);
+    const f2 nL2 = f2_pack(-L, -L);
+    const float c2 = (float)K.contact2f;
+    const float dcz = sqrtf(c2) + 1e-3f;
+    f2 X[H], Y[H], Z[H], NQ[H], CX[H], CY[H], CZ[H], TX[H], TY[H], TZ[H], QP[H];
+    float ilo = INFINITY, ihi = -INFINITY;
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        float v[2][7];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t g = base + (2 * h + e) * NT + tid;
+            if (g < end) {
+                v[e][0] = (float)A.in.x[g]; v[e][1] = (float)A.in.y[g]; v[e][2] = (float)A.in.z[g];
+                v[e][3] = (float)(A.in.w[g] * xi * A.qhat[g]);
+                v[e][4] = (float)A.cx[g]; v[e][5] = (float)A.cy[g]; v[e][6] = (float)A.cz[g];
+                ilo = fminf(ilo, v[e][2]);
+                ihi = fmaxf(ihi, v[e][2]);
+            } else {     // padding: far off the axis, no charge, no cotangent
+                v[e][0] = 1e15f;
+#pragma unroll
+                for (int q = 1; q < 7; ++q) v[e][q] = 0.f;
+            }
+        }
+        X[h] = f2_pack(v[0][0], v[1][0]); Y[h] = f2_pack(v[0][1], v[1][1]); Z[h] = f2_pack(v[0][2], v[1][2]);
+        NQ[h] = f2_pack(-v[0][3], -v[1][3]);
+        CX[h] = f2_pack(v[0][4], v[1][4]); CY[h] = f2_pack(v[0][5], v[1][5]); CZ[h] = f2_pack(v[0][6], v[1][6]);
+        TX[h] = TY[h] = TZ[h] = QP[h] = 0ull;
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        ilo = fminf(ilo, __shfl_xor_sync(0xffffffffu, ilo, d));
+        ihi = fmaxf(ihi, __shfl_xor_sync(0xffffffffu, ihi, d));
+    }
+    for (int64_t j0 = base; j0 < end; j0 += NT) {
+        const bool diag = j0 < dend;
+        const int64_t jlim = diag ? dend : end;
+        const int64_t j = j0 + tid;
+        float v[7] = {-1e15f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (j < jlim) {
+            v[0] = (float)A.in.x[j]; v[1] = (float)A.in.y[j]; v[2] = (float)A.in.z[j];
+            v[3] = (float)(A.in.w[j] * xi * A.qhat[j]);
+            v[4] = (float)A.cx[j]; v[5] = (float)A.cy[j]; v[6] = (float)A.cz[j];
+        }
+        const float2 r = warp_range(j < jlim ? v[2] : INFINITY, j < jlim ? v[2] : -INFINITY);
+        if (lane == 0) s_zr[warp] = r;
+        sA[tid] = make_ulonglong2(f2_pack(v[0], v[0]), f2_pack(v[1], v[1]));
+        sB[tid] = make_ulonglong2(f2_pack(v[2], v[2]), f2_pack(v[3], v[3]));
+        sC[tid] = make_ulonglong2(f2_pack(v[4], v[4]), f2_pack(v[5], v[5]));
+        sD[tid] = make_ulonglong2(f2_pack(v[6], v[6]), 0ull);
+        __syncthreads();
+        if (diag) {      // one-sided over the tile's own particles (self pair: d = 0, u = 0)
+            float blo = INFINITY, bhi = -INFINITY;
+#pragma unroll
+            for (int w = 0; w < W; ++w) { blo = fminf(blo, s_zr[w].x); bhi = fmaxf(bhi, s_zr[w].y); }
+            const ZClass zc = zclass(ilo, ihi, blo, bhi, L, dcz);
+            auto block = [&](auto minimg, const f2* Zt) {
+#pragma unroll 2
+                for (int k = 0; k < NT; ++k) {
+                    const ulonglong2 a = sA[k], b = sB[k], cc = sC[k], dd = sD[k];
+                    const VjpJ J{a.x, a.y, b.x, b.y, cc.x, cc.y, dd.x};
+                    f2 ux = 0ull, uy = 0ull, uz = 0ull, uq = 0ull;      // j sums: not used
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        vjp_pair_x2_sym<decltype(minimg)::value, true>(X[h], Y[h], Zt[h], NQ[h], CX[h], CY[h], CZ[h],
+                                                                        J, invL2, M2, nM2, nL2, c2, TX[h], TY[h],
+                                                                        TZ[h], QP[h], ux, uy, uz, uq);
+                }
+            };
+            if (zc.direct) {
+                const f2 sh = f2_pack(zc.shift, zc.shift);
+                f2 Zs[H];
+#pragma unroll
+                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+                block(std::false_type{}, Zs);
+            } else {
+                block(std::true_type{}, Z);
+            }
+            __syncthreads();
+            continue;
+        }
+#pragma unroll 1
+        for (int g = 0; g < W; ++g) {
+            const float2 zr = s_zr[g];
+            const ZClass zc = zclass(ilo, ihi, zr.x, zr.y, L, dcz);
+            float jx = 0.f, jy = 0.f, jz = 0.f, jq = 0.f;
+            auto group = [&](auto minimg, auto clamp, const f2* Zt) {
+#pragma unroll 2
+                for (int k = 0; k < 32; ++k) {
+                    const int jj = g * 32 + ((lane + k) & 31);
+                    const ulonglong2 a = sA[jj], b = sB[jj], cc = sC[jj], dd = sD[jj];
+                    const VjpJ J{a.x, a.y, b.x, b.y, cc.x, cc.y, dd.x};
+                    f2 JX = f2_pack(jx, 0.f), JY = f2_pack(jy, 0.f), JZ = f2_pack(jz, 0.f), JQ = f2_pack(jq, 0.f);
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        vjp_pair_x2_sym<decltype(minimg)::value, decltype(clamp)::value>(
+                            X[h], Y[h], Zt[h], NQ[h], CX[h], CY[h], CZ[h], J, invL2, M2, nM2, nL2, c2, TX[h], TY[h],
+                            TZ[h], QP[h], JX, JY, JZ, JQ);
+                    float l0, l1;
+                    f2_unpack(JX, l0, l1); jx = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                    f2_unpack(JY, l0, l1); jy = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                    f2_unpack(JZ, l0, l1); jz = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                    f2_unpack(JQ, l0, l1); jq = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                }
+            };
+            if (zc.direct) {
+                const f2 sh = f2_pack(zc.shift, zc.shift);
+                f2 Zs[H];
+#pragma unroll
+                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+                if (zc.apart) group(std::false_type{}, std::false_type{}, Zs);
+                else group(std::false_type{}, std::true_type{}, Zs);
+            } else {
+                group(std::true_type{}, std::true_type{}, Z);
+            }
+            s_jacc[warp][0][g * 32 + lane] = jx;
+            s_jacc[warp][1][g * 32 + lane] = jy;
+            s_jacc[warp][2][g * 32 + lane] = jz;
+            s_jacc[warp][3][g * 32 + lane] = jq;
+        }
+        __syncthreads();
+        if (j < end) {     // j's terms carry the opposite sign
+            float sx = 0.f, sy = 0.f, sz = 0.f, sq = 0.f;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                sx += s_jacc[w][0][tid]; sy += s_jacc[w][1][tid]; sz += s_jacc[w][2][tid]; sq += s_jacc[w][3][tid];
+            }
+            atomicAdd(&A.acc4[j], make_float4(-sx, -sy, -sz, -sq));
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        float t0[4], t1[4];
+        f2_unpack(TX[h], t0[0], t1[0]);
+        f2_unpack(TY[h], t0[1], t1[1]);
+        f2_unpack(TZ[h], t0[2], t1[2]);
+        f2_unpack(QP[h], t0[3], t1[3]);
+        const int64_t g0 = base + (2 * h) * NT + tid, g1 = g0 + NT;
+        if (g0 < end) atomicAdd(&A.acc4[g0], make_float4(t0[0], t0[1], t0[2], t0[3]));
+        if (g1 < end) atomicAdd(&A.acc4[g1], make_float4(t1[0], t1[1], t1[2], t1[3]));
+    }
+}
+
+// Applies the Newton-pair VJP sums: x-bar += (x, y, z), w-bar += -Qp xi qhat, and the xi
+// cotangent (q-bar - Qp w) qhat summed per sample.  Grid (particles / 256, samples).
+__global__ void k_adj_pairs_finish(const AdjArgs A) {
+    const int s = blockIdx.y;
+    const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double xs = 0.0;
+    if (i < n) {
+        const int64_t g = o + i;
+        const float4 t = A.acc4[g];
+        A.xb[g] += (double)t.x;
+        A.yb[g] += (double)t.y;
+        A.zb[g] += (double)t.z;
+        const double qm = A.params[s].xi * A.qhat[g];
+        A.wb[g] += (double)(-t.w) * qm;
+        xs = (A.qb[g] + (double)(-t.w) * A.in.w[g]) * A.qhat[g];
+    }
+    warp_add(xs, A.pbar + (int64_t)s * 3 + 0);
+}
+
 // J = (R+/2) num / (dt den) and the cotangents of num and den for one vector gbar.
 __global__ void k_adj_finish(const double* num, const double* den, const double* gbar, int n, double R, double dt,
                              double* J, double* nbar, double* dbar) {
@@ -1034,6 +1289,7 @@ static AdjLayout adj_layout(int64_t N, int32_t S, int32_t C, int64_t n_steps, in
     // per checkpoint, the z-binned order's qhat, classes and permutation; 7 scratch cotangents
     b += (vec + 2 * a256(sizeof(int32_t) * (size_t)(N > 0 ? N : 1))) * (size_t)L.n_ck;
     b += vec * 7;
+    b += a256(sizeof(float) * 4 * (size_t)(N > 0 ? N : 1));   // MIXED Newton-pair sums
     b += a256(sizeof(double) * (size_t)S * C) * 4; // num, den, nbar, dbar
     L.bytes = b;
     return L;
@@ -1128,6 +1384,8 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
     }
     double* scratch[7];
     for (auto& q : scratch) q = (double*)take(vec);
+    A.acc4 = (float4*)take(a256(sizeof(float) * 4 * (size_t)(N > 0 ? N : 1)));
+    const size_t acc_bytes = sizeof(float4) * (size_t)(N > 0 ? N : 1);
     const size_t sc = a256(sizeof(double) * (size_t)A.S * A.C);
     A.num = (double*)take(sc); A.den = (double*)take(sc);
     double* nbar = (double*)take(sc);
@@ -1148,10 +1406,25 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
     const int ilp = mixed ? adj_ilp<PDQ_MIXED>() : adj_ilp<PDQ_FP64>();             // particles per thread
     const dim3 grid((unsigned)((nmax + ilp * NT - 1) / (ilp * NT)), (unsigned)A.S);
 
-    auto fwd = [&](const Slot& in, const Slot& out, int64_t step, int tally) {
+    // MIXED with Coulomb forces: the pair sums (forward) and the pair VJP (reverse) take Newton
+    // pairs, each unordered pair once, through A.acc4
+    const bool newton = mixed && (A.K.forces & PDQ_F_COULOMB);
+    const int NTN = 128;
+    const dim3 grid_sums((unsigned)((nmax + 8 * NTN - 1) / (8 * NTN)), (unsigned)A.S);
+    const dim3 grid_vjp((unsigned)((nmax + 4 * NTN - 1) / (4 * NTN)), (unsigned)A.S);
+    auto fwd = [&](const Slot& in, const Slot& out, int64_t step, int tally) -> cudaError_t {
         A.in = in; A.out = out; A.step = step; A.tally = tally;
-        if (mixed) k_adj_forward<PDQ_MIXED, NT><<<grid, NT, 0, s>>>(A);
-        else k_adj_forward<PDQ_FP64, NT><<<grid, NT, 0, s>>>(A);
+        if (newton) {
+            const cudaError_t e = cudaMemsetAsync(A.acc4, 0, acc_bytes, s);
+            if (e != cudaSuccess) return e;
+            k_adj_sums_sym<NTN, 8><<<grid_sums, NTN, 0, s>>>(A);
+            k_adj_forward<PDQ_MIXED, NT, true><<<grid, NT, 0, s>>>(A);
+        } else if (mixed) {
+            k_adj_forward<PDQ_MIXED, NT><<<grid, NT, 0, s>>>(A);
+        } else {
+            k_adj_forward<PDQ_FP64, NT><<<grid, NT, 0, s>>>(A);
+        }
+        return cudaSuccess;
     };
     auto copy_state = [&](const Slot& dst, const Slot& src) -> cudaError_t {
         const size_t nb = sizeof(double) * (size_t)N;
@@ -1186,7 +1459,7 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
     PDQ_CUDA(checkpoint(0, seg[0]));
     // forward sweep: ping-pong between segment slots 0 and 1, checkpoint every K steps
     for (int64_t n = 0; n < n_steps; ++n) {
-        fwd(seg[n & 1], seg[(n + 1) & 1], n, 1);
+        PDQ_CUDA(fwd(seg[n & 1], seg[(n + 1) & 1], n, 1));
         if ((n + 1) % K == 0 && (n + 1) < n_steps) PDQ_CUDA(checkpoint((n + 1) / K, seg[(n + 1) & 1]));
     }
     const int nsc = A.S * A.C;
@@ -1206,11 +1479,16 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
             A.qhat = ck_qh[kseg];
             A.cls = ck_cl[kseg];
             PDQ_CUDA(copy_state(seg[0], ck[kseg]));
-            for (int64_t t = 0; t < len; ++t) fwd(seg[t], seg[t + 1], n0 + t, 0);
+            for (int64_t t = 0; t < len; ++t) PDQ_CUDA(fwd(seg[t], seg[t + 1], n0 + t, 0));
             for (int64_t t = len - 1; t >= 0; --t) {
                 A.in = seg[t];
                 A.step = n0 + t;
-                if (mixed) {
+                if (newton) {
+                    PDQ_CUDA(cudaMemsetAsync(A.acc4, 0, acc_bytes, s));
+                    k_adj_local<PDQ_MIXED><<<dim3((unsigned)((nmax + 127) / 128), (unsigned)A.S), 128, 0, s>>>(A);
+                    k_adj_pairs_sym<NTN, 4><<<grid_vjp, NTN, 0, s>>>(A);
+                    k_adj_pairs_finish<<<dim3((unsigned)((nmax + 255) / 256), (unsigned)A.S), 256, 0, s>>>(A);
+                } else if (mixed) {
                     k_adj_local<PDQ_MIXED><<<dim3((unsigned)((nmax + 127) / 128), (unsigned)A.S), 128, 0, s>>>(A);
                     k_adj_pairs<PDQ_MIXED, NT><<<grid, NT, 0, s>>>(A);
                 } else {

@@ -1,0 +1,221 @@
+// pdq_newton.cuh -- Coulomb sums with each unordered pair evaluated once (Newton pairs),
+// packed FP32: the pair math, the z-range classification of tile pairs and the per-tile
+// sum shared by the step (k_pairs_sym) and the adjoint's forward sweep.
+#pragma once
+
+#include <type_traits>
+
+#include "pdq_device.cuh"
+
+namespace pdq {
+
+// ---------------------------------------------------------------------------
+// The Coulomb sums with each unordered pair evaluated once
+// (Newton's third law, G(-d) = -G(d)): a_i += q_j G(d) and a_j -= q_i G(d), d = x_i - x_j,
+// G(d) = d / max(|d|, d_c)^3.  Per packed pair (two i-particles, one j) 16 f32x2
+// operations and 2 rsqrt give four ordered pairs, against 12 and 2 for two ordered pairs
+// in the one-sided loop.  MINIMG: per-pair minimum image in z (else the tile pair's uniform
+// shift is folded into zi); CLAMP: some pair of the tiles may come closer than d_c.
+// nqi = -q_i; the j-side sums of the two lanes land in (jx, jy, jz).
+// ---------------------------------------------------------------------------
+template <bool MINIMG, bool CLAMP>
+__device__ __forceinline__ void coulomb_pair_x2_sym(f2 xi, f2 yi, f2 zi, f2 nqi, f2 xj, f2 yj, f2 zj, f2 qj,
+                                                    f2 invL2, f2 M2, f2 nM2, f2 nL2, float c2, f2& ax, f2& ay,
+                                                    f2& az, f2& jx, f2& jy, f2& jz) {
+    const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj);
+    f2 dz = f2_sub(zi, zj);
+    if constexpr (MINIMG) {
+        const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
+        dz = f2_fma(nL2, t, dz);
+    }
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    if constexpr (CLAMP) { ra = fmaxf(ra, c2); rb = fmaxf(rb, c2); }
+    const f2 ri = f2_pack(rsqrt_ftz(ra), rsqrt_ftz(rb));
+    const f2 ri3 = f2_mul(f2_mul(ri, ri), ri);
+    const f2 si = f2_mul(ri3, qj), sj = f2_mul(ri3, nqi);
+    ax = f2_fma(si, dx, ax);
+    ay = f2_fma(si, dy, ay);
+    az = f2_fma(si, dz, az);
+    jx = f2_fma(sj, dx, jx);
+    jy = f2_fma(sj, dy, jy);
+    jz = f2_fma(sj, dz, jz);
+}
+
+// z-range classification of an i-range [alo, ahi] against a j-range [blo, bhi] (as in k_step):
+// inside one period window the minimum image is a uniform shift; z-separated by more than
+// dcz the clamp is dropped too.
+struct ZClass { bool direct, apart; float shift; };
+__device__ __forceinline__ ZClass zclass(float alo, float ahi, float blo, float bhi, float Lf, float dcz) {
+    const float dlo = alo - bhi, dhi = ahi - blo, halfL = 0.5f * Lf;
+    ZClass t{true, false, 0.f};
+    if (dlo > -halfL && dhi < halfL) t.shift = 0.f;
+    else if (dlo > halfL && dhi < 3.f * halfL) t.shift = Lf;
+    else if (dhi < -halfL && dlo > -3.f * halfL) t.shift = -Lf;
+    else t.direct = false;
+    t.apart = t.direct && ((dlo - t.shift > dcz) || (dhi - t.shift < -dcz));
+    return t;
+}
+
+// Coulomb sums of one i-tile: particles [base, base + NT*U) of a sample ending at `end`, paired
+// with every particle of the sample from `base` on, added into acc (x, y, z; w untouched):
+//   - the tile's own particles (the diagonal block): one-sided, each i against every j of it;
+//   - the later particles: Newton pairs.  A j-tile of NT particles is staged in shared memory;
+//     each warp takes it in groups of 32 j, lane l holding j = (l + k) mod 32 at step k and
+//     passing that j's running sum to lane l - 1 after the step, so that within a warp no two
+//     lanes touch the same j and after 32 steps every sum is back at its own lane.  The per-warp
+//     sums of the tile are added in shared memory and leave with one float4 atomic per j.
+// The earlier particles of the sample reach this tile as the j side of earlier tiles.
+// load(g) gives particle g as (x, y, z, q).  Padding particles sit far off the axis
+// (x = +-1e15) with zero charge, so they add nothing.  All threads of the CTA take part; the
+// shared arrays are the calling kernel's (one set per kernel instantiation).
+template <int NT, int U, class Load>
+__device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int64_t end, float Lf, float invL,
+                                            float c2, float4* __restrict__ acc) {
+    constexpr int W = NT / 32, H = U / 2;
+    static_assert(U % 2 == 0 && NT % 32 == 0, "packed pairs over whole warps");
+    // the staged j-tile pre-duplicated, (x,x,y,y) at sj2[j] and (z,z,q,q) at sj2[NT + j] (16-byte
+    // strides, so the skewed per-lane reads of the Newton loop are free of bank conflicts);
+    // per-warp j-side sums; z range of each 32-j group
+    __shared__ __align__(32) ulonglong2 sj2[2 * NT];
+    __shared__ float s_jacc[W][3][NT];
+    __shared__ float2 s_zr[W];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float M = 12582912.0f;
+    const f2 invL2 = f2_pack(invL, invL), M2 = f2_pack(M, M), nM2 = f2_pack(-M, -M);
+    const f2 nL2 = f2_pack(-Lf, -Lf);
+    const float dcz = sqrtf(c2) + 1e-3f;     // contact distance + rounding margin
+    const float kPadI = 1e15f, kPadJ = -1e15f;
+    const int64_t dend = base + NT * U < end ? base + NT * U : end;
+    f2 X[H], Y[H], Z[H], NQ[H], AX[H], AY[H], AZ[H];
+    float ilo = INFINITY, ihi = -INFINITY;
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        float4 p[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t g = base + (2 * h + e) * NT + tid;
+            if (g < end) {
+                p[e] = load(g);
+                ilo = fminf(ilo, p[e].z);
+                ihi = fmaxf(ihi, p[e].z);
+            } else {
+                p[e] = make_float4(kPadI, 0.f, 0.f, 0.f);
+            }
+        }
+        X[h] = f2_pack(p[0].x, p[1].x);
+        Y[h] = f2_pack(p[0].y, p[1].y);
+        Z[h] = f2_pack(p[0].z, p[1].z);
+        NQ[h] = f2_pack(-p[0].w, -p[1].w);
+        AX[h] = AY[h] = AZ[h] = 0ull;
+    }
+    for (int d = 16; d > 0; d >>= 1) {     // this warp's i range
+        ilo = fminf(ilo, __shfl_xor_sync(0xffffffffu, ilo, d));
+        ihi = fmaxf(ihi, __shfl_xor_sync(0xffffffffu, ihi, d));
+    }
+    for (int64_t j0 = base; j0 < end; j0 += NT) {
+        const bool diag = j0 < dend;
+        const int64_t jlim = diag ? dend : end;
+        const int64_t j = j0 + tid;
+        const float4 pj = j < jlim ? load(j) : make_float4(kPadJ, 0.f, 0.f, 0.f);
+        float jlo = j < jlim ? pj.z : INFINITY, jhi = j < jlim ? pj.z : -INFINITY;
+        for (int d = 16; d > 0; d >>= 1) {
+            jlo = fminf(jlo, __shfl_xor_sync(0xffffffffu, jlo, d));
+            jhi = fmaxf(jhi, __shfl_xor_sync(0xffffffffu, jhi, d));
+        }
+        if (lane == 0) s_zr[warp] = make_float2(jlo, jhi);
+        sj2[tid] = make_ulonglong2(f2_pack(pj.x, pj.x), f2_pack(pj.y, pj.y));
+        sj2[NT + tid] = make_ulonglong2(f2_pack(pj.z, pj.z), f2_pack(pj.w, pj.w));
+        __syncthreads();
+        if (diag) {
+            // one-sided over the tile's own particles (self pair: d = 0 adds nothing)
+            float blo = INFINITY, bhi = -INFINITY;
+#pragma unroll
+            for (int w = 0; w < W; ++w) { blo = fminf(blo, s_zr[w].x); bhi = fmaxf(bhi, s_zr[w].y); }
+            const ZClass zc = zclass(ilo, ihi, blo, bhi, Lf, dcz);
+            float mn = 0.f;
+            if (zc.direct) {
+                const f2 sh = f2_pack(zc.shift, zc.shift);
+                f2 Zs[H];
+#pragma unroll
+                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+#pragma unroll 4
+                for (int k = 0; k < NT; ++k) {
+                    const ulonglong2 a = sj2[k], b = sj2[NT + k];
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        coulomb_pair_x2_direct<true>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, c2, AX[h], AY[h], AZ[h],
+                                                     mn);
+                }
+            } else {
+#pragma unroll 4
+                for (int k = 0; k < NT; ++k) {
+                    const ulonglong2 a = sj2[k], b = sj2[NT + k];
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        coulomb_pair_x2<false>(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2, AX[h],
+                                               AY[h], AZ[h], mn);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        // Newton pairs with the later particles, one 32-j group at a time
+#pragma unroll 1
+        for (int g = 0; g < W; ++g) {
+            const float2 zr = s_zr[g];
+            const ZClass zc = zclass(ilo, ihi, zr.x, zr.y, Lf, dcz);
+            float jx = 0.f, jy = 0.f, jz = 0.f;
+            auto group = [&](auto minimg, auto clamp, const f2* Zt) {
+#pragma unroll 4
+                for (int k = 0; k < 32; ++k) {
+                    const int jj = g * 32 + ((lane + k) & 31);
+                    const ulonglong2 a = sj2[jj], b = sj2[NT + jj];
+                    f2 JX = f2_pack(jx, 0.f), JY = f2_pack(jy, 0.f), JZ = f2_pack(jz, 0.f);
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        coulomb_pair_x2_sym<decltype(minimg)::value, decltype(clamp)::value>(
+                            X[h], Y[h], Zt[h], NQ[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2, AX[h], AY[h],
+                            AZ[h], JX, JY, JZ);
+                    float l0, l1;
+                    f2_unpack(JX, l0, l1); jx = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                    f2_unpack(JY, l0, l1); jy = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                    f2_unpack(JZ, l0, l1); jz = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                }
+            };
+            if (zc.direct) {
+                const f2 sh = f2_pack(zc.shift, zc.shift);
+                f2 Zs[H];
+#pragma unroll
+                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+                if (zc.apart) group(std::false_type{}, std::false_type{}, Zs);
+                else group(std::false_type{}, std::true_type{}, Zs);
+            } else {
+                group(std::true_type{}, std::true_type{}, Z);
+            }
+            s_jacc[warp][0][g * 32 + lane] = jx;
+            s_jacc[warp][1][g * 32 + lane] = jy;
+            s_jacc[warp][2][g * 32 + lane] = jz;
+        }
+        __syncthreads();
+        if (j < end) {
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+            for (int w = 0; w < W; ++w) { sx += s_jacc[w][0][tid]; sy += s_jacc[w][1][tid]; sz += s_jacc[w][2][tid]; }
+            atomicAdd(&acc[j], make_float4(sx, sy, sz, 0.f));
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        float a0[3], a1[3];
+        f2_unpack(AX[h], a0[0], a1[0]);
+        f2_unpack(AY[h], a0[1], a1[1]);
+        f2_unpack(AZ[h], a0[2], a1[2]);
+        const int64_t g0 = base + (2 * h) * NT + tid, g1 = g0 + NT;
+        if (g0 < end) atomicAdd(&acc[g0], make_float4(a0[0], a0[1], a0[2], 0.f));
+        if (g1 < end) atomicAdd(&acc[g1], make_float4(a1[0], a1[1], a1[2], 0.f));
+    }
+}
+
+}  // namespace pdq
