@@ -372,8 +372,11 @@ int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_steps, int32_t 
  * - 2 A_cont gamma_c/m (m^2/s^2; eps_stick > 0 required), and the rest of the
  * particle rebounds with CoR_n (0 when arg <= 0, capped at 1), mirrored into
  * the pipe.  J (device [S][C]) is always written.  Reads offset[] to the host
- * (synchronises `stream`).
- * Errors: INVALID_ARG, WORKSPACE, CUDA.                                      */
+ * (synchronises `stream`).  PDQ_MIXED with Coulomb forces evaluates each
+ * particle pair once for both particles (float sums through atomics, so not
+ * bit-reproducible from run to run) and takes at most 33,553,920 particles
+ * per sample.
+ * Errors: INVALID_ARG, WORKSPACE, UNSUPPORTED (sample too large), CUDA.     */
 int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
                     const pdq_sample_params* params, double charge_sigma, uint64_t seed, const pdq_step_cfg* cfg,
                     int64_t n_steps, int32_t K, double eps, double eps_stick, int32_t n_vec, const double* gbar,

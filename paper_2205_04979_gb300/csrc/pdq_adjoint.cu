@@ -1001,13 +1001,14 @@ __global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
 // Newton pairs (MIXED): each unordered pair evaluated once for both particles.
 // ---------------------------------------------------------------------------
 // Forward Coulomb sums S_i = sum_j Q_j G(x_i - x_j), Q = w xi qhat, into A.acc4 (zeroed before
-// the launch) with the step's newton_tile; grid (i-tiles of NT*U, samples).  k_adj_forward
-// with SUMS then does the local part.
+// the launch) with the step's newton_tile; grid (samples, i-tiles of NT*U): CTAs go out in
+// tile order, so the first tiles of every sample (the most later particles) start first.
+// k_adj_forward with SUMS then does the local part.
 template <int NT, int U>
 __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_sums_sym(const AdjArgs A) {
-    const int s = blockIdx.y;
+    const int s = blockIdx.x;
     const int64_t o = A.offset[s], end = A.offset[s + 1];
-    const int64_t base = o + (int64_t)blockIdx.x * NT * U;
+    const int64_t base = o + (int64_t)blockIdx.y * NT * U;
     if (base >= end) return;
     const double xi = A.params[s].xi;
     const auto load = [&](int64_t g) {
@@ -1065,8 +1066,8 @@ __device__ __forceinline__ void vjp_pair_x2_sym(f2 xm, f2 ym, f2 zm, f2 nQm, f2 
     jq = f2_fma(ri3, dcm, jq);
 }
 
-// Pair VJP with Newton pairs (MIXED), the scheme of newton_tile: grid (m-tiles of NT*U,
-// samples); the tile's own block one-sided (the j sums of vjp_pair_x2_sym left unused), every
+// Pair VJP with Newton pairs (MIXED), the scheme of newton_tile: grid (samples, m-tiles of
+// NT*U), heavy first tiles first; the tile's own block one-sided (the j sums of vjp_pair_x2_sym left unused), every
 // later particle of the sample as a Newton pair with 32-j groups walked by skewed lanes.  Sums
 // (x-bar x, y, z, Qp) go to A.acc4 by float4 atomics; k_adj_pairs_finish applies them.
 template <int NT, int U>
@@ -1077,9 +1078,9 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_pairs_sym(const A
     __shared__ __align__(16) ulonglong2 sA[NT], sB[NT], sC[NT], sD[NT];
     __shared__ float s_jacc[W][4][NT];
     __shared__ float2 s_zr[W];
-    const int s = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t o = A.offset[s], end = A.offset[s + 1];
-    const int64_t base = o + (int64_t)blockIdx.x * NT * U;
+    const int64_t base = o + (int64_t)blockIdx.y * NT * U;
     if (base >= end) return;
     const int64_t dend = base + NT * U < end ? base + NT * U : end;
     const double xi = A.params[s].xi;
@@ -1410,8 +1411,10 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
     // pairs, each unordered pair once, through A.acc4
     const bool newton = mixed && (A.K.forces & PDQ_F_COULOMB);
     const int NTN = 128;
-    const dim3 grid_sums((unsigned)((nmax + 8 * NTN - 1) / (8 * NTN)), (unsigned)A.S);
-    const dim3 grid_vjp((unsigned)((nmax + 4 * NTN - 1) / (4 * NTN)), (unsigned)A.S);
+    // grid y counts the tiles of the largest sample (at most 65,535: 33.5 M particles per sample)
+    if (newton && (nmax + 4 * NTN - 1) / (4 * NTN) > 65535) return PDQ_ERR_UNSUPPORTED;
+    const dim3 grid_sums((unsigned)A.S, (unsigned)((nmax + 8 * NTN - 1) / (8 * NTN)));
+    const dim3 grid_vjp((unsigned)A.S, (unsigned)((nmax + 4 * NTN - 1) / (4 * NTN)));
     auto fwd = [&](const Slot& in, const Slot& out, int64_t step, int tally) -> cudaError_t {
         A.in = in; A.out = out; A.step = step; A.tally = tally;
         if (newton) {
