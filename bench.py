@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--workload", default="batched_mixed")
     ap.add_argument("--samples", type=int, default=None, help="truncate the workload (testing only)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-groups", type=int, default=4,
+                    help="sample groups pipelined in the e2e measurement (1 = upload, step, download in turn)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -234,6 +236,73 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_e2e(pdq, field, phys, state, prm, cfg, w, args, stream):
+    """End-to-end particle-steps/s through the public API, host state in pinned memory."""
+    import torch
+    S = state.n_samples
+    G = max(1, min(args.e2e_groups, S))
+    bounds = [S * k // G for k in range(G + 1)]
+    off = state.offset.cpu().numpy()
+    pos, vel, xy = state.current()
+    groups = []
+    for k in range(G):
+        s0, s1 = bounds[k], bounds[k + 1]
+        o0, o1 = int(off[s0]), int(off[s1])
+        st = pdq.State(state.precision, state.counts0[s0:s1], state.st_plus)
+        st.pos[0].copy_(pos[o0:o1])
+        st.vel[0].copy_(vel[o0:o1])
+        if xy is not None:
+            st.xy[0].copy_(xy[o0:o1])
+        st.tag.copy_(state.tag[o0:o1])
+        st.count.copy_(state.count[s0:s1])
+        st.ctl[0] = state.step_index
+        st.st.step = state.step_index
+        tl = pdq.Tally(s1 - s0, state.n_classes)
+        dev = [t for t in st.current() if t is not None] + [st.tag, st.count]
+        hosts = [t.cpu().pin_memory() for t in dev]
+        htal = [tl.n_alive.cpu().pin_memory(), tl.n_dep.cpu().pin_memory()]
+        groups.append(dict(st=st, tally=tl, prm=prm[s0:s1], ws=pdq.workspace(st, cfg), hosts=hosts, htal=htal))
+    torch.cuda.synchronize()
+
+    def dev_state(st):
+        return [t for t in st.current() if t is not None] + [st.tag, st.count]
+
+    h2d = sum(sum(t.numel() * t.element_size() for t in g["hosts"]) for g in groups)
+    d2h = h2d + sum(sum(t.numel() * t.element_size() for t in g["htal"]) for g in groups)
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def one_step():
+        for g in groups:
+            with torch.cuda.stream(s_in):
+                for dst, src in zip(dev_state(g["st"]), g["hosts"]):
+                    dst.copy_(src, non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(s_in)
+            stream.wait_event(ev_in)
+            pdq.step_particles(field, phys, g["st"], g["prm"], cfg, 1, g["tally"], g["ws"], stream)
+            ev_done = torch.cuda.Event()
+            ev_done.record(stream)
+            s_out.wait_event(ev_done)
+            with torch.cuda.stream(s_out):
+                for dst, src in zip(g["hosts"], dev_state(g["st"])):
+                    dst.copy_(src, non_blocking=True)
+                g["htal"][0].copy_(g["tally"].n_alive, non_blocking=True)
+                g["htal"][1].copy_(g["tally"].n_dep, non_blocking=True)
+        s_out.synchronize()
+
+    one_step()                                       # untimed warm-up (first calls read offsets)
+    torch.cuda.synchronize()
+    alive0 = sum(int(g["tally"].n_alive.sum().item()) for g in groups)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        one_step()
+    te = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    alive = sum(int(g["tally"].n_alive.sum().item()) for g in groups) - alive0
+    return {"value": float(alive) / te, "unit": "particle-steps/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "sample_groups": G}
+
+
 def run_ours(args):
     import torch
     import paper_2205_04979_gb300.pdq as pdq
@@ -300,40 +369,13 @@ def run_ours(args):
         per_step = 2 if cfg.variant == 3 and not args.contact else 1
         launches = 1 + 1 + per_step * args.steps + 2 * n_rebin
 
-        # e2e: state in pinned host memory; upload, one step, download state + tallies
+        # e2e: state in pinned host memory; every step uploads the state, steps it and downloads the
+        # state and the tallies.  The batch is cut into --e2e-groups contiguous sample groups, each
+        # a state of its own; group g's upload (copy-in stream), step (compute stream) and
+        # download (copy-out stream) are ordered by events, so copies overlap other groups' steps.
         e2e = None
         if args.e2e_steps > 0:
-            def dev_state():
-                return [t for t in state.current() if t is not None] + [state.tag]
-
-            hosts = [t.cpu().pin_memory() for t in dev_state()]
-            hcnt = state.count.cpu().pin_memory()
-            htal = tally.n_alive.cpu().pin_memory()
-            hdep = tally.n_dep.cpu().pin_memory()
-            h2d = sum(t.numel() * t.element_size() for t in hosts) + hcnt.numel() * 4
-            d2h = h2d + htal.numel() * 8 * 2
-            alive_e = 0
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for rep in range(args.e2e_steps + 1):            # the first pass is an untimed warm-up
-                if rep == 1:
-                    alive_e = 0
-                    t0 = time.perf_counter()
-                for dst, src in zip(dev_state(), hosts):
-                    dst.copy_(src, non_blocking=True)
-                state.count.copy_(hcnt, non_blocking=True)
-                a0 = tally.n_alive.sum()
-                pdq.step_particles(field, phys, state, prm, cfg, 1, tally, ws, stream)
-                alive_e += tally.n_alive.sum() - a0
-                for dst, src in zip(hosts, dev_state()):
-                    dst.copy_(src, non_blocking=True)
-                hcnt.copy_(state.count, non_blocking=True)
-                htal.copy_(tally.n_alive, non_blocking=True)
-                hdep.copy_(tally.n_dep, non_blocking=True)
-                stream.synchronize()
-            te = time.perf_counter() - t0
-            e2e = {"value": float(alive_e.item()) / te, "unit": "particle-steps/s", "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(d2h)}
+            e2e = run_e2e(pdq, field, phys, state, prm, cfg, w, args, stream)
 
         # plain FP64 single-sample path (the comparison the metric names)
         fp64 = None

@@ -253,8 +253,9 @@ int pdq_step_workspace_size(const pdq_state* state, const pdq_step_cfg* cfg, siz
  * identify particles by tag, not by row) at the start of the call and every
  * min(compact_every, 10) steps (every 10 when compact_every = 0); when
  * compact_every > 0 the same pass compacts deposited particles out, updating
- * count[].  The first call for a state reads offset[] to the host
- * (synchronises `stream`).
+ * count[].  All work is enqueued on `stream`; the call does not wait for it
+ * (except graph mode's first call for an argument set, which instantiates a
+ * graph).
  * Errors: INVALID_ARG, WORKSPACE, CUDA.  Non-finite states set the error word
  * read by pdq_check_state.                                                   */
 int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, pdq_state* state,
