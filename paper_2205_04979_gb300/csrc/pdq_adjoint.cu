@@ -417,10 +417,7 @@ __global__ void k_adj_unperm(const int64_t* __restrict__ offset, const int32_t* 
     if (i < n) out[o + perm[o + i]] = in[o + i];
 }
 
-// Tile pairs of a z-binned sample (MIXED pair loops): the dz of an (i-tile, j-tile) pair lies in
-// [a_lo - b_hi, a_hi - b_lo]; inside one period window the minimum image is a uniform shift
-// (0 or +-L, folded into z_i), and when every |dz| also exceeds the contact distance the clamp
-// goes too (as in the step kernel).
+// z range (min, max) over a warp.
 __device__ __forceinline__ float2 warp_range(float lo, float hi) {
     for (int d = 16; d > 0; d >>= 1) {
         lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, d));
@@ -428,17 +425,9 @@ __device__ __forceinline__ float2 warp_range(float lo, float hi) {
     }
     return make_float2(lo, hi);
 }
-__device__ __forceinline__ ZClass classify_tiles(const float2* s_zi, const float2* s_zr, int nw, float L, float dcz) {
-    float alo = INFINITY, ahi = -INFINITY, blo = INFINITY, bhi = -INFINITY;
-    for (int w = 0; w < nw; ++w) {
-        alo = fminf(alo, s_zi[w].x); ahi = fmaxf(ahi, s_zi[w].y);
-        blo = fminf(blo, s_zr[w].x); bhi = fmaxf(bhi, s_zr[w].y);
-    }
-    return zclass(alo, ahi, blo, bhi, L, dcz);
-}
 
-// Particles per thread of the forward and pair-VJP kernels: MIXED packs two i-particles
-// per f32x2 instruction (4 per thread), FP64 keeps 2 for ILP.
+// Particles per thread of k_adj_forward and k_adj_pairs: MIXED 4 (their local parts only: its
+// pair sums and pair VJP are the Newton-pair kernels below), FP64 2 for ILP in the pair loops.
 template <int P> __host__ __device__ constexpr int adj_ilp() { return P == PDQ_MIXED ? 4 : 2; }
 
 // SUMS: the Coulomb sums come from A.acc4 (the Newton-pair kernel k_adj_sums_sym) instead of the
@@ -449,7 +438,6 @@ __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
     typedef typename Real<P>::T4 T4;
     constexpr int U = adj_ilp<P>();          // particles per thread (ILP over the shared j-tile)
     __shared__ __align__(32) unsigned char smem_raw[NT * 32];
-    __shared__ float2 s_zi[NT / 32], s_zr[NT / 32];
     T4* sj = reinterpret_cast<T4*>(smem_raw);
     const int s = blockIdx.y, tid = threadIdx.x;
     const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
@@ -476,90 +464,8 @@ __global__ void __launch_bounds__(NT) k_adj_forward(const AdjArgs A) {
                 ax[u] = (T)a.x; ay[u] = (T)a.y; az[u] = (T)a.z;
             }
         }
-    } else if ((K.forces & PDQ_F_COULOMB) && P == PDQ_MIXED) {
-        // packed: j-tile staged pre-duplicated (x, x, y, y), (z, z, qw, qw); two i-particles per lane op
-        constexpr int H = U / 2;
-        ulonglong2* sj2 = reinterpret_cast<ulonglong2*>(smem_raw);
-        const float L = (float)K.L, M = 12582912.0f;
-        const f2 invL2 = f2_pack((float)K.invL, (float)K.invL), M2 = f2_pack(M, M), nM2 = f2_pack(-M, -M);
-        const f2 nL2 = f2_pack(-L, -L);
-        const float c2 = (float)K.contact2f;
-        f2 X[H], Y[H], Z[H], AX[H], AY[H], AZ[H];
-        float unused = 0.f;
-#pragma unroll
-        for (int h = 0; h < H; ++h) {
-            X[h] = f2_pack((float)xi[2 * h], (float)xi[2 * h + 1]);
-            Y[h] = f2_pack((float)yi[2 * h], (float)yi[2 * h + 1]);
-            Z[h] = f2_pack((float)zi[2 * h], (float)zi[2 * h + 1]);
-            AX[h] = AY[h] = AZ[h] = 0ull;
-        }
-        {
-            float lo = INFINITY, hi = -INFINITY;
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if ((int64_t)blockIdx.x * NT * U + u * NT + tid < n) { lo = fminf(lo, (float)zi[u]); hi = fmaxf(hi, (float)zi[u]); }
-            const float2 r = warp_range(lo, hi);
-            if ((tid & 31) == 0) s_zi[tid >> 5] = r;
-        }
-        const float dcz = sqrtf(c2) + 1e-3f;
-        for (int64_t j0 = 0; j0 < n; j0 += NT) {
-            const int64_t j = j0 + tid;
-            float px = 0.f, py = 0.f, pz = 0.f, pq = 0.f;
-            if (j < n) {
-                const int64_t gj = o + j;
-                px = (float)A.in.x[gj]; py = (float)A.in.y[gj]; pz = (float)A.in.z[gj];
-                pq = (float)(A.in.w[gj] * sp.xi * A.qhat[gj]);
-            }
-            const float2 r = warp_range(j < n ? pz : INFINITY, j < n ? pz : -INFINITY);
-            if ((tid & 31) == 0) s_zr[tid >> 5] = r;
-            sj2[2 * tid] = make_ulonglong2(f2_pack(px, px), f2_pack(py, py));
-            sj2[2 * tid + 1] = make_ulonglong2(f2_pack(pz, pz), f2_pack(pq, pq));
-            __syncthreads();
-            const ZClass tc = classify_tiles(s_zi, s_zr, NT / 32, L, dcz);
-            if (tc.direct) {
-                const f2 sh = f2_pack(tc.shift, tc.shift);
-                f2 Zs[H];
-#pragma unroll
-                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
-                if (tc.apart) {
-#pragma unroll 4
-                    for (int k = 0; k < NT; ++k) {
-                        const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
-#pragma unroll
-                        for (int h = 0; h < H; ++h)
-                            coulomb_pair_x2_direct<false>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, c2, AX[h], AY[h],
-                                                          AZ[h], unused);
-                    }
-                } else {
-#pragma unroll 4
-                    for (int k = 0; k < NT; ++k) {
-                        const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
-#pragma unroll
-                        for (int h = 0; h < H; ++h)
-                            coulomb_pair_x2_direct<true>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, c2, AX[h], AY[h],
-                                                         AZ[h], unused);
-                    }
-                }
-            } else {
-#pragma unroll 4
-                for (int k = 0; k < NT; ++k) {
-                    const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
-#pragma unroll
-                    for (int h = 0; h < H; ++h)
-                        coulomb_pair_x2<false>(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2, AX[h],
-                                               AY[h], AZ[h], unused);
-                }
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int h = 0; h < H; ++h) {
-            float a0, a1;
-            f2_unpack(AX[h], a0, a1); ax[2 * h] = (T)a0; ax[2 * h + 1] = (T)a1;
-            f2_unpack(AY[h], a0, a1); ay[2 * h] = (T)a0; ay[2 * h + 1] = (T)a1;
-            f2_unpack(AZ[h], a0, a1); az[2 * h] = (T)a0; az[2 * h + 1] = (T)a1;
-        }
-    } else if (K.forces & PDQ_F_COULOMB) {
+    } else if (P == PDQ_FP64 && (K.forces & PDQ_F_COULOMB)) {
+        // (MIXED takes the Coulomb sums from k_adj_sums_sym: SUMS)
         const T L = (T)K.L, invL = (T)K.invL;
         const T c2 = P == PDQ_FP64 ? (T)K.contact2 : (T)K.contact2f;
         for (int64_t j0 = 0; j0 < n; j0 += NT) {
@@ -748,54 +654,14 @@ __global__ void __launch_bounds__(128) k_adj_local(const AdjArgs A) {
 // All-pairs adjoint of S_m = sum_j Q_j G(x_m - x_j), Q = w q, G(d) = d / max(|d|, d_c)^3:
 //   xbar_m += sum_j J(d_mj) (Q_j c_m - Q_m c_j),  J = (I - 3 d d^T / |d|^2) / |d|^3 (|d| > d_c) or I / d_c^3,
 //   Qbar_m  = -sum_j c_j . G(d_mj);  then qbar_m += w_m Qbar_m, wbar_m += q_m Qbar_m, xi-bar += qbar_m qhat_m.
-// One j against two m-particles of the pair VJP, packed f32x2 (the scalar loop below, two
-// lanes per instruction).  nQm = -Q_m; mask3 = -3 where r^2 exceeds the clamp, 0 inside it.
-// Accumulates A1 += Q_j/r^3, A2 += c_j/r^3, A3 += k d with k = -3 (Q_j d.c_m - Q_m d.c_j)/r^5,
-// Qp += (d.c_j)/r^3 (the caller negates it).  MINIMG: fold dz to the minimum image (else zm
-// carries the tile pair's uniform shift); CLAMP: some pair of the tiles may be closer than d_c.
+// A j-particle of the packed pair VJP, each value duplicated in both halves: position, Q, c.
 struct VjpJ { f2 x, y, z, Q, cx, cy, cz; };
-template <bool MINIMG, bool CLAMP>
-__device__ __forceinline__ void vjp_pair_x2(f2 xm, f2 ym, f2 zm, f2 nQm, f2 cmx, f2 cmy, f2 cmz, const VjpJ& J,
-                                            f2 invL2, f2 M2, f2 nM2, f2 nL2, float c2, f2& A1, f2& A2x, f2& A2y,
-                                            f2& A2z, f2& A3x, f2& A3y, f2& A3z, f2& Qp) {
-    const f2 dx = f2_sub(xm, J.x), dy = f2_sub(ym, J.y);
-    f2 dz = f2_sub(zm, J.z);
-    if constexpr (MINIMG) {
-        const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
-        dz = f2_fma(nL2, t, dz);
-    }
-    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
-    float ra, rb;
-    f2_unpack(r2, ra, rb);
-    f2 ri, mask3;
-    if constexpr (CLAMP) {
-        ri = f2_pack(rsqrt_ftz(fmaxf(ra, c2)), rsqrt_ftz(fmaxf(rb, c2)));
-        mask3 = f2_pack(ra > c2 ? -3.f : 0.f, rb > c2 ? -3.f : 0.f);
-    } else {
-        ri = f2_pack(rsqrt_ftz(ra), rsqrt_ftz(rb));
-        mask3 = f2_pack(-3.f, -3.f);
-    }
-    const f2 ri2 = f2_mul(ri, ri), ri3 = f2_mul(ri2, ri);
-    const f2 dcj = f2_fma(dx, J.cx, f2_fma(dy, J.cy, f2_mul(dz, J.cz)));
-    const f2 dcm = f2_fma(dx, cmx, f2_fma(dy, cmy, f2_mul(dz, cmz)));
-    A1 = f2_fma(J.Q, ri3, A1);
-    A2x = f2_fma(ri3, J.cx, A2x);
-    A2y = f2_fma(ri3, J.cy, A2y);
-    A2z = f2_fma(ri3, J.cz, A2z);
-    const f2 w = f2_fma(J.Q, dcm, f2_mul(nQm, dcj));       // Q_j d.c_m - Q_m d.c_j
-    const f2 kk = f2_mul(f2_mul(f2_mul(ri3, ri2), mask3), w);
-    A3x = f2_fma(kk, dx, A3x);
-    A3y = f2_fma(kk, dy, A3y);
-    A3z = f2_fma(kk, dz, A3z);
-    Qp = f2_fma(ri3, dcj, Qp);
-}
 
 template <int P, int NT>
 __global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
     typedef typename Real<P>::T T;
     constexpr int U = adj_ilp<P>();          // particles m per thread
     __shared__ __align__(16) unsigned char smem_raw[P == PDQ_MIXED ? NT * 64 : 7 * NT * sizeof(T)];
-    __shared__ float2 s_zi[NT / 32], s_zr[NT / 32];
     T (*sj)[NT] = reinterpret_cast<T (*)[NT]>(smem_raw);
     const int s = blockIdx.y, tid = threadIdx.x;
     const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
@@ -805,114 +671,8 @@ __global__ void __launch_bounds__(NT) k_adj_pairs(const AdjArgs A) {
     double xi_bar[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) xi_bar[u] = 0.0;
-    if ((K.forces & PDQ_F_COULOMB) && P == PDQ_MIXED) {
-        constexpr int H = U / 2;
-        ulonglong2* sj2 = reinterpret_cast<ulonglong2*>(smem_raw);    // [NT][4]: (x,y), (z,Q), (cx,cy), (cz,-)
-        const float L = (float)K.L, M = 12582912.0f;
-        const f2 invL2 = f2_pack((float)K.invL, (float)K.invL), M2 = f2_pack(M, M), nM2 = f2_pack(-M, -M);
-        const f2 nL2 = f2_pack(-L, -L);
-        const float c2 = (float)K.contact2f;
-        float xm[U], ym[U], zm[U], Qm[U], cmx[U], cmy[U], cmz[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = (int64_t)blockIdx.x * NT * U + u * NT + tid;
-            const bool valid = i < n;
-            const int64_t g = o + (valid ? i : 0);
-            xm[u] = valid ? (float)A.in.x[g] : 0.f;
-            ym[u] = valid ? (float)A.in.y[g] : 0.f;
-            zm[u] = valid ? (float)A.in.z[g] : 0.f;
-            Qm[u] = valid ? (float)(A.in.w[g] * sp.xi * A.qhat[g]) : 0.f;
-            cmx[u] = valid ? (float)A.cx[g] : 0.f;
-            cmy[u] = valid ? (float)A.cy[g] : 0.f;
-            cmz[u] = valid ? (float)A.cz[g] : 0.f;
-        }
-        f2 X[H], Y[H], Z[H], NQ[H], CX[H], CY[H], CZ[H];
-        f2 A1[H], A2x[H], A2y[H], A2z[H], A3x[H], A3y[H], A3z[H], Qp[H];
-#pragma unroll
-        for (int h = 0; h < H; ++h) {
-            X[h] = f2_pack(xm[2 * h], xm[2 * h + 1]);
-            Y[h] = f2_pack(ym[2 * h], ym[2 * h + 1]);
-            Z[h] = f2_pack(zm[2 * h], zm[2 * h + 1]);
-            NQ[h] = f2_pack(-Qm[2 * h], -Qm[2 * h + 1]);
-            CX[h] = f2_pack(cmx[2 * h], cmx[2 * h + 1]);
-            CY[h] = f2_pack(cmy[2 * h], cmy[2 * h + 1]);
-            CZ[h] = f2_pack(cmz[2 * h], cmz[2 * h + 1]);
-            A1[h] = A2x[h] = A2y[h] = A2z[h] = A3x[h] = A3y[h] = A3z[h] = Qp[h] = 0ull;
-        }
-        {
-            float lo = INFINITY, hi = -INFINITY;
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if ((int64_t)blockIdx.x * NT * U + u * NT + tid < n) { lo = fminf(lo, zm[u]); hi = fmaxf(hi, zm[u]); }
-            const float2 r = warp_range(lo, hi);
-            if ((tid & 31) == 0) s_zi[tid >> 5] = r;
-        }
-        const float dcz = sqrtf(c2) + 1e-3f;
-        for (int64_t j0 = 0; j0 < n; j0 += NT) {
-            const int64_t j = j0 + tid;
-            float v[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (j < n) {
-                const int64_t gj = o + j;
-                v[0] = (float)A.in.x[gj]; v[1] = (float)A.in.y[gj]; v[2] = (float)A.in.z[gj];
-                v[3] = (float)(A.in.w[gj] * sp.xi * A.qhat[gj]);
-                v[4] = (float)A.cx[gj]; v[5] = (float)A.cy[gj]; v[6] = (float)A.cz[gj];
-            }
-            sj2[4 * tid + 0] = make_ulonglong2(f2_pack(v[0], v[0]), f2_pack(v[1], v[1]));
-            sj2[4 * tid + 1] = make_ulonglong2(f2_pack(v[2], v[2]), f2_pack(v[3], v[3]));
-            sj2[4 * tid + 2] = make_ulonglong2(f2_pack(v[4], v[4]), f2_pack(v[5], v[5]));
-            sj2[4 * tid + 3] = make_ulonglong2(f2_pack(v[6], v[6]), 0ull);
-            const float2 r = warp_range(j < n ? v[2] : INFINITY, j < n ? v[2] : -INFINITY);
-            if ((tid & 31) == 0) s_zr[tid >> 5] = r;
-            __syncthreads();
-            const ZClass tc = classify_tiles(s_zi, s_zr, NT / 32, L, dcz);
-            auto tile = [&](auto minimg, auto clamp, const f2* Zt) {
-#pragma unroll 2
-                for (int k = 0; k < NT; ++k) {
-                    const ulonglong2 a = sj2[4 * k], b = sj2[4 * k + 1], cc = sj2[4 * k + 2], d = sj2[4 * k + 3];
-                    const VjpJ J{a.x, a.y, b.x, b.y, cc.x, cc.y, d.x};
-#pragma unroll
-                    for (int h = 0; h < H; ++h)
-                        vjp_pair_x2<decltype(minimg)::value, decltype(clamp)::value>(
-                            X[h], Y[h], Zt[h], NQ[h], CX[h], CY[h], CZ[h], J, invL2, M2, nM2, nL2, c2, A1[h], A2x[h],
-                            A2y[h], A2z[h], A3x[h], A3y[h], A3z[h], Qp[h]);
-                }
-            };
-            if (tc.direct) {
-                const f2 sh = f2_pack(tc.shift, tc.shift);
-                f2 Zs[H];
-#pragma unroll
-                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
-                if (tc.apart) tile(std::false_type{}, std::false_type{}, Zs);
-                else tile(std::false_type{}, std::true_type{}, Zs);
-            } else {
-                tile(std::true_type{}, std::true_type{}, Z);
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int h = 0; h < H; ++h) {
-            float a1[2], a2x[2], a2y[2], a2z[2], a3x[2], a3y[2], a3z[2], qp[2];
-            f2_unpack(A1[h], a1[0], a1[1]);
-            f2_unpack(A2x[h], a2x[0], a2x[1]); f2_unpack(A2y[h], a2y[0], a2y[1]); f2_unpack(A2z[h], a2z[0], a2z[1]);
-            f2_unpack(A3x[h], a3x[0], a3x[1]); f2_unpack(A3y[h], a3y[0], a3y[1]); f2_unpack(A3z[h], a3z[0], a3z[1]);
-            f2_unpack(Qp[h], qp[0], qp[1]);
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int u = 2 * h + e;
-                const int64_t i = (int64_t)blockIdx.x * NT * U + u * NT + tid;
-                if (i < n) {
-                    const int64_t g = o + i;
-                    A.xb[g] += (double)(cmx[u] * a1[e] - Qm[u] * a2x[e] + a3x[e]);
-                    A.yb[g] += (double)(cmy[u] * a1[e] - Qm[u] * a2y[e] + a3y[e]);
-                    A.zb[g] += (double)(cmz[u] * a1[e] - Qm[u] * a2z[e] + a3z[e]);
-                    const double qm = sp.xi * A.qhat[g];
-                    const double w = A.in.w[g];
-                    A.wb[g] += (double)(-qp[e]) * qm;
-                    xi_bar[u] = (A.qb[g] + (double)(-qp[e]) * w) * A.qhat[g];
-                }
-            }
-        }
-    } else if (K.forces & PDQ_F_COULOMB) {
+    // (MIXED with Coulomb forces runs the Newton-pair VJP, k_adj_pairs_sym, instead)
+    if (P == PDQ_FP64 && (K.forces & PDQ_F_COULOMB)) {
         T xm[U], ym[U], zm[U], Qm[U], cmx[U], cmy[U], cmz[U];
         // per m: A1 = sum_j Q_j / r^3, A2 = sum_j c_j / r^3, A3 = sum_j k_mj d (J's outer-product term),
         // Qb = -sum_j c_j . d / r^3; then xbar_m = c_m A1 - Q_m A2 + A3

@@ -220,14 +220,17 @@ def test_fp64_newton_pairs_chunked_single_sample(pdq, fields):
     assert np.array_equal(tally.n_dep.cpu().numpy(), nd) and np.array_equal(tally.n_alive.cpu().numpy(), na)
 
 
-def test_fp64_rebound_parity(pdq, fields):
+@pytest.mark.parametrize("variant", [0, 3])
+def test_fp64_rebound_parity(pdq, fields, variant):
     # Rebounding particles bounce inside the stiff vdW zone (accelerations ~1e4 wall units),
     # which amplifies rounding differences: the bound is 10x the oracle's own response to a
-    # 1e-14 relative perturbation of the initial positions, floored at 1e-9.
+    # 1e-14 relative perturbation of the initial positions, floored at 1e-9.  Variant 3 sums the
+    # Coulomb pairs in yet another order (Newton pairs, atomics).
     f, of, grid, _ = fields
     counts = [700, 300]
     prm = np.array([[0.1, 0.05, 0.1], [0.1, 1.0, 0.9]])   # mostly rebound / mostly stick
-    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, prm, 50, {"mode": 1})
+    st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, prm, 50, {"mode": 1, "variant": variant},
+                                       block=128 if variant == 3 else 0)
     a, off = oracle.seed(of, ST3, counts, prm, 1)
     b = a.copy()
     b.x *= 1 + 1e-14
