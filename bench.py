@@ -219,6 +219,18 @@ def vdep_check(pdq, stream, samples=16, count=4096, steps=600, dt=0.05, t_window
             "deposits_fp64": int(nf.sum()), "deposit_count_diff": int(np.abs(nm - nf).sum())}
 
 
+def workload_label(name, counts, contact=False):
+    """The workload description both arms print in config.workload."""
+    w = workloads.WORKLOADS[name]
+    return ("%s: %d samples, %d..%d particles each (%d total), %d St+ classes, %dx%dx%d field, dt+=%g, "
+            "compaction every %d steps, %s" % (
+                name, len(counts), int(np.min(counts)), int(np.max(counts)), int(np.sum(counts)),
+                len(w["st_plus"]), *w["grid"], w["dt"], w.get("compact_every", 0), w["precision"]) +
+            (" (z-binned, re-binned and compacted every 10 steps)"
+             if w["precision"] == "mixed" and w.get("compact_every", 0) > 0 else "") +
+            ("; half the charges negative, soft-sphere collisions and particle-particle vdW" if contact else ""))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -229,7 +241,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "particle-steps/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload},
+           "config": {"workload": workload_label(args.workload, counts, args.contact)},
            "cpu_baseline": base,
            "e2e": {"value": base["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
@@ -430,15 +442,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if prec == pdq.MIXED else "f64",
         "data": "synthetic",
-        "config": {"workload": "%s: %d samples, %d..%d particles each (%d total), %d St+ classes, "
-                               "%dx%dx%d field, dt+=%g, compaction every %d steps, %s" % (
-                                   args.workload, len(counts), int(np.min(counts)), int(np.max(counts)),
-                                   int(np.sum(counts)), len(w["st_plus"]), *w["grid"], w["dt"],
-                                   w.get("compact_every", 0), w["precision"]) + (
-                                   " (z-binned, re-binned and compacted every 10 steps)"
-                                   if w["precision"] == "mixed" and w.get("compact_every", 0) > 0 else "") + (
-                                   "; half the charges negative, soft-sphere collisions and particle-particle vdW"
-                                   if args.contact else ""),
+        "config": {"workload": workload_label(args.workload, counts, args.contact),
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (
                        sum(t.numel() * t.element_size() for t in state.current() if t is not None) / 1e9),
                    "parallelism": "samples sharded by rank" if world > 1 else "1 GPU",

@@ -1,0 +1,29 @@
+"""The reference arm of bench.py (the FP64 oracle on the host cores) prints the
+contract's JSON line: same metric, unit and workload description as the GPU arm,
+impl = "reference", a cpu_baseline object and a host-only e2e object."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_json_line():
+    env = dict(os.environ)
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "particle-steps/s" and d["higher_is_better"] is True
+    assert d["metric"].startswith("particle-steps/s")
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["config"]["workload"].startswith("batched_mixed: 1024 samples, 4107..32737 particles each")
+    b = d["cpu_baseline"]
+    assert b["kind"] == "oracle" and b["cores"] >= 1 and b["value"] == d["value"] and b["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
