@@ -187,8 +187,9 @@ def reduce_over_ranks(ms, psteps, world, device):
     return float(tmax[0]), float(t[1])
 
 
-def vdep_check(pdq, stream, samples=16, count=4096, steps=600, dt=0.05, t_window=10.0):
-    """V_dep+ of the batched MIXED path against the plain FP64 GPU path on the same seeds."""
+def vdep_check(pdq, stream, block, variant, samples=16, count=4096, steps=1200, dt=0.05, t_window=10.0):
+    """V_dep+ of the batched MIXED path, in the timed launch configuration (block, pair variant),
+    against the plain FP64 GPU path (Newton-pair sums in double) on the same seeds."""
     import torch
     w = workloads.WORKLOADS["batched_mixed"]
     params = workloads.sample_params(samples, 4242)
@@ -201,7 +202,8 @@ def vdep_check(pdq, stream, samples=16, count=4096, steps=600, dt=0.05, t_window
             st = pdq.State(prec, [count] * samples, w["st_plus"])
             prm = pdq.params_tensor(params)
             pdq.seed_particles(field, phys, st, prm, w["particle_seed"], 0.0, stream)
-            cfg = pdq.step_cfg(dt, window_start=workloads.window_start_step(t_window, dt), compact_every=100)
+            tile = dict(block=block, variant=variant) if prec == pdq.MIXED else dict(block=64, variant=3)
+            cfg = pdq.step_cfg(dt, window_start=workloads.window_start_step(t_window, dt), compact_every=100, **tile)
             tally = pdq.Tally(samples, len(w["st_plus"]))
             pdq.step_particles(field, phys, st, prm, cfg, steps, tally, pdq.workspace(st, cfg), stream)
             vdep, _, _ = pdq.deposition_tally(tally, dt, stream=stream)
@@ -214,6 +216,7 @@ def vdep_check(pdq, stream, samples=16, count=4096, steps=600, dt=0.05, t_window
     rel = np.abs(mean_m - mean_f) / np.where(mean_f > 0, mean_f, 1.0)
     return {"workload": "%d samples x %d particles, %d St+ classes, %d steps at dt+=%g, window t+>=%g" % (
                 samples, count, len(w["st_plus"]), steps, dt, t_window),
+            "mixed_tile": {"block": block, "variant": variant}, "fp64_tile": {"block": 64, "variant": 3},
             "vdep_fp64_mean": mean_f.tolist(), "vdep_mixed_mean": mean_m.tolist(), "mc_se_fp64": se.tolist(),
             "rel_err": rel.tolist(), "err_over_se": (np.abs(mean_m - mean_f) / np.where(se > 0, se, 1.0)).tolist(),
             "deposits_fp64": int(nf.sum()), "deposit_count_diff": int(np.abs(nm - nf).sum())}
@@ -473,7 +476,7 @@ def run_ours(args):
         "plain_fp64": fp64,
     }
     if not args.no_vdep_check and rank == 0 and args.workload == "batched_mixed":
-        out["vdep_check"] = vdep_check(pdq, stream)
+        out["vdep_check"] = vdep_check(pdq, stream, cfg.block, cfg.variant)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, params, counts, args.cpu_seconds)
     print(json.dumps(out), flush=True)
