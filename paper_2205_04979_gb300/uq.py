@@ -53,6 +53,7 @@ def sobol_deposition(m, particles, steps, st_plus=(0.1, 1.0, 10.0), ranges=((0.0
         pdq.seed_particles(field, phys, state, params, seed + 1, 0.0, stream)
         w0 = int(np.ceil(t_window / dt - 1e-9))
         cfg = pdq.step_cfg(dt, mode=mode, window_start=w0, compact_every=100)
+        pdq.autotune(field, phys, state, params, cfg, stream)      # tile shape and pair variant
         tally = pdq.Tally(S, len(st_plus))
         ws = pdq.workspace(state, cfg)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
