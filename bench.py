@@ -381,7 +381,7 @@ def run_ours(args):
         ci = min(cfg.compact_every, 10) if cfg.compact_every > 0 else 10
         n_rebin = sum(1 for k in range(args.steps - 1) if (s0 + k + 1) % ci == 0)
         # sort, build_items, the step kernel(s) per step (Newton pairs: pair sums + update), re-bin + items
-        per_step = 2 if cfg.variant == 3 and not args.contact else 1
+        per_step = 2 if cfg.variant == 3 and (not args.contact or prec == pdq.MIXED) else 1
         launches = 1 + 1 + per_step * args.steps + 2 * n_rebin
 
         # e2e: state in pinned host memory; every step uploads the state, steps it and downloads the
@@ -421,7 +421,7 @@ def run_ours(args):
         return
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    newton = cfg.variant == 3 and not args.contact
+    newton = cfg.variant == 3 and (not args.contact or prec == pdq.MIXED)
     flops_per_pair = NEWTON_FLOPS_PER_PAIR if newton else FLOPS_PER_PAIR
     if newton and prec == pdq.MIXED:
         peak_tflops = SM_COUNT * FP32_LANES * NEWTON_FLOPS_PER_LANE_OP * sm_max * 1e6 / 1e12
@@ -450,7 +450,7 @@ def run_ours(args):
                        sum(t.numel() * t.element_size() for t in state.current() if t is not None) / 1e9),
                    "parallelism": "samples sharded by rank" if world > 1 else "1 GPU",
                    "tile": {"block": cfg.block,
-                            "i_per_thread": (8 if cfg.variant in (2, 3) and not args.contact else 4)
+                            "i_per_thread": (8 if (cfg.variant == 2 and not args.contact) or newton else 4)
                             if prec == pdq.MIXED else (2 if newton else 1),
                             "variant": cfg.variant, "autotuned": args.block == 0 and not args.no_autotune}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
@@ -462,7 +462,9 @@ def run_ours(args):
                      # variant without a capture of its kernel
                      "traffic": KSTEP_DRAM_BYTES[cfg.variant] / 4557792 * float(np.sum(counts))
                      if prec == pdq.MIXED and cfg.variant in KSTEP_DRAM_BYTES and not args.contact else None,
-                     "kernel": ("k_pairs_sym (Newton-pair Coulomb sums), then the given-sums k_step update"
+                     "kernel": ("k_pairs_sym (Newton-pair Coulomb sums), then the k_step contact variant "
+                                "taking them (near pairs, contact forces, update)" if args.contact else
+                                "k_pairs_sym (Newton-pair Coulomb sums), then the given-sums k_step update"
                                 if prec == pdq.MIXED else
                                 "k_pairs_sym64 (FP64 Newton-pair Coulomb sums), then the given-sums k_step update")
                                if newton else "k_step (all-pairs Coulomb + local step)",

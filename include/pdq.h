@@ -214,8 +214,9 @@ typedef struct pdq_step_cfg {
                           /*   (Eq. coulomb is odd in x_i - x_j), summed through atomics     */
                           /*   (float for MIXED, double for PDQ_FP64; not bit-reproducible   */
                           /*   from run to run), then the local update; block 64 or 128      */
-                          /*   only.  Ignored by contact runs; for PDQ_FP64 the only other   */
-                          /*   value read is 0                                                */
+                          /*   only.  MIXED contact runs take the Coulomb sums this way and  */
+                          /*   keep the contact forces one-sided; PDQ_FP64 contact runs      */
+                          /*   ignore it.  For PDQ_FP64 the only other value read is 0       */
 } pdq_step_cfg;
 
 /* Caller-owned tallies, device int64 [S][C], accumulated across calls:

@@ -350,11 +350,24 @@ __device__ __forceinline__ void contact_tile(const StepArgs& A, int64_t gi, int6
     const double zi = (double)pi4.z;
     const ClassK& ci = K.cls[A.tag[gi].y];
     const double near2 = K.near * K.near;
+    // MIXED: an FP32 screen on the FP32 snapshot first.  Its separation differs from the FP64
+    // one by ~3e-5 at most (the snapshot's rounding at |x| <= R, |z| <= L; z itself is FP32 in
+    // MIXED), so with a 0.05 margin it only drops pairs that the FP64 test drops as well, and
+    // results are unchanged; it keeps most candidate pairs off the narrow FP64 pipe.
+    const float h2f = 0.5f * K.dtf, Lf = (float)K.L, invLf = (float)K.invL;
+    const float scr = (float)K.near + 0.05f, scr2 = scr * scr;
     for (int64_t j = jb; j < je; ++j) {
         if (j == gi) continue;
         const T4 vj = vel[j];
         if (!((double)vj.w > 0.5)) continue;
         const T4 pj = pos[j];
+        if constexpr (P == PDQ_MIXED) {
+            const float fx = (pi4.x - pj.x) + h2f * (vi.x - vj.x);
+            const float fy = (pi4.y - pj.y) + h2f * (vi.y - vj.y);
+            float fz = (pi4.z - pj.z) + h2f * (vi.z - vj.z);
+            fz -= Lf * rintf(fz * invLf);
+            if (!(fx * fx + fy * fy + fz * fz < scr2)) continue;
+        }
         double xj, yj;
         if (P == PDQ_FP64) { xj = (double)pj.x; yj = (double)pj.y; }
         else { const double2 xy = A.xy_in[j]; xj = xy.x; yj = xy.y; }
@@ -489,10 +502,29 @@ __device__ __forceinline__ void coulomb_pair_track(double xi, double yi, double 
     az = __fma_rn(s, dz, az);
 }
 
+// Smallest nonzero r^2 of two i-particles against one j (the near-pair test of the contact
+// variant whose Coulomb sums come from the Newton-pair kernel, V = 6; the self pair, r = 0, is
+// left out).  MINIMG folds dz to the minimum image, else zi carries the tile pair's shift.
+template <bool MINIMG>
+__device__ __forceinline__ void near_pair_x2(f2 xi, f2 yi, f2 zi, f2 xj, f2 yj, f2 zj, f2 invL2, f2 M2, f2 nM2,
+                                             f2 nL2, float& mn) {
+    const f2 dx = f2_sub(xi, xj), dy = f2_sub(yi, yj);
+    f2 dz = f2_sub(zi, zj);
+    if constexpr (MINIMG) {
+        const f2 t = f2_add(f2_fma(dz, invL2, M2), nM2);
+        dz = f2_fma(nL2, t, dz);
+    }
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    mn = fminf(mn, fminf(ra > 0.f ? ra : INFINITY, rb > 0.f ? rb : INFINITY));
+}
+
 // The MIXED contact variant is held to 96 registers (its rare FP64 contact path would
 // otherwise set the register count, and the occupancy, of the whole pair loop).
 template <int P, int NT, int U, int V>
-__global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT * 96) : 0) k_step(const StepArgs A) {
+__global__ void __launch_bounds__(NT, ((V == 4 || V == 6) && P == PDQ_MIXED) ? 65536 / (NT * 96) : 0)
+    k_step(const StepArgs A) {
     typedef typename Real<P>::T T;
     typedef typename Real<P>::T4 T4;
     // j-tile: FP64 holds double4 (x, y, z, q); MIXED holds each value twice,
@@ -503,9 +535,10 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
     __shared__ double2 s_z64[P == PDQ_FP64 ? 2 * (NT / 32) : 1];   // FP64: i ranges, then j ranges
     __shared__ int s_item, s_last;
     __shared__ unsigned int s_alive[PDQ_MAX_CLASSES], s_dep[PDQ_MAX_CLASSES];
-    // contact-force variant (V == 4): per-particle contact accelerations of the item, and the
-    // per-warp largest speeds of the i-particles and of the staged j-tile (near-pair bound)
-    constexpr bool CT = V == 4;
+    // contact-force variants (V == 4; V == 6 with the Coulomb sums of the Newton-pair kernel in
+    // A.acc4): per-particle contact accelerations of the item, and the per-warp largest speeds of
+    // the i-particles and of the staged j-tile (near-pair bound)
+    constexpr bool CT = V == 4 || V == 6;
     __shared__ double s_ct[CT ? 3 * NT * U : 1];
     __shared__ float s_vi[NT / 32], s_vj[NT / 32];
     // j-tiles (first index) flagged as holding a near pair of this item; evaluated after the pair
@@ -634,12 +667,40 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
                     if constexpr (CT) thr = fmaxf(dcz, near_bound(K, s_vi, s_vj, NT / 32));
                     float mn = INFINITY;
                     float shift = 0.f;
-                    bool direct = V == 0 || V == 4;
+                    bool direct = V == 0 || V == 4 || V == 6;
                     if (dlo > -halfL && dhi < halfL) shift = 0.f;
                     else if (dlo > halfL && dhi < 3.f * halfL) shift = Lf;
                     else if (dhi < -halfL && dlo > -3.f * halfL) shift = -Lf;
                     else direct = false;
-                    if (direct) {
+                    if constexpr (V == 6) {
+                        // Coulomb sums from A.acc4: a tile pair is visited only when it may hold a
+                        // pair within reach of the contact range, and only for the nearest r^2
+                        const bool far = direct && ((dlo - shift > thr) || (dhi - shift < -thr));
+                        if (!far) {
+                            if (direct) {
+                                const f2 sh = f2_pack(shift, shift);
+                                f2 Zs[H];
+#pragma unroll
+                                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+#pragma unroll 4
+                                for (int k = 0; k < NT; ++k) {
+                                    const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+#pragma unroll
+                                    for (int h = 0; h < H; ++h)
+                                        near_pair_x2<false>(X[h], Y[h], Zs[h], a.x, a.y, b.x, invL2, M2, nM2, nL2,
+                                                            mn);
+                                }
+                            } else {
+#pragma unroll 4
+                                for (int k = 0; k < NT; ++k) {
+                                    const ulonglong2 a = sj2[2 * k], b = sj2[2 * k + 1];
+#pragma unroll
+                                    for (int h = 0; h < H; ++h)
+                                        near_pair_x2<true>(X[h], Y[h], Z[h], a.x, a.y, b.x, invL2, M2, nM2, nL2, mn);
+                                }
+                            }
+                        }
+                    } else if (direct) {
                         const f2 sh = f2_pack(shift, shift);
                         f2 Zs[H];
 #pragma unroll
@@ -691,7 +752,13 @@ __global__ void __launch_bounds__(NT, (V == 4 && P == PDQ_MIXED) ? 65536 / (NT *
                         __syncthreads();
                 }
                 if constexpr (CT) flush_flags<P, NT, U>(A, nflag, s_flag, base, end, zeta, s_ct);
-                if constexpr (V != 1) {
+                if constexpr (V == 6) {       // the Coulomb sums of the Newton-pair kernel
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int64_t g = base + u * NT + tid;
+                        if (g < end) { const float4 a = A.acc4[g]; ax[u] = a.x; ay[u] = a.y; az[u] = a.z; }
+                    }
+                } else if constexpr (V != 1) {
 #pragma unroll
                     for (int h = 0; h < H; ++h) {
                         float a0, a1;
@@ -1379,16 +1446,18 @@ static int tile_threads(const pdq_state* st, const pdq_step_cfg* cfg) {
     if (cfg && cfg->block) return cfg->block;
     return st->precision == PDQ_FP64 ? 128 : 128;
 }
-// Pair variant 3 (Newton pairs) applies to runs without contact forces, both precisions.
+// Pair variant 3 (Newton pairs): both precisions; with contact forces MIXED only (its contact
+// forces stay in the contact variant of k_step, V = 6).
 static bool newton_pairs(const pdq_state* st, const pdq_step_cfg* cfg) {
-    return cfg && cfg->variant == 3 && !(cfg->forces & PDQ_F_CONTACT);
+    return cfg && cfg->variant == 3 && (!(cfg->forces & PDQ_F_CONTACT) || st->precision == PDQ_MIXED);
 }
 // particles per thread: FP64 1 (2 for its Newton-pair kernel); MIXED 4 (two packed pairs), 8 for
 // pair variants 2 and 3
 static int tile_ilp(const pdq_state* st, const pdq_step_cfg* cfg = nullptr) {
     if (st->precision == PDQ_FP64) return newton_pairs(st, cfg) ? 2 : 1;
+    if (newton_pairs(st, cfg)) return 8;
     if (cfg && (cfg->forces & PDQ_F_CONTACT)) return 4;      // contact runs: variant 0 layout
-    return (cfg && (cfg->variant == 2 || cfg->variant == 3)) ? 8 : 4;
+    return (cfg && cfg->variant == 2) ? 8 : 4;
 }
 
 static int sm_count() {
@@ -1432,6 +1501,21 @@ static int launch_newton64(const StepArgs& A, cudaStream_t s) {
     B.ext = A.acc64;
     return launch_step<PDQ_FP64, 2 * NT, 1, 5>(B, s);
 }
+// MIXED contact runs under pair variant 3: the Newton-pair sums, then the contact variant of the
+// step that takes them from A.acc4 (V = 6) over the same tiles.
+template <int NT>
+static int launch_newton_contact(const StepArgs& A, cudaStream_t s) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_sym<NT, 8>, NT, 0);
+        if (per_sm <= 0) per_sm = 1;
+    }
+    const int64_t full = (int64_t)sm_count() * per_sm;
+    PDQ_CUDA(cudaMemsetAsync(A.acc4, 0, sizeof(float4) * (size_t)(A.cap > 0 ? A.cap : 1), s));
+    k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, std::min(full, A.max_items > 0 ? A.max_items : full)), NT, 0,
+                         s>>>(A);
+    return launch_step<PDQ_MIXED, 2 * NT, 4, 6>(A, s);
+}
 template <int NT>
 static int launch_newton(const StepArgs& A, cudaStream_t s) {
     static int per_sm = 0;
@@ -1452,8 +1536,8 @@ static int launch_newton(const StepArgs& A, cudaStream_t s) {
 // Coulomb sums (A.ext, P3M): V = 5, no pair loop.
 static int dispatch_step(int prec, int NT, int variant, bool contact, const StepArgs& A, cudaStream_t s) {
     if (A.acc4) {
-        if (NT == 64) return launch_newton<64>(A, s);
-        if (NT == 128) return launch_newton<128>(A, s);
+        if (NT == 64) return contact ? launch_newton_contact<64>(A, s) : launch_newton<64>(A, s);
+        if (NT == 128) return contact ? launch_newton_contact<128>(A, s) : launch_newton<128>(A, s);
         return PDQ_ERR_INVALID_ARG;
     }
     if (A.acc64) {
@@ -1953,11 +2037,12 @@ extern "C" int pdq_autotune(const pdq_field* field, const pdq_phys* phys, pdq_st
     }
     const int blocks[4] = {64, 128, 256, 32};
     const int n_blk = st->precision == PDQ_FP64 ? 4 : 3;    // 32-thread tiles: FP64 only
-    // candidate pair variants: MIXED 0-3, FP64 0 and 3 (Newton pairs); contact runs 0 only
+    // candidate pair variants: MIXED 0-3, FP64 0 and 3 (Newton pairs); contact runs: MIXED 0 and 3,
+    // FP64 0
     const bool contact_run = (cfg->forces & PDQ_F_CONTACT) != 0;
-    const int vars_mixed[4] = {0, 1, 2, 3}, vars_f64[2] = {0, 3};
-    const int* vars = st->precision == PDQ_MIXED ? vars_mixed : vars_f64;
-    const int n_var = contact_run ? 1 : (st->precision == PDQ_MIXED ? 4 : 2);
+    const int vars_mixed[4] = {0, 1, 2, 3}, vars_03[2] = {0, 3};
+    const int* vars = st->precision == PDQ_MIXED && !contact_run ? vars_mixed : vars_03;
+    const int n_var = contact_run ? (st->precision == PDQ_MIXED ? 2 : 1) : (st->precision == PDQ_MIXED ? 4 : 2);
     cudaEvent_t e0, e1;
     PDQ_CUDA(cudaEventCreate(&e0));
     PDQ_CUDA(cudaEventCreate(&e1));

@@ -94,11 +94,11 @@ def _load(pdq, precision, counts, arrays):
     return st, ost
 
 
-def _run(pdq, fields, precision, counts, arrays, steps, forces, block=0, compact_every=0, mode=0):
+def _run(pdq, fields, precision, counts, arrays, steps, forces, block=0, compact_every=0, mode=0, variant=0):
     f, of, grid = fields
     prm = np.array([[0.05, 0.8, 0.5], [0.1, 0.3, 0.2]])[:len(counts)]
     st, ost = _load(pdq, precision, counts, arrays)
-    cfg = pdq.step_cfg(DT, forces=forces, block=block, compact_every=compact_every, mode=mode)
+    cfg = pdq.step_cfg(DT, forces=forces, block=block, compact_every=compact_every, mode=mode, variant=variant)
     tally = pdq.Tally(len(counts), 3)
     pdq.step_particles(f, pdq.phys_default(), st, pdq.params_tensor(prm), cfg, steps, tally, pdq.workspace(st, cfg))
     assert pdq.check_state(st) == 0
@@ -198,14 +198,16 @@ def test_fp64_contact_terms_separately(pdq, fields, forces):
     _compare(st, ost, off, max(1e-9, 10 * sx), max(1e-9, 10 * sv))
 
 
-@pytest.mark.parametrize("compact_every", [0, 5])
-def test_mixed_contact_parity(pdq, fields, compact_every):
+@pytest.mark.parametrize("compact_every,variant", [(0, 0), (5, 0), (0, 3), (5, 3)])
+def test_mixed_contact_parity(pdq, fields, compact_every, variant):
     # MIXED rounds z to FP32 every step: the bound is the oracle's response to one FP32 unit of
-    # z, times the number of steps
+    # z, times the number of steps.  Variant 3: Coulomb sums by Newton pairs, contact forces in
+    # the contact variant that takes them.
     counts = [517, 301]
     arr = _contact_state(counts, 6, z_range=(2.0, 12.0))
     fl = oracle.F_ALL | oracle.F_CONTACT
-    st, tally, ost, off, nd, na = _run(pdq, fields, 1, counts, arr, 30, fl, block=64, compact_every=compact_every)
+    st, tally, ost, off, nd, na = _run(pdq, fields, 1, counts, arr, 30, fl, block=64, compact_every=compact_every,
+                                       variant=variant)
     sx, sv = _oracle_sensitivity(counts, arr, 30, fl, z_ulp32=True)
     _compare(st, ost, off, max(2e-5, 30 * sx), max(2e-3, 30 * sv))
 
