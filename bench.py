@@ -315,7 +315,7 @@ def run_e2e(pdq, field, phys, state, prm, cfg, w, args, stream):
     torch.cuda.synchronize()
     alive = sum(int(g["tally"].n_alive.sum().item()) for g in groups) - alive0
     return {"value": float(alive) / te, "unit": "particle-steps/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "sample_groups": G}
+            "d2h_bytes_per_step": int(d2h), "sample_groups": G, "ms": te * 1e3, "particle_steps": float(alive)}
 
 
 def run_ours(args):
@@ -391,6 +391,13 @@ def run_ours(args):
         e2e = None
         if args.e2e_steps > 0:
             e2e = run_e2e(pdq, field, phys, state, prm, cfg, w, args, stream)
+            # whole job: particle-steps of all ranks over the slowest rank's time, bytes summed
+            te_ms, alive_all = reduce_over_ranks(e2e.pop("ms"), e2e.pop("particle_steps"), world, "cuda")
+            e2e["value"] = alive_all / (te_ms / 1e3)
+            if world > 1:
+                _, h2d_all = reduce_over_ranks(0.0, e2e["h2d_bytes_per_step"], world, "cuda")
+                _, d2h_all = reduce_over_ranks(0.0, e2e["d2h_bytes_per_step"], world, "cuda")
+                e2e["h2d_bytes_per_step"], e2e["d2h_bytes_per_step"] = int(h2d_all), int(d2h_all)
 
         # plain FP64 single-sample path (the comparison the metric names)
         fp64 = None
