@@ -151,3 +151,35 @@ def test_newton_pair_variant_host_logic(pdq):
         rc = L.pdq_step_particles(fake, C.byref(pdq.phys_default()), C.byref(s), fake, C.byref(cfg), 1, C.byref(t),
                                   C.c_void_p(256), 1 << 40, None)
         assert rc == -1, (block, variant)
+
+
+def test_newton_pair_workspace_by_precision_and_forces(pdq):
+    # FP64 variant 3 keeps double sums [capacity][3] (24 B each, no one-sided chunk partials);
+    # MIXED contact runs under variant 3 take the float sums too; FP64 contact runs ignore it
+    L = pdq.lib()
+    cap = 50_000
+
+    def size(precision, variant, forces=pdq.F_ALL, block=128):
+        s = _fake_mixed_state(pdq, cap)
+        s.precision = precision
+        cfg = pdq.step_cfg(0.05, block=block, variant=variant, forces=forces)
+        n = C.c_size_t()
+        assert L.pdq_step_workspace_size(C.byref(s), C.byref(cfg), C.byref(n)) == 0
+        return n.value
+
+    assert size(0, 3) >= 24 * cap
+    assert size(1, 3, pdq.F_ALL | pdq.F_CONTACT) - size(1, 0, pdq.F_ALL | pdq.F_CONTACT) >= 16 * cap
+    assert size(0, 3, pdq.F_ALL | pdq.F_CONTACT) == size(0, 0, pdq.F_ALL | pdq.F_CONTACT)
+
+
+def test_adjoint_workspace_holds_the_newton_pair_sums(pdq):
+    # per particle: 8 FP64 + 2 int32 arrays per checkpoint, 10 per segment level, 19 more, and
+    # 16 B of float sums
+    L = pdq.lib()
+    b = pdq.BatchStruct()
+    b.precision, b.n_samples, b.n_classes, b.capacity = 1, 4, 3, 4096
+    n = C.c_size_t()
+    assert L.pdq_adjoint_workspace_size(C.byref(b), 100, 10, C.byref(n)) == 0
+    per = 10 * (8 * 8 + 2 * 4) + 11 * 10 * 8 + 19 * 8 + 16
+    assert n.value >= per * 4096
+    assert L.pdq_adjoint_workspace_size(C.byref(b), 0, 10, C.byref(n)) == -1
