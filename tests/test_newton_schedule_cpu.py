@@ -1,0 +1,121 @@
+"""Host model of the Newton-pair schedule (pair variant 3): the index arithmetic of
+newton_tile and of the FP64 chunked items, replayed in Python on small ragged
+samples.  Every ordered pair (i, j), i != j, of a sample must reach i's sum exactly
+once: either one-sided inside i's own tile, or as a Newton pair from the tile of the
+earlier particle (added to the earlier one, subtracted, i.e. taken with the opposite
+sign of d, for the later one); and the j-side sums must come home to their own lane
+after the 32-step rotation.
+"""
+import numpy as np
+import pytest
+
+
+def newton_tile_visits(n, NT, U, base):
+    """(i, j, side) visits of the tile starting at `base`, as newton_tile orders them.
+
+    side 'i': pair adds to i one-sided or as the i side of a Newton pair;
+    side 'j': the Newton pair's reaction, added to j (the later particle)."""
+    W = NT // 32
+    dend = min(base + NT * U, n)
+    tile_i = [base + u * NT + t for u in range(U) for t in range(NT) if base + u * NT + t < n]
+    visits = []
+    for j0 in range(base, n, NT):
+        if j0 < dend:        # the tile's own block: one-sided, every i of the tile with every j of the block
+            for i in tile_i:
+                for j in range(j0, min(j0 + NT, dend)):
+                    if i != j:
+                        visits.append((i, j, "i"))
+            continue
+        for warp in range(W):
+            for g in range(W):
+                # lane l at step k holds j = g*32 + (l + k) % 32 and that j's running sum, which moves
+                # to lane l - 1 after the step: follow where each j's sum sits
+                holder = {jj: jj for jj in range(32)}          # j offset -> lane holding its sum
+                for k in range(32):
+                    for lane in range(32):
+                        jj = (lane + k) % 32
+                        assert holder[jj] == lane              # the lane working on j holds j's sum
+                        j = j0 + g * 32 + jj
+                        if j >= n:
+                            continue
+                        for u in range(U):
+                            i = base + u * NT + warp * 32 + lane
+                            if i < n:
+                                visits.append((i, j, "i"))
+                                visits.append((j, i, "j"))
+                    holder = {jj: (h - 1) % 32 for jj, h in holder.items()}
+                assert all(holder[jj] == jj for jj in range(32))   # home after 32 steps
+    return visits
+
+
+@pytest.mark.parametrize("n,NT,U", [(1500, 64, 8), (2049, 128, 8), (700, 128, 4), (1, 64, 8), (64 * 8, 64, 8)])
+def test_every_ordered_pair_once(n, NT, U):
+    TI = NT * U
+    count = np.zeros((n, n), np.int64)
+    for base in range(0, n, TI):
+        for a, b, _ in newton_tile_visits(n, NT, U, base):
+            count[a, b] += 1
+    want = np.ones((n, n), np.int64) - np.eye(n, dtype=np.int64)
+    assert np.array_equal(count, want)
+
+
+def test_sums_match_the_direct_coulomb_sum():
+    # the schedule's sums of G(d) = d / max(|d|, dc)^3 weighted by q equal the direct sum (float64)
+    rng = np.random.default_rng(0)
+    n, NT, U, dc = 777, 64, 8, 0.3
+    x = rng.uniform(-5, 5, (n, 3))
+    q = rng.uniform(-1, 1, n)
+
+    def G(d):
+        r = max(np.linalg.norm(d), dc)
+        return d / r ** 3
+
+    acc = np.zeros((n, 3))
+    for base in range(0, n, NT * U):
+        for a, b, side in newton_tile_visits(n, NT, U, base):
+            if side == "i":
+                acc[a] += q[b] * G(x[a] - x[b])
+            else:       # reaction on the later particle a = j of the pair (b, a): -q_b G(x_b - x_a)
+                acc[a] -= q[b] * G(x[b] - x[a])
+    ref = np.array([sum(q[j] * G(x[i] - x[j]) for j in range(n) if j != i) for i in range(n)])
+    assert np.allclose(acc, ref, rtol=1e-12, atol=1e-12)
+
+
+def newton_chunks(cap, TI):
+    """Chunks per tile of the FP64 Newton-pair items (about 8 tiles of j each, at most 64)."""
+    return max(1, min(64, -(-cap // (8 * TI))))
+
+
+@pytest.mark.parametrize("n,NT", [(6000, 128), (1000, 64), (100000 // 40, 64)])
+def test_fp64_chunked_items_cover_each_pair_once(n, NT):
+    # item (tile, chunk): j in [max(chunk start, tile start), chunk end); own block one-sided,
+    # later particles as Newton pairs; chunks are whole NT-particle j-tiles
+    U = 2
+    TI = NT * U
+    JS = newton_chunks(n, TI)
+    ch = -(-(-(-n // JS)) // NT) * NT
+    count = np.zeros((n, n), np.int64)
+    n_items = 0
+    for tile in range(-(-n // TI)):
+        base = tile * TI
+        dend = min(base + TI, n)
+        tile_i = np.arange(base, dend)
+        for jc in range(JS):
+            cb, ce = jc * ch, min((jc + 1) * ch, n)
+            jb = max(cb, base)
+            if jb >= ce:
+                continue            # the chunk lies before the tile: an empty item
+            n_items += 1
+            for j0 in range(jb, ce, NT):
+                js = np.arange(j0, min(j0 + NT, ce))
+                assert (j0 - base) % NT == 0
+                if j0 < dend:
+                    assert js[-1] < dend or dend == n       # a j-tile never straddles the block's end
+                    for i in tile_i:
+                        count[i, js[js != i]] += 1
+                else:
+                    count[np.ix_(tile_i, js)] += 1
+                    count[np.ix_(js, tile_i)] += 1
+    assert n_items > 0
+    want = np.ones((n, n), np.int64) - np.eye(n, dtype=np.int64)
+    assert np.array_equal(count, want)
