@@ -1,6 +1,8 @@
-// pdq_newton.cuh -- Coulomb sums with each unordered pair evaluated once (Newton pairs),
-// packed FP32: the pair math, the z-range classification of tile pairs and the per-tile
-// sum shared by the step (k_pairs_sym) and the adjoint's forward sweep.
+// pdq_newton.cuh -- the particle-particle Coulomb sums of Eq. coulomb (App. A.2: a direct
+// sum within a sample, minimum image in z, the contact-distance clamp) with each unordered
+// pair evaluated once (Newton pairs), packed FP32: the pair math, the z-range
+// classification of tile pairs and the per-tile sum shared by the step (k_pairs_sym) and the
+// adjoint's forward sweep.
 #pragma once
 
 #include <type_traits>
