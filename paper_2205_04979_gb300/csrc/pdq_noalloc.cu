@@ -14,8 +14,10 @@
 
 namespace {
 
-// Built-in scratch: holds the step's work-item table and sample order.  Every
-// GPU that loads libpdq keeps this array until the process exits.
+// Built-in scratch: holds the step's whole workspace (work-item table, sample
+// order, the z-binning sort's tag scratch, and, as the configuration needs them,
+// the Newton-pair sums or the FP64 j-chunk partial sums).  Every GPU that loads
+// libpdq keeps this array until the process exits.
 constexpr size_t kScratchBytes = PDQ_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_step_scratch[kScratchBytes];
 
@@ -47,14 +49,12 @@ extern "C" int pdq_step_particles_noalloc(const pdq_field* field, const pdq_phys
                                           pdq_tally* tally, pdq_stream_t stream) {
     if (!cfg || !state) return PDQ_ERR_INVALID_ARG;
     if (cfg->use_graph) return PDQ_ERR_INVALID_ARG;   // graph instantiation may allocate
-    size_t need = 0;
-    int rc = pdq_step_workspace_size(state, cfg, &need);
-    if (rc) return rc;
-    if (need > kScratchBytes) return PDQ_ERR_WORKSPACE;
     void* scratch = nullptr;
-    rc = scratch_address(&scratch);
+    const int rc = scratch_address(&scratch);
     if (rc) return rc;
-    // The work queue is rebuilt from count[] at the start of every call, so the
-    // previous call's contents need no clearing.
+    // The step compares the scratch size with the exact workspace of the tile shape it
+    // runs and returns PDQ_ERR_WORKSPACE before any device work when it does not fit.
+    // Every part of the workspace is rebuilt (work queue from count[]) or zeroed (sums)
+    // inside the call, so the previous call's contents need no clearing.
     return pdq_step_particles(field, phys, state, params, cfg, n_steps, tally, scratch, kScratchBytes, stream);
 }
