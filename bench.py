@@ -509,16 +509,16 @@ def run_adjoint(args):
         cfg = pdq.step_cfg(w["dt"], window_start=0)
         prm = pdq.params_tensor(params)
         gbar = torch.ones((1, S, len(w["st_plus"])), dtype=torch.float64, device="cuda")
-        pdq.adjoint_run(field, phys, batch, prm, cfg, max(2, args.warmup), 1, w["eps"][1], w["particle_seed"],
-                        gbar=gbar, stream=stream)
+        pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, max(2, args.warmup), 1, w["eps"][1],
+                               w["particle_seed"], gbar=gbar, stream=stream)
         stream.synchronize()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         e[0].record(stream)
-        J, _ = pdq.adjoint_run(field, phys, batch, prm, cfg, args.steps, K, w["eps"][1], w["particle_seed"],
-                               stream=stream)
+        J, _ = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, args.steps, K, w["eps"][1],
+                                      w["particle_seed"], stream=stream)
         e[1].record(stream)
-        J2, pbar = pdq.adjoint_run(field, phys, batch, prm, cfg, args.steps, K, w["eps"][1], w["particle_seed"],
-                                   gbar=gbar, stream=stream)
+        J2, pbar = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, args.steps, K, w["eps"][1],
+                                          w["particle_seed"], gbar=gbar, stream=stream)
         e[2].record(stream)
         e[2].synchronize()
     fwd_ms, tot_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])

@@ -275,17 +275,27 @@ int pdq_step_particles(const pdq_field* field, const pdq_phys* phys, pdq_state* 
  * compiled into libpdq (PDQ_NOALLOC_SCRATCH_BYTES), which every GPU that
  * loads the library keeps until the process exits.  The call allocates
  * nothing (no cudaMalloc, cudaFree or allocating library routine).
- * Limits: the state must fit the scratch, i.e. pdq_step_workspace_size() <=
- * PDQ_NOALLOC_SCRATCH_BYTES (about capacity / (threads x particles per
- * thread) + 1.5 S items of 8 bytes), else PDQ_ERR_WORKSPACE; cfg->use_graph
- * must be 0 (PDQ_ERR_INVALID_ARG otherwise).
+ * Limits: the step's whole workspace must fit the scratch, else the call
+ * returns PDQ_ERR_WORKSPACE before any device work.  It holds the work-item
+ * table (8 B per (sample, i-tile) item, times the j-chunks of FP64 runs), 4 B
+ * per sample, the z-binning sort's tag scratch (8 B per slot of capacity),
+ * with pair variant 3 the Newton-pair sums (16 B per slot MIXED, 24 B FP64),
+ * and for FP64 one-sided runs whose few i-tiles are split over JS > 1
+ * j-chunks (JS <= 64) partial sums of 24 JS B per slot.  Approximate largest
+ * capacity: MIXED pair variants 0-2 130,000 slots, variant 3 43,000; FP64
+ * variant 3 30,000; FP64 one-sided 9,900, and again from 32,768 to 128,000
+ * (above 32,768 slots JS = 1).  pdq_step_workspace_size() <=
+ * PDQ_NOALLOC_SCRATCH_BYTES is a sufficient test (it sizes the item table
+ * for the narrower tile the P3M driver also uses); the call itself checks
+ * the exact need.  cfg->use_graph must be 0 (PDQ_ERR_INVALID_ARG otherwise).
  * Set-up: the first call on each device resolves the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.
  * Sharing: all calls share the one array and it keeps the last call's
- * contents; each call rebuilds the work queue before using it, so nothing
- * needs clearing, but calls whose GPU work overlaps (different streams, or
- * host threads, without ordering between them) race on it.                  */
+ * contents; each call rebuilds the work queue and zeroes the sums before
+ * using them, so nothing needs clearing, but calls whose GPU work overlaps
+ * (different streams, or host threads, without ordering between them) race
+ * on it.                                                                    */
 int pdq_step_particles_noalloc(const pdq_field* field, const pdq_phys* phys, pdq_state* state,
                                const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
                                pdq_tally* tally, pdq_stream_t stream);
@@ -337,9 +347,9 @@ int pdq_capture_efficiency(const pdq_field* field, const pdq_phys* phys, const d
                            pdq_stream_t stream);
 
 /* ---------------------------------------------------------------- adjoint
- * Batch description for the adjoint (it seeds and owns its own particle
- * state inside the workspace): offset is a device array [S+1] as in
- * pdq_state; st_plus the class Stokes numbers.                               */
+ * Batch description for the adjoint's workspace layout and for its
+ * self-seeding form: offset is a device array [S+1] as in pdq_state; st_plus
+ * the class Stokes numbers.                                                  */
 typedef struct pdq_batch {
     int32_t precision;                 /* PDQ_FP64 or PDQ_MIXED             */
     int32_t n_samples;                 /* S >= 1                            */
@@ -350,21 +360,34 @@ typedef struct pdq_batch {
     const int64_t* offset;             /* device [S+1]                      */
 } pdq_batch;
 
-/* Workspace bytes of pdq_adjoint_run: FP64 storage of 8 arrays per particle
+/* Workspace bytes of the adjoint: FP64 storage of 8 arrays per particle
  * and 2 int32 ones per checkpoint (ceil(n_steps/K) of them: the state
  * z-binned, its charges, classes and binning permutation), 10 per step of one
  * segment (K + 1 levels), 19 for cotangents and charges, 16 B per particle of
- * float sums (the MIXED Newton-pair kernels), plus 4 [S][C] tallies.         */
+ * float sums (the MIXED Newton-pair kernels), plus 4 [S][C] tallies.  The
+ * layout depends only on (capacity, S, C, n_steps, K).
+ * pdq_adjoint_state_workspace_size sizes it for a pdq_state (its batch is
+ * {precision, S, C, st_plus, capacity, offset} of the state).                */
 int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_steps, int32_t K, size_t* bytes);
+int pdq_adjoint_state_workspace_size(const pdq_state* init, int64_t n_steps, int32_t K, size_t* bytes);
 
-/* Smoothed deposition functional and its hand-written reverse-mode adjoint.
- * Forward (App. A.2 step of pdq_step_particles, STICK mode only) with the wall
- * removal replaced by a weight update w' = w (1 - sigma(-gap'/eps)),
+/* Smoothed deposition functional and its hand-written reverse-mode adjoint,
+ * starting from the caller's particle state `init` (e.g. one that
+ * pdq_step_particles has advanced through a transient).
+ * Forward (App. A.2 step of pdq_step_particles) with the wall removal
+ * replaced by a weight update w' = w (1 - sigma(-gap'/eps)),
  * sigma(a) = 1/(1+e^-a), gap' = R - r' - d/2, and the Coulomb sum taken over
  * weighted charges w_j q_j; per (sample, class) over the counted steps
  * J = (R+/2) sum_n sum_p (w_n - w_{n+1}) / (dt+ sum_n sum_p w_n), which tends
- * to V_dep+ (Sec. 2.1) as eps -> 0.  The particles are seeded inside as
- * pdq_seed_particles(seed, charge_sigma) would (common random numbers).
+ * to V_dep+ (Sec. 2.1) as eps -> 0.
+ * Initial state: init's current half.  Particle p of sample s starts with its
+ * position, velocity, class (tag), weight w = its alive flag (0 for a particle
+ * deposited but not yet compacted out) and charge q = xi_s qhat_p with
+ * qhat_p = q_eff / xi_s, so xi_s must be non-zero and finite for every sample
+ * (params is read to the host to check this).  Slots [count[s], offset[s+1])
+ * become weightless, uncharged particles at rest on the axis.  The adjoint
+ * runs in init->precision; init is not modified.  Steps are numbered from 0
+ * at the start of this call: cfg->window_start counts from there.
  * Reverse: checkpoints every K steps; each of the n_vec cotangent vectors
  * gbar[v] (device [S][C]) gives pbar[v] (device [S][3]) = sum_c gbar[v][s][c]
  * dJ[s][c]/d(xi_s, zeta_s, theta_s).  Under PDQ_STICK theta does not enter
@@ -373,16 +396,41 @@ int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_steps, int32_t 
  * sigma(-arg/eps_stick), arg = sigma_y0^2 (1-theta)^2/(rho_p E)
  * - 2 A_cont gamma_c/m (m^2/s^2; eps_stick > 0 required), and the rest of the
  * particle rebounds with CoR_n (0 when arg <= 0, capped at 1), mirrored into
- * the pipe.  J (device [S][C]) is always written.  Reads offset[] to the host
- * (synchronises `stream`).  PDQ_MIXED with Coulomb forces evaluates each
- * particle pair once for both particles (float sums through atomics, so not
- * bit-reproducible from run to run) and takes at most 33,553,920 particles
- * per sample.
+ * the pipe.  J (device [S][C]) is always written; n_vec = 0 runs the forward
+ * sweep alone and leaves its checkpoints in the workspace for
+ * pdq_adjoint_reverse.  Reads offset[] to the host (synchronises `stream`).
+ * PDQ_MIXED with Coulomb forces evaluates each particle pair once for both
+ * particles (float sums through atomics, so not bit-reproducible from run to
+ * run) and takes at most 33,553,920 particles per sample.  Contact forces
+ * (PDQ_F_CONTACT) are not differentiated: cfg->forces must lie in PDQ_F_ALL.
+ * workspace: device, 256-byte aligned, >= pdq_adjoint_state_workspace_size.
  * Errors: INVALID_ARG, WORKSPACE, UNSUPPORTED (sample too large), CUDA.     */
-int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
-                    const pdq_sample_params* params, double charge_sigma, uint64_t seed, const pdq_step_cfg* cfg,
-                    int64_t n_steps, int32_t K, double eps, double eps_stick, int32_t n_vec, const double* gbar,
-                    double* J, double* pbar, void* workspace, size_t workspace_bytes, pdq_stream_t stream);
+int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, const pdq_state* init,
+                    const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps, int32_t K,
+                    double eps, double eps_stick, int32_t n_vec, const double* gbar, double* J, double* pbar,
+                    void* workspace, size_t workspace_bytes, pdq_stream_t stream);
+
+/* pdq_adjoint_run on particles it seeds itself, as
+ * pdq_seed_particles(seed, charge_sigma) would (common random numbers), in
+ * batch->precision: the same functional, sweeps, outputs and errors.        */
+int pdq_adjoint_run_seeded(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
+                           const pdq_sample_params* params, double charge_sigma, uint64_t seed,
+                           const pdq_step_cfg* cfg, int64_t n_steps, int32_t K, double eps, double eps_stick,
+                           int32_t n_vec, const double* gbar, double* J, double* pbar, void* workspace,
+                           size_t workspace_bytes, pdq_stream_t stream);
+
+/* The reverse sweeps alone (n_vec >= 1 cotangent vectors), on the forward
+ * sweep that an earlier pdq_adjoint_run or pdq_adjoint_run_seeded call left in
+ * `workspace`: pass the same batch layout (for pdq_adjoint_run, the state's:
+ * see pdq_adjoint_state_workspace_size), params, cfg, n_steps, K, eps and
+ * eps_stick, and the workspace unchanged since.  pbar as above.  Lets a
+ * caller (the autograd function of the binding) take J first and gradients
+ * later without a second forward sweep.
+ * Errors: INVALID_ARG, WORKSPACE, UNSUPPORTED, CUDA.                         */
+int pdq_adjoint_reverse(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
+                        const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps, int32_t K,
+                        double eps, double eps_stick, int32_t n_vec, const double* gbar, double* pbar,
+                        void* workspace, size_t workspace_bytes, pdq_stream_t stream);
 
 /* ---------------------------------------------------- multi-fidelity MC
  * Optimal MFMC allocation (Sec. 3.2, Eqs. opt1-opt3 and mf-precond) for k

@@ -86,7 +86,7 @@ def lib():
                                   _D, _D, _D, _D, _D, _D, _D, _I32, _I32, _I64, _I64]),
             "orc_vdep": (None, [C.c_int, _I64, _I64, C.c_double, C.c_double, _D]),
             "orc_smooth_run": (C.c_int, [P, Fp, _D, Cp, C.c_int, _D, C.c_int, _I64, _D, C.c_int64,
-                                         _D, _D, _D, _D, _I32, C.c_int, _D, _D]),
+                                         _D, _D, _D, _D, _I32, C.c_void_p, C.c_void_p, C.c_int, _D, _D]),
             "orc_coulomb_accel": (None, [P, Fp, C.c_int, _D, C.c_int, _D, _D, _D, _D, _I32, _I32, _D]),
             "orc_wall_accel": (None, [P, Fp, Cp, C.c_int, _D, C.c_int, _D, _D, _D, _I32, C.c_double, _D]),
             "orc_cor": (C.c_double, [P, C.c_double, C.c_double, C.c_double, C.c_double]),
@@ -255,17 +255,26 @@ def vdep(ndep, nalive, dt, r_plus=180.0):
     return out
 
 
-def smooth_run(f, grid, c, st_plus, offset, params, x0, y0, z0, qhat, cls, n_steps, want_grad=True, p=None):
-    """Smoothed functional J [S, C] and (if want_grad) dJ/d(xi, zeta, theta) [S, C, 3]."""
+def smooth_run(f, grid, c, st_plus, offset, params, x0, y0, z0, qhat, cls, n_steps, want_grad=True, p=None,
+               v0=None, w0=None):
+    """Smoothed functional J [S, C] and (if want_grad) dJ/d(xi, zeta, theta) [S, C, 3].
+
+    The particles start at (x0, y0, z0) with velocities v0 [N, 3] (None: at rest) and weights
+    w0 [N] (None: 1); charge xi * qhat.
+    """
     p = p or phys()
     S, nc = len(offset) - 1, len(st_plus)
     J = np.zeros((S, nc))
     dJ = np.zeros((S, nc, 3))
+    v0 = None if v0 is None else np.ascontiguousarray(v0, np.float64).reshape(-1, 3)
+    w0 = None if w0 is None else np.ascontiguousarray(w0, np.float64)
     rc = lib().orc_smooth_run(C.byref(p), C.byref(f), np.ascontiguousarray(grid), C.byref(c), nc,
                               np.ascontiguousarray(st_plus, np.float64), S, np.ascontiguousarray(offset, np.int64),
                               np.ascontiguousarray(params, np.float64).reshape(-1, 3), n_steps,
                               *(np.ascontiguousarray(a, np.float64) for a in (x0, y0, z0, qhat)),
-                              np.ascontiguousarray(cls, np.int32), int(want_grad), J, dJ)
+                              np.ascontiguousarray(cls, np.int32),
+                              None if v0 is None else v0.ctypes.data, None if w0 is None else w0.ctypes.data,
+                              int(want_grad), J, dJ)
     assert rc == 0
     return J, dJ
 

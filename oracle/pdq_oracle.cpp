@@ -780,7 +780,9 @@ int orc_smooth_run(const OrcPhys* p, const OrcField* f, const double* grid, cons
                    int n_classes, const double* st_plus, int n_samples, const int64_t* offset,
                    const double* params, int64_t n_steps,
                    const double* x0, const double* y0, const double* z0, const double* qhat /*charge per unit xi*/,
-                   const int32_t* cls, int want_grad, double* J /*[S][C]*/, double* dJ /*[S][C][3]*/) {
+                   const int32_t* cls, const double* v0 /*[N][3] or NULL: at rest*/,
+                   const double* w0 /*[N] or NULL: all 1*/, int want_grad, double* J /*[S][C]*/,
+                   double* dJ /*[S][C][3]*/) {
     if (cfg->smooth_eps <= 0 || (cfg->mode == 1 && !(cfg->stick_eps > 0))) return -1;
     if (cfg->forces & (F_COLLIDE | F_VDWPP)) return -1;     // contact forces: plain runs only
     for (int s = 0; s < n_samples; ++s) {
@@ -798,8 +800,10 @@ int orc_smooth_run(const OrcPhys* p, const OrcField* f, const double* grid, cons
             xi.d[0] = 1; zeta.d[1] = 1; theta.d[2] = 1;
             for (int i = 0; i < n; ++i) {
                 x[i] = Dual(x0[o + i]); y[i] = Dual(y0[o + i]); z[i] = Dual(z0[o + i]);
-                vx[i] = vy[i] = vz[i] = Dual(0.0);
-                q[i] = xi * qhat[o + i]; w[i] = Dual(1.0);
+                vx[i] = Dual(v0 ? v0[3 * (o + i)] : 0.0);
+                vy[i] = Dual(v0 ? v0[3 * (o + i) + 1] : 0.0);
+                vz[i] = Dual(v0 ? v0[3 * (o + i) + 2] : 0.0);
+                q[i] = xi * qhat[o + i]; w[i] = Dual(w0 ? w0[o + i] : 1.0);
             }
             std::vector<Dual> num(n_classes, Dual(0.0)), den(n_classes, Dual(0.0));
             for (int64_t st = 0; st < n_steps; ++st)
@@ -819,7 +823,11 @@ int orc_smooth_run(const OrcPhys* p, const OrcField* f, const double* grid, cons
             std::vector<double> x(x0 + o, x0 + o + n), y(y0 + o, y0 + o + n), z(z0 + o, z0 + o + n);
             std::vector<double> vx(n, 0.0), vy(n, 0.0), vz(n, 0.0), q(n), w(n, 1.0);
             std::vector<int32_t> alive(n, 1);
-            for (int i = 0; i < n; ++i) q[i] = sp.xi * qhat[o + i];
+            for (int i = 0; i < n; ++i) {
+                q[i] = sp.xi * qhat[o + i];
+                if (v0) { vx[i] = v0[3 * (o + i)]; vy[i] = v0[3 * (o + i) + 1]; vz[i] = v0[3 * (o + i) + 2]; }
+                if (w0) w[i] = w0[o + i];
+            }
             std::vector<double> num(n_classes, 0.0), den(n_classes, 0.0);
             for (int64_t st = 0; st < n_steps; ++st)
                 step_sample<double>(rn, n, x.data(), y.data(), z.data(), vx.data(), vy.data(), vz.data(), q.data(),

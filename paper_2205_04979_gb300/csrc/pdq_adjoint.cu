@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
 #include <vector>
 
@@ -351,6 +352,41 @@ __global__ void k_adj_seed(const AdjArgs A) {
     A.out.vx[g] = 0.0; A.out.vy[g] = 0.0; A.out.vz[g] = 0.0; A.out.w[g] = 1.0;
     ((int32_t*)A.cls)[g] = c;
     ((double*)A.qhat)[g] = qh;
+}
+
+// Initial smoothed state from a caller's particle state (its current half): positions and
+// velocities, weight = the alive flag (a deposited particle keeps weight 0), charge per unit xi
+// = q_eff / xi_s (the host has checked xi_s != 0), class from the tag.  Slots past count[s]
+// become weightless, uncharged particles at rest on the axis; they add nothing to J or to any
+// Coulomb sum.
+template <int P>
+__global__ void k_adj_load(const AdjArgs A, const int32_t* __restrict__ count, const void* __restrict__ pos,
+                           const void* __restrict__ vel, const double2* __restrict__ xy,
+                           const int2* __restrict__ tag) {
+    const int s = blockIdx.y;
+    const int64_t o = A.offset[s], n = A.offset[s + 1] - o;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t g = o + i;
+    double x = 0.0, y = 0.0, z = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, w = 0.0, qe = 0.0;
+    int c = 0;
+    if (i < count[s]) {
+        if constexpr (P == PDQ_FP64) {
+            const double4_32a pp = ((const double4_32a*)pos)[g], vv = ((const double4_32a*)vel)[g];
+            x = pp.x; y = pp.y; z = pp.z; qe = pp.w;
+            vx = vv.x; vy = vv.y; vz = vv.z; w = vv.w;
+        } else {
+            const double2 q2 = xy[g];
+            const float4 pp = ((const float4*)pos)[g], vv = ((const float4*)vel)[g];
+            x = q2.x; y = q2.y; z = (double)pp.z; qe = (double)pp.w;
+            vx = (double)vv.x; vy = (double)vv.y; vz = (double)vv.z; w = (double)vv.w;
+        }
+        c = min(max(tag[g].y, 0), A.C - 1);   // the class table has C entries
+    }
+    A.out.x[g] = x; A.out.y[g] = y; A.out.z[g] = z;
+    A.out.vx[g] = vx; A.out.vy[g] = vy; A.out.vz[g] = vz; A.out.w[g] = w;
+    ((int32_t*)A.cls)[g] = c;
+    ((double*)A.qhat)[g] = qe / A.params[s].xi;
 }
 
 // z-binning of the adjoint state at a checkpoint: one CTA per sample copies the state slot
@@ -1068,13 +1104,23 @@ extern "C" int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_step
     return PDQ_OK;
 }
 
-extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
-                               const pdq_sample_params* params, double charge_sigma, uint64_t seed,
-                               const pdq_step_cfg* cfg, int64_t n_steps, int32_t K, double eps, double eps_stick,
-                               int32_t n_vec, const double* gbar, double* J, double* pbar, void* workspace,
-                               size_t workspace_bytes, pdq_stream_t stream) {
-    if (!field || !phys || !batch || !params || !cfg || !J || n_steps < 1 || K < 1 || !(eps > 0) || n_vec < 0 ||
-        (n_vec > 0 && (!gbar || !pbar)) || !(charge_sigma >= 0))
+namespace pdq {
+
+// Where the adjoint's initial state comes from.
+enum AdjInit { ADJ_SEED = 0, ADJ_STATE = 1, ADJ_REVERSE_ONLY = 2 };
+
+// The three entry points below share this routine.  ADJ_SEED seeds the particles as
+// pdq_seed_particles would; ADJ_STATE loads them from `init`; ADJ_REVERSE_ONLY skips the forward
+// sweep and runs the reverse sweeps on the checkpoints and sums a forward sweep left in the
+// workspace (the workspace layout depends only on the batch, n_steps and K).
+static int adjoint_impl(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
+                        const pdq_sample_params* params, AdjInit init_kind, const pdq_state* init,
+                        double charge_sigma, uint64_t seed, const pdq_step_cfg* cfg, int64_t n_steps, int32_t K,
+                        double eps, double eps_stick, int32_t n_vec, const double* gbar, double* J, double* pbar,
+                        void* workspace, size_t workspace_bytes, pdq_stream_t stream) {
+    const bool forward = init_kind != ADJ_REVERSE_ONLY;
+    if (!field || !phys || !batch || !params || !cfg || (forward && !J) || n_steps < 1 || K < 1 || !(eps > 0) ||
+        n_vec < 0 || (n_vec > 0 && (!gbar || !pbar)) || (!forward && n_vec < 1) || !(charge_sigma >= 0))
         return PDQ_ERR_INVALID_ARG;
     if (cfg->mode != PDQ_STICK && cfg->mode != PDQ_REBOUND) return PDQ_ERR_INVALID_ARG;
     if (cfg->mode == PDQ_REBOUND && !(eps_stick > 0)) return PDQ_ERR_INVALID_ARG;
@@ -1214,20 +1260,32 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
         A.cls = ck_cl[k];
         return copy_state(from, ck[k]);
     };
-    // seed into segment slot 0, save as checkpoint 0
-    A.out = seg[0];
-    k_adj_seed<<<dim3((unsigned)((nmax + NT - 1) / NT), (unsigned)A.S), NT, 0, s>>>(A);
-    PDQ_CUDA(cudaMemsetAsync(A.num, 0, sc, s));
-    PDQ_CUDA(cudaMemsetAsync(A.den, 0, sc, s));
-    PDQ_CUDA(checkpoint(0, seg[0]));
-    // forward sweep: ping-pong between segment slots 0 and 1, checkpoint every K steps
-    for (int64_t n = 0; n < n_steps; ++n) {
-        PDQ_CUDA(fwd(seg[n & 1], seg[(n + 1) & 1], n, 1));
-        if ((n + 1) % K == 0 && (n + 1) < n_steps) PDQ_CUDA(checkpoint((n + 1) / K, seg[(n + 1) & 1]));
-    }
     const int nsc = A.S * A.C;
-    k_adj_finish<<<(nsc + 255) / 256, 256, 0, s>>>(A.num, A.den, nullptr, nsc, A.K.R, A.K.dt, J, nullptr, nullptr);
-    PDQ_CUDA(cudaGetLastError());
+    if (forward) {
+        // seed (or load) into segment slot 0, save as checkpoint 0
+        A.out = seg[0];
+        const dim3 g1((unsigned)((nmax + NT - 1) / NT), (unsigned)A.S);
+        if (init_kind == ADJ_SEED) {
+            k_adj_seed<<<g1, NT, 0, s>>>(A);
+        } else if (init->precision == PDQ_FP64) {
+            k_adj_load<PDQ_FP64><<<g1, NT, 0, s>>>(A, init->count, init->pos[init->cur], init->vel[init->cur],
+                                                  nullptr, (const int2*)init->tag);
+        } else {
+            k_adj_load<PDQ_MIXED><<<g1, NT, 0, s>>>(A, init->count, init->pos[init->cur], init->vel[init->cur],
+                                                   (const double2*)init->xy[init->cur], (const int2*)init->tag);
+        }
+        PDQ_CUDA(cudaMemsetAsync(A.num, 0, sc, s));
+        PDQ_CUDA(cudaMemsetAsync(A.den, 0, sc, s));
+        PDQ_CUDA(checkpoint(0, seg[0]));
+        // forward sweep: ping-pong between segment slots 0 and 1, checkpoint every K steps
+        for (int64_t n = 0; n < n_steps; ++n) {
+            PDQ_CUDA(fwd(seg[n & 1], seg[(n + 1) & 1], n, 1));
+            if ((n + 1) % K == 0 && (n + 1) < n_steps) PDQ_CUDA(checkpoint((n + 1) / K, seg[(n + 1) & 1]));
+        }
+        k_adj_finish<<<(nsc + 255) / 256, 256, 0, s>>>(A.num, A.den, nullptr, nsc, A.K.R, A.K.dt, J, nullptr,
+                                                       nullptr);
+        PDQ_CUDA(cudaGetLastError());
+    }
 
     // backward sweeps, one per cotangent vector
     for (int v = 0; v < n_vec; ++v) {
@@ -1273,4 +1331,62 @@ extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, con
     }
     PDQ_CUDA(cudaGetLastError());
     return PDQ_OK;
+}
+
+// The pdq_batch a state's adjoint is laid out by.
+static void batch_of_state(const pdq_state* st, pdq_batch* b) {
+    memset(b, 0, sizeof(*b));
+    b->precision = st->precision;
+    b->n_samples = st->n_samples;
+    b->n_classes = st->n_classes;
+    for (int c = 0; c < st->n_classes && c < PDQ_MAX_CLASSES; ++c) b->st_plus[c] = st->st_plus[c];
+    b->capacity = st->capacity;
+    b->offset = st->offset;
+}
+
+}  // namespace pdq
+
+extern "C" int pdq_adjoint_state_workspace_size(const pdq_state* init, int64_t n_steps, int32_t K, size_t* bytes) {
+    if (!init) return PDQ_ERR_INVALID_ARG;
+    pdq_batch b;
+    batch_of_state(init, &b);
+    return pdq_adjoint_workspace_size(&b, n_steps, K, bytes);
+}
+
+extern "C" int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, const pdq_state* init,
+                               const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps, int32_t K,
+                               double eps, double eps_stick, int32_t n_vec, const double* gbar, double* J,
+                               double* pbar, void* workspace, size_t workspace_bytes, pdq_stream_t stream) {
+    if (!init || !params || !init->offset || !init->count || !init->tag || (init->cur != 0 && init->cur != 1) ||
+        !init->pos[init->cur] || !init->vel[init->cur] || (init->precision == PDQ_MIXED && !init->xy[init->cur]))
+        return PDQ_ERR_INVALID_ARG;
+    if (init->n_samples < 1 || init->n_samples > (1 << 20)) return PDQ_ERR_INVALID_ARG;
+    // charge per unit xi = q_eff / xi: every sample needs xi != 0
+    std::vector<pdq_sample_params> hp((size_t)init->n_samples);
+    cudaStream_t s = (cudaStream_t)stream;
+    PDQ_CUDA(cudaMemcpyAsync(hp.data(), params, sizeof(pdq_sample_params) * hp.size(), cudaMemcpyDeviceToHost, s));
+    PDQ_CUDA(cudaStreamSynchronize(s));
+    for (const auto& q : hp)
+        if (!(q.xi != 0.0) || !std::isfinite(q.xi)) return PDQ_ERR_INVALID_ARG;
+    pdq_batch b;
+    batch_of_state(init, &b);
+    return adjoint_impl(field, phys, &b, params, ADJ_STATE, init, 0.0, 0, cfg, n_steps, K, eps, eps_stick, n_vec,
+                        gbar, J, pbar, workspace, workspace_bytes, stream);
+}
+
+extern "C" int pdq_adjoint_run_seeded(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
+                                      const pdq_sample_params* params, double charge_sigma, uint64_t seed,
+                                      const pdq_step_cfg* cfg, int64_t n_steps, int32_t K, double eps,
+                                      double eps_stick, int32_t n_vec, const double* gbar, double* J, double* pbar,
+                                      void* workspace, size_t workspace_bytes, pdq_stream_t stream) {
+    return adjoint_impl(field, phys, batch, params, ADJ_SEED, nullptr, charge_sigma, seed, cfg, n_steps, K, eps,
+                        eps_stick, n_vec, gbar, J, pbar, workspace, workspace_bytes, stream);
+}
+
+extern "C" int pdq_adjoint_reverse(const pdq_field* field, const pdq_phys* phys, const pdq_batch* batch,
+                                   const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps,
+                                   int32_t K, double eps, double eps_stick, int32_t n_vec, const double* gbar,
+                                   double* pbar, void* workspace, size_t workspace_bytes, pdq_stream_t stream) {
+    return adjoint_impl(field, phys, batch, params, ADJ_REVERSE_ONLY, nullptr, 0.0, 0, cfg, n_steps, K, eps,
+                        eps_stick, n_vec, gbar, nullptr, pbar, workspace, workspace_bytes, stream);
 }

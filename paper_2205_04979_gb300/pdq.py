@@ -106,9 +106,17 @@ def lib():
             "pdq_mfmc_allocate": (C.c_int, [C.c_int32, P, P, P, C.c_double, C.c_int32, P, P, P, P]),
             "pdq_adjoint_workspace_size": (C.c_int, [C.POINTER(BatchStruct), C.c_int64, C.c_int32,
                                                      C.POINTER(C.c_size_t)]),
-            "pdq_adjoint_run": (C.c_int, [P, C.POINTER(Phys), C.POINTER(BatchStruct), P, C.c_double, C.c_uint64,
-                                          C.POINTER(StepCfg), C.c_int64, C.c_int32, C.c_double, C.c_double,
-                                          C.c_int32, P, P, P, P, C.c_size_t, P]),
+            "pdq_adjoint_state_workspace_size": (C.c_int, [C.POINTER(StateStruct), C.c_int64, C.c_int32,
+                                                           C.POINTER(C.c_size_t)]),
+            "pdq_adjoint_run": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P, C.POINTER(StepCfg),
+                                          C.c_int64, C.c_int32, C.c_double, C.c_double, C.c_int32, P, P, P, P,
+                                          C.c_size_t, P]),
+            "pdq_adjoint_run_seeded": (C.c_int, [P, C.POINTER(Phys), C.POINTER(BatchStruct), P, C.c_double,
+                                                 C.c_uint64, C.POINTER(StepCfg), C.c_int64, C.c_int32, C.c_double,
+                                                 C.c_double, C.c_int32, P, P, P, P, C.c_size_t, P]),
+            "pdq_adjoint_reverse": (C.c_int, [P, C.POINTER(Phys), C.POINTER(BatchStruct), P, C.POINTER(StepCfg),
+                                              C.c_int64, C.c_int32, C.c_double, C.c_double, C.c_int32, P, P, P,
+                                              C.c_size_t, P]),
             "pdq_dgsm_bounds": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P]),
             "pdq_capture_efficiency": (C.c_int, [P, C.POINTER(Phys), P, C.c_int64, P, P]),
             "pdq_p3m_create": (C.c_int, [P, C.POINTER(P3MDesc), C.c_int64, P, C.POINTER(C.c_void_p)]),
@@ -448,45 +456,97 @@ class Batch:
         self.n_samples, self.n_classes = len(counts), len(st_plus)
 
 
-def adjoint_run(field, phys, batch, params_dev, cfg, n_steps, K, eps, seed, charge_sigma=0.0, gbar=None,
-                stream=None, eps_stick=10.0):
-    """J [S, C] and, for cotangents gbar [V, S, C], pbar [V, S, 3] = gbar . dJ/d(xi, zeta, theta)."""
-    n = C.c_size_t()
-    _check(lib().pdq_adjoint_workspace_size(C.byref(batch.b), int(n_steps), int(K), C.byref(n)),
-           "adjoint_workspace_size")
-    ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
-    S, Cn = batch.n_samples, batch.n_classes
+def batch_of_state(state):
+    """The pdq_batch (workspace layout) of a state's adjoint."""
+    b = BatchStruct()
+    st = state.st
+    b.precision, b.n_samples, b.n_classes = st.precision, st.n_samples, st.n_classes
+    for k in range(st.n_classes):
+        b.st_plus[k] = st.st_plus[k]
+    b.capacity, b.offset = st.capacity, st.offset
+    return b
+
+
+def _adjoint_outputs(S, Cn, gbar):
     J = torch.empty((S, Cn), dtype=torch.float64, device="cuda")
     nv = 0 if gbar is None else gbar.shape[0]
     pbar = torch.zeros((max(nv, 1), S, 3), dtype=torch.float64, device="cuda")
     g = gbar.contiguous().to(torch.float64) if gbar is not None else None
-    _check(lib().pdq_adjoint_run(field.handle, C.byref(phys), C.byref(batch.b), _ptr(params_dev), charge_sigma,
-                                 seed, C.byref(cfg), int(n_steps), int(K), float(eps), float(eps_stick), nv, _ptr(g),
-                                 _ptr(J), _ptr(pbar), _ptr(ws), ws.numel(), _stream(stream)), "adjoint_run")
+    return J, nv, pbar, g
+
+
+def adjoint_workspace(batch_struct, n_steps, K):
+    n = C.c_size_t()
+    _check(lib().pdq_adjoint_workspace_size(C.byref(batch_struct), int(n_steps), int(K), C.byref(n)),
+           "adjoint_workspace_size")
+    return torch.empty(n.value, dtype=torch.uint8, device="cuda")
+
+
+def adjoint_run(field, phys, state, params_dev, cfg, n_steps, K, eps, gbar=None, stream=None, eps_stick=10.0,
+                ws=None):
+    """pdq_adjoint_run from the current half of `state`: J [S, C] and, for cotangents gbar [V, S, C],
+    pbar [V, S, 3] = gbar . dJ/d(xi, zeta, theta).  Returns (J, pbar or None, workspace)."""
+    if ws is None:
+        n = C.c_size_t()
+        _check(lib().pdq_adjoint_state_workspace_size(C.byref(state.st), int(n_steps), int(K), C.byref(n)),
+               "adjoint_state_workspace_size")
+        ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+    J, nv, pbar, g = _adjoint_outputs(state.n_samples, state.n_classes, gbar)
+    _check(lib().pdq_adjoint_run(field.handle, C.byref(phys), C.byref(state.st), _ptr(params_dev), C.byref(cfg),
+                                 int(n_steps), int(K), float(eps), float(eps_stick), nv, _ptr(g), _ptr(J),
+                                 _ptr(pbar), _ptr(ws), ws.numel(), _stream(stream)), "adjoint_run")
+    return J, (pbar[:nv] if nv else None), ws
+
+
+def adjoint_run_seeded(field, phys, batch, params_dev, cfg, n_steps, K, eps, seed, charge_sigma=0.0, gbar=None,
+                       stream=None, eps_stick=10.0, ws=None):
+    """pdq_adjoint_run_seeded: J [S, C] and, for cotangents gbar [V, S, C], pbar [V, S, 3]."""
+    if ws is None:
+        ws = adjoint_workspace(batch.b, n_steps, K)
+    J, nv, pbar, g = _adjoint_outputs(batch.n_samples, batch.n_classes, gbar)
+    _check(lib().pdq_adjoint_run_seeded(field.handle, C.byref(phys), C.byref(batch.b), _ptr(params_dev),
+                                        charge_sigma, seed, C.byref(cfg), int(n_steps), int(K), float(eps),
+                                        float(eps_stick), nv, _ptr(g), _ptr(J), _ptr(pbar), _ptr(ws), ws.numel(),
+                                        _stream(stream)), "adjoint_run_seeded")
     return J, (pbar[:nv] if nv else None)
+
+
+def adjoint_reverse(field, phys, batch_struct, params_dev, cfg, n_steps, K, eps, gbar, ws, stream=None,
+                    eps_stick=10.0):
+    """pdq_adjoint_reverse: pbar [V, S, 3] from the forward sweep an earlier call left in `ws`."""
+    nv = gbar.shape[0]
+    pbar = torch.zeros((nv, batch_struct.n_samples, 3), dtype=torch.float64, device="cuda")
+    g = gbar.contiguous().to(torch.float64)
+    _check(lib().pdq_adjoint_reverse(field.handle, C.byref(phys), C.byref(batch_struct), _ptr(params_dev),
+                                     C.byref(cfg), int(n_steps), int(K), float(eps), float(eps_stick), nv, _ptr(g),
+                                     _ptr(pbar), _ptr(ws), ws.numel(), _stream(stream)), "adjoint_reverse")
+    return pbar
 
 
 class PdqDeposition(torch.autograd.Function):
     """J = smoothed V_dep+ [S, C] of the particle model as a function of params [S, 3] = (xi, zeta, theta).
 
-    forward runs the smoothed forward sweep; backward runs the hand-written adjoint with the
-    incoming gradient as cotangent (one forward + one reverse sweep with checkpoints every K steps).
+    forward runs the smoothed forward sweep (pdq_adjoint_run_seeded with no cotangent) and keeps
+    its workspace, checkpoints included, until backward; backward runs only the reverse sweep
+    (pdq_adjoint_reverse) with the incoming gradient as cotangent.
     """
 
     @staticmethod
     def forward(ctx, params, field, phys, batch, cfg, n_steps, K, eps, seed, charge_sigma):
-        J, _ = adjoint_run(field, phys, batch, params_tensor(params.detach()), cfg, n_steps, K, eps, seed,
-                           charge_sigma)
+        prm = params_tensor(params.detach())
+        ws = adjoint_workspace(batch.b, n_steps, K)
+        J, _ = adjoint_run_seeded(field, phys, batch, prm, cfg, n_steps, K, eps, seed, charge_sigma, ws=ws)
         ctx.save_for_backward(params.detach())
-        ctx.args = (field, phys, batch, cfg, n_steps, K, eps, seed, charge_sigma)
+        ctx.args = (field, phys, batch, cfg, n_steps, K, eps, prm, ws)
         return J
 
     @staticmethod
     def backward(ctx, grad_out):
         (params,) = ctx.saved_tensors
-        field, phys, batch, cfg, n_steps, K, eps, seed, charge_sigma = ctx.args
-        _, pbar = adjoint_run(field, phys, batch, params_tensor(params), cfg, n_steps, K, eps, seed, charge_sigma,
-                              gbar=grad_out.detach().to(torch.float64).unsqueeze(0))
+        field, phys, batch, cfg, n_steps, K, eps, prm, ws = ctx.args
+        pbar = adjoint_reverse(field, phys, batch.b, prm, cfg, n_steps, K, eps,
+                               grad_out.detach().to(torch.float64).unsqueeze(0), ws)
+        ctx.args = None
         return (pbar[0].to(device=params.device, dtype=params.dtype),) + (None,) * 9
 
 

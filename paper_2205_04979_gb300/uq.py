@@ -78,7 +78,7 @@ def dgsm_deposition(samples, particles, steps, st_plus=(0.1, 1.0, 10.0),
                     stream=None):
     """Derivative-based bounds on the total Sobol' indices of the smoothed V_dep+ per class.
 
-    The adjoint (pdq_adjoint_run) gives dJ/d(xi, zeta, theta) for every sample with one cotangent
+    The adjoint (pdq_adjoint_run_seeded) gives dJ/d(xi, zeta, theta) for every sample with one cotangent
     vector per class; pdq_dgsm_bounds turns them into s_j^t <= (b_j - a_j)^2 E[(dJ/dx_j)^2] /
     (pi^2 Var J).  Returns dict(J [S, C], grad [S, C, 3], nu [3, C], bound [3, C]).
     """
@@ -97,8 +97,8 @@ def dgsm_deposition(samples, particles, steps, st_plus=(0.1, 1.0, 10.0),
         gbar = torch.zeros((C, samples, C), dtype=torch.float64, device="cuda")
         for c in range(C):
             gbar[c, :, c] = 1.0
-        J, pbar = pdq.adjoint_run(field, phys, batch, pdq.params_tensor(x), cfg, steps, min(K, steps), eps,
-                                  seed + 1, gbar=gbar, stream=stream, eps_stick=eps_stick)
+        J, pbar = pdq.adjoint_run_seeded(field, phys, batch, pdq.params_tensor(x), cfg, steps, min(K, steps),
+                                         eps, seed + 1, gbar=gbar, stream=stream, eps_stick=eps_stick)
         grad = pbar.permute(1, 0, 2).contiguous()          # [S, C, 3]
         nu, bound = pdq.dgsm_bounds(grad, J, hi - lo, stream=stream)
     return {"J": J.cpu().numpy(), "grad": grad.cpu().numpy(), "nu": nu, "bound": bound, "inputs": x}

@@ -1,5 +1,6 @@
-"""GPU adjoint of the smoothed deposition functional (pdq_adjoint_run) against
-the oracle's forward-mode dual numbers and against central finite differences.
+"""GPU adjoint of the smoothed deposition functional (pdq_adjoint_run, pdq_adjoint_run_seeded,
+pdq_adjoint_reverse) against the oracle's forward-mode dual numbers and against central
+finite differences.
 
 Two cases: A exercises the charge path (Coulomb, image; eps = 0.5), B the van
 der Waals path (St+ = 10, 100 pushed to the wall by a test-only gravity vector;
@@ -65,8 +66,8 @@ def _run(pdq, case, precision, params, K=7, gbar=None):
     field = pdq.Field(pdq.field_desc(**GRID), 0)
     batch = pdq.Batch(precision, COUNTS, c["st"])
     cfg = pdq.step_cfg(c["dt"], window_start=c["win"], gravity=c["gravity"], mode=c.get("mode", 0))
-    return pdq.adjoint_run(field, pdq.phys_default(), batch, pdq.params_tensor(params), cfg, c["steps"], K,
-                           c["eps"], SEED, gbar=gbar, eps_stick=c.get("eps_stick", 10.0))
+    return pdq.adjoint_run_seeded(field, pdq.phys_default(), batch, pdq.params_tensor(params), cfg, c["steps"],
+                                  K, c["eps"], SEED, gbar=gbar, eps_stick=c.get("eps_stick", 10.0))
 
 
 def _onehot():
@@ -149,3 +150,181 @@ def test_dgsm_pipeline(pdq):
     nu, bound = mfmc.dgsm_bound(r["grad"], r["J"], [0.1, 1.0, 1.0])
     assert np.allclose(r["nu"], nu, rtol=1e-12) and np.allclose(r["bound"], bound, rtol=1e-12, equal_nan=True)
     assert np.all(r["bound"][2] == 0)
+
+
+# ---------------------------------------------------------------------------
+# Sizes that cross the MIXED Newton-pair tiles: the forward sums take 1,024-particle i-tiles
+# and the pair VJP 512-particle ones, so only samples above those sizes run the off-diagonal
+# blocks, where the pair term enters the j side with the opposite sign.  Charge active
+# (case A's forces), eps+ = 0.5 and 0.02 (the widest and narrowest smoothing of the
+# 256 x 16,384 adjoint workload).
+# ---------------------------------------------------------------------------
+TILE_COUNTS = [1025, 513, 2049, 1, 0]
+TILE_PARAMS = np.array([[0.09, 0.7, 0.4], [0.06, 0.3, 0.8], [0.075, 0.5, 0.5], [0.05, 0.6, 0.3],
+                        [0.07, 0.4, 0.6]])
+TILE = dict(st=[0.1, 1.0], steps=24, dt=0.05, gravity=(0, 0, 1), win=5)
+_TREF = {}
+
+
+def _onehot_sc(S, Cn):
+    g = torch.zeros((Cn, S, Cn), dtype=torch.float64, device="cuda")
+    for c in range(Cn):
+        g[c, :, c] = 1.0
+    return g
+
+
+def _rounding_bars(run, x, y, z, J, dJ):
+    """FP64 bars: 10x the oracle's own response to +-4e-16 relative changes of the initial positions
+    (the narrow sigmoid at eps+ = 0.02 and the stiff vdW zone amplify rounding), at least 1e-12
+    for J and 1e-8 of each gradient column's largest entry."""
+    rng = np.random.default_rng(7)
+
+    def pert(a):
+        return a * (1 + 4e-16 * rng.choice([-1.0, 1.0], a.shape))
+    J2, dJ2 = run(pert(x), pert(y), pert(z))
+    nz = np.abs(J) > 0
+    rJ = np.max(np.abs(J2 - J)[nz] / np.abs(J)[nz]) if nz.any() else 0.0
+    sc = np.max(np.abs(dJ), axis=(0, 1))
+    rg = np.max(np.max(np.abs(dJ2 - dJ), axis=(0, 1)) / np.where(sc > 0, sc, 1.0))
+    return max(1e-12, 10 * rJ), max(1e-8, 10 * rg)
+
+
+def _tile_ref(eps):
+    if eps not in _TREF:
+        of = oracle.field_desc(**GRID)
+        grid = oracle.field_grid(of, oracle.field_modes(of, 0))
+        st, off = oracle.seed(of, TILE["st"], TILE_COUNTS, np.c_[np.ones(5), TILE_PARAMS[:, 1:]], SEED)
+        cf = oracle.cfg(TILE["dt"], gravity=TILE["gravity"], smooth_eps=eps, window_start=TILE["win"])
+
+        def run(x, y, z):
+            return oracle.smooth_run(of, grid, cf, TILE["st"], off, TILE_PARAMS, x, y, z, st.q, st.cls,
+                                     TILE["steps"])
+        J, dJ = run(st.x, st.y, st.z)
+        _TREF[eps] = (J, dJ) + _rounding_bars(run, st.x, st.y, st.z, J, dJ)
+    return _TREF[eps]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("eps", [0.5, 0.02])
+def test_adjoint_across_newton_tiles_matches_dual_numbers(pdq, precision, eps):
+    J_ref, dJ_ref, bar_J, bar_g = _tile_ref(eps)
+    field = pdq.Field(pdq.field_desc(**GRID), 0)
+    batch = pdq.Batch(precision, TILE_COUNTS, TILE["st"])
+    cfg = pdq.step_cfg(TILE["dt"], window_start=TILE["win"], gravity=TILE["gravity"])
+    J, pbar = pdq.adjoint_run_seeded(field, pdq.phys_default(), batch, pdq.params_tensor(TILE_PARAMS), cfg,
+                                     TILE["steps"], 5, eps, SEED, gbar=_onehot_sc(5, 2))
+    got = np.transpose(pbar.cpu().numpy(), (1, 0, 2))     # [sample, class, param]
+    J = J.cpu().numpy()
+    assert np.all(J[4] == 0) and np.all(got[4] == 0)      # the empty sample
+    assert np.all(got[..., 1:] == 0.0) and np.all(dJ_ref[..., 1:] == 0.0)   # no particle within d/4 of the wall
+    if precision == 0:
+        assert np.allclose(J, J_ref, rtol=bar_J, atol=1e-300), (bar_J, np.max(np.abs(J / J_ref - 1)[J_ref > 0]))
+        _check_grad(got, dJ_ref, bar_g, (0,))
+    else:
+        assert np.allclose(J, J_ref, rtol=3e-3, atol=1e-6 * np.max(J_ref))
+        _check_grad(got, dJ_ref, 3e-2, (0,))
+
+
+# ---------------------------------------------------------------------------
+# The adjoint started from a caller's state: pdq_step_particles advances a transient (with
+# deposits; with and without compaction), then pdq_adjoint_run differentiates the next steps
+# from that state; the oracle's dual numbers start from the same arrays (positions,
+# velocities, alive flags as weights, charge per unit xi = q_eff / xi, classes from the tags).
+# ---------------------------------------------------------------------------
+def _state_arrays(state, params):
+    pos_t, vel_t, xy_t = state.current()
+    pos = pos_t.cpu().numpy().astype(np.float64)
+    vel = vel_t.cpu().numpy().astype(np.float64)
+    xy = None if xy_t is None else xy_t.cpu().numpy()
+    tag = state.tag.cpu().numpy()
+    cnt = state.count.cpu().numpy()
+    off = state.offset.cpu().numpy()
+    N = off[-1]
+    x, y, z, qh, w = (np.zeros(N) for _ in range(5))
+    v = np.zeros((N, 3))
+    cls = np.zeros(N, np.int32)
+    for s in range(len(cnt)):
+        r = np.arange(off[s], off[s] + cnt[s])
+        x[r] = xy[r, 0] if xy is not None else pos[r, 0]
+        y[r] = xy[r, 1] if xy is not None else pos[r, 1]
+        z[r], v[r] = pos[r, 2], vel[r, :3]
+        w[r], cls[r] = vel[r, 3], tag[r, 1]
+        qh[r] = pos[r, 3] / params[s, 0]
+    return off, x, y, z, qh, cls, v, w
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("compact_every", [0, 5])
+def test_adjoint_from_stepped_state_matches_dual_numbers(pdq, precision, compact_every):
+    c = CASES["B"]
+    P = _params("B")
+    field = pdq.Field(pdq.field_desc(**GRID), 0)
+    phys = pdq.phys_default()
+    state = pdq.State(precision, COUNTS, c["st"])
+    prm = pdq.params_tensor(P)
+    pdq.seed_particles(field, phys, state, prm, seed=SEED)
+    # a transient under a stronger test-only gravity toward the wall, so that a few particles
+    # deposit before the adjoint starts (the oracle deposits 5 of 429 in these 60 steps)
+    cfg_t = pdq.step_cfg(c["dt"], gravity=(20.0, 0.0, 0.0), compact_every=compact_every)
+    tally = pdq.Tally(2, 2)
+    pdq.step_particles(field, phys, state, prm, cfg_t, 60, tally, pdq.workspace(state, cfg_t))
+    assert int(tally.n_dep.sum()) > 0                       # deposits before the adjoint starts
+    if compact_every:
+        assert np.all(state.count.cpu().numpy() < np.array(COUNTS))   # empty slots after compaction
+    before = [t.clone() for t in state.current() if t is not None] + [state.tag.clone(), state.count.clone()]
+
+    # the adjoint keeps the stronger gravity, so particles reach the vdW range (zeta enters)
+    cfg = pdq.step_cfg(c["dt"], window_start=c["win"], gravity=(20.0, 0.0, 0.0))
+    J, pbar, _ = pdq.adjoint_run(field, phys, state, prm, cfg, 40, 7, c["eps"], gbar=_onehot())
+    after = [t for t in state.current() if t is not None] + [state.tag, state.count]
+    assert all(torch.equal(a, b) for a, b in zip(before, after))          # init is read only
+
+    off, x, y, z, qh, cls, v, w = _state_arrays(state, P)
+    of = oracle.field_desc(**GRID)
+    grid = oracle.field_grid(of, oracle.field_modes(of, 0))
+    cf = oracle.cfg(c["dt"], gravity=(20.0, 0.0, 0.0), smooth_eps=c["eps"], window_start=c["win"])
+
+    def run(x, y, z):
+        return oracle.smooth_run(of, grid, cf, c["st"], off, P, x, y, z, qh, cls, 40, v0=v, w0=w)
+    J_ref, dJ_ref = run(x, y, z)
+    got = np.transpose(pbar.cpu().numpy(), (1, 0, 2))
+    assert np.all(got[..., 2] == 0.0) and np.all(dJ_ref[..., 2] == 0.0)
+    if precision == 0:
+        bar_J, bar_g = _rounding_bars(run, x, y, z, J_ref, dJ_ref)
+        assert np.allclose(J.cpu().numpy(), J_ref, rtol=bar_J, atol=1e-300)
+        _check_grad(got, dJ_ref, bar_g, (0, 1))
+    else:
+        assert np.allclose(J.cpu().numpy(), J_ref, rtol=3e-3, atol=1e-6 * np.max(J_ref))
+        _check_grad(got, dJ_ref, 3e-2, (0, 1))
+
+
+def test_adjoint_reverse_alone_matches_the_combined_call(pdq):
+    c = CASES["A"]
+    field = pdq.Field(pdq.field_desc(**GRID), 0)
+    phys = pdq.phys_default()
+    batch = pdq.Batch(0, COUNTS, c["st"])
+    cfg = pdq.step_cfg(c["dt"], window_start=c["win"], gravity=c["gravity"])
+    prm = pdq.params_tensor(PARAMS)
+    J1, p1 = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, c["steps"], 7, c["eps"], SEED, gbar=_onehot())
+    ws = pdq.adjoint_workspace(batch.b, c["steps"], 7)
+    J2, none = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, c["steps"], 7, c["eps"], SEED, ws=ws)
+    assert none is None
+    p2 = pdq.adjoint_reverse(field, phys, batch.b, prm, cfg, c["steps"], 7, c["eps"], _onehot(), ws)
+    p3 = pdq.adjoint_reverse(field, phys, batch.b, prm, cfg, c["steps"], 7, c["eps"], _onehot(), ws)
+    # the double atomics of the tallies and pbar may add in another order: rounding only
+    assert torch.allclose(J1, J2, rtol=1e-13, atol=0)
+    assert torch.allclose(p1, p2, rtol=1e-12, atol=1e-14 * float(p1.abs().max()))
+    assert torch.allclose(p2, p3, rtol=1e-12, atol=1e-14 * float(p1.abs().max()))
+
+
+def test_adjoint_from_state_rejects_zero_charge_scale(pdq):
+    c = CASES["A"]
+    field = pdq.Field(pdq.field_desc(**GRID), 0)
+    phys = pdq.phys_default()
+    state = pdq.State(0, COUNTS, c["st"])
+    P = PARAMS.copy()
+    pdq.seed_particles(field, phys, state, pdq.params_tensor(P), seed=SEED)
+    P[1, 0] = 0.0                                          # charge per unit xi is undefined
+    cfg = pdq.step_cfg(c["dt"], window_start=c["win"], gravity=c["gravity"])
+    with pytest.raises(pdq.PdqError):
+        pdq.adjoint_run(field, phys, state, pdq.params_tensor(P), cfg, 10, 5, c["eps"])
