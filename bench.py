@@ -462,11 +462,10 @@ def run_ours(args):
                             "variant": cfg.variant, "autotuned": args.block == 0 and not args.no_autotune}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
-                     # dram bytes read + written per launch from the ncu captures in
-                     # profiles/k_step_mixed_batched.md (pair variant 2: 495.4 MB) and
-                     # profiles/k_pairs_sym_batched.md (variant 3: 178.7 MB), both on 4,557,792
-                     # particles, scaled by the particle count of this launch; null for a
-                     # variant without a capture of its kernel
+                     # dram bytes read + written per launch from ncu captures of the pair
+                     # kernels (pair variant 2: 495.4 MB, variant 3: 178.7 MB, both on
+                     # 4,557,792 particles), scaled by the particle count of this launch; null
+                     # for a variant without a capture of its kernel
                      "traffic": KSTEP_DRAM_BYTES[cfg.variant] / 4557792 * float(np.sum(counts))
                      if prec == pdq.MIXED and cfg.variant in KSTEP_DRAM_BYTES and not args.contact else None,
                      "kernel": ("k_pairs_sym (Newton-pair Coulomb sums), then the k_step contact variant "

@@ -478,11 +478,13 @@ int pdq_mfmc_sobol(int32_t k, const double* const* y, const int64_t* m, const do
  * from S >= 2 Monte Carlo samples: grad device [S][C][d] (e.g. from
  * pdq_adjoint_run with one-hot cotangents), y device [S][C] the outputs,
  * width host [d] = b_j - a_j.  Host outputs nu [d][C], bound [d][C] (NaN
- * where Var f = 0).  FP64 fixed-order reductions on the device.  Uses a
- * (d+1) x C scratch from the stream-ordered allocator; synchronises `stream`.
- * Errors: INVALID_ARG, CUDA.                                                 */
+ * where Var f = 0).  FP64 fixed-order reductions on the device into the
+ * caller's workspace (device, 8-byte aligned, >= pdq_dgsm_workspace_size =
+ * 8 (d+1) C bytes); synchronises `stream`.
+ * Errors: INVALID_ARG, WORKSPACE, CUDA.                                      */
+int pdq_dgsm_workspace_size(int32_t C, int32_t d, size_t* bytes);
 int pdq_dgsm_bounds(int32_t S, int32_t C, int32_t d, const double* grad, const double* y, const double* width,
-                    double* nu, double* bound, pdq_stream_t stream);
+                    double* nu, double* bound, void* workspace, size_t workspace_bytes, pdq_stream_t stream);
 
 /* ------------------------------------------------------------------ P3M
  * Electrostatics by P3M (App. A.2: the particle-particle particle-mesh method

@@ -278,20 +278,26 @@ __global__ void __launch_bounds__(256) k_dgsm(const double* __restrict__ grad, c
 }
 }  // namespace pdq
 
+extern "C" int pdq_dgsm_workspace_size(int32_t C, int32_t d, size_t* bytes) {
+    if (C < 1 || d < 1 || d > 64 || !bytes) return PDQ_ERR_INVALID_ARG;
+    *bytes = sizeof(double) * (size_t)(d + 1) * (size_t)C;
+    return PDQ_OK;
+}
+
 extern "C" int pdq_dgsm_bounds(int32_t S, int32_t C, int32_t d, const double* grad, const double* y,
-                               const double* width, double* nu, double* bound, pdq_stream_t stream) {
+                               const double* width, double* nu, double* bound, void* workspace,
+                               size_t workspace_bytes, pdq_stream_t stream) {
     if (S < 2 || C < 1 || d < 1 || d > 64 || !grad || !y || !width || !nu || !bound) return PDQ_ERR_INVALID_ARG;
+    size_t need = 0;
+    pdq_dgsm_workspace_size(C, d, &need);
+    if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 7)) return PDQ_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    double* dev = nullptr;
-    // small result buffer on the stream's device (d+1) x C doubles
-    PDQ_CUDA(cudaMallocAsync(&dev, sizeof(double) * (size_t)(d + 1) * C, s));
+    double* dev = (double*)workspace;   // (d+1) x C results: nu per input, then Var f
     k_dgsm<<<dim3(C, d + 1), 256, 0, s>>>(grad, y, S, C, d, dev);
     std::vector<double> h((size_t)(d + 1) * C);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dev, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(dev, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(e);
+    PDQ_CUDA(cudaGetLastError());
+    PDQ_CUDA(cudaMemcpyAsync(h.data(), dev, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    PDQ_CUDA(cudaStreamSynchronize(s));
     const double pi2 = kPi * kPi;
     for (int j = 0; j < d; ++j)
         for (int c = 0; c < C; ++c) {

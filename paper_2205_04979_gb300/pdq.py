@@ -117,7 +117,8 @@ def lib():
             "pdq_adjoint_reverse": (C.c_int, [P, C.POINTER(Phys), C.POINTER(BatchStruct), P, C.POINTER(StepCfg),
                                               C.c_int64, C.c_int32, C.c_double, C.c_double, C.c_int32, P, P, P,
                                               C.c_size_t, P]),
-            "pdq_dgsm_bounds": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P]),
+            "pdq_dgsm_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+            "pdq_dgsm_bounds": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, C.c_size_t, P]),
             "pdq_capture_efficiency": (C.c_int, [P, C.POINTER(Phys), P, C.c_int64, P, P]),
             "pdq_p3m_create": (C.c_int, [P, C.POINTER(P3MDesc), C.c_int64, P, C.POINTER(C.c_void_p)]),
             "pdq_p3m_destroy": (C.c_int, [P]),
@@ -557,6 +558,9 @@ def dgsm_bounds(grad, y, width, stream=None):
     w = np.ascontiguousarray(width, np.float64)
     nu, bound = np.zeros((d, Cn)), np.zeros((d, Cn))
     g, yy = grad.contiguous().to(torch.float64), y.contiguous().to(torch.float64)
-    _check(lib().pdq_dgsm_bounds(S, Cn, d, _ptr(g), _ptr(yy), _np_ptr(w), _np_ptr(nu), _np_ptr(bound),
-                                 _stream(stream)), "dgsm_bounds")
+    n = C.c_size_t()
+    _check(lib().pdq_dgsm_workspace_size(Cn, d, C.byref(n)), "dgsm_workspace_size")
+    ws = torch.empty(n.value, dtype=torch.uint8, device=grad.device)
+    _check(lib().pdq_dgsm_bounds(S, Cn, d, _ptr(g), _ptr(yy), _np_ptr(w), _np_ptr(nu), _np_ptr(bound), _ptr(ws),
+                                 ws.numel(), _stream(stream)), "dgsm_bounds")
     return nu, bound
