@@ -20,10 +20,7 @@ has) on a bounded sample of the same workload, on the host cores.
 import argparse
 import json
 import os
-import statistics
-import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -32,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
+from paper_2205_04979_gb300.clocks import ClockSampler  # noqa: E402
 
 METRIC = "particle-steps/s, batched mixed vs plain FP64 on GB300 at ≤1e-3 rel V_dep error"
 FLOPS_PER_PAIR = 21          # 3 sub, 4 minimum image, 5 r^2, 3 r^-3 q, 6 accumulate (FMA = 2); + 1 rsqrt
@@ -42,8 +40,8 @@ NEWTON_FLOPS_PER_LANE_OP = 24.0 / 16.0
 # DRAM bytes per launch of the dominant kernel on 4,557,792 particles (ncu): k_step for pair variant 2,
 # k_pairs_sym for pair variant 3
 KSTEP_DRAM_BYTES = {2: 495.4e6, 3: 178.7e6}
-SM_COUNT, FP32_LANES = 152, 128
-FP64_NOMINAL_TFLOPS = 1.25
+# pipe peaks measured by the project microbenchmarks (python -m paper_2205_04979_gb300.peaks)
+PEAKS_FILE = os.path.join(ROOT, "profiles", "peaks.md")
 
 
 def parse():
@@ -76,65 +74,35 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def measured_peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        return {}
+def pipe_peak(mixed, newton):
+    """(peak TFLOP/s, note, instruction-mix peak or None) of the pair kernel's pipe, measured.
 
-
-class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples during the timed region."""
-
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, uuid):
-        self.uuid = uuid
-        self.proc = None
-        self.lines = []
-
-    def start(self):
-        try:
-            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
-            if self.uuid:
-                cmd += ["-i", self.uuid]
-            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except Exception:
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
-    def stop(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.t.join(timeout=2)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+    FP32: the packed FFMA2 rate (fma.rn.f32x2, 4 flops per lane per instruction), the pipe's
+    highest flop rate.  FP64: the DFMA rate.  The Newton-pair kernels issue 16 pipe operations
+    (packed FP32 lane-operations, or FP64 operations) for 24 flops, so the secondary figure is
+    the pipe's operation rate x 24/16: what the pipe delivers for that instruction mix.
+    """
+    from paper_2205_04979_gb300 import peaks as pk
+    rec = pk.load(PEAKS_FILE)
+    if rec is None:
+        raise RuntimeError("no measured pipe peaks: run python -m paper_2205_04979_gb300.peaks --write %s"
+                           % PEAKS_FILE)
+    k = rec["kernels"]
+    clk = rec["clocks"].get("sm_mhz")
+    if mixed:
+        peak = k["ffma2"]["flops_per_s"] / 1e12
+        note = ("measured FP32 FFMA2 (packed f32x2) peak, %.2f TFLOP/s at %.0f MHz on %d SMs" %
+                (peak, clk, rec["sms"]))
+        ops = 2 * k["ffma2"]["lane_ops_per_s"]          # FP32 lane-operations per second
+    else:
+        peak = k["dfma"]["flops_per_s"] / 1e12
+        note = "measured FP64 DFMA peak, %.3f TFLOP/s at %.0f MHz on %d SMs" % (peak, clk, rec["sms"])
+        ops = k["dfma"]["lane_ops_per_s"]
+    mix = None
+    if newton:
+        mix = {"peak": ops * NEWTON_FLOPS_PER_LANE_OP / 1e12,
+               "note": "the measured pipe operation rate x 24 flops / 16 operations (Newton-pair mix)"}
+    return peak, note, mix
 
 
 def cpu_baseline(name, params, counts, seconds, steps_max=50):
@@ -426,26 +394,12 @@ def run_ours(args):
     ms_max, psteps_all = reduce_over_ranks(ms, psteps, world, "cuda")
     if rank != 0:
         return
-    peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
     newton = cfg.variant == 3 and (not args.contact or prec == pdq.MIXED)
     flops_per_pair = NEWTON_FLOPS_PER_PAIR if newton else FLOPS_PER_PAIR
-    if newton and prec == pdq.MIXED:
-        peak_tflops = SM_COUNT * FP32_LANES * NEWTON_FLOPS_PER_LANE_OP * sm_max * 1e6 / 1e12
-        peak_note = ("FP32 pipe peak for the Newton-pair instruction mix = 152 SMs x 128 lanes x %.0f MHz "
-                     "(max SM clock) x 24 flops / 16 lane-ops" % sm_max)
-    elif newton:
-        peak_tflops = FP64_NOMINAL_TFLOPS * NEWTON_FLOPS_PER_LANE_OP / 2
-        peak_note = ("FP64 pipe peak for the Newton-pair instruction mix = the nominal 1.25 TFLOP/s (FMA = 2) "
-                     "x (24 flops / 16 operations) / 2; the FP64 rsqrt's refinement steps run on the same pipe "
-                     "and are not counted")
-    elif prec == pdq.MIXED:
-        peak_tflops = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
-        peak_note = "FP32 pipe peak = 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % sm_max
-    else:
-        peak_tflops = FP64_NOMINAL_TFLOPS
-        peak_note = "FP64 nominal dense peak of the GB300 (1.25 TFLOP/s)"
+    peak_tflops, peak_note, mix = pipe_peak(prec == pdq.MIXED, newton)
     achieved = flops_per_pair * pairs / (ms / 1e3) / 1e12
+    if mix is not None:
+        mix["frac"] = achieved / mix["peak"]
     out = {
         "metric": METRIC, "value": psteps_all / (ms_max / 1e3), "unit": "particle-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -461,7 +415,7 @@ def run_ours(args):
                             if prec == pdq.MIXED else (2 if newton else 1),
                             "variant": cfg.variant, "autotuned": args.block == 0 and not args.no_autotune}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops,
+                     "frac": achieved / peak_tflops, "instruction_mix": mix,
                      # dram bytes read + written per launch from ncu captures of the pair
                      # kernels (pair variant 2: 495.4 MB, variant 3: 178.7 MB, both on
                      # 4,557,792 particles), scaled by the particle count of this launch; null

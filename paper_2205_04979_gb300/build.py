@@ -15,6 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpdq.so")
+PEAKS_SRC = os.path.join(HERE, "csrc_peaks", "pdq_peaks.cu")
+PEAKS_LIB = os.path.join(OUT, "libpdqpeaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,8 +39,24 @@ def _stale():
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def build_peaks(force=False):
+    """Compile the roofline microbenchmarks (csrc_peaks/) into _build/libpdqpeaks.so."""
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_LIB
+    os.makedirs(OUT, exist_ok=True)
+    tmp = PEAKS_LIB + ".%d.tmp" % os.getpid()
+    cmd = [nvcc()] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart",
+                             "shared", "-o", tmp, PEAKS_SRC]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed on %s:\n%s" % (PEAKS_SRC, r.stderr))
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 def build(force=False, verbose=False):
-    """Compile every .cu under csrc/ and link _build/libpdq.so; returns its path."""
+    """Compile every .cu under csrc/ and link _build/libpdq.so (and the microbenchmarks); returns its path."""
+    build_peaks(force)
     if not force and not _stale():
         return LIB
     os.makedirs(OUT, exist_ok=True)

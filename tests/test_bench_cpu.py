@@ -27,3 +27,17 @@ def test_reference_arm_json_line():
     assert b["kind"] == "oracle" and b["cores"] >= 1 and b["value"] == d["value"] and b["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_measured_pipe_peaks_are_read_from_the_committed_summary():
+    import bench
+    from paper_2205_04979_gb300 import peaks
+    rec = peaks.load(bench.PEAKS_FILE)
+    assert rec is not None and rec["sms"] > 0 and rec["clocks"]["sm_mhz"] > 0
+    fp32, _, mix32 = bench.pipe_peak(True, True)
+    fp64, _, mix64 = bench.pipe_peak(False, False)
+    assert fp32 == rec["kernels"]["ffma2"]["flops_per_s"] / 1e12
+    assert fp64 == rec["kernels"]["dfma"]["flops_per_s"] / 1e12
+    # the Newton-pair mix: 16 pipe operations for 24 flops
+    assert abs(mix32["peak"] - 2 * rec["kernels"]["ffma2"]["lane_ops_per_s"] * 1.5 / 1e12) < 1e-9
+    assert mix64 is None
