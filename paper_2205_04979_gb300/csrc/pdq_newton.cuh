@@ -66,7 +66,10 @@ __device__ __forceinline__ ZClass zclass(float alo, float ahi, float blo, float 
 //   - the later particles: Newton pairs.  A j-tile of NT particles is staged in shared memory;
 //     each warp takes it in groups of 32 j, lane l holding j = (l + k) mod 32 at step k and
 //     passing that j's running sum to lane l - 1 after the step, so that within a warp no two
-//     lanes touch the same j and after 32 steps every sum is back at its own lane.  The per-warp
+//     lanes touch the same j and after 32 steps every sum is back at its own lane.  The running
+//     sums stay packed (one half per i-half of the packed pairs) and move as 64-bit shuffles;
+//     the halves are added once, at home.  Each 32-j group is staged twice in a row, so lane l
+//     reads entry l + k without wrapping (constant offsets in the unrolled loop).  The per-warp
 //     sums of the tile are added in shared memory and leave with one float4 atomic per j.
 // The earlier particles of the sample reach this tile as the j side of earlier tiles.
 // load(g) gives particle g as (x, y, z, q).  Padding particles sit far off the axis
@@ -77,19 +80,26 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
                                             float c2, float4* __restrict__ acc) {
     constexpr int W = NT / 32, H = U / 2;
     static_assert(U % 2 == 0 && NT % 32 == 0, "packed pairs over whole warps");
-    // the staged j-tile pre-duplicated, (x,x,y,y) at sj2[j] and (z,z,q,q) at sj2[NT + j] (16-byte
-    // strides, so the skewed per-lane reads of the Newton loop are free of bank conflicts);
-    // per-warp j-side sums; z range of each 32-j group
-    __shared__ __align__(32) ulonglong2 sj2[2 * NT];
+    // the staged j-tile pre-duplicated, (x,x,y,y) in sxy, (z,z,q,q) in szq and (z-L,z-L,q,q) in szm
+    // (16-byte strides, so the skewed per-lane reads of the Newton loop are free of bank
+    // conflicts), j = 32 g + t of group g at entries 64 g + t and 64 g + 32 + t; per-warp j-side
+    // sums; z range of each group
+    __shared__ __align__(32) ulonglong2 sxy[2 * NT];
+    __shared__ __align__(32) ulonglong2 szq[2 * NT];
+    __shared__ __align__(32) ulonglong2 szm[2 * NT];
     __shared__ float s_jacc[W][3][NT];
     __shared__ float2 s_zr[W];
+    // Register budget: the hot loop holds 7 H packed i-values and 4 H calls' temporaries, so
+    // little else stays live across it: positions relative to `base` as 32-bit offsets (a
+    // sample has fewer than 2^31 particles), no shifted copy of Z, and the minimum-image
+    // constants built inside their (rare) branch.  A tile pair's uniform z shift is exact either
+    // way: shift -L takes the j side from szm (z_j - L is exact: such j have z_j > L/2, Sterbenz);
+    // shift +L moves Z in place (z_i - L is exact for z_i > L/2, and adding L back restores z_i).
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float M = 12582912.0f;
-    const f2 invL2 = f2_pack(invL, invL), M2 = f2_pack(M, M), nM2 = f2_pack(-M, -M);
-    const f2 nL2 = f2_pack(-Lf, -Lf);
     const float dcz = sqrtf(c2) + 1e-3f;     // contact distance + rounding margin
     const float kPadI = 1e15f, kPadJ = -1e15f;
-    const int64_t dend = base + NT * U < end ? base + NT * U : end;
+    const int n = (int)(end - base);                 // particles of the sample from base on
+    const int nd = n < NT * U ? n : NT * U;          // the diagonal block
     f2 X[H], Y[H], Z[H], NQ[H], AX[H], AY[H], AZ[H];
     float ilo = INFINITY, ihi = -INFINITY;
 #pragma unroll
@@ -97,9 +107,9 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
         float4 p[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int64_t g = base + (2 * h + e) * NT + tid;
-            if (g < end) {
-                p[e] = load(g);
+            const int g = (2 * h + e) * NT + tid;
+            if (g < n) {
+                p[e] = load(base + g);
                 ilo = fminf(ilo, p[e].z);
                 ihi = fmaxf(ihi, p[e].z);
             } else {
@@ -116,19 +126,33 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
         ilo = fminf(ilo, __shfl_xor_sync(0xffffffffu, ilo, d));
         ihi = fmaxf(ihi, __shfl_xor_sync(0xffffffffu, ihi, d));
     }
-    for (int64_t j0 = base; j0 < end; j0 += NT) {
-        const bool diag = j0 < dend;
-        const int64_t jlim = diag ? dend : end;
-        const int64_t j = j0 + tid;
-        const float4 pj = j < jlim ? load(j) : make_float4(kPadJ, 0.f, 0.f, 0.f);
+    auto shift_z = [&](float sh) {
+        const f2 s2 = f2_pack(sh, sh);
+#pragma unroll
+        for (int h = 0; h < H; ++h) Z[h] = f2_sub(Z[h], s2);
+    };
+    const float nLf = -Lf;
+    for (int j0 = 0; j0 < n; j0 += NT) {
+        const bool diag = j0 < nd;
+        const int jlim = diag ? nd : n;
+        const int j = j0 + tid;
+        const float4 pj = j < jlim ? load(base + j) : make_float4(kPadJ, 0.f, 0.f, 0.f);
         float jlo = j < jlim ? pj.z : INFINITY, jhi = j < jlim ? pj.z : -INFINITY;
         for (int d = 16; d > 0; d >>= 1) {
             jlo = fminf(jlo, __shfl_xor_sync(0xffffffffu, jlo, d));
             jhi = fmaxf(jhi, __shfl_xor_sync(0xffffffffu, jhi, d));
         }
         if (lane == 0) s_zr[warp] = make_float2(jlo, jhi);
-        sj2[tid] = make_ulonglong2(f2_pack(pj.x, pj.x), f2_pack(pj.y, pj.y));
-        sj2[NT + tid] = make_ulonglong2(f2_pack(pj.z, pj.z), f2_pack(pj.w, pj.w));
+        {
+            const ulonglong2 vxy = make_ulonglong2(f2_pack(pj.x, pj.x), f2_pack(pj.y, pj.y));
+            const ulonglong2 vzq = make_ulonglong2(f2_pack(pj.z, pj.z), f2_pack(pj.w, pj.w));
+            const float zm = pj.z + nLf;
+            const ulonglong2 vzm = make_ulonglong2(f2_pack(zm, zm), f2_pack(pj.w, pj.w));
+            const int e = warp * 64 + lane;
+            sxy[e] = vxy; sxy[e + 32] = vxy;
+            szq[e] = vzq; szq[e + 32] = vzq;
+            szm[e] = vzm; szm[e + 32] = vzm;
+        }
         __syncthreads();
         if (diag) {
             // one-sided over the tile's own particles (self pair: d = 0 adds nothing)
@@ -138,26 +162,36 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
             const ZClass zc = zclass(ilo, ihi, blo, bhi, Lf, dcz);
             float mn = 0.f;
             if (zc.direct) {
-                const f2 sh = f2_pack(zc.shift, zc.shift);
-                f2 Zs[H];
-#pragma unroll
-                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
+                const bool up = zc.shift > 0.f;
+                if (up) shift_z(Lf);
+#pragma unroll 1
+                for (int w = 0; w < W; ++w) {
+                    const ulonglong2 *pa = sxy + 64 * w, *pb = (zc.shift < 0.f ? szm : szq) + 64 * w;
 #pragma unroll 4
-                for (int k = 0; k < NT; ++k) {
-                    const ulonglong2 a = sj2[k], b = sj2[NT + k];
+                    for (int k = 0; k < 32; ++k) {
+                        const ulonglong2 a = pa[k], b = pb[k];
 #pragma unroll
-                    for (int h = 0; h < H; ++h)
-                        coulomb_pair_x2_direct<true>(X[h], Y[h], Zs[h], a.x, a.y, b.x, b.y, c2, AX[h], AY[h], AZ[h],
-                                                     mn);
+                        for (int h = 0; h < H; ++h)
+                            coulomb_pair_x2_direct<true>(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, c2, AX[h], AY[h],
+                                                         AZ[h], mn);
+                    }
                 }
+                if (up) shift_z(nLf);
             } else {
+                const float M = 12582912.0f;
+                const f2 invL2 = f2_pack(invL, invL), M2 = f2_pack(M, M), nM2 = f2_pack(-M, -M);
+                const f2 nL2 = f2_pack(-Lf, -Lf);
+#pragma unroll 1
+                for (int w = 0; w < W; ++w) {
+                    const ulonglong2 *pa = sxy + 64 * w, *pb = szq + 64 * w;
 #pragma unroll 4
-                for (int k = 0; k < NT; ++k) {
-                    const ulonglong2 a = sj2[k], b = sj2[NT + k];
+                    for (int k = 0; k < 32; ++k) {
+                        const ulonglong2 a = pa[k], b = pb[k];
 #pragma unroll
-                    for (int h = 0; h < H; ++h)
-                        coulomb_pair_x2<false>(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2, AX[h],
-                                               AY[h], AZ[h], mn);
+                        for (int h = 0; h < H; ++h)
+                            coulomb_pair_x2<false>(X[h], Y[h], Z[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2,
+                                                   AX[h], AY[h], AZ[h], mn);
+                    }
                 }
             }
             __syncthreads();
@@ -168,44 +202,48 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
         for (int g = 0; g < W; ++g) {
             const float2 zr = s_zr[g];
             const ZClass zc = zclass(ilo, ihi, zr.x, zr.y, Lf, dcz);
-            float jx = 0.f, jy = 0.f, jz = 0.f;
-            auto group = [&](auto minimg, auto clamp, const f2* Zt) {
+            f2 JX = 0ull, JY = 0ull, JZ = 0ull;
+            const int from = (lane + 1) & 31;
+            const ulonglong2 *pa = sxy + 64 * g + lane, *pb = (zc.direct && zc.shift < 0.f ? szm : szq) + 64 * g + lane;
+            auto group = [&](auto minimg, auto clamp) {
+                f2 invL2 = 0ull, M2 = 0ull, nM2 = 0ull, nL2 = 0ull;
+                if constexpr (decltype(minimg)::value) {
+                    const float M = 12582912.0f;
+                    invL2 = f2_pack(invL, invL); M2 = f2_pack(M, M); nM2 = f2_pack(-M, -M); nL2 = f2_pack(-Lf, -Lf);
+                }
 #pragma unroll 4
                 for (int k = 0; k < 32; ++k) {
-                    const int jj = g * 32 + ((lane + k) & 31);
-                    const ulonglong2 a = sj2[jj], b = sj2[NT + jj];
-                    f2 JX = f2_pack(jx, 0.f), JY = f2_pack(jy, 0.f), JZ = f2_pack(jz, 0.f);
+                    const ulonglong2 a = pa[k], b = pb[k];
 #pragma unroll
                     for (int h = 0; h < H; ++h)
                         coulomb_pair_x2_sym<decltype(minimg)::value, decltype(clamp)::value>(
-                            X[h], Y[h], Zt[h], NQ[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2, AX[h], AY[h],
+                            X[h], Y[h], Z[h], NQ[h], a.x, a.y, b.x, b.y, invL2, M2, nM2, nL2, c2, AX[h], AY[h],
                             AZ[h], JX, JY, JZ);
-                    float l0, l1;
-                    f2_unpack(JX, l0, l1); jx = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
-                    f2_unpack(JY, l0, l1); jy = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
-                    f2_unpack(JZ, l0, l1); jz = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                    JX = __shfl_sync(0xffffffffu, JX, from);
+                    JY = __shfl_sync(0xffffffffu, JY, from);
+                    JZ = __shfl_sync(0xffffffffu, JZ, from);
                 }
             };
             if (zc.direct) {
-                const f2 sh = f2_pack(zc.shift, zc.shift);
-                f2 Zs[H];
-#pragma unroll
-                for (int h = 0; h < H; ++h) Zs[h] = f2_sub(Z[h], sh);
-                if (zc.apart) group(std::false_type{}, std::false_type{}, Zs);
-                else group(std::false_type{}, std::true_type{}, Zs);
+                const bool up = zc.shift > 0.f;
+                if (up) shift_z(Lf);
+                if (zc.apart) group(std::false_type{}, std::false_type{});
+                else group(std::false_type{}, std::true_type{});
+                if (up) shift_z(nLf);
             } else {
-                group(std::true_type{}, std::true_type{}, Z);
+                group(std::true_type{}, std::true_type{});
             }
-            s_jacc[warp][0][g * 32 + lane] = jx;
-            s_jacc[warp][1][g * 32 + lane] = jy;
-            s_jacc[warp][2][g * 32 + lane] = jz;
+            float l0, l1;
+            f2_unpack(JX, l0, l1); s_jacc[warp][0][g * 32 + lane] = l0 + l1;
+            f2_unpack(JY, l0, l1); s_jacc[warp][1][g * 32 + lane] = l0 + l1;
+            f2_unpack(JZ, l0, l1); s_jacc[warp][2][g * 32 + lane] = l0 + l1;
         }
         __syncthreads();
-        if (j < end) {
+        if (j < n) {
             float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
             for (int w = 0; w < W; ++w) { sx += s_jacc[w][0][tid]; sy += s_jacc[w][1][tid]; sz += s_jacc[w][2][tid]; }
-            atomicAdd(&acc[j], make_float4(sx, sy, sz, 0.f));
+            atomicAdd(&acc[base + j], make_float4(sx, sy, sz, 0.f));
         }
     }
 #pragma unroll
@@ -214,9 +252,9 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
         f2_unpack(AX[h], a0[0], a1[0]);
         f2_unpack(AY[h], a0[1], a1[1]);
         f2_unpack(AZ[h], a0[2], a1[2]);
-        const int64_t g0 = base + (2 * h) * NT + tid, g1 = g0 + NT;
-        if (g0 < end) atomicAdd(&acc[g0], make_float4(a0[0], a0[1], a0[2], 0.f));
-        if (g1 < end) atomicAdd(&acc[g1], make_float4(a1[0], a1[1], a1[2], 0.f));
+        const int g0 = (2 * h) * NT + tid, g1 = g0 + NT;
+        if (g0 < n) atomicAdd(&acc[base + g0], make_float4(a0[0], a0[1], a0[2], 0.f));
+        if (g1 < n) atomicAdd(&acc[base + g1], make_float4(a1[0], a1[1], a1[2], 0.f));
     }
 }
 

@@ -952,40 +952,27 @@ __global__ void __launch_bounds__(NT, ((V == 4 || V == 6) && P == PDQ_MIXED) ? 6
 }
 
 // Coulomb sums of pair variant 3 into A.acc4 (zeroed before the launch); the given-sums step
-// then does the local update.  Persistent CTAs take (sample, i-tile) items from CTL_QUEUE2 and
-// sum each tile's pairs with newton_tile (its own block one-sided, every later particle of the
-// sample as Newton pairs).
+// then does the local update.  One CTA per (sample, i-tile) item of the table k_build_items
+// sorted heaviest first; the grid covers the host's bound on the item count and CTAs past the
+// device count return at once.  The hardware hands out CTAs in index order as SMs free up,
+// which balances the triangular per-tile work like a queue would: a persistent CTA looping
+// over a queue measured ~5 more register moves per packed pair evaluation in the hot loop.
+// Each CTA sums its tile's pairs with newton_tile (its own block one-sided, every later
+// particle of the sample as Newton pairs).
 // Register budget: 3 CTAs of 128 threads per SM (up to 168 registers), so that the 32-step loop
 // unrolled by 4 keeps more independent pair chains in flight (measured 2.6 % faster than 4 CTAs
 // at 128 registers).
 template <int NT, int U>
 __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_pairs_sym(const StepArgs A) {
-    __shared__ int s_item;
-    const StepConst& K = A.K;
-    const int tid = threadIdx.x;
-    const int64_t n_items = A.ctl[CTL_NITEMS];
+    const int item = blockIdx.x;
+    if (item >= A.ctl[CTL_NITEMS]) return;
     const float4* __restrict__ pos_in = (const float4*)A.pos_in;
     const auto load = [&](int64_t g) { return pos_in[g]; };
-    for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd((unsigned long long*)&A.ctl[CTL_QUEUE2], 1ull);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= n_items) break;
-        const int2 it = A.items[item];
-        const int64_t o = A.offset[it.x];
-        const int64_t end = o + A.count[it.x];
-        const int64_t base = o + (int64_t)it.y * (NT * U);
-        newton_tile<NT, U>(load, base, end, (float)K.L, (float)K.invL, (float)K.contact2f, A.acc4);
-    }
-    if (tid == 0) {
-        __threadfence();
-        const unsigned long long prev = atomicAdd((unsigned long long*)&A.ctl[CTL_DONE2], 1ull);
-        if (prev == gridDim.x - 1) {   // last CTA: reset the queue for the next step
-            A.ctl[CTL_QUEUE2] = 0;
-            A.ctl[CTL_DONE2] = 0;
-            __threadfence();
-        }
-    }
+    const int2 it = A.items[item];
+    const int64_t o = A.offset[it.x];
+    const int64_t end = o + A.count[it.x];
+    const int64_t base = o + (int64_t)it.y * (NT * U);
+    newton_tile<NT, U>(load, base, end, (float)A.K.L, (float)A.K.invL, (float)A.K.contact2f, A.acc4);
 }
 
 // FP64 Newton pair: coulomb_pair_x2_sym for one i-particle in double (minimum image by the
@@ -1505,28 +1492,14 @@ static int launch_newton64(const StepArgs& A, cudaStream_t s) {
 // step that takes them from A.acc4 (V = 6) over the same tiles.
 template <int NT>
 static int launch_newton_contact(const StepArgs& A, cudaStream_t s) {
-    static int per_sm = 0;
-    if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_sym<NT, 8>, NT, 0);
-        if (per_sm <= 0) per_sm = 1;
-    }
-    const int64_t full = (int64_t)sm_count() * per_sm;
     PDQ_CUDA(cudaMemsetAsync(A.acc4, 0, sizeof(float4) * (size_t)(A.cap > 0 ? A.cap : 1), s));
-    k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, std::min(full, A.max_items > 0 ? A.max_items : full)), NT, 0,
-                         s>>>(A);
+    k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, A.max_items), NT, 0, s>>>(A);
     return launch_step<PDQ_MIXED, 2 * NT, 4, 6>(A, s);
 }
 template <int NT>
 static int launch_newton(const StepArgs& A, cudaStream_t s) {
-    static int per_sm = 0;
-    if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_sym<NT, 8>, NT, 0);
-        if (per_sm <= 0) per_sm = 1;
-    }
-    const int64_t full = (int64_t)sm_count() * per_sm;
     PDQ_CUDA(cudaMemsetAsync(A.acc4, 0, sizeof(float4) * (size_t)(A.cap > 0 ? A.cap : 1), s));
-    k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, std::min(full, A.max_items > 0 ? A.max_items : full)), NT, 0,
-                         s>>>(A);
+    k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, A.max_items), NT, 0, s>>>(A);
     return launch_step<PDQ_MIXED, 2 * NT, 4, 5>(A, s);
 }
 
