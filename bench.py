@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--block", type=int, default=0, help="threads per CTA of the step kernel (0 = library default)")
     ap.add_argument("--variant", type=int, default=0, help="MIXED pair-math variant")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time direct launches instead of one graph launch")
     ap.add_argument("--no-vdep-check", action="store_true")
     ap.add_argument("--particles", type=int, default=100_000, help="P3M workload: particles in the sample")
     ap.add_argument("--p3m-mesh", type=int, nargs=2, default=None, metavar=("M", "NZ"),
@@ -134,12 +135,38 @@ def cpu_baseline(name, params, counts, seconds, steps_max=50):
 
 
 def rank_workload(name, rank, world, samples=None):
-    """(params, counts) of one rank: weak scaling gives every rank a full batch of its own samples."""
+    """(params, counts, ranges) of one rank.
+
+    Under N ranks the study holds N times the workload's samples (drawn by the same seeded
+    recipe, so its first samples are the single-GPU workload), partitioned into contiguous
+    ranges balanced by sum N_s^2: each rank steps about one workload's worth (weak scaling).
+    """
+    from paper_2205_04979_gb300 import shard
     w = workloads.WORKLOADS[name]
     params, counts = workloads.workload_inputs(name, samples)
-    if world > 1 and w["samples"] > 1:
-        params = workloads.sample_params(len(counts), w["param_seed"] + 7919 * rank)
-    return params, counts
+    if world == 1 or w["samples"] == 1:
+        return params, counts, [(0, len(counts))]
+    S = len(counts) * world
+    params = workloads.sample_params(S, w["param_seed"])
+    counts = workloads.sample_counts(S, w["count"][0], w["count"][1], w["param_seed"])
+    ranges = shard.partition(counts, world)
+    lo, hi = ranges[rank]
+    return params[lo:hi], counts[lo:hi], ranges
+
+
+def study_vdep(pdq, tally, ranges, rank, dt, r_plus, stream):
+    """V_dep+ per class over the whole study: the ranks' tallies gathered in sample order, then
+    pdq_deposition_tally once on the full [S][C] table (MC mean and SE over all samples)."""
+    import torch
+    from paper_2205_04979_gb300 import shard
+    nd = shard.gather_rows(tally.n_dep, ranges, rank)
+    na = shard.gather_rows(tally.n_alive, ranges, rank)
+    full = pdq.Tally(nd.shape[0], nd.shape[1])
+    full.n_dep.copy_(nd)
+    full.n_alive.copy_(na)
+    vdep, mean, se = pdq.deposition_tally(full, dt, r_plus, stream=stream)
+    return {"samples": int(nd.shape[0]), "ranges": [list(r) for r in ranges],
+            "deposits": int(nd.sum().item()), "vdep_mean": mean.cpu().tolist(), "vdep_se": se.cpu().tolist()}
 
 
 def reduce_over_ranks(ms, psteps, world, device):
@@ -296,7 +323,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     w = workloads.WORKLOADS[args.workload]
-    params, counts = rank_workload(args.workload, rank, world, args.samples)
+    params, counts, ranges = rank_workload(args.workload, rank, world, args.samples)
     prec = pdq.MIXED if w["precision"] == "mixed" else pdq.FP64
     phys = pdq.phys_default()
     if args.contact:
@@ -327,14 +354,23 @@ def run_ours(args):
             uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
         except Exception:
             pass
+        # the K timed steps run as one CUDA-graph launch: captured and instantiated here (use_graph
+        # = 2 runs nothing), replayed in the timed region
+        gcfg = pdq.StepCfg.from_buffer_copy(cfg)
+        if not args.no_graph:
+            gcfg.use_graph = 2
+            pdq.step_particles(field, phys, state, prm, gcfg, args.steps, tally, ws, stream)
+            gcfg.use_graph = 1
+            stream.synchronize()
         clk = ClockSampler(uuid)
         clk.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        pdq.step_particles(field, phys, state, prm, cfg, args.steps, tally, ws, stream)
+        pdq.step_particles(field, phys, state, prm, gcfg, args.steps, tally, ws, stream)
         e1.record(stream)
         e1.synchronize()
         clocks = clk.stop()
+        pdq.release_graphs()
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -392,6 +428,10 @@ def run_ours(args):
                     "unit": "particle-steps/s", "steps": w1["steps"], "block": c1.block}
 
     ms_max, psteps_all = reduce_over_ranks(ms, psteps, world, "cuda")
+    study = None
+    if world > 1:
+        with torch.cuda.stream(stream):
+            study = study_vdep(pdq, tally, ranges, rank, w["dt"], desc.r_plus, stream)
     if rank != 0:
         return
     newton = cfg.variant == 3 and (not args.contact or prec == pdq.MIXED)
@@ -409,7 +449,10 @@ def run_ours(args):
         "config": {"workload": workload_label(args.workload, counts, args.contact),
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (
                        sum(t.numel() * t.element_size() for t in state.current() if t is not None) / 1e9),
-                   "parallelism": "samples sharded by rank" if world > 1 else "1 GPU",
+                   "parallelism": ("one study of %d samples in contiguous ranges balanced by sum N_s^2, one "
+                                   "per rank; tallies gathered at the end" % sum(h - l for l, h in ranges))
+                   if world > 1 else "1 GPU",
+                   "launch": "direct" if args.no_graph else "one CUDA-graph launch of the timed steps",
                    "tile": {"block": cfg.block,
                             "i_per_thread": (8 if (cfg.variant == 2 and not args.contact) or newton else 4)
                             if prec == pdq.MIXED else (2 if newton else 1),
@@ -437,6 +480,8 @@ def run_ours(args):
         "e2e": e2e,
         "plain_fp64": fp64,
     }
+    if study is not None:
+        out["study"] = study
     if not args.no_vdep_check and rank == 0 and args.workload == "batched_mixed":
         out["vdep_check"] = vdep_check(pdq, stream, cfg.block, cfg.variant)
     if not args.no_cpu_baseline:

@@ -207,7 +207,10 @@ typedef struct pdq_step_cfg {
                           /* (and 32 for PDQ_FP64)                                           */
     int32_t use_graph;    /* 1: capture the call as a CUDA graph (first call with a given      */
                           /*    argument set) and replay it afterwards; needs a created        */
-                          /*    (non-default) stream; see pdq_release_graphs                   */
+                          /*    (non-default) stream; see pdq_release_graphs.                  */
+                          /* 2: capture and instantiate that graph without running it: the    */
+                          /*    state, tallies and host fields are left as they were, and a    */
+                          /*    later call with use_graph = 1 and the same arguments replays it */
     int32_t variant;      /* MIXED pair math: 0 packed f32x2 (4 particles per thread),      */
                           /* 1 packed with scalar sums, 2 packed with 8 particles per thread, */
                           /* 3 Newton pairs: each pair evaluated once for both particles     */

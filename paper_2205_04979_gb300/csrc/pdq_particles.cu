@@ -1742,7 +1742,8 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
     int rc = validate_state(st);
     if (rc) return rc;
     if (!(cfg->dt > 0) || (cfg->mode != PDQ_STICK && cfg->mode != PDQ_REBOUND) ||
-        (cfg->forces & ~(PDQ_F_ALL | PDQ_F_CONTACT)) || cfg->compact_every < 0 || cfg->variant < 0 || cfg->variant > 3)
+        (cfg->forces & ~(PDQ_F_ALL | PDQ_F_CONTACT)) || cfg->compact_every < 0 || cfg->variant < 0 || cfg->variant > 3 ||
+        cfg->use_graph < 0 || cfg->use_graph > 2)
         return PDQ_ERR_INVALID_ARG;
     const bool contact = (cfg->forces & PDQ_F_CONTACT) != 0;
     if (contact && (!(phys->restitution > 0.0 && phys->restitution <= 1.0) || !(phys->tau_col_steps > 0.0)))
@@ -1842,12 +1843,18 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
         return PDQ_OK;
     }
     // Graph mode: the whole call (binning, work lists, n_steps step launches, compactions) is
-    // captured once per distinct argument set and replayed afterwards.
-    const std::string key = graph_key(field, phys, st, params, cfg, n_steps, tally, workspace, workspace_bytes, s);
+    // captured once per distinct argument set and replayed afterwards.  use_graph = 2 only
+    // prepares: it captures and instantiates the graph (if not cached) and leaves the state as
+    // it was, so that a later use_graph = 1 call with the same arguments is a replay.
+    const bool prepare_only = cfg->use_graph == 2;
+    pdq_step_cfg kcfg = *cfg;
+    kcfg.use_graph = 1;                     // both modes share one cache entry
+    const std::string key = graph_key(field, phys, st, params, &kcfg, n_steps, tally, workspace, workspace_bytes, s);
     {
         std::lock_guard<std::mutex> lock(g_graph_mu);
         auto it = g_graphs.find(key);
         if (it != g_graphs.end()) {
+            if (prepare_only) return PDQ_OK;
             PDQ_CUDA(cudaGraphLaunch(it->second.exec, s));
             st->cur = it->second.cur_after;
             st->step += n_steps;
@@ -1873,6 +1880,14 @@ int step_impl(const pdq_field* field, const pdq_phys* phys, pdq_state* st, const
         st->cur = cur0;
         st->step = step0;
         return cuda_status(e);
+    }
+    if (prepare_only) {
+        const int cur_after = st->cur;
+        st->cur = cur0;
+        st->step = step0;
+        std::lock_guard<std::mutex> lock(g_graph_mu);
+        g_graphs[key] = GraphEntry{exec, cur_after};
+        return PDQ_OK;
     }
     e = cudaGraphLaunch(exec, s);
     if (e != cudaSuccess) {

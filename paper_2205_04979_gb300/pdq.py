@@ -305,7 +305,8 @@ def step_cfg(dt, forces=F_ALL, mode=STICK, gravity=(0.0, 0.0, 1.0), window_start
     for k in range(3):
         c.gravity[k] = gravity[k]
     c.mode, c.forces, c.window_start = mode, forces, window_start
-    c.compact_every, c.block, c.use_graph, c.variant = compact_every, block, int(bool(use_graph)), variant
+    # use_graph: False/0 direct, True/1 captured graph (replayed on later calls), 2 capture only
+    c.compact_every, c.block, c.use_graph, c.variant = compact_every, block, int(use_graph), variant
     return c
 
 

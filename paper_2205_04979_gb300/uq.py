@@ -29,20 +29,26 @@ def pick_freeze(x, xp):
 
 def sobol_deposition(m, particles, steps, st_plus=(0.1, 1.0, 10.0), ranges=((0.0, 0.1), (0.0, 1.0), (0.0, 1.0)),
                      dt=0.05, t_window=10.0, mode=pdq.STICK, grid=(64, 32, 64), n_modes=64, seed=0, n_boot=200,
-                     precision=pdq.MIXED, qoi="vdep", stream=None):
+                     precision=pdq.MIXED, qoi="vdep", stream=None, rank=0, world=1):
     """Main and total Sobol' indices of V_dep+ (qoi="vdep") or of the capture efficiency
     (qoi="ce", Sec. 4.3; use mode=pdq.REBOUND) per class from m pick-freeze groups.
 
     Returns a dict with s_main / s_total [d, C], their bootstrap intervals, mean and variance of
     V_dep+ [C], the V_dep+ table [m, d+2, C] and the device time of the particle runs (ms).
+    With world > 1 (torch.distributed initialised, one GPU per rank) the groups are split into
+    contiguous ranges, each rank runs its own, and the V_dep+ tables are gathered so that every
+    rank evaluates the estimators on all m groups.
     """
+    from . import shard
     rng = np.random.Generator(np.random.Philox(seed))
     lo = np.array([r[0] for r in ranges])
     hi = np.array([r[1] for r in ranges])
     d = len(ranges)
     x = lo + (hi - lo) * rng.random((m, d))
     xp = lo + (hi - lo) * rng.random((m, d))
-    inputs = pick_freeze(x, xp).reshape(-1, d)              # [(d+2) m, d], group-major
+    granges = shard.partition([particles] * m, world)         # equal groups: equal split
+    g0, g1 = granges[rank]
+    inputs = pick_freeze(x[g0:g1], xp[g0:g1]).reshape(-1, d)  # [(d+2) (g1-g0), d], group-major
     S = inputs.shape[0]
     stream = stream or torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -64,7 +70,9 @@ def sobol_deposition(m, particles, steps, st_plus=(0.1, 1.0, 10.0), ranges=((0.0
         if qoi == "ce":
             vdep = pdq.capture_efficiency(field, phys, vdep, stream)
         e1.synchronize()
-        y = vdep.reshape(m, d + 2, len(st_plus)).contiguous()
+        y = vdep.reshape(g1 - g0, d + 2, len(st_plus)).contiguous()
+        if world > 1:
+            y = shard.gather_rows(y, granges, rank)
         out = pdq.mfmc_sobol([y], [m], [1.0], n_boot=n_boot, seed=seed + 2, stream=stream)
     out["vdep"] = y.cpu().numpy()
     out["ms"] = e0.elapsed_time(e1)

@@ -116,3 +116,34 @@ def test_autotune_mixed_binned(pdq):
                 assert np.all(np.abs(pa[k] - xb[g]) < 1e-3)
                 n_cmp += 1
     assert n_cmp > 0.99 * sum(counts) * 0.9
+
+
+def test_graph_prepare_then_replay_matches_direct_run(pdq):
+    # use_graph = 2 captures and instantiates the call's graph without running it; the state,
+    # tallies and host fields stay as they were, and the next use_graph = 1 call replays it
+    counts = [700, 333]
+    field, phys, a, prm = _setup(pdq, 0, counts)
+    stream = torch.cuda.Stream()
+    cfg = pdq.step_cfg(0.1, window_start=2, block=64, use_graph=2)
+    ta = pdq.Tally(2, 3)
+    wa = pdq.workspace(a, cfg)
+    with torch.cuda.stream(stream):
+        pdq.step_particles(field, phys, a, prm, cfg, 3, ta, wa, stream)      # capture only
+    stream.synchronize()
+    before = _by_id(a)
+    assert a.step_index == 0 and int(a.ctl[0]) == 0 and int(ta.n_alive.sum()) == 0
+    _, _, b, _ = _setup(pdq, 0, counts)
+    assert all(np.array_equal(x, y) for x, y in zip(before, _by_id(b)))
+    cfg.use_graph = 1
+    with torch.cuda.stream(stream):
+        pdq.step_particles(field, phys, a, prm, cfg, 3, ta, wa, stream)      # replays the prepared graph
+        pdq.step_particles(field, phys, a, prm, cfg, 3, ta, wa, stream)      # another phase: captured now
+    stream.synchronize()
+    tb = pdq.Tally(2, 3)
+    cfg_b = pdq.step_cfg(0.1, window_start=2, block=64)
+    pdq.step_particles(field, phys, b, prm, cfg_b, 6, tb, pdq.workspace(b, cfg_b))
+    assert a.step_index == b.step_index == 6 and int(a.ctl[0]) == 6
+    for x, y in zip(_by_id(a), _by_id(b)):
+        assert np.array_equal(x, y)
+    assert torch.equal(ta.n_dep, tb.n_dep) and torch.equal(ta.n_alive, tb.n_alive)
+    pdq.release_graphs()
