@@ -177,6 +177,15 @@ typedef struct pdq_sample_params {
 int pdq_seed_particles(const pdq_field* field, const pdq_phys* phys, double charge_sigma, uint64_t seed,
                        const pdq_sample_params* params, pdq_state* state, pdq_stream_t stream);
 
+/* pdq_seed_particles with a random stream per sample: sample s draws with
+ * counter word 3 = s + 1, i.e. counters (j, 0, 0, s+1), (j, 1, 0, s+1) and
+ * (j, 2, 0, s+1), so its particles are independent of the other samples'
+ * (the common-random-numbers default uses word 3 = 0).  For studies that
+ * need many distinct trajectories, such as validating V_dep+ statistics,
+ * rather than the paired comparisons common random numbers serve.        */
+int pdq_seed_particles_independent(const pdq_field* field, const pdq_phys* phys, double charge_sigma, uint64_t seed,
+                                   const pdq_sample_params* params, pdq_state* state, pdq_stream_t stream);
+
 /* ------------------------------------------------------------------ step */
 enum { PDQ_STICK = 0, PDQ_REBOUND = 1 };
 /* PDQ_F_ALL: the forces of the batched model (drag, gravity, Coulomb, image

@@ -81,7 +81,7 @@ def lib():
             "orc_field_grid": (None, [Fp, _D, _D]),
             "orc_interp": (None, [Fp, _D, C.c_int, _D, _D]),
             "orc_seed": (C.c_int, [P, Fp, C.c_int, _D, C.c_double, C.c_uint64, C.c_int, _I64, _D,
-                                   _D, _D, _D, _D, _D, _D, _D, _I32, _I32, _I32]),
+                                   _D, _D, _D, _D, _D, _D, _D, _I32, _I32, _I32, C.c_int]),
             "orc_run": (C.c_int, [P, Fp, _D, Cp, C.c_int, _D, C.c_int, _I64, _D, C.c_int64, C.c_int64,
                                   _D, _D, _D, _D, _D, _D, _D, _I32, _I32, _I64, _I64]),
             "orc_vdep": (None, [C.c_int, _I64, _I64, C.c_double, C.c_double, _D]),
@@ -190,8 +190,9 @@ class State:
         return s
 
 
-def seed(f, st_plus, counts, params, seed_value, charge_sigma=0.0, p=None):
-    """Initial state of S samples with counts[s] particles; params [S,3] = (xi, zeta, theta)."""
+def seed(f, st_plus, counts, params, seed_value, charge_sigma=0.0, p=None, independent=False):
+    """Initial state of S samples with counts[s] particles; params [S,3] = (xi, zeta, theta).
+    independent: a Philox stream per sample (counter word 3 = s + 1) instead of common random numbers."""
     p = p or phys()
     counts = np.asarray(counts, np.int64)
     offset = np.zeros(len(counts) + 1, np.int64)
@@ -200,7 +201,8 @@ def seed(f, st_plus, counts, params, seed_value, charge_sigma=0.0, p=None):
     prm = np.ascontiguousarray(params, np.float64).reshape(-1, 3)
     stp = np.ascontiguousarray(st_plus, np.float64)
     rc = lib().orc_seed(C.byref(p), C.byref(f), len(stp), stp, charge_sigma, seed_value, len(counts),
-                        offset, prm, st.x, st.y, st.z, st.vx, st.vy, st.vz, st.q, st.alive, st.cls, st.id)
+                        offset, prm, st.x, st.y, st.z, st.vx, st.vy, st.vz, st.q, st.alive, st.cls, st.id,
+                        int(independent))
     assert rc == 0
     return st, offset
 

@@ -390,34 +390,36 @@ extern "C" void orc_interp(const OrcField* f, const double* grid, int n, const d
 
 // ---------------------------------------------------------------------------
 // Seeding (Sec. 2.1: particles randomly distributed in the pipe, q_p = xi
-// q_max).  Particle j of every sample uses Philox counter (j, 0, 0, 0) (and
-// (j, 1, 0, 0) for the charge factor), so all samples share their first
-// particles (common random numbers).  Class = j mod C.
+// q_max).  Particle j of every sample uses Philox counter (j, 0, 0, w3) (and
+// (j, 1, 0, w3) for the charge factor, (j, 2, 0, w3) for its sign), with
+// w3 = 0, so all samples share their first particles (common random numbers),
+// or, when `independent`, w3 = s + 1: a stream per sample.  Class = j mod C.
 // ---------------------------------------------------------------------------
 extern "C" int orc_seed(const OrcPhys* p, const OrcField* f, int n_classes, const double* st_plus,
                         double charge_sigma, uint64_t seed, int n_samples, const int64_t* offset,
                         const double* params /*[S][3]: xi, zeta, theta*/,
                         double* x, double* y, double* z, double* vx, double* vy, double* vz,
-                        double* q, int32_t* alive, int32_t* cls, int32_t* id) {
+                        double* q, int32_t* alive, int32_t* cls, int32_t* id, int independent) {
     std::vector<ClassProps> cp(n_classes);
     for (int c = 0; c < n_classes; ++c) cp[c] = class_props(*p, st_plus[c]);
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (int s = 0; s < n_samples; ++s) {
         double xi = params[3 * s];
+        const uint32_t w3 = independent ? (uint32_t)(s + 1) : 0u;
         for (int64_t g = offset[s]; g < offset[s + 1]; ++g) {
             uint32_t j = (uint32_t)(g - offset[s]);
-            uint32_t c0[4] = {j, 0u, 0u, 0u}, a[4];
+            uint32_t c0[4] = {j, 0u, 0u, w3}, a[4];
             philox4x32_10(c0, key, a);
             int c = (int)(j % (uint32_t)n_classes);
             double lam = 1.0;
             if (p->neg_charge_frac > 0) {
                 // sign of the charge: negative with probability neg_charge_frac (counter word 2)
-                uint32_t c2[4] = {j, 2u, 0u, 0u}, b[4];
+                uint32_t c2[4] = {j, 2u, 0u, w3}, b[4];
                 philox4x32_10(c2, key, b);
                 if (u01(b[0]) < p->neg_charge_frac) lam = -1.0;
             }
             if (charge_sigma > 0) {
-                uint32_t c1[4] = {j, 1u, 0u, 0u}, b[4];
+                uint32_t c1[4] = {j, 1u, 0u, w3}, b[4];
                 philox4x32_10(c1, key, b);
                 double nrm = std::sqrt(-2.0 * std::log(u01(b[0]))) * std::cos(2.0 * M_PI * u01(b[1]));
                 lam *= std::exp(charge_sigma * nrm);

@@ -150,20 +150,22 @@ __device__ __forceinline__ void coulomb_pair(double xi, double yi, double zi, co
 
 
 // Initial state of local particle j (Sec. 2.1: uniform in the pipe, at rest):
-// Philox4x32-10 counter (j, 0, 0, 0) gives (r, theta, z) = ((R - d/2) sqrt(u0),
-// 2 pi u1, L u2); counter (j, 1, 0, 0) the lognormal charge factor
-// exp(sigma sqrt(-2 ln u0) cos(2 pi u1)).  qhat = charge per unit xi (units of q_unit).
+// Philox4x32-10 counter (j, 0, 0, w3) gives (r, theta, z) = ((R - d/2) sqrt(u0),
+// 2 pi u1, L u2); counter (j, 1, 0, w3) the lognormal charge factor
+// exp(sigma sqrt(-2 ln u0) cos(2 pi u1)); counter (j, 2, 0, w3) the sign when neg_frac > 0.
+// w3 = 0: every sample draws the same particles (common random numbers); w3 = s + 1 gives
+// sample s a stream of its own.  qhat = charge per unit xi (units of q_unit).
 __device__ __forceinline__ void seed_particle(uint2 key, uint32_t j, double sigma, double neg_frac, double R, double L,
                                               double half_d, double qfac, double& x, double& y, double& z,
-                                              double& qhat) {
-    const uint4 a = philox4x32_10(make_uint4(j, 0u, 0u, 0u), key);
+                                              double& qhat, uint32_t w3 = 0u) {
+    const uint4 a = philox4x32_10(make_uint4(j, 0u, 0u, w3), key);
     double lam = 1.0;
     if (neg_frac > 0.0) {      // negative charge with probability neg_frac (counter word 2)
-        const uint4 b = philox4x32_10(make_uint4(j, 2u, 0u, 0u), key);
+        const uint4 b = philox4x32_10(make_uint4(j, 2u, 0u, w3), key);
         if (unit_open(b.x) < neg_frac) lam = -1.0;
     }
     if (sigma > 0.0) {
-        const uint4 b = philox4x32_10(make_uint4(j, 1u, 0u, 0u), key);
+        const uint4 b = philox4x32_10(make_uint4(j, 1u, 0u, w3), key);
         lam *= exp(sigma * sqrt(-2.0 * log(unit_open(b.x))) * cos(2.0 * kPi * unit_open(b.y)));
     }
     const double rr = (R - half_d) * sqrt(unit_open(a.x));

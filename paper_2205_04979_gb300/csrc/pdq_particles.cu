@@ -105,6 +105,7 @@ struct SeedArgs {
     const pdq_sample_params* params;
     void* pos; void* vel; double2* xy; int2* tag;
     int64_t capacity; int32_t S, C; double sigma, neg_frac; uint2 key;
+    int32_t independent;   // 1: sample s draws with Philox counter word 3 = s + 1
     double R, L; double half_d[PDQ_MAX_CLASSES]; double qfac[PDQ_MAX_CLASSES];
 };
 
@@ -123,7 +124,8 @@ __global__ void k_seed(const SeedArgs A) {
     const uint32_t j = (uint32_t)(g - A.offset[s]);
     const int c = (int)(j % (uint32_t)A.C);
     double x, y, z, qhat;
-    seed_particle(A.key, j, A.sigma, A.neg_frac, A.R, A.L, A.half_d[c], A.qfac[c], x, y, z, qhat);
+    seed_particle(A.key, j, A.sigma, A.neg_frac, A.R, A.L, A.half_d[c], A.qfac[c], x, y, z, qhat,
+                  A.independent ? (uint32_t)(s + 1) : 0u);
     const double q = A.params[s].xi * qhat;
     if (P == PDQ_FP64) {
         ((double4_32a*)A.pos)[g] = make_double4_32a(x, y, z, q);
@@ -1683,8 +1685,8 @@ static std::string graph_key(const pdq_field* field, const pdq_phys* phys, const
 
 using namespace pdq;
 
-extern "C" int pdq_seed_particles(const pdq_field* field, const pdq_phys* phys, double charge_sigma, uint64_t seed,
-                                  const pdq_sample_params* params, pdq_state* st, pdq_stream_t stream) {
+static int seed_impl(const pdq_field* field, const pdq_phys* phys, double charge_sigma, uint64_t seed,
+                     const pdq_sample_params* params, pdq_state* st, pdq_stream_t stream, int independent) {
     if (!field || !phys || !params || !(charge_sigma >= 0)) return PDQ_ERR_INVALID_ARG;
     int rc = validate_state(st);
     if (rc) return rc;
@@ -1698,6 +1700,7 @@ extern "C" int pdq_seed_particles(const pdq_field* field, const pdq_phys* phys, 
     A.capacity = st->capacity; A.S = st->n_samples; A.C = st->n_classes; A.sigma = charge_sigma;
     A.neg_frac = phys->neg_charge_frac;
     A.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    A.independent = independent;
     A.R = K.R; A.L = K.L;
     for (int c = 0; c < st->n_classes; ++c) { A.half_d[c] = K.cls[c].half_d; A.qfac[c] = K.cls[c].qfac; }
     const int64_t n = st->capacity > st->n_samples ? st->capacity : st->n_samples;
@@ -1709,6 +1712,18 @@ extern "C" int pdq_seed_particles(const pdq_field* field, const pdq_phys* phys, 
     st->cur = 0;
     st->step = 0;
     return PDQ_OK;
+}
+
+extern "C" int pdq_seed_particles(const pdq_field* field, const pdq_phys* phys, double charge_sigma, uint64_t seed,
+                                  const pdq_sample_params* params, pdq_state* st, pdq_stream_t stream) {
+    return seed_impl(field, phys, charge_sigma, seed, params, st, stream, 0);
+}
+
+extern "C" int pdq_seed_particles_independent(const pdq_field* field, const pdq_phys* phys, double charge_sigma,
+                                              uint64_t seed, const pdq_sample_params* params, pdq_state* st,
+                                              pdq_stream_t stream) {
+    if (st && st->n_samples > 0x7ffffffe) return PDQ_ERR_INVALID_ARG;
+    return seed_impl(field, phys, charge_sigma, seed, params, st, stream, 1);
 }
 
 extern "C" int pdq_step_workspace_size(const pdq_state* st, const pdq_step_cfg* cfg, size_t* bytes) {

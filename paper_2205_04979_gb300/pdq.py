@@ -89,6 +89,8 @@ def lib():
             "pdq_field_copy": (C.c_int, [P, P, P, P, P]),
             "pdq_seed_particles": (C.c_int, [P, C.POINTER(Phys), C.c_double, C.c_uint64, P,
                                              C.POINTER(StateStruct), P]),
+            "pdq_seed_particles_independent": (C.c_int, [P, C.POINTER(Phys), C.c_double, C.c_uint64, P,
+                                                         C.POINTER(StateStruct), P]),
             "pdq_step_workspace_size": (C.c_int, [C.POINTER(StateStruct), C.POINTER(StepCfg),
                                                   C.POINTER(C.c_size_t)]),
             "pdq_step_particles": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P, C.POINTER(StepCfg),
@@ -321,6 +323,11 @@ def params_tensor(params, device="cuda"):
 def seed_particles(field, phys, state, params_dev, seed, charge_sigma=0.0, stream=None):
     _check(lib().pdq_seed_particles(field.handle, C.byref(phys), charge_sigma, seed, _ptr(params_dev),
                                     C.byref(state.st), _stream(stream)), "seed_particles")
+
+
+def seed_particles_independent(field, phys, state, params_dev, seed, charge_sigma=0.0, stream=None):
+    _check(lib().pdq_seed_particles_independent(field.handle, C.byref(phys), charge_sigma, seed, _ptr(params_dev),
+                                                C.byref(state.st), _stream(stream)), "seed_particles_independent")
 
 
 def workspace(state, cfg):

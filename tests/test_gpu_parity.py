@@ -101,6 +101,32 @@ def test_seed_parity(pdq, fields, precision):
     assert np.all(v[:, :3] == 0) and np.all(v[:, 3] == 1)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_seed_independent_parity(pdq, fields, precision):
+    # a Philox stream per sample (counter word 3 = s + 1), with lognormal and signed charges so
+    # that all three counters are drawn; ids, classes bit-exact, positions as the shared draw
+    f, of, _, _ = fields
+    st_plus = [0.1, 1.0, 10.0]
+    counts = [1000, 333, 1, 0]
+    params = np.array([[0.05, 0.5, 0.5], [0.1, 0.2, 0.3], [0.02, 0.9, 0.1], [0.03, 0.1, 0.1]])
+    phys = pdq.phys_default()
+    phys.neg_charge_frac = 0.3
+    ophys = oracle.phys()
+    ophys.neg_charge_frac = 0.3
+    st = pdq.State(precision, counts, st_plus)
+    pdq.seed_particles_independent(f, phys, st, pdq.params_tensor(params), 7, charge_sigma=0.5)
+    ost, off = oracle.seed(of, st_plus, counts, params, 7, charge_sigma=0.5, p=ophys, independent=True)
+    x, v, q, tag = _gpu_arrays(st)
+    ref = np.stack([ost.x, ost.y, ost.z], 1)
+    assert np.array_equal(tag[:, 0], ost.id) and np.array_equal(tag[:, 1], ost.cls)
+    if precision == 0:
+        assert np.max(np.abs(x - ref)) < 1e-12 and np.allclose(q, ost.q, rtol=1e-13)
+    else:
+        assert np.max(np.abs(x[:, :2] - ref[:, :2])) < 1e-12
+        assert np.max(np.abs(x[:, 2] - ref[:, 2])) < 1e-4 and np.allclose(q, ost.q, rtol=1e-6)
+    assert np.any(q < 0) and not np.array_equal(x[1000:1333], x[:333])     # signed; not shared
+
+
 def _run_both(pdq, fields, precision, counts, st_plus, params, n_steps, cfg_kw, sigma=0.0, block=0):
     f, of, grid, _ = fields
     phys, st, prm, ost, off = _setup(pdq, fields, precision, counts, st_plus, params, sigma)

@@ -1,10 +1,13 @@
 """V_dep+ over a 400-step run: GPU FP64 and batched MIXED against the FP64 oracle.
 
-Deposition decisions at the wall are discontinuous, so over a long run a
-rounding difference can move a single deposition event; the bar is therefore
-the tallies within 2 events for FP64 (the runs share the oracle's arithmetic up
-to rounding) and, for MIXED, the Monte Carlo mean of V_dep+ per class within one
-Monte Carlo standard error of the oracle's.
+Every sample draws its own particles (a Philox stream per sample), identical on
+the three sides.  Deposition decisions at the wall are discontinuous, so over a
+long run a rounding difference can move a single deposition event; the FP64 bar
+is therefore the tallies within 2 events (the runs share the oracle's
+arithmetic up to rounding).  For MIXED the bar is the metric's validity
+condition: the Monte Carlo mean of V_dep+ per class within 1e-3 relative of the
+oracle's and within one Monte Carlo standard error (a class where neither run
+deposits meets both with equality).
 """
 import numpy as np
 import pytest
@@ -35,7 +38,7 @@ def runs():
     for name, prec, ce in (("fp64", pdq.FP64, 0), ("mixed", pdq.MIXED, 100)):
         st = pdq.State(prec, [N] * S, ST)
         prm = pdq.params_tensor(params)
-        pdq.seed_particles(field, phys, st, prm, 1)
+        pdq.seed_particles_independent(field, phys, st, prm, 1)
         cfg = pdq.step_cfg(DT, window_start=WIN, compact_every=ce)
         tally = pdq.Tally(S, len(ST))
         pdq.step_particles(field, phys, st, prm, cfg, STEPS, tally, pdq.workspace(st, cfg))
@@ -43,7 +46,7 @@ def runs():
         out[name] = (tally.n_dep.cpu().numpy(), tally.n_alive.cpu().numpy())
     of = oracle.field_desc(**grid_shape)
     grid = oracle.field_grid(of, oracle.field_modes(of, 0))
-    ost, off = oracle.seed(of, ST, [N] * S, params, 1)
+    ost, off = oracle.seed(of, ST, [N] * S, params, 1, independent=True)
     out["oracle"] = oracle.run(of, grid, oracle.cfg(DT, window_start=WIN), ST, off, params, ost, STEPS)
     return out
 
@@ -61,7 +64,7 @@ def test_mixed_vdep_within_mc_error(runs):
     v_o = oracle.vdep(*runs["oracle"], DT)
     mean_m, mean_o = v_m.mean(0), v_o.mean(0)
     se = v_o.std(0, ddof=1) / np.sqrt(S)
+    assert runs["oracle"][0].sum() > 0
     for c in range(len(ST)):
-        if mean_o[c] == 0 and mean_m[c] == 0:
-            continue
-        assert abs(mean_m[c] - mean_o[c]) <= max(se[c], 1e-3 * mean_o[c]), (c, mean_m, mean_o, se)
+        d = abs(mean_m[c] - mean_o[c])
+        assert d <= 1e-3 * mean_o[c] and d <= se[c], (c, mean_m, mean_o, se)

@@ -194,3 +194,26 @@ def test_seed_lognormal_charge(orc):
     ln = np.log(lam)
     assert abs(np.mean(ln)) < 4 * 0.5 / np.sqrt(len(ln))          # median 1
     assert abs(np.std(ln) - 0.5) < 0.02
+
+
+def test_seed_independent_streams(orc):
+    # a stream per sample: the samples no longer share particles, each is still uniform in the
+    # pipe, and the draw of sample s equals the common-random-numbers draw only when s + 1 = 0
+    f = orc.field_desc()
+    st_plus = [0.1, 1.0, 10.0]
+    params = np.array([[0.05, 0.5, 0.5], [0.1, 0.2, 0.3], [0.07, 0.4, 0.6]])
+    st, off = orc.seed(f, st_plus, [4000, 4000, 4000], params, seed_value=1, independent=True)
+    crn, _ = orc.seed(f, st_plus, [4000, 4000, 4000], params, seed_value=1)
+    t = orc.class_table(st_plus)
+    for s in range(3):
+        sl = slice(off[s], off[s + 1])
+        assert np.array_equal(st.id[sl], np.arange(4000)) and np.array_equal(st.cls[sl], np.arange(4000) % 3)
+        r = np.hypot(st.x[sl], st.y[sl])
+        rmax = f.r_plus - 0.5 * t[st.cls[sl], 1]
+        se = np.sqrt(1 / 12 / 4000)
+        assert np.all(r < rmax) and abs(np.mean((r / rmax) ** 2) - 0.5) < 4 * se
+        assert abs(np.mean(st.z[sl] / f.l_plus) - 0.5) < 4 * se
+        # independent of the shared draw and of the other samples: correlations near 0
+        assert abs(np.corrcoef(st.z[sl], crn.z[sl])[0, 1]) < 4 / np.sqrt(4000)
+    assert abs(np.corrcoef(st.x[off[0]:off[1]], st.x[off[1]:off[2]])[0, 1]) < 4 / np.sqrt(4000)
+    assert not np.any(st.x[off[0]:off[1]] == st.x[off[1]:off[2]])
