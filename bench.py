@@ -589,6 +589,138 @@ def run_sobol(args):
     print(json.dumps(out), flush=True)
 
 
+def run_mfmc(args):
+    """Config 5 with the models this build has: MFMC (Sec. 3) against plain MC at equal GPU cost.
+
+    High fidelity: the batched particle model, 4,096 particles per sample, dt+ = 0.05, 600 steps.
+    Low fidelity: the same particles without the particle-particle Coulomb sum and with 2x dt
+    (300 steps to the same t+ = 30); the paper's 1-D Eulerian model needs closures it does not
+    print.  A pilot gives rho, sigma and the measured GPU time per sample w of each model;
+    pdq_mfmc_allocate gives m and alpha.  R replicate studies, each with fresh pick-freeze
+    groups, measure the variance of the MFMC and plain-MC estimates of the mean V_dep+ and of
+    the Sobol' indices at the same budget; the variance ratio of the mean is reported beside
+    gamma(rho, w).  Then one MFMC and one plain-MC Sobol' study at a larger budget, and the
+    MIXED-vs-FP64 comparison of the Sobol' indices on the same inputs.
+    """
+    import torch
+    from paper_2205_04979_gb300 import pdq, uq
+    torch.cuda.set_device(0)
+    st_plus = (0.1, 1.0, 10.0)
+    ranges = ((0.0, 0.1), (0.0, 1.0), (0.0, 1.0))
+    lo, hi = np.array([r[0] for r in ranges]), np.array([r[1] for r in ranges])
+    d, C = 3, len(st_plus)
+    hf = dict(particles=4096, steps=600, dt=0.05, forces=pdq.F_ALL)
+    lf = dict(particles=4096, steps=300, dt=0.10, forces=pdq.F_ALL & ~pdq.F_COULOMB)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        field = pdq.Field(pdq.field_desc(n_r=64, n_th=32, n_z=64), 0, stream)
+
+    def run(model, inputs, precision=pdq.MIXED, chunk=12000):
+        outs, ms = [], 0.0
+        for a in range(0, len(inputs), chunk):
+            y, t = uq.vdep_runs(inputs[a:a + chunk], model["particles"], model["steps"], st_plus=st_plus,
+                                dt=model["dt"], forces=model["forces"], precision=precision, stream=stream,
+                                field=field)
+            outs.append(y)
+            ms += t
+        return np.concatenate(outs, 0), ms
+
+    def draw(n, seed):
+        rng = np.random.Generator(np.random.Philox(seed))
+        x = lo + (hi - lo) * rng.random((n, d))
+        xp = lo + (hi - lo) * rng.random((n, d))
+        return uq.pick_freeze(x, xp)                        # [n, d+2, d]
+
+    run(hf, draw(4, 1).reshape(-1, d))                      # warm-up: builds, autotuner caches
+    run(lf, draw(4, 1).reshape(-1, d))
+    # pilot: rho, sigma per class and the GPU cost per sample of each model
+    npil = args.samples or 256
+    xpil = lo + (hi - lo) * np.random.Generator(np.random.Philox(11)).random((npil, d))
+    yh, th = run(hf, xpil)
+    yl, tl = run(lf, xpil)
+    w = np.array([th / npil, tl / npil])                    # ms per sample
+    rho = np.array([np.corrcoef(yh[:, c], yl[:, c])[0, 1] for c in range(C)])
+    sig = np.stack([yh.std(0, ddof=1), yl.std(0, ddof=1)], 1)
+    cq = int(np.argmax(yh.mean(0)))                         # allocate for the class with most deposition
+    p_eff = 24                                              # budget: 24 HF pick-freeze groups per study
+    wn = w / w[0]                                           # costs in units of one HF evaluation
+    try:
+        m, alpha, m_real, gamma = pdq.mfmc_allocate([1.0, rho[cq]], sig[cq], wn, p_eff)
+    except pdq.PdqError as e:                               # precondition violated: MFMC does not pay
+        print(json.dumps({"metric": "MFMC vs plain MC", "pilot": {"rho": _finite(rho.tolist()),
+                          "w_ms_per_sample": w.tolist()}, "allocation_error": str(e)}), flush=True)
+        return
+    m1, m2 = max(2, int(m[0])), int(m[1])
+    gam = [float((np.sqrt(1 - r ** 2) + r * np.sqrt(w[1] / w[0])) ** 2) for r in rho]
+    # replicates: HF on the first p_eff groups (MC uses them all, MFMC the first m1), LF on m2
+    R = 100
+    groups = [draw(max(p_eff, m2), 1000 + r) for r in range(R)]
+    y_hf, t_hf = run(hf, np.concatenate([g[:p_eff] for g in groups]).reshape(-1, d))
+    y_lf, t_lf = run(lf, np.concatenate([g[:m2] for g in groups]).reshape(-1, d))
+    y_hf = y_hf.reshape(R, p_eff, d + 2, C)
+    y_lf = y_lf.reshape(R, m2, d + 2, C)
+    est = {"mc": [], "mfmc": []}
+    for r in range(R):
+        a = torch.tensor(y_hf[r], device="cuda")
+        b = torch.tensor(y_lf[r], device="cuda")
+        est["mc"].append(pdq.mfmc_sobol([a], [p_eff], [1.0], stream=stream))
+        est["mfmc"].append(pdq.mfmc_sobol([a[:m1], b], [m1, m2], alpha, stream=stream))
+
+    def var_of(key, q):
+        return np.var(np.array([e[q] for e in est[key]]), axis=0, ddof=1)
+    def ratio(q):
+        a, b = var_of("mfmc", q), var_of("mc", q)
+        return np.where(b > 0, a / np.where(b > 0, b, 1.0), np.nan)
+    ratio_mean, ratio_sm, ratio_st = ratio("mean"), ratio("s_main"), ratio("s_total")
+    # one study at a larger budget, MFMC and plain MC, with bootstrap intervals
+    pb = 200
+    mb, ab, _, gb = pdq.mfmc_allocate([1.0, rho[cq]], sig[cq], wn, pb)
+    gbig = draw(max(pb, int(mb[1])), 7)
+    yhb, thb = run(hf, gbig[:pb].reshape(-1, d))
+    ylb, tlb = run(lf, gbig[:int(mb[1])].reshape(-1, d))
+    yhb = torch.tensor(yhb.reshape(pb, d + 2, C), device="cuda")
+    ylb = torch.tensor(ylb.reshape(-1, d + 2, C), device="cuda")
+    big_mc = pdq.mfmc_sobol([yhb], [pb], [1.0], n_boot=200, seed=3, stream=stream)
+    big_mf = pdq.mfmc_sobol([yhb[:int(mb[0])], ylb], [int(mb[0]), int(mb[1])], ab, n_boot=200, seed=3,
+                            stream=stream)
+    # MIXED vs FP64 Sobol' indices of the high-fidelity model on the same 64 groups
+    g64 = draw(64, 9).reshape(-1, d)
+    ym, tm = run(hf, g64, pdq.MIXED)
+    yf, tf = run(hf, g64, pdq.FP64)
+    sm = pdq.mfmc_sobol([torch.tensor(ym.reshape(64, d + 2, C), device="cuda")], [64], [1.0], n_boot=200, seed=5)
+    sf = pdq.mfmc_sobol([torch.tensor(yf.reshape(64, d + 2, C), device="cuda")], [64], [1.0], n_boot=200, seed=5)
+    half = 0.5 * (sf["s_main_ci"][..., 1] - sf["s_main_ci"][..., 0])
+    halft = 0.5 * (sf["s_total_ci"][..., 1] - sf["s_total_ci"][..., 0])
+    dm, dt_ = np.abs(sm["s_main"] - sf["s_main"]), np.abs(sm["s_total"] - sf["s_total"])
+
+    def fin(a):
+        return _finite(np.asarray(a).tolist())
+    out = {"metric": "MFMC vs plain MC at equal GPU cost: variance of the estimates over replicate studies",
+           "config": {"workload": "mfmc: HF = particle model 4,096 particles/sample, dt+ 0.05, 600 steps; LF = same "
+                                  "without the Coulomb pair sum, dt+ 0.1, 300 steps; classes %s; inputs xi [0,0.1], "
+                                  "zeta [0,1], theta [0,1]" % (list(st_plus),)},
+           "pilot": {"samples": npil, "rho": fin(rho), "sigma": fin(sig.T), "w_ms_per_sample": fin(w),
+                     "allocation_class": st_plus[cq], "m": [m1, m2], "alpha": fin(alpha),
+                     "gamma_predicted_per_class": fin(gam), "gamma_allocation": gamma},
+           "replicates": {"R": R, "budget_hf_groups": p_eff, "mc_groups": p_eff, "mfmc_groups": [m1, m2],
+                          "var_ratio_mean": fin(ratio_mean), "var_ratio_s_main": fin(ratio_sm),
+                          "var_ratio_s_total": fin(ratio_st),
+                          "gpu_ms": {"hf_all": t_hf, "lf_all": t_lf,
+                                     "mc_per_study": w[0] * p_eff * (d + 2),
+                                     "mfmc_per_study": (w[0] * m1 + w[1] * m2) * (d + 2)}},
+           "study": {"budget_hf_groups": pb, "mfmc_m": [int(mb[0]), int(mb[1])], "gamma": gb,
+                     "mc": {k: fin(v) for k, v in big_mc.items()}, "mfmc": {k: fin(v) for k, v in big_mf.items()}},
+           "mixed_vs_fp64_sobol": {"groups": 64, "s_main_mixed": fin(sm["s_main"]), "s_main_fp64": fin(sf["s_main"]),
+                                   "s_total_mixed": fin(sm["s_total"]), "s_total_fp64": fin(sf["s_total"]),
+                                   "abs_diff_main": fin(dm), "abs_diff_total": fin(dt_),
+                                   # a class without variance has no interval (NaN): equal values pass
+                                   "within_fp64_ci_halfwidth": bool(np.all((dm <= half + 1e-15) | (dm == 0)) and
+                                                                    np.all((dt_ <= halft + 1e-15) | (dt_ == 0))),
+                                   "vdep_max_abs_diff": float(np.max(np.abs(ym - yf))),
+                                   "gpu_ms": {"mixed": tm, "fp64": tf}}}
+    print(json.dumps(out), flush=True)
+
+
 def run_p3m(args):
     """Paper-scale single sample (FP64, 10 classes, lognormal charges) with P3M electrostatics,
     against the all-pairs FP64 step on the same state."""
@@ -695,6 +827,8 @@ def main():
         run_p3m(args)
     elif args.workload == "vdep_validation":
         run_vdep_validation(args)
+    elif args.workload == "mfmc":
+        run_mfmc(args)
     else:
         run_ours(args)
 

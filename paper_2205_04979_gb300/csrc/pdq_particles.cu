@@ -1484,8 +1484,10 @@ static int launch_newton64(const StepArgs& A, cudaStream_t s) {
     }
     const int64_t full = (int64_t)sm_count() * per_sm;
     PDQ_CUDA(cudaMemsetAsync(A.acc64, 0, 3 * sizeof(double) * (size_t)(A.cap > 0 ? A.cap : 1), s));
-    k_pairs_sym64<NT, 2><<<(unsigned)std::max<int64_t>(1, std::min(full, A.max_items > 0 ? A.max_items : full)), NT,
-                           0, s>>>(A);
+    if (A.K.forces & PDQ_F_COULOMB) {    // the sums enter the update only with the Coulomb force on
+        k_pairs_sym64<NT, 2><<<(unsigned)std::max<int64_t>(1, std::min(full, A.max_items > 0 ? A.max_items : full)),
+                               NT, 0, s>>>(A);
+    }
     StepArgs B = A;
     B.ext = A.acc64;
     return launch_step<PDQ_FP64, 2 * NT, 1, 5>(B, s);
@@ -1495,13 +1497,15 @@ static int launch_newton64(const StepArgs& A, cudaStream_t s) {
 template <int NT>
 static int launch_newton_contact(const StepArgs& A, cudaStream_t s) {
     PDQ_CUDA(cudaMemsetAsync(A.acc4, 0, sizeof(float4) * (size_t)(A.cap > 0 ? A.cap : 1), s));
-    k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, A.max_items), NT, 0, s>>>(A);
+    if (A.K.forces & PDQ_F_COULOMB)      // the sums enter the update only with the Coulomb force on
+        k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, A.max_items), NT, 0, s>>>(A);
     return launch_step<PDQ_MIXED, 2 * NT, 4, 6>(A, s);
 }
 template <int NT>
 static int launch_newton(const StepArgs& A, cudaStream_t s) {
     PDQ_CUDA(cudaMemsetAsync(A.acc4, 0, sizeof(float4) * (size_t)(A.cap > 0 ? A.cap : 1), s));
-    k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, A.max_items), NT, 0, s>>>(A);
+    if (A.K.forces & PDQ_F_COULOMB)      // the sums enter the update only with the Coulomb force on
+        k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, A.max_items), NT, 0, s>>>(A);
     return launch_step<PDQ_MIXED, 2 * NT, 4, 5>(A, s);
 }
 

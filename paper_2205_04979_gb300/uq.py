@@ -27,6 +27,38 @@ def pick_freeze(x, xp):
     return out
 
 
+def vdep_runs(inputs, particles, steps, st_plus=(0.1, 1.0, 10.0), dt=0.05, t_window=10.0, mode=pdq.STICK,
+              forces=pdq.F_ALL, grid=(64, 32, 64), n_modes=64, seed=0, precision=pdq.MIXED, stream=None,
+              field=None):
+    """V_dep+ [n, C] of n particle-model runs, one per row of inputs [n, 3] = (xi, zeta, theta),
+    all in one batched state (common random particle seeds), and the device time of the steps (ms).
+
+    One evaluation of the model f(x) of Sec. 3 per sample; `forces`, `dt` and `particles` define
+    the model (a cheaper setting serves as a low-fidelity model).
+    """
+    n = len(inputs)
+    stream = stream or torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        phys = pdq.phys_default()
+        if field is None:
+            field = pdq.Field(pdq.field_desc(n_r=grid[0], n_th=grid[1], n_z=grid[2], n_modes=n_modes), seed, stream)
+        state = pdq.State(precision, [particles] * n, list(st_plus))
+        params = pdq.params_tensor(np.asarray(inputs, np.float64))
+        pdq.seed_particles(field, phys, state, params, seed + 1, 0.0, stream)
+        w0 = int(np.ceil(t_window / dt - 1e-9))
+        cfg = pdq.step_cfg(dt, mode=mode, window_start=w0, compact_every=100, forces=forces)
+        pdq.autotune(field, phys, state, params, cfg, stream)
+        tally = pdq.Tally(n, len(st_plus))
+        ws = pdq.workspace(state, cfg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pdq.step_particles(field, phys, state, params, cfg, steps, tally, ws, stream)
+        e1.record(stream)
+        vdep, _, _ = pdq.deposition_tally(tally, dt, stream=stream)
+        e1.synchronize()
+    return vdep.cpu().numpy(), e0.elapsed_time(e1)
+
+
 def sobol_deposition(m, particles, steps, st_plus=(0.1, 1.0, 10.0), ranges=((0.0, 0.1), (0.0, 1.0), (0.0, 1.0)),
                      dt=0.05, t_window=10.0, mode=pdq.STICK, grid=(64, 32, 64), n_modes=64, seed=0, n_boot=200,
                      precision=pdq.MIXED, qoi="vdep", stream=None, rank=0, world=1):
