@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--vdep-classes", type=float, nargs="+", default=[0.1, 0.316, 1.0, 3.16, 10.0],
                     help="St+ classes of --workload vdep_validation")
     ap.add_argument("--vdep-steps", type=int, default=1200, help="steps of --workload vdep_validation")
+    ap.add_argument("--adjoint-config4", action="store_true",
+                    help="--workload adjoint as stated: 2,000 steps, checkpoints every 100, three widths")
     ap.add_argument("--no-vdep-check", action="store_true")
     ap.add_argument("--particles", type=int, default=100_000, help="P3M workload: particles in the sample")
     ap.add_argument("--p3m-mesh", type=int, nargs=2, default=None, metavar=("M", "NZ"),
@@ -517,10 +519,59 @@ def run_ours(args):
     print(json.dumps(out), flush=True)
 
 
+def run_adjoint_config4(args):
+    """The adjoint workload as stated: 256 samples x 16,384 particles, 2,000 steps, a checkpoint
+    every 100 steps, eps+ = 0.5, 0.1, 0.02: one forward + reverse sweep per width."""
+    import torch
+    import paper_2205_04979_gb300.pdq as pdq
+    w = workloads.WORKLOADS["adjoint"]
+    S, steps, K = w["samples"], w["steps"], w["checkpoint"]
+    params = workloads.sample_params(S, w["param_seed"])
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    phys = pdq.phys_default()
+    out = {"metric": "gradient particle-steps/s (smoothed V_dep, forward + reverse sweep)", "unit": "particle-steps/s",
+           "n_gpus": 1, "steps": steps, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "adjoint: %d samples x %d particles, classes %s, %d steps, checkpoint every %d steps"
+                                  % (S, w["count"], w["st_plus"], steps, K)}, "eps": {}}
+    with torch.cuda.stream(stream):
+        field = pdq.Field(pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2],
+                                         n_modes=w["n_modes"]), w["field_seed"], stream)
+        batch = pdq.Batch(pdq.MIXED, [w["count"]] * S, w["st_plus"])
+        cfg = pdq.step_cfg(w["dt"], window_start=workloads.window_start_step(w["t_window"], w["dt"]))
+        prm = pdq.params_tensor(params)
+        C = len(w["st_plus"])
+        gbar = torch.ones((1, S, C), dtype=torch.float64, device="cuda")   # d(sum_c J_c)/d(xi, zeta, theta)
+        ws = pdq.adjoint_workspace(batch.b, steps, K)
+        out["workspace_bytes"] = int(ws.numel())
+        pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, 4, 2, w["eps"][0], w["particle_seed"], gbar=gbar,
+                               stream=stream)             # warm-up
+        for eps in w["eps"]:
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            J, _ = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, steps, K, eps, w["particle_seed"], ws=ws,
+                                          stream=stream)     # forward sweep alone (checkpoints kept)
+            e1.record(stream)
+            pbar = pdq.adjoint_reverse(field, phys, batch.b, prm, cfg, steps, K, eps, gbar, ws, stream=stream)
+            e2.record(stream)
+            e2.synchronize()
+            fwd, rev = e0.elapsed_time(e1), e1.elapsed_time(e2)
+            psteps = float(S) * w["count"] * steps
+            g = pbar.cpu().numpy()[0]                       # [S, 3]
+            out["eps"][str(eps)] = {
+                "forward_ms": fwd, "reverse_ms": rev,
+                "value": psteps / ((fwd + rev) / 1e3), "forward_only": psteps / (fwd / 1e3),
+                "J_mean": J.mean(0).cpu().numpy().tolist(),
+                "grad_sumJ_mean_abs": np.abs(g).mean(axis=0).tolist()}
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint(args):
     """Forward + reverse sweep of the smoothed-V_dep adjoint on 256 samples x 16,384 particles."""
     import torch
     import paper_2205_04979_gb300.pdq as pdq
+    if args.adjoint_config4:
+        return run_adjoint_config4(args)
     w = workloads.WORKLOADS["adjoint"]
     S = args.samples or w["samples"]
     params = workloads.sample_params(S, w["param_seed"])

@@ -318,6 +318,21 @@ def test_mixed_parity(pdq, fields, variant, block):
     _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 2e-6, 2e-5, max_flip=0.005)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_newton_variant_without_coulomb(pdq, fields, precision):
+    # with the Coulomb force off the Newton-pair sums are not launched; the update runs alone
+    counts = [1000, 333, 129]
+    forces = oracle.F_ALL & ~oracle.F_COUL
+    st, tally, ost, nd, na = _run_both(pdq, fields, precision, counts, ST3, PRM3, 20,
+                                       {"variant": 3, "forces": forces, "window_start": 5}, block=64)
+    off = np.r_[0, np.cumsum(counts)]
+    if precision == 0:
+        assert _compare_by_id(st, ost, off, 1e-11, 1e-11) > 0
+        assert np.array_equal(tally.n_dep.cpu().numpy(), nd)
+    else:
+        assert _compare_by_id(st, ost, off, 2e-6, 2e-5, max_flip=0.005) > 0
+
+
 def test_vdep_tally_parity(pdq, fields):
     counts = [1000, 333, 129]
     st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3, 50, {"window_start": 10})
