@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--vdep-classes", type=float, nargs="+", default=[0.1, 0.316, 1.0, 3.16, 10.0],
                     help="St+ classes of --workload vdep_validation")
     ap.add_argument("--vdep-steps", type=int, default=1200, help="steps of --workload vdep_validation")
+    ap.add_argument("--clamp-check", action="store_true",
+                    help="--workload vdep_validation: compare the Coulomb clamp at the largest and smallest diameter")
     ap.add_argument("--adjoint-config4", action="store_true",
                     help="--workload adjoint as stated: 2,000 steps, checkpoints every 100, three widths")
     ap.add_argument("--no-vdep-check", action="store_true")
@@ -838,6 +840,45 @@ def run_p3m(args):
     print(json.dumps(out), flush=True)
 
 
+def clamp_check(pdq, stream, block, variant, samples, count, steps, st_plus, dt=0.05, t_window=10.0,
+                param_seed=4242):
+    """Does V_dep+ depend on the Coulomb distance clamp (reading c1: the largest class diameter for
+    every pair)?  The batched MIXED step with the clamp at the largest class diameter and at the
+    smallest (contact_scale = d_min / d_max), same particles (a stream per sample) and inputs;
+    any pair-dependent contact distance lies between the two."""
+    import torch
+    w = workloads.WORKLOADS["batched_mixed"]
+    params = workloads.sample_params(samples, param_seed)
+    desc = pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
+    scale = float(np.sqrt(min(st_plus) / max(st_plus)))       # d+ grows as sqrt(St+)
+    res = {}
+    for name, sc in (("largest", 1.0), ("smallest", scale)):
+        phys = pdq.phys_default()
+        phys.contact_scale = sc
+        with torch.cuda.stream(stream):
+            field = pdq.Field(desc, w["field_seed"], stream)
+            st = pdq.State(pdq.MIXED, [count] * samples, list(st_plus))
+            prm = pdq.params_tensor(params)
+            pdq.seed_particles_independent(field, phys, st, prm, w["particle_seed"], 0.0, stream)
+            cfg = pdq.step_cfg(dt, window_start=workloads.window_start_step(t_window, dt), compact_every=100,
+                               block=block, variant=variant)
+            tally = pdq.Tally(samples, len(st_plus))
+            pdq.step_particles(field, phys, st, prm, cfg, steps, tally, pdq.workspace(st, cfg), stream)
+            vdep, _, _ = pdq.deposition_tally(tally, dt, stream=stream)
+            stream.synchronize()
+            res[name] = (vdep.cpu().numpy(), tally.n_dep.cpu().numpy())
+            del st, tally
+    va, na = res["largest"]
+    vb, nb = res["smallest"]
+    se = va.std(0, ddof=1) / np.sqrt(samples)
+    diff = np.abs(vb.mean(0) - va.mean(0))
+    return {"contact_scale": [1.0, scale], "deposits": [na.sum(0).tolist(), nb.sum(0).tolist()],
+            "events_differing": np.abs(na - nb).sum(0).tolist(),
+            "vdep_mean": [va.mean(0).tolist(), vb.mean(0).tolist()],
+            "rel_diff": (diff / np.where(va.mean(0) > 0, va.mean(0), 1.0)).tolist(),
+            "diff_over_se": (diff / np.where(se > 0, se, 1.0)).tolist()}
+
+
 def run_vdep_validation(args):
     """The metric's validity condition at scale: V_dep+ of the batched MIXED path (autotuned
     launch configuration) against the FP64 GPU path, the latter pinned to the oracle by the
@@ -860,6 +901,12 @@ def run_vdep_validation(args):
         cfg = pdq.step_cfg(w["dt"], window_start=0, compact_every=100)
         pdq.autotune(field, phys, st, prm, cfg, stream)
         del st
+    if args.clamp_check:
+        res = clamp_check(pdq, stream, cfg.block, cfg.variant, S, 4096, args.vdep_steps, classes)
+        print(json.dumps({"metric": "V_dep+ with the Coulomb clamp at the largest vs the smallest class diameter",
+                          "workload": "%d samples x 4096 particles (a particle stream per sample), St+ classes %s, "
+                                      "%d steps" % (S, classes, args.vdep_steps), "clamp_check": res}), flush=True)
+        return
     res = vdep_check(pdq, stream, cfg.block, cfg.variant, samples=S, count=4096, steps=args.vdep_steps,
                      st_plus=classes)
     print(json.dumps({"metric": "V_dep+ of batched MIXED vs FP64 GPU (relative error, error / MC SE)",

@@ -77,6 +77,9 @@ typedef struct pdq_phys {
     double tau_col_steps;   /* collision time tau_col in steps (15, App. A.2)                       */
     double neg_charge_frac; /* seeding: share of particles with a negative charge (0: like-signed,   */
                             /* as in the paper; the sign draws Philox counter word 2)               */
+    double contact_scale;   /* Coulomb distance clamp d_c = contact_scale x the largest class       */
+                            /* diameter (1 by default; > 0): a smaller value tests how much the     */
+                            /* clamp matters (d_min/d_max puts it at the smallest class diameter)   */
 } pdq_phys;
 void pdq_phys_default(pdq_phys* out);
 
@@ -249,7 +252,8 @@ int pdq_step_workspace_size(const pdq_state* state, const pdq_step_cfg* cfg, siz
 
 /* Advance all samples n_steps steps (App. A.2).  One step of particle i:
  *   a_i = sum_{j != i, same sample} k q_i q_j (x_i - x_j) / (m_i max(|x_i - x_j|, d_c)^3)
- *         (Eq. coulomb; minimum image in z; d_c the largest class diameter)
+ *         (Eq. coulomb; minimum image in z; d_c = phys->contact_scale x the largest
+ *         class diameter)
  *       + image charge q_i^2 / (4 pi eps0 (2 y)^2 m_i) toward the wall (Sec. 2.2)
  *       + 2 F_vw(delta)/m_i toward the wall (Eq. vdw; delta saturated at
  *         delta_min, zero beyond d/4)  + gravity;

@@ -34,7 +34,7 @@ class Phys(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "nu", "radius", "re_tau", "u_bulk", "rho_p", "rho_f", "eps0", "qmax_coef",
         "hamaker0", "delta_min", "young", "delta_c", "sigma_y0", "g",
-        "restitution", "tau_col_steps", "neg_charge_frac")]
+        "restitution", "tau_col_steps", "neg_charge_frac", "contact_scale")]
 
 
 class Field(C.Structure):

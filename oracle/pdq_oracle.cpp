@@ -118,7 +118,8 @@ extern "C" {
 struct OrcPhys {
     double nu, radius, re_tau, u_bulk, rho_p, rho_f, eps0, qmax_coef,
            hamaker0, delta_min, young, delta_c, sigma_y0, g,
-           restitution, tau_col_steps, neg_charge_frac;
+           restitution, tau_col_steps, neg_charge_frac,
+           contact_scale;   // Coulomb distance clamp = contact_scale x the largest class diameter
 };
 
 struct OrcField {
@@ -149,6 +150,7 @@ void orc_phys_default(OrcPhys* p) {
     p->hamaker0 = 1e-18; p->delta_min = 1e-9; p->young = 70e9; p->delta_c = 0.165e-9;
     p->sigma_y0 = 200e6; p->g = 9.81;
     p->restitution = 0.9; p->tau_col_steps = 15.0; p->neg_charge_frac = 0.0;
+    p->contact_scale = 1.0;
 }
 
 }  // extern "C"
@@ -731,10 +733,11 @@ static void step_sample(const Run<T>& rn, int n, T* x, T* y, T* z, T* vx, T* vy,
     }
 }
 
-static double contact_distance(const std::vector<ClassProps>& cp) {
+// Coulomb contact distance (reading c1): contact_scale x the largest class diameter.
+static double contact_distance(const OrcPhys& p, const std::vector<ClassProps>& cp) {
     double m = 0;
     for (auto& c : cp) m = std::max(m, c.d_plus);
-    return m;
+    return p.contact_scale * m;
 }
 
 extern "C" {
@@ -750,7 +753,7 @@ int orc_run(const OrcPhys* p, const OrcField* f, const double* grid, const OrcCf
     Run<double> rn;
     rn.p = p; rn.f = f; rn.grid = grid; rn.cfg = cfg; rn.un = units(*p);
     for (int c = 0; c < n_classes; ++c) rn.cp.push_back(class_props(*p, st_plus[c]));
-    rn.contact = contact_distance(rn.cp);
+    rn.contact = contact_distance(*rn.p, rn.cp);
     for (int s = 0; s < n_samples; ++s) {
         int64_t o = offset[s];
         int n = (int)(offset[s + 1] - o);
@@ -795,7 +798,7 @@ int orc_smooth_run(const OrcPhys* p, const OrcField* f, const double* grid, cons
             Run<Dual> rn;
             rn.p = p; rn.f = f; rn.grid = grid; rn.cfg = cfg; rn.un = units(*p);
             for (int c = 0; c < n_classes; ++c) rn.cp.push_back(class_props(*p, st_plus[c]));
-            rn.contact = contact_distance(rn.cp);
+            rn.contact = contact_distance(*rn.p, rn.cp);
             std::vector<Dual> x(n), y(n), z(n), vx(n), vy(n), vz(n), q(n), w(n);
             std::vector<int32_t> alive(n, 1);
             Dual xi(sp.xi), zeta(sp.zeta), theta(sp.theta);
@@ -821,7 +824,7 @@ int orc_smooth_run(const OrcPhys* p, const OrcField* f, const double* grid, cons
             Run<double> rn;
             rn.p = p; rn.f = f; rn.grid = grid; rn.cfg = cfg; rn.un = units(*p);
             for (int c = 0; c < n_classes; ++c) rn.cp.push_back(class_props(*p, st_plus[c]));
-            rn.contact = contact_distance(rn.cp);
+            rn.contact = contact_distance(*rn.p, rn.cp);
             std::vector<double> x(x0 + o, x0 + o + n), y(y0 + o, y0 + o + n), z(z0 + o, z0 + o + n);
             std::vector<double> vx(n, 0.0), vy(n, 0.0), vz(n, 0.0), q(n), w(n, 1.0);
             std::vector<int32_t> alive(n, 1);
@@ -850,7 +853,7 @@ void orc_coulomb_accel(const OrcPhys* p, const OrcField* f, int n_classes, const
     Run<double> rn;
     rn.p = p; rn.f = f; rn.grid = nullptr; rn.cfg = &cfg; rn.un = units(*p);
     for (int c = 0; c < n_classes; ++c) rn.cp.push_back(class_props(*p, st_plus[c]));
-    rn.contact = contact_distance(rn.cp);
+    rn.contact = contact_distance(*rn.p, rn.cp);
     const double L = f->l_plus;
     for (int i = 0; i < n; ++i) {
         double s[3] = {0, 0, 0};
@@ -911,7 +914,7 @@ int orc_run_ext(const OrcPhys* p, const OrcField* f, const double* grid, const O
     Run<double> rn;
     rn.p = p; rn.f = f; rn.grid = grid; rn.cfg = cfg; rn.un = units(*p);
     for (int c = 0; c < n_classes; ++c) rn.cp.push_back(class_props(*p, st_plus[c]));
-    rn.contact = contact_distance(rn.cp);
+    rn.contact = contact_distance(*rn.p, rn.cp);
     for (int s = 0; s < n_samples; ++s) {
         int64_t o = offset[s];
         int n = (int)(offset[s + 1] - o);
@@ -931,7 +934,7 @@ void orc_wall_accel(const OrcPhys* p, const OrcField* f, const OrcCfg* cfg, int 
     Run<double> rn;
     rn.p = p; rn.f = f; rn.grid = nullptr; rn.cfg = cfg; rn.un = units(*p);
     for (int c = 0; c < n_classes; ++c) rn.cp.push_back(class_props(*p, st_plus[c]));
-    rn.contact = contact_distance(rn.cp);
+    rn.contact = contact_distance(*rn.p, rn.cp);
     for (int i = 0; i < n; ++i) {
         double acc[3];
         wall_and_body<double>(rn, rn.cp[cls[i]], x[i], y[i], q[i], zeta, acc);

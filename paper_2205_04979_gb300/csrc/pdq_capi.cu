@@ -53,4 +53,5 @@ extern "C" void pdq_phys_default(pdq_phys* p) {
     p->restitution = 0.9;
     p->tau_col_steps = 15.0;
     p->neg_charge_frac = 0.0;
+    p->contact_scale = 1.0;
 }

@@ -33,14 +33,14 @@ enum { ERR_NONFINITE = 1 };
 // ---------------------------------------------------------------------------
 // Host: per-class constants from the physical constants (all SI -> wall units).
 // ---------------------------------------------------------------------------
-// Largest class diameter of a state, wall units (the Coulomb contact distance).
+// The Coulomb contact distance of a state, wall units: contact_scale x the largest class diameter.
 double contact_distance(const pdq_phys* p, const pdq_state* st) {
     const double ustar = p->re_tau * p->nu / p->radius;
     const double ell = p->nu / ustar, tauf = p->nu / (ustar * ustar);
     double dmax = 0.0;
     for (int c = 0; c < st->n_classes; ++c)
         dmax = fmax(dmax, sqrt(18.0 * p->rho_f * p->nu * st->st_plus[c] * tauf / p->rho_p) / ell);
-    return dmax;
+    return p->contact_scale * dmax;
 }
 
 int make_step_const(const pdq_field* f, const pdq_phys* p, const pdq_state* st, StepConst* K) {
@@ -51,6 +51,7 @@ int make_step_const(const pdq_field* f, const pdq_phys* p, const pdq_state* st, 
     const double acc = p->nu / (ustar * ustar * ustar);     // SI acceleration -> wall units
     const double ke = 1.0 / (4.0 * kPi * p->eps0);
     if (fabs(f->desc.r_plus - p->re_tau) > 1e-9 * p->re_tau) return PDQ_ERR_INVALID_ARG;
+    if (!(p->contact_scale > 0.0) || !(p->contact_scale <= 1e6)) return PDQ_ERR_INVALID_ARG;
     double dmax = 0.0;
     K->n_classes = st->n_classes;
     for (int c = 0; c < st->n_classes; ++c) {
@@ -84,7 +85,7 @@ int make_step_const(const pdq_field* f, const pdq_phys* p, const pdq_state* st, 
     K->delta_min = p->delta_min;
     K->ustar = ustar;
     K->elastic0 = p->sigma_y0 * p->sigma_y0 / (p->rho_p * p->young);
-    K->contact2 = dmax * dmax;
+    K->contact2 = (p->contact_scale * dmax) * (p->contact_scale * dmax);
     K->near = 1.25 * dmax;      // (d_i + d_j)/2 + d_eff/4 <= 1.25 d_max
     K->inv_beta = 1.0 / f->desc.beta;
     K->tanh_beta = tanh(f->desc.beta);

@@ -31,7 +31,7 @@ class PdqError(RuntimeError):
 class Phys(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "nu", "radius", "re_tau", "u_bulk", "rho_p", "rho_f", "eps0", "q_unit", "hamaker0", "delta_min",
-        "young", "delta_c", "sigma_y0", "g", "restitution", "tau_col_steps", "neg_charge_frac")]
+        "young", "delta_c", "sigma_y0", "g", "restitution", "tau_col_steps", "neg_charge_frac", "contact_scale")]
 
 
 class FieldDesc(C.Structure):

@@ -333,6 +333,32 @@ def test_newton_variant_without_coulomb(pdq, fields, precision):
         assert _compare_by_id(st, ost, off, 2e-6, 2e-5, max_flip=0.005) > 0
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_contact_scale_parity(pdq, fields, precision):
+    # the Coulomb clamp at the smallest class diameter (contact_scale = d_min / d_max) on both sides
+    f, of, grid, _ = fields
+    counts = [1000, 333, 129]
+    scale = (0.1 / 10.0) ** 0.5                              # d+ grows as sqrt(St+)
+    phys = pdq.phys_default()
+    phys.contact_scale = scale
+    ophys = oracle.phys()
+    ophys.contact_scale = scale
+    st = pdq.State(precision, counts, ST3)
+    prm = pdq.params_tensor(PRM3)
+    pdq.seed_particles(f, phys, st, prm, 1)
+    ost, off = oracle.seed(of, ST3, counts, PRM3, 1, p=ophys)
+    cfg = pdq.step_cfg(0.1, window_start=5, variant=3, block=64)
+    tally = pdq.Tally(3, 3)
+    pdq.step_particles(f, phys, st, prm, cfg, 20, tally, pdq.workspace(st, cfg))
+    nd, na = oracle.run(of, grid, oracle.cfg(0.1, window_start=5), ST3, off, PRM3, ost, 20, p=ophys)
+    off = np.r_[0, np.cumsum(counts)]
+    if precision == 0:
+        assert _compare_by_id(st, ost, off, 1e-10, 1e-10) > 0
+        assert np.array_equal(tally.n_dep.cpu().numpy(), nd)
+    else:
+        assert _compare_by_id(st, ost, off, 2e-6, 2e-5, max_flip=0.005) > 0
+
+
 def test_vdep_tally_parity(pdq, fields):
     counts = [1000, 333, 129]
     st, tally, ost, nd, na = _run_both(pdq, fields, 0, counts, ST3, PRM3, 50, {"window_start": 10})

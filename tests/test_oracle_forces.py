@@ -189,6 +189,25 @@ def test_coulomb_minimum_image_and_clamp(orc):
     assert a[1, 0] == pytest.approx(coef * 0.3 * dplus / dplus ** 3, rel=1e-12)
 
 
+def test_coulomb_clamp_scale(orc):
+    # the clamp distance is contact_scale x the largest class diameter: with the smallest class's
+    # diameter (scale d_min/d_max) a pair at 0.3 d_max feels the unclamped 1/r^2 force, and a pair
+    # closer than d_min saturates there
+    f = orc.field_desc()
+    st_plus = [0.1, 10.0]
+    t = orc.class_table(st_plus)
+    dmin, dmax = t[0, 1], t[1, 1]
+    p = orc.phys()
+    p.contact_scale = dmin / dmax
+    coef = K_E * (8e-17) ** 2 / t[1, 3] / ELL ** 2 * ACC     # on the St+ = 10 particle (class 1)
+    cls = np.array([1, 1], np.int32)
+    for r, expect in ((0.3 * dmax, 1.0 / (0.3 * dmax) ** 2), (0.5 * dmin, 0.5 * dmin / dmin ** 3)):
+        a = orc.coulomb_accel(f, st_plus, np.array([0.0, r]), np.zeros(2), np.zeros(2), np.ones(2), cls, p=p)
+        assert a[1, 0] == pytest.approx(coef * expect, rel=1e-12)
+        a1 = orc.coulomb_accel(f, st_plus, np.array([0.0, r]), np.zeros(2), np.zeros(2), np.ones(2), cls)
+        assert a1[1, 0] == pytest.approx(coef * r / dmax ** 3, rel=1e-12)     # default: clamped at d_max
+
+
 def test_rebound_model(orc):
     # Sec. 4.3 / Fig. 12: CoR_n falls with zeta, theta and the impact velocity; CoR_n = 0 is sticking.
     st = 0.1
