@@ -72,6 +72,10 @@ __device__ __forceinline__ ZClass zclass(float alo, float ahi, float blo, float 
 //     reads entry l + k without wrapping (constant offsets in the unrolled loop).  The per-warp
 //     sums of the tile are added in shared memory and leave with one float4 atomic per j.
 // The earlier particles of the sample reach this tile as the j side of earlier tiles.
+// Warp w holds the i-particles [32 U w, 32 U (w + 1)) of the tile (lane l: 32 k + l, k < U), a
+// contiguous run of the z-binned sample, so its z range is narrow and more j groups are z-separated
+// from it (no clamp, no per-pair minimum image: 1.2 % of the groups need them for a z-sorted sample,
+// against 4 % with the particles strided over the tile).
 // load(g) gives particle g as (x, y, z, q).  Padding particles sit far off the axis
 // (x = +-1e15) with zero charge, so they add nothing.  All threads of the CTA take part; the
 // shared arrays are the calling kernel's (one set per kernel instantiation).
@@ -107,7 +111,7 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
         float4 p[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int g = (2 * h + e) * NT + tid;
+            const int g = warp * (32 * U) + (2 * h + e) * 32 + lane;
             if (g < n) {
                 p[e] = load(base + g);
                 ilo = fminf(ilo, p[e].z);
@@ -252,7 +256,7 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
         f2_unpack(AX[h], a0[0], a1[0]);
         f2_unpack(AY[h], a0[1], a1[1]);
         f2_unpack(AZ[h], a0[2], a1[2]);
-        const int g0 = (2 * h) * NT + tid, g1 = g0 + NT;
+        const int g0 = warp * (32 * U) + (2 * h) * 32 + lane, g1 = g0 + 32;
         if (g0 < n) atomicAdd(&acc[base + g0], make_float4(a0[0], a0[1], a0[2], 0.f));
         if (g1 < n) atomicAdd(&acc[base + g1], make_float4(a1[0], a1[1], a1[2], 0.f));
     }

@@ -962,11 +962,10 @@ __global__ void __launch_bounds__(NT, ((V == 4 || V == 6) && P == PDQ_MIXED) ? 6
 // over a queue measured ~5 more register moves per packed pair evaluation in the hot loop.
 // Each CTA sums its tile's pairs with newton_tile (its own block one-sided, every later
 // particle of the sample as Newton pairs).
-// Register budget: 3 CTAs of 128 threads per SM (up to 168 registers), so that the 32-step loop
-// unrolled by 4 keeps more independent pair chains in flight (measured 2.6 % faster than 4 CTAs
-// at 128 registers).
+// Register budget: 4 CTAs of 128 threads per SM (128 registers; 1 % faster than 3 CTAs at 168
+// registers once the CTAs stopped looping over a queue), 6 CTAs of 64.
 template <int NT, int U>
-__global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_pairs_sym(const StepArgs A) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 4 : 6) k_pairs_sym(const StepArgs A) {
     const int item = blockIdx.x;
     if (item >= A.ctl[CTL_NITEMS]) return;
     const float4* __restrict__ pos_in = (const float4*)A.pos_in;

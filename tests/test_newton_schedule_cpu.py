@@ -17,7 +17,9 @@ def newton_tile_visits(n, NT, U, base):
     side 'j': the Newton pair's reaction, added to j (the later particle)."""
     W = NT // 32
     dend = min(base + NT * U, n)
-    tile_i = [base + u * NT + t for u in range(U) for t in range(NT) if base + u * NT + t < n]
+    # warp w holds the tile's particles [32 U w, 32 U (w + 1)): lane l the ones 32 u + l, u < U
+    tile_i = [base + w * 32 * U + u * 32 + lane for w in range(W) for u in range(U) for lane in range(32)
+              if base + w * 32 * U + u * 32 + lane < n]
     visits = []
     for j0 in range(base, n, NT):
         if j0 < dend:        # the tile's own block: one-sided, every i of the tile with every j of the block
@@ -39,7 +41,7 @@ def newton_tile_visits(n, NT, U, base):
                         if j >= n:
                             continue
                         for u in range(U):
-                            i = base + u * NT + warp * 32 + lane
+                            i = base + warp * 32 * U + u * 32 + lane
                             if i < n:
                                 visits.append((i, j, "i"))
                                 visits.append((j, i, "j"))
