@@ -486,7 +486,8 @@ def run_ours(args):
                    if world > 1 else "1 GPU",
                    "launch": "direct" if args.no_graph else "one CUDA-graph launch of the timed steps",
                    "tile": {"block": cfg.block,
-                            "i_per_thread": (8 if (cfg.variant == 2 and not args.contact) or newton else 4)
+                            "i_per_thread": ((12 if not args.contact else 8) if newton else
+                                             8 if cfg.variant == 2 and not args.contact else 4)
                             if prec == pdq.MIXED else (2 if newton else 1),
                             "variant": cfg.variant, "autotuned": args.block == 0 and not args.no_autotune}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",

@@ -962,10 +962,10 @@ __global__ void __launch_bounds__(NT, ((V == 4 || V == 6) && P == PDQ_MIXED) ? 6
 // over a queue measured ~5 more register moves per packed pair evaluation in the hot loop.
 // Each CTA sums its tile's pairs with newton_tile (its own block one-sided, every later
 // particle of the sample as Newton pairs).
-// Register budget: 4 CTAs of 128 threads per SM (128 registers; 1 % faster than 3 CTAs at 168
-// registers once the CTAs stopped looping over a queue), 6 CTAs of 64.
+// Register budget: 3 CTAs of 128 threads per SM (168 registers) for 12 particles per thread (8 per
+// thread ran 1 % faster at 4 CTAs and 128 registers than at 3), 6 CTAs of 64.
 template <int NT, int U>
-__global__ void __launch_bounds__(NT, NT == 128 ? 4 : 6) k_pairs_sym(const StepArgs A) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_pairs_sym(const StepArgs A) {
     const int item = blockIdx.x;
     if (item >= A.ctl[CTL_NITEMS]) return;
     const float4* __restrict__ pos_in = (const float4*)A.pos_in;
@@ -1441,10 +1441,12 @@ static bool newton_pairs(const pdq_state* st, const pdq_step_cfg* cfg) {
     return cfg && cfg->variant == 3 && (!(cfg->forces & PDQ_F_CONTACT) || st->precision == PDQ_MIXED);
 }
 // particles per thread: FP64 1 (2 for its Newton-pair kernel); MIXED 4 (two packed pairs), 8 for
-// pair variants 2 and 3
+// pair variant 2, 12 for pair variant 3 (8 with contact forces: their update runs 4 per thread
+// over 2 NT threads); 12 gave 1.2 % over 8 (six packed calls share each step's shared loads and
+// shuffles) at 3 CTAs of 128 threads per SM
 static int tile_ilp(const pdq_state* st, const pdq_step_cfg* cfg = nullptr) {
     if (st->precision == PDQ_FP64) return newton_pairs(st, cfg) ? 2 : 1;
-    if (newton_pairs(st, cfg)) return 8;
+    if (newton_pairs(st, cfg)) return (cfg->forces & PDQ_F_CONTACT) ? 8 : 12;
     if (cfg && (cfg->forces & PDQ_F_CONTACT)) return 4;      // contact runs: variant 0 layout
     return (cfg && cfg->variant == 2) ? 8 : 4;
 }
@@ -1473,8 +1475,9 @@ static int launch_step(const StepArgs& A, cudaStream_t s) {
     return PDQ_OK;
 }
 
-// Pair variant 3: the Newton-pair sums (NT threads, 8 particles per thread) into A.acc4, then
-// the given-sums step over the same tiles (2 NT threads, 4 particles per thread).
+// Pair variant 3: the Newton-pair sums (NT threads, 12 particles per thread) into A.acc4, then
+// the given-sums step over the same tiles (2 NT threads, 6 particles per thread; with contact forces
+// the sums take 8 per thread and the contact variant 4 per thread over 2 NT threads).
 template <int NT>
 static int launch_newton64(const StepArgs& A, cudaStream_t s) {
     static int per_sm = 0;
@@ -1505,8 +1508,8 @@ template <int NT>
 static int launch_newton(const StepArgs& A, cudaStream_t s) {
     PDQ_CUDA(cudaMemsetAsync(A.acc4, 0, sizeof(float4) * (size_t)(A.cap > 0 ? A.cap : 1), s));
     if (A.K.forces & PDQ_F_COULOMB)      // the sums enter the update only with the Coulomb force on
-        k_pairs_sym<NT, 8><<<(unsigned)std::max<int64_t>(1, A.max_items), NT, 0, s>>>(A);
-    return launch_step<PDQ_MIXED, 2 * NT, 4, 5>(A, s);
+        k_pairs_sym<NT, 12><<<(unsigned)std::max<int64_t>(1, A.max_items), NT, 0, s>>>(A);
+    return launch_step<PDQ_MIXED, 2 * NT, 6, 5>(A, s);
 }
 
 // variant: MIXED pair math, 0 = all packed f32x2, 1 = packed with scalar accumulation,

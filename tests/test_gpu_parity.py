@@ -459,14 +459,15 @@ def test_capture_efficiency(pdq, fields):
     assert torch.allclose(ce.cpu(), v.cpu() * oracle.capture_factor(of), rtol=1e-14, atol=0)
 
 
-@pytest.mark.parametrize("counts", [[0, 5, 1, 0], [1024, 1025, 1023, 2049]])
-def test_mixed_newton_pairs_edge_sizes(pdq, fields, counts):
-    # pair variant 3 at 128 threads x 8 particles: 1,024-particle tiles; empty and one-particle
-    # samples, samples of exactly one tile, one tile +-1 and two tiles + 1 (the boundary between a
-    # tile's own block and the later particles), with compaction every step
+@pytest.mark.parametrize("block,counts", [(128, [0, 5, 1, 0]), (128, [1536, 1537, 1535, 3073]),
+                                          (64, [768, 769, 767, 1537])])
+def test_mixed_newton_pairs_edge_sizes(pdq, fields, block, counts):
+    # pair variant 3 at 12 particles per thread: 1,536-particle tiles at 128 threads, 768 at 64;
+    # empty and one-particle samples, samples of exactly one tile, one tile +-1 and two tiles + 1
+    # (the boundary between a tile's own block and the later particles), with compaction every step
     prm = np.tile(PRM3[:1], (len(counts), 1))
     st, tally, ost, nd, na = _run_both(pdq, fields, 1, counts, ST3, prm, 5, {"variant": 3, "compact_every": 1},
-                                       block=128)
+                                       block=block)
     _compare_by_id(st, ost, np.r_[0, np.cumsum(counts)], 2e-6, 2e-5, max_flip=0.005)
     assert np.array_equal(tally.n_alive.cpu().numpy(), na)
 
