@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--workload", default="batched_mixed")
     ap.add_argument("--samples", type=int, default=None, help="truncate the workload (testing only)")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--e2e-groups", type=int, default=4,
+    ap.add_argument("--e2e-groups", type=int, default=2,
                     help="sample groups pipelined in the e2e measurement (1 = upload, step, download in turn)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -314,8 +314,13 @@ def run_e2e(pdq, field, phys, state, prm, cfg, w, args, stream):
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
 
     def one_step():
+        # no host synchronisation between steps: a group's upload waits on the copy-out stream's
+        # event of its previous download (the host buffers it reads), so copies of one step
+        # overlap the other groups' steps of the next one as well
         for g in groups:
             with torch.cuda.stream(s_in):
+                if g.get("ev_out") is not None:
+                    s_in.wait_event(g["ev_out"])
                 for dst, src in zip(dev_state(g["st"]), g["hosts"]):
                     dst.copy_(src, non_blocking=True)
                 ev_in = torch.cuda.Event()
@@ -330,7 +335,8 @@ def run_e2e(pdq, field, phys, state, prm, cfg, w, args, stream):
                     dst.copy_(src, non_blocking=True)
                 g["htal"][0].copy_(g["tally"].n_alive, non_blocking=True)
                 g["htal"][1].copy_(g["tally"].n_dep, non_blocking=True)
-        s_out.synchronize()
+                g["ev_out"] = torch.cuda.Event()
+                g["ev_out"].record(s_out)
 
     one_step()                                       # untimed warm-up (first calls read offsets)
     torch.cuda.synchronize()
@@ -338,6 +344,7 @@ def run_e2e(pdq, field, phys, state, prm, cfg, w, args, stream):
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         one_step()
+    s_out.synchronize()                              # every download of the last step has landed
     te = time.perf_counter() - t0
     torch.cuda.synchronize()
     alive = sum(int(g["tally"].n_alive.sum().item()) for g in groups) - alive0
