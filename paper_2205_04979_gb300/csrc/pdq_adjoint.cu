@@ -863,7 +863,8 @@ __device__ __forceinline__ void vjp_pair_x2_sym(f2 xm, f2 ym, f2 zm, f2 nQm, f2 
 }
 
 // Pair VJP with Newton pairs (MIXED), the scheme of newton_tile: grid (samples, m-tiles of
-// NT*U), heavy first tiles first; the tile's own block one-sided (the j sums of vjp_pair_x2_sym left unused), every
+// NT*U), heavy first tiles first; warp w holds the m-particles [32 U w, 32 U (w + 1)) of the
+// tile, a contiguous run of the z-binned checkpoint (narrow z range: fewer clamped groups); the tile's own block one-sided (the j sums of vjp_pair_x2_sym left unused), every
 // later particle of the sample as a Newton pair with 32-j groups walked by skewed lanes.  Sums
 // (x-bar x, y, z, Qp) go to A.acc4 by float4 atomics; k_adj_pairs_finish applies them.
 template <int NT, int U>
@@ -893,7 +894,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_pairs_sym(const A
         float v[2][7];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int64_t g = base + (2 * h + e) * NT + tid;
+            const int64_t g = base + warp * (32 * U) + (2 * h + e) * 32 + lane;   // contiguous per warp
             if (g < end) {
                 v[e][0] = (float)A.in.x[g]; v[e][1] = (float)A.in.y[g]; v[e][2] = (float)A.in.z[g];
                 v[e][3] = (float)(A.in.w[g] * xi * A.qhat[g]);
@@ -1018,7 +1019,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_pairs_sym(const A
         f2_unpack(TY[h], t0[1], t1[1]);
         f2_unpack(TZ[h], t0[2], t1[2]);
         f2_unpack(QP[h], t0[3], t1[3]);
-        const int64_t g0 = base + (2 * h) * NT + tid, g1 = g0 + NT;
+        const int64_t g0 = base + warp * (32 * U) + (2 * h) * 32 + lane, g1 = g0 + 32;
         if (g0 < end) atomicAdd(&A.acc4[g0], make_float4(t0[0], t0[1], t0[2], t0[3]));
         if (g1 < end) atomicAdd(&A.acc4[g1], make_float4(t1[0], t1[1], t1[2], t1[3]));
     }
@@ -1219,14 +1220,15 @@ static int adjoint_impl(const pdq_field* field, const pdq_phys* phys, const pdq_
     const int NTN = 128;
     // grid y counts the tiles of the largest sample (at most 65,535: 33.5 M particles per sample)
     if (newton && (nmax + 4 * NTN - 1) / (4 * NTN) > 65535) return PDQ_ERR_UNSUPPORTED;
-    const dim3 grid_sums((unsigned)A.S, (unsigned)((nmax + 8 * NTN - 1) / (8 * NTN)));
+    constexpr int US = 12;   // forward sums: 12 particles per thread (as the step's Newton kernel)
+    const dim3 grid_sums((unsigned)A.S, (unsigned)((nmax + US * NTN - 1) / (US * NTN)));
     const dim3 grid_vjp((unsigned)A.S, (unsigned)((nmax + 4 * NTN - 1) / (4 * NTN)));
     auto fwd = [&](const Slot& in, const Slot& out, int64_t step, int tally) -> cudaError_t {
         A.in = in; A.out = out; A.step = step; A.tally = tally;
         if (newton) {
             const cudaError_t e = cudaMemsetAsync(A.acc4, 0, acc_bytes, s);
             if (e != cudaSuccess) return e;
-            k_adj_sums_sym<NTN, 8><<<grid_sums, NTN, 0, s>>>(A);
+            k_adj_sums_sym<NTN, US><<<grid_sums, NTN, 0, s>>>(A);
             k_adj_forward<PDQ_MIXED, NT, true><<<grid, NT, 0, s>>>(A);
         } else if (mixed) {
             k_adj_forward<PDQ_MIXED, NT><<<grid, NT, 0, s>>>(A);

@@ -153,13 +153,14 @@ def test_dgsm_pipeline(pdq):
 
 
 # ---------------------------------------------------------------------------
-# Sizes that cross the MIXED Newton-pair tiles: the forward sums take 1,024-particle i-tiles
+# Sizes that cross the MIXED Newton-pair tiles: the forward sums take 1,536-particle i-tiles
 # and the pair VJP 512-particle ones, so only samples above those sizes run the off-diagonal
-# blocks, where the pair term enters the j side with the opposite sign.  Charge active
+# blocks, where the pair term enters the j side with the opposite sign (1,537 and 3,073: one
+# particle past one and two sums tiles, and past 3 and 6 VJP tiles).  Charge active
 # (case A's forces), eps+ = 0.5 and 0.02 (the widest and narrowest smoothing of the
 # 256 x 16,384 adjoint workload).
 # ---------------------------------------------------------------------------
-TILE_COUNTS = [1025, 513, 2049, 1, 0]
+TILE_COUNTS = [1537, 513, 3073, 1, 0]
 TILE_PARAMS = np.array([[0.09, 0.7, 0.4], [0.06, 0.3, 0.8], [0.075, 0.5, 0.5], [0.05, 0.6, 0.3],
                         [0.07, 0.4, 0.6]])
 TILE = dict(st=[0.1, 1.0], steps=24, dt=0.05, gravity=(0, 0, 1), win=5)
