@@ -1,10 +1,12 @@
 """Host model of the Newton-pair schedule (pair variant 3): the index arithmetic of
 newton_tile and of the FP64 chunked items, replayed in Python on small ragged
 samples.  Every ordered pair (i, j), i != j, of a sample must reach i's sum exactly
-once: either one-sided inside i's own tile, or as a Newton pair from the tile of the
-earlier particle (added to the earlier one, subtracted, i.e. taken with the opposite
-sign of d, for the later one); and the j-side sums must come home to their own lane
-after the 32-step rotation.
+once: one-sided inside the block of i's warp, or as a Newton pair (added to one
+particle, subtracted, i.e. taken with the opposite sign of d, for the other): between
+two warps' blocks of one tile by the cyclic block schedule, or from the tile of the
+earlier particle; and the j-side sums must come home to their own lane after the
+32-step rotation.  (900, 96, 8) has an odd number of warps, a case no kernel
+instantiates, to check the schedule's other branch.
 """
 import numpy as np
 import pytest
@@ -14,43 +16,72 @@ def newton_tile_visits(n, NT, U, base):
     """(i, j, side) visits of the tile starting at `base`, as newton_tile orders them.
 
     side 'i': pair adds to i one-sided or as the i side of a Newton pair;
-    side 'j': the Newton pair's reaction, added to j (the later particle)."""
-    W = NT // 32
-    dend = min(base + NT * U, n)
-    # warp w holds the tile's particles [32 U w, 32 U (w + 1)): lane l the ones 32 u + l, u < U
-    tile_i = [base + w * 32 * U + u * 32 + lane for w in range(W) for u in range(U) for lane in range(32)
-              if base + w * 32 * U + u * 32 + lane < n]
+    side 'j': the Newton pair's reaction, added to j."""
+    W, H = NT // 32, U // 2
+    nd = min(n - base, NT * U)                 # the diagonal block
+    ngd = -(-nd // 32)
+
+    def i_of(w, h, e, lane):                   # warp w, packed pair h, half e, lane
+        return base + w * 32 * U + (2 * h + e) * 32 + lane
+
+    def rotation(G, hs, w, visits):
+        # lane l at step k holds j = 32 G + (l + k) % 32 and that j's running sum, which moves
+        # to lane l - 1 after the step: follow where each j's sum sits
+        holder = {jj: jj for jj in range(32)}
+        for k in range(32):
+            for lane in range(32):
+                jj = (lane + k) % 32
+                assert holder[jj] == lane
+                j = base + 32 * G + jj
+                if j >= n:
+                    continue
+                for h in hs:
+                    for e in range(2):
+                        i = i_of(w, h, e, lane)
+                        if i < n:
+                            visits.append((i, j, "i"))
+                            visits.append((j, i, "j"))
+            holder = {jj: (hh - 1) % 32 for jj, hh in holder.items()}
+        assert all(holder[jj] == jj for jj in range(32))   # home after 32 steps
+
     visits = []
-    for j0 in range(base, n, NT):
-        if j0 < dend:        # the tile's own block: one-sided, every i of the tile with every j of the block
-            for i in tile_i:
-                for j in range(j0, min(j0 + NT, dend)):
-                    if i != j:
-                        visits.append((i, j, "i"))
-            continue
-        for warp in range(W):
-            for g in range(W):
-                # lane l at step k holds j = g*32 + (l + k) % 32 and that j's running sum, which moves
-                # to lane l - 1 after the step: follow where each j's sum sits
-                holder = {jj: jj for jj in range(32)}          # j offset -> lane holding its sum
-                for k in range(32):
-                    for lane in range(32):
-                        jj = (lane + k) % 32
-                        assert holder[jj] == lane              # the lane working on j holds j's sum
-                        j = j0 + g * 32 + jj
-                        if j >= n:
+    # the diagonal block, warp by warp: warp w's i-particles are block B_w (2H groups of 32)
+    for w in range(W):
+        ival = nd - w * 32 * U
+        passes = [(2 * H * w + t, 0) for t in range(2 * H)]                 # own block, one-sided
+        for d in range(1, (W - 1) // 2 + 1):                                 # B_{w+d}, Newton pairs
+            passes += [(2 * H * ((w + d) % W) + t, "all") for t in range(2 * H)]
+        if W % 2 == 0:
+            if w < W // 2:       # first H groups of B_{w+W/2}, all packed pairs
+                passes += [(2 * H * (w + W // 2) + t, "all") for t in range(H)]
+            else:                # every group of B_{w-W/2}, packed pairs h >= H/2
+                passes += [(2 * H * (w - W // 2) + t, "upper") for t in range(2 * H)]
+        for G, kind in passes:
+            if G >= ngd or ival <= (32 * H if kind == "upper" else 0):
+                continue
+            if kind == 0:
+                for lane in range(32):
+                    for k in range(32):
+                        j = base + 32 * G + k
+                        if j - base >= nd:
                             continue
-                        for u in range(U):
-                            i = base + warp * 32 * U + u * 32 + lane
-                            if i < n:
-                                visits.append((i, j, "i"))
-                                visits.append((j, i, "j"))
-                    holder = {jj: (h - 1) % 32 for jj, h in holder.items()}
-                assert all(holder[jj] == jj for jj in range(32))   # home after 32 steps
+                        for h in range(H):
+                            for e in range(2):
+                                i = i_of(w, h, e, lane)
+                                if i - base < nd and i != j:
+                                    visits.append((i, j, "i"))
+            else:
+                rotation(G, range(H // 2 if kind == "upper" else 0, H), w, visits)
+    # the later particles, by j-tiles of NT staged for the whole CTA
+    for j0 in range(base + nd, n, NT):
+        for w in range(W):
+            for g in range(W):
+                rotation((j0 - base) // 32 + g, range(H), w, visits)
     return visits
 
 
-@pytest.mark.parametrize("n,NT,U", [(1500, 64, 8), (2049, 128, 8), (700, 128, 4), (1, 64, 8), (64 * 8, 64, 8)])
+@pytest.mark.parametrize("n,NT,U", [(1500, 64, 8), (2049, 128, 8), (700, 128, 4), (1, 64, 8), (64 * 8, 64, 8),
+                                    (1537, 128, 12), (1000, 64, 12), (777, 128, 12), (900, 96, 8)])
 def test_every_ordered_pair_once(n, NT, U):
     TI = NT * U
     count = np.zeros((n, n), np.int64)
