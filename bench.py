@@ -39,7 +39,7 @@ NEWTON_FLOPS_PER_PAIR = 12   # per ordered pair
 NEWTON_FLOPS_PER_LANE_OP = 24.0 / 16.0
 # DRAM bytes per launch of the dominant kernel on 4,557,792 particles (ncu): k_step for pair variant 2,
 # k_pairs_sym for pair variant 3
-KSTEP_DRAM_BYTES = {2: 495.4e6, 3: 178.5e6}
+KSTEP_DRAM_BYTES = {2: 495.4e6, 3: 177.4e6}
 # pipe peaks measured by the project microbenchmarks (python -m paper_2205_04979_gb300.peaks)
 PEAKS_FILE = os.path.join(ROOT, "profiles", "peaks.md")
 
@@ -500,7 +500,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "instruction_mix": mix,
                      # dram bytes read + written per launch from ncu captures of the pair
-                     # kernels (pair variant 2: 495.4 MB, variant 3: 178.5 MB, both on
+                     # kernels (pair variant 2: 495.4 MB, variant 3: 177.4 MB, both on
                      # 4,557,792 particles), scaled by the particle count of this launch; null
                      # for a variant without a capture of its kernel
                      "traffic": KSTEP_DRAM_BYTES[cfg.variant] / 4557792 * float(np.sum(counts))
