@@ -281,10 +281,11 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
         __syncthreads();                       // every warp's slice free, s_dj complete
     }
 
-    // ---- Newton pairs with the later particles, by j-tiles of NT ----
+    // ---- Newton pairs with the later particles, by j-tiles of NT (the next tile's particle in
+    // flight during a tile) ----
+    float4 pj = nd + tid < n ? load(base + nd + tid) : make_float4(kPadJ, 0.f, 0.f, 0.f);
     for (int j0 = nd; j0 < n; j0 += NT) {
         const int j = j0 + tid;
-        const float4 pj = j < n ? load(base + j) : make_float4(kPadJ, 0.f, 0.f, 0.f);
         float jlo = j < n ? pj.z : INFINITY, jhi = j < n ? pj.z : -INFINITY;
         for (int d = 16; d > 0; d >>= 1) {
             jlo = fminf(jlo, __shfl_xor_sync(0xffffffffu, jlo, d));
@@ -302,6 +303,7 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
             szm[e] = vzm; szm[e + 32] = vzm;
         }
         __syncthreads();
+        const float4 pnext = j + NT < n ? load(base + j + NT) : make_float4(kPadJ, 0.f, 0.f, 0.f);
 #pragma unroll 1
         for (int g = 0; g < W; ++g) {
             f2 JX, JY, JZ;
@@ -318,6 +320,7 @@ __device__ __forceinline__ void newton_tile(const Load& load, int64_t base, int6
             for (int w = 0; w < W; ++w) { sx += s_jacc[w][0][tid]; sy += s_jacc[w][1][tid]; sz += s_jacc[w][2][tid]; }
             atomicAdd(&acc[base + j], make_float4(sx, sy, sz, 0.f));
         }
+        pj = pnext;
     }
 #pragma unroll
     for (int h = 0; h < H; ++h) {
