@@ -871,8 +871,10 @@ template <int NT, int U>
 __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_pairs_sym(const AdjArgs A) {
     constexpr int W = NT / 32, H = U / 2;
     static_assert(U % 2 == 0 && NT % 32 == 0, "packed pairs over whole warps");
-    // staged j: (x,x,y,y), (z,z,Q,Q), (cx,cx,cy,cy), (cz,cz,-,-), each array at a 16-byte stride
-    __shared__ __align__(16) ulonglong2 sA[NT], sB[NT], sC[NT], sD[NT];
+    // staged j: (x,x,y,y), (z,z,Q,Q), (cx,cx,cy,cy), (cz,cz,-,-), each array at a 16-byte stride;
+    // j = 32 g + t of group g at entries 64 g + t and 64 g + 32 + t, so that lane l reads entry
+    // l + k at step k without wrapping
+    __shared__ __align__(16) ulonglong2 sA[2 * NT], sB[2 * NT], sC[2 * NT], sD[2 * NT];
     __shared__ float s_jacc[W][4][NT];
     __shared__ float2 s_zr[W];
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -928,10 +930,13 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_pairs_sym(const A
         }
         const float2 r = warp_range(j < jlim ? v[2] : INFINITY, j < jlim ? v[2] : -INFINITY);
         if (lane == 0) s_zr[warp] = r;
-        sA[tid] = make_ulonglong2(f2_pack(v[0], v[0]), f2_pack(v[1], v[1]));
-        sB[tid] = make_ulonglong2(f2_pack(v[2], v[2]), f2_pack(v[3], v[3]));
-        sC[tid] = make_ulonglong2(f2_pack(v[4], v[4]), f2_pack(v[5], v[5]));
-        sD[tid] = make_ulonglong2(f2_pack(v[6], v[6]), 0ull);
+        {
+            const int e = warp * 64 + lane;
+            sA[e] = sA[e + 32] = make_ulonglong2(f2_pack(v[0], v[0]), f2_pack(v[1], v[1]));
+            sB[e] = sB[e + 32] = make_ulonglong2(f2_pack(v[2], v[2]), f2_pack(v[3], v[3]));
+            sC[e] = sC[e + 32] = make_ulonglong2(f2_pack(v[4], v[4]), f2_pack(v[5], v[5]));
+            sD[e] = sD[e + 32] = make_ulonglong2(f2_pack(v[6], v[6]), 0ull);
+        }
         __syncthreads();
         if (diag) {      // one-sided over the tile's own particles (self pair: d = 0, u = 0)
             float blo = INFINITY, bhi = -INFINITY;
@@ -941,7 +946,8 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_pairs_sym(const A
             auto block = [&](auto minimg, const f2* Zt) {
 #pragma unroll 2
                 for (int k = 0; k < NT; ++k) {
-                    const ulonglong2 a = sA[k], b = sB[k], cc = sC[k], dd = sD[k];
+                    const int e = 64 * (k >> 5) + (k & 31);
+                    const ulonglong2 a = sA[e], b = sB[e], cc = sC[e], dd = sD[e];
                     const VjpJ J{a.x, a.y, b.x, b.y, cc.x, cc.y, dd.x};
                     f2 ux = 0ull, uy = 0ull, uz = 0ull, uq = 0ull;      // j sums: not used
 #pragma unroll
@@ -967,24 +973,26 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_pairs_sym(const A
         for (int g = 0; g < W; ++g) {
             const float2 zr = s_zr[g];
             const ZClass zc = zclass(ilo, ihi, zr.x, zr.y, L, dcz);
-            float jx = 0.f, jy = 0.f, jz = 0.f, jq = 0.f;
+            // the j sums stay packed (one half per i-half) and rotate as 64-bit shuffles; the
+            // halves are added once, back at home after 32 steps
+            f2 JX = 0ull, JY = 0ull, JZ = 0ull, JQ = 0ull;
+            const int from = (lane + 1) & 31;
+            const ulonglong2 *pA = sA + 64 * g + lane, *pB = sB + 64 * g + lane, *pC = sC + 64 * g + lane,
+                             *pD = sD + 64 * g + lane;
             auto group = [&](auto minimg, auto clamp, const f2* Zt) {
-#pragma unroll 2
+#pragma unroll 4
                 for (int k = 0; k < 32; ++k) {
-                    const int jj = g * 32 + ((lane + k) & 31);
-                    const ulonglong2 a = sA[jj], b = sB[jj], cc = sC[jj], dd = sD[jj];
+                    const ulonglong2 a = pA[k], b = pB[k], cc = pC[k], dd = pD[k];
                     const VjpJ J{a.x, a.y, b.x, b.y, cc.x, cc.y, dd.x};
-                    f2 JX = f2_pack(jx, 0.f), JY = f2_pack(jy, 0.f), JZ = f2_pack(jz, 0.f), JQ = f2_pack(jq, 0.f);
 #pragma unroll
                     for (int h = 0; h < H; ++h)
                         vjp_pair_x2_sym<decltype(minimg)::value, decltype(clamp)::value>(
                             X[h], Y[h], Zt[h], NQ[h], CX[h], CY[h], CZ[h], J, invL2, M2, nM2, nL2, c2, TX[h], TY[h],
                             TZ[h], QP[h], JX, JY, JZ, JQ);
-                    float l0, l1;
-                    f2_unpack(JX, l0, l1); jx = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
-                    f2_unpack(JY, l0, l1); jy = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
-                    f2_unpack(JZ, l0, l1); jz = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
-                    f2_unpack(JQ, l0, l1); jq = __shfl_sync(0xffffffffu, l0 + l1, (lane + 1) & 31);
+                    JX = __shfl_sync(0xffffffffu, JX, from);
+                    JY = __shfl_sync(0xffffffffu, JY, from);
+                    JZ = __shfl_sync(0xffffffffu, JZ, from);
+                    JQ = __shfl_sync(0xffffffffu, JQ, from);
                 }
             };
             if (zc.direct) {
@@ -997,10 +1005,11 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_pairs_sym(const A
             } else {
                 group(std::true_type{}, std::true_type{}, Z);
             }
-            s_jacc[warp][0][g * 32 + lane] = jx;
-            s_jacc[warp][1][g * 32 + lane] = jy;
-            s_jacc[warp][2][g * 32 + lane] = jz;
-            s_jacc[warp][3][g * 32 + lane] = jq;
+            float l0, l1;
+            f2_unpack(JX, l0, l1); s_jacc[warp][0][g * 32 + lane] = l0 + l1;
+            f2_unpack(JY, l0, l1); s_jacc[warp][1][g * 32 + lane] = l0 + l1;
+            f2_unpack(JZ, l0, l1); s_jacc[warp][2][g * 32 + lane] = l0 + l1;
+            f2_unpack(JQ, l0, l1); s_jacc[warp][3][g * 32 + lane] = l0 + l1;
         }
         __syncthreads();
         if (j < end) {     // j's terms carry the opposite sign
