@@ -39,7 +39,7 @@ NEWTON_FLOPS_PER_PAIR = 12   # per ordered pair
 NEWTON_FLOPS_PER_LANE_OP = 24.0 / 16.0
 # DRAM bytes per launch of the dominant kernel on 4,557,792 particles (ncu): k_step for pair variant 2,
 # k_pairs_sym for pair variant 3
-KSTEP_DRAM_BYTES = {2: 495.4e6, 3: 177.4e6}
+KSTEP_DRAM_BYTES = {2: 495.4e6, 3: 176.6e6}
 # pipe peaks measured by the project microbenchmarks (python -m paper_2205_04979_gb300.peaks)
 PEAKS_FILE = os.path.join(ROOT, "profiles", "peaks.md")
 
@@ -500,7 +500,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "instruction_mix": mix,
                      # dram bytes read + written per launch from ncu captures of the pair
-                     # kernels (pair variant 2: 495.4 MB, variant 3: 177.4 MB, both on
+                     # kernels (pair variant 2: 495.4 MB, variant 3: 176.6 MB, both on
                      # 4,557,792 particles), scaled by the particle count of this launch; null
                      # for a variant without a capture of its kernel
                      "traffic": KSTEP_DRAM_BYTES[cfg.variant] / 4557792 * float(np.sum(counts))
@@ -889,7 +889,7 @@ def clamp_check(pdq, stream, block, variant, samples, count, steps, st_plus, dt=
 
 def run_vdep_validation(args):
     """The metric's validity condition at scale: V_dep+ of the batched MIXED path (autotuned
-    launch configuration) against the FP64 GPU path, the latter pinned to the oracle by the
+    launch configuration, or --block / --variant) against the FP64 GPU path, the latter pinned to the oracle by the
     parity tests, on --samples samples of 4,096 particles over 1,200 steps (t+ = 60, window
     from t+ = 10), with enough samples for >= 1,000 FP64 deposits in every class St+ >= 1."""
     import torch
@@ -898,17 +898,21 @@ def run_vdep_validation(args):
     classes = args.vdep_classes
     stream = torch.cuda.Stream()
     w = workloads.WORKLOADS["batched_mixed"]
-    # the timed configuration of the MIXED step on this batch: autotuned
-    with torch.cuda.stream(stream):
-        phys = pdq.phys_default()
-        desc = pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
-        field = pdq.Field(desc, w["field_seed"], stream)
-        st = pdq.State(pdq.MIXED, [4096] * S, classes)
-        prm = pdq.params_tensor(workloads.sample_params(S, 4242))
-        pdq.seed_particles(field, phys, st, prm, w["particle_seed"], 0.0, stream)
-        cfg = pdq.step_cfg(w["dt"], window_start=0, compact_every=100)
-        pdq.autotune(field, phys, st, prm, cfg, stream)
-        del st
+    # the MIXED step's launch configuration: --block / --variant when given (e.g. the one the
+    # batched workload autotunes to), else autotuned on this batch
+    if args.block:
+        cfg = pdq.step_cfg(w["dt"], window_start=0, compact_every=100, block=args.block, variant=args.variant)
+    else:
+        with torch.cuda.stream(stream):
+            phys = pdq.phys_default()
+            desc = pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
+            field = pdq.Field(desc, w["field_seed"], stream)
+            st = pdq.State(pdq.MIXED, [4096] * S, classes)
+            prm = pdq.params_tensor(workloads.sample_params(S, 4242))
+            pdq.seed_particles(field, phys, st, prm, w["particle_seed"], 0.0, stream)
+            cfg = pdq.step_cfg(w["dt"], window_start=0, compact_every=100)
+            pdq.autotune(field, phys, st, prm, cfg, stream)
+            del st
     if args.clamp_check:
         res = clamp_check(pdq, stream, cfg.block, cfg.variant, S, 4096, args.vdep_steps, classes)
         print(json.dumps({"metric": "V_dep+ with the Coulomb clamp at the largest vs the smallest class diameter",
