@@ -66,7 +66,9 @@ struct ClassK {
     double stick;     // 2 A_cont gamma_c / (m zeta) = pi d^2 A0 / (24 pi delta_c^2 m) * ... (m^2/s^2 per unit zeta)
     double d3;        // d+^3 (mass ratios of the contact forces)
     double vdw_pp;    // particle-particle vdW: a+ = zeta * vdw_pp * d^6 / (delta^2 (2d+delta)^2 (d+delta)^3), SI lengths
+    double wall2;     // (R+ - d+/2)^2: contact when x^2 + y^2 reaches it (MIXED)
     float tau_f, inv_tau_f, d_plus_f, half_d_f, coul_f, img_f;
+    float vdw_reach_f;  // R+ - r below which the wall vdW term may act (3/4 d+, with a margin; MIXED screen)
 };
 
 struct StepConst {

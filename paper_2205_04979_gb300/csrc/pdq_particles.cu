@@ -76,6 +76,8 @@ int make_step_const(const pdq_field* f, const pdq_phys* p, const pdq_state* st, 
         k.half_d_f = (float)k.half_d;
         k.coul_f = (float)k.coul;
         k.img_f = (float)(0.25 * k.coul);                     // image at distance 2y: coul / 4 / y^2
+        k.wall2 = (f->desc.r_plus - k.half_d) * (f->desc.r_plus - k.half_d);
+        k.vdw_reach_f = (float)(0.75 * k.d_plus * 1.001 + 1e-6);   // gap + d/2 <= d/4 + d/2, widened
         if (k.d_plus > dmax) dmax = k.d_plus;
     }
     K->R = f->desc.r_plus;
@@ -229,39 +231,58 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
         a[0] += (T)K.grav[0]; a[1] += (T)K.grav[1]; a[2] += (T)K.grav[2];
     }
     if constexpr (CT) { a[0] += (T)cx; a[1] += (T)cy; a[2] += (T)cz; }
-    const double r = sqrt(x * x + y * y);
-    if (r > 0.0 && (K.forces & (PDQ_F_IMAGE | PDQ_F_VDW))) {
-        double aw = 0.0;   // toward the wall
-        if (K.forces & PDQ_F_IMAGE) {
-            // image of opposite sign mirrored across the wall: q^2 / (4 pi eps0 (2y)^2 m), y >= d/2
-            if (P == PDQ_FP64) {
+    // 2 F_vw(delta) at the gap delta (m): Eq. (vdw) written as A d^6 / (6 delta^2 (2d+delta)^2 (d+delta)^3),
+    // zero beyond d/4 and saturated at delta_min
+    auto vdw_wall = [&](double gap) {
+        if (!(gap <= 0.25 * c.d_m)) return 0.0;
+        const double dl = fmax(gap, K.delta_min);
+        const double d = c.d_m;
+        const double d2 = d * d, d6 = d2 * d2 * d2;
+        const double e1 = 2.0 * d + dl, e2 = d + dl;
+        return sp.zeta * c.vdw * d6 / (dl * dl * e1 * e1 * e2 * e2 * e2);
+    };
+    const double r2 = x * x + y * y;
+    T rT;                  // radius for the field interpolation
+    if constexpr (P == PDQ_FP64) {
+        const double r = sqrt(r2);
+        rT = r;
+        if (r > 0.0 && (K.forces & (PDQ_F_IMAGE | PDQ_F_VDW))) {
+            double aw = 0.0;   // toward the wall
+            if (K.forces & PDQ_F_IMAGE) {
+                // image of opposite sign mirrored across the wall: q^2 / (4 pi eps0 (2y)^2 m), y >= d/2
                 const double yw = fmax(K.R - r, c.half_d);
                 aw += 0.25 * c.coul * (double)q * (double)q / (yw * yw);
-            } else {
-                const float yw = fmaxf((float)(K.R - r), c.half_d_f);
-                aw += (double)(c.img_f * (float)q * (float)q / (yw * yw));
             }
+            if (K.forces & PDQ_F_VDW) aw += vdw_wall((K.R - r - c.half_d) * K.ell);
+            const double inv_r = 1.0 / r;
+            a[0] += (T)(aw * x * inv_r);
+            a[1] += (T)(aw * y * inv_r);
         }
-        if (K.forces & PDQ_F_VDW) {
-            // 2 F_vw(delta): Eq. (vdw) written as A d^6 / (6 delta^2 (2d+delta)^2 (d+delta)^3)
-            const double gap = (K.R - r - c.half_d) * K.ell;
-            if (gap <= 0.25 * c.d_m) {
-                const double dl = fmax(gap, K.delta_min);
-                const double d = c.d_m;
-                const double d2 = d * d, d6 = d2 * d2 * d2;
-                const double e1 = 2.0 * d + dl, e2 = d + dl;
-                aw += sp.zeta * c.vdw * d6 / (dl * dl * e1 * e1 * e2 * e2 * e2);
+    } else {
+        // The wall distance R - r = (R^2 - r^2) / (R + r): the difference in FP64 (no cancellation
+        // near the wall), the quotient and the force direction in FP32 (the forces are FP32); the
+        // vdW gap in FP64 from the FP64 radius, taken only near the wall.
+        rT = sqrtf((float)r2);
+        if (r2 > 0.0 && (K.forces & (PDQ_F_IMAGE | PDQ_F_VDW))) {
+            const float yw0 = (float)(K.R * K.R - r2) / (K.Rf + rT);
+            float aw = 0.f;    // toward the wall
+            if (K.forces & PDQ_F_IMAGE) {
+                const float yw = fmaxf(yw0, c.half_d_f);
+                aw = c.img_f * (float)q * (float)q / (yw * yw);
             }
+            if ((K.forces & PDQ_F_VDW) && yw0 <= c.vdw_reach_f)
+                aw = (float)((double)aw + vdw_wall((K.R - sqrt(r2) - c.half_d) * K.ell));
+            const float ir = 1.0f / rT;
+            a[0] += aw * (p4.x * ir);
+            a[1] += aw * (p4.y * ir);
         }
-        const double inv_r = 1.0 / r;
-        a[0] += (T)(aw * x * inv_r);
-        a[1] += (T)(aw * y * inv_r);
     }
     T v[3] = {v4.x, v4.y, v4.z};
     T u[3] = {(T)0, (T)0, (T)0};
     T lam = (T)0;
     if (K.forces & PDQ_F_DRAG) {
-        interp<T, T4>(K, (T)r, (T)x, (T)y, z, u);
+        if constexpr (P == PDQ_FP64) interp<T, T4>(K, rT, (T)x, (T)y, z, u);
+        else interp<T, T4>(K, rT, p4.x, p4.y, z, u);       // p4.x, p4.y: x, y rounded to FP32
         const T rx = u[0] - v[0], ry = u[1] - v[1], rz = u[2] - v[2];
         const T re = sqrt_(rx * rx + ry * ry + rz * rz) * (P == PDQ_FP64 ? (T)c.d_plus : (T)c.d_plus_f);
         const T fd = (T)1 + (T)0.15 * (re > (T)0 ? pow_(re, (T)0.687) : (T)0);   // Schiller-Naumann
@@ -285,11 +306,20 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
     zn -= (T)K.L * floor_(zn * (T)K.invL);
     if (zn >= (T)K.L) zn -= (T)K.L;
     if (zn < (T)0) zn = (T)0;
-    // wall contact: gap R - r - d/2 <= 0 (App. A: removal on impact)
-    const double rn = sqrt(xn * xn + yn * yn);
-    const double gapn = K.R - rn - c.half_d;
+    // wall contact: gap R - r - d/2 <= 0 (App. A: removal on impact); MIXED compares r^2 with
+    // (R - d/2)^2 in FP64 and takes the square root only on contact
+    double rn;
+    bool contact;
+    if constexpr (P == PDQ_FP64) {
+        rn = sqrt(xn * xn + yn * yn);
+        contact = K.R - rn - c.half_d <= 0.0;
+    } else {
+        const double rn2 = xn * xn + yn * yn;
+        contact = rn2 >= c.wall2;
+        rn = contact ? sqrt(rn2) : 0.0;
+    }
     bool alive = true;
-    if (gapn <= 0.0) {
+    if (contact) {
         bool stick = true;
         if (K.mode == PDQ_REBOUND) {
             // Bons et al. (Sec. 4.3): CoR_n = sqrt(sigma_y^2/(rho_p E) - 2 A_cont gamma_c / m) / V_n1
@@ -311,8 +341,7 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
         }
         if (stick) { alive = false; dep = true; }
     }
-    if (!(isfinite(xn) && isfinite(yn) && isfinite((double)zn) && isfinite((double)v[0]) &&
-          isfinite((double)v[1]) && isfinite((double)v[2])))
+    if (!(isfinite(xn) && isfinite(yn) && isfinite(zn) && isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2])))
         atomicOr((unsigned long long*)&A.ctl[CTL_ERROR], (unsigned long long)ERR_NONFINITE);
     if (P == PDQ_FP64) {
         ((double4_32a*)A.pos_out)[g] = make_double4_32a(xn, yn, (double)zn, alive ? (double)q : 0.0);

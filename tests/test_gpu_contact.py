@@ -198,16 +198,17 @@ def test_fp64_contact_terms_separately(pdq, fields, forces):
     _compare(st, ost, off, max(1e-9, 10 * sx), max(1e-9, 10 * sv))
 
 
-@pytest.mark.parametrize("compact_every,variant", [(0, 0), (5, 0), (0, 3), (5, 3)])
-def test_mixed_contact_parity(pdq, fields, compact_every, variant):
+@pytest.mark.parametrize("compact_every,variant,block", [(0, 0, 64), (5, 0, 64), (0, 3, 64), (5, 3, 64), (0, 3, 128)])
+def test_mixed_contact_parity(pdq, fields, compact_every, variant, block):
     # MIXED rounds z to FP32 every step: the bound is the oracle's response to one FP32 unit of
     # z, times the number of steps.  Variant 3: Coulomb sums by Newton pairs, contact forces in
-    # the contact variant that takes them.
+    # the contact variant that takes them; at 128 threads each sample is one 1,024-particle tile
+    # whose four warp blocks are full, nearly empty (5 of 517) or empty.
     counts = [517, 301]
     arr = _contact_state(counts, 6, z_range=(2.0, 12.0))
     fl = oracle.F_ALL | oracle.F_CONTACT
-    st, tally, ost, off, nd, na = _run(pdq, fields, 1, counts, arr, 30, fl, block=64, compact_every=compact_every,
-                                       variant=variant)
+    st, tally, ost, off, nd, na = _run(pdq, fields, 1, counts, arr, 30, fl, block=block,
+                                       compact_every=compact_every, variant=variant)
     sx, sv = _oracle_sensitivity(counts, arr, 30, fl, z_ulp32=True)
     _compare(st, ost, off, max(2e-5, 30 * sx), max(2e-3, 30 * sv))
 
