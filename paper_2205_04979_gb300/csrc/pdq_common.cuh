@@ -89,7 +89,9 @@ struct StepConst {
     double near;             // range of the contact forces: 1.25 x largest diameter, wall units
     double col_k, col_h;     // collision spring and damping rates per unit effective mass (wall units)
     double inv_beta, tanh_beta;
+    double R2;               // R^2
     float Rf, Lf, invLf, contact2f, dtf, inv_beta_f, tanh_beta_f, gravf[3];
+    float th_scale_f, z_scale_f;   // n_th / (2 pi) and n_z / L: cell index per radian and per unit z
     const double4_32a* grid64;
     const float4* grid32;
 };

@@ -3,6 +3,8 @@
 // scalar Coulomb pair.
 #pragma once
 
+#include <type_traits>
+
 #include "pdq_common.cuh"
 
 namespace pdq {
@@ -71,21 +73,27 @@ __device__ __forceinline__ void interp(const StepConst& K, T r, T x, T y, T z, T
         u[0] = u[1] = u[2] = (T)NAN;
         return;
     }
-    const T R = (T)K.R;
+    // the constants in T (their FP32 copies rounded once on the host, so no conversion here)
+    T R, tanh_b, inv_b, th_scale, z_scale;
+    if constexpr (std::is_same<T, float>::value) {
+        R = K.Rf; tanh_b = K.tanh_beta_f; inv_b = K.inv_beta_f; th_scale = K.th_scale_f; z_scale = K.z_scale_f;
+    } else {
+        R = K.R; tanh_b = K.tanh_beta; inv_b = K.inv_beta; th_scale = K.n_th / (2.0 * kPi); z_scale = K.n_z * K.invL;
+    }
     const T rho = fmin(r / R, (T)1);
-    const T s = atanh_(rho * (T)K.tanh_beta) * (T)K.inv_beta;
+    const T s = atanh_(rho * tanh_b) * inv_b;
     const T fi = s * (T)(K.n_r - 1);
     int i0 = (int)floor_(fi);
     i0 = i0 < 0 ? 0 : (i0 > K.n_r - 2 ? K.n_r - 2 : i0);
     const T tr = fi - (T)i0;
-    T fj = atan2_(y, x) * (T)(K.n_th / (2.0 * kPi));
+    T fj = atan2_(y, x) * th_scale;
     if (fj < (T)0) fj += (T)K.n_th;
     int j0 = (int)floor_(fj);
     const T tt = fj - (T)j0;
     j0 %= K.n_th;                    // any int (also a non-finite input's) maps into [0, n_th)
     if (j0 < 0) j0 += K.n_th;
     const int j1 = (j0 + 1 == K.n_th) ? 0 : j0 + 1;
-    const T fk = z * (T)(K.n_z * K.invL);
+    const T fk = z * z_scale;
     int k0 = (int)floor_(fk);
     const T tz = fk - (T)k0;
     k0 %= K.n_z;

@@ -92,6 +92,9 @@ int make_step_const(const pdq_field* f, const pdq_phys* p, const pdq_state* st, 
     K->inv_beta = 1.0 / f->desc.beta;
     K->tanh_beta = tanh(f->desc.beta);
     K->n_r = f->desc.n_r; K->n_th = f->desc.n_th; K->n_z = f->desc.n_z;
+    K->R2 = K->R * K->R;
+    K->th_scale_f = (float)(K->n_th / (2.0 * kPi));
+    K->z_scale_f = (float)(K->n_z * K->invL);
     K->Rf = (float)K->R; K->Lf = (float)K->L; K->invLf = (float)K->invL;
     K->contact2f = (float)K->contact2;
     K->inv_beta_f = (float)K->inv_beta; K->tanh_beta_f = (float)K->tanh_beta;
@@ -228,7 +231,8 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
         a[0] = kq * acx; a[1] = kq * acy; a[2] = kq * acz;
     }
     if (K.forces & PDQ_F_GRAVITY) {
-        a[0] += (T)K.grav[0]; a[1] += (T)K.grav[1]; a[2] += (T)K.grav[2];
+        if constexpr (P == PDQ_FP64) { a[0] += K.grav[0]; a[1] += K.grav[1]; a[2] += K.grav[2]; }
+        else { a[0] += K.gravf[0]; a[1] += K.gravf[1]; a[2] += K.gravf[2]; }
     }
     if constexpr (CT) { a[0] += (T)cx; a[1] += (T)cy; a[2] += (T)cz; }
     // 2 F_vw(delta) at the gap delta (m): Eq. (vdw) written as A d^6 / (6 delta^2 (2d+delta)^2 (d+delta)^3),
@@ -264,7 +268,7 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
         // vdW gap in FP64 from the FP64 radius, taken only near the wall.
         rT = sqrtf((float)r2);
         if (r2 > 0.0 && (K.forces & (PDQ_F_IMAGE | PDQ_F_VDW))) {
-            const float yw0 = (float)(K.R * K.R - r2) / (K.Rf + rT);
+            const float yw0 = (float)(K.R2 - r2) / (K.Rf + rT);
             float aw = 0.f;    // toward the wall
             if (K.forces & PDQ_F_IMAGE) {
                 const float yw = fmaxf(yw0, c.half_d_f);
@@ -288,7 +292,7 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
         const T fd = (T)1 + (T)0.15 * (re > (T)0 ? pow_(re, (T)0.687) : (T)0);   // Schiller-Naumann
         lam = fd * (P == PDQ_FP64 ? (T)(1.0 / c.tau) : (T)c.inv_tau_f);
     }
-    const T h = (T)K.dt;
+    const T h = P == PDQ_FP64 ? (T)K.dt : (T)K.dtf;
     const T zz = -lam * h;
     T p1, p2;
     phi12(zz, p1, p2);
@@ -303,8 +307,9 @@ __device__ __forceinline__ void local_update(const StepArgs& A, int64_t g, typen
     double xn = x + (double)dxv[0];
     double yn = y + (double)dxv[1];
     T zn = z + dxv[2];
-    zn -= (T)K.L * floor_(zn * (T)K.invL);
-    if (zn >= (T)K.L) zn -= (T)K.L;
+    const T Lz = P == PDQ_FP64 ? (T)K.L : (T)K.Lf, invLz = P == PDQ_FP64 ? (T)K.invL : (T)K.invLf;
+    zn -= Lz * floor_(zn * invLz);
+    if (zn >= Lz) zn -= Lz;
     if (zn < (T)0) zn = (T)0;
     // wall contact: gap R - r - d/2 <= 0 (App. A: removal on impact); MIXED compares r^2 with
     // (R - d/2)^2 in FP64 and takes the square root only on contact
