@@ -107,21 +107,22 @@ __device__ __forceinline__ void interp_jac(const StepConst& K, double r, double 
         return;
     }
     // derivatives of the trilinear weights in (s(r), theta, z) chained to (x, y, z)
-    const T R = (T)K.R;
+    const GridT<T> G(K);
+    const T R = G.R;
     const T rho = fmin((T)r / R, (T)1);
-    const T s = atanh_(rho * (T)K.tanh_beta) * (T)K.inv_beta;
+    const T s = atanh_(rho * G.tanh_b) * G.inv_b;
     const T fi = s * (T)(K.n_r - 1);
     int i0 = (int)floor_(fi);
     i0 = i0 < 0 ? 0 : (i0 > K.n_r - 2 ? K.n_r - 2 : i0);
     const T tr = fi - (T)i0;
-    T fj = atan2_((T)y, (T)x) * (T)(K.n_th / (2.0 * kPi));
+    T fj = atan2_((T)y, (T)x) * G.th_scale;
     if (fj < (T)0) fj += (T)K.n_th;
     int j0 = (int)floor_(fj);
     const T tt = fj - (T)j0;
     j0 %= K.n_th;
     if (j0 < 0) j0 += K.n_th;
     const int j1 = (j0 + 1 == K.n_th) ? 0 : j0 + 1;
-    const T fk = z * (T)(K.n_z * K.invL);
+    const T fk = z * G.z_scale;
     int k0 = (int)floor_(fk);
     const T tz = fk - (T)k0;
     k0 %= K.n_z;
@@ -149,19 +150,19 @@ __device__ __forceinline__ void interp_jac(const StepConst& K, double r, double 
     // d tr / d r, d tt / d(x, y), d tz / dz
     T dsdr = (T)0;
     if ((T)r < R) {
-        const T a = rho * (T)K.tanh_beta;
-        dsdr = (T)K.tanh_beta * (T)K.inv_beta / (R * ((T)1 - a * a));
+        const T a = rho * G.tanh_b;
+        dsdr = G.tanh_b * G.inv_b / (R * ((T)1 - a * a));
     }
     const T dtr_dr = dsdr * (T)(K.n_r - 1);
     T drdx = 0, drdy = 0, dthdx = 0, dthdy = 0;
     if (r > 1e-12) {
         drdx = (T)(x / r);
         drdy = (T)(y / r);
-        const T k2 = (T)(K.n_th / (2.0 * kPi)) / (T)(r * r);
+        const T k2 = G.th_scale / (T)(r * r);
         dthdx = -(T)y * k2;
         dthdy = (T)x * k2;
     }
-    const T dtz_dz = (T)(K.n_z * K.invL);
+    const T dtz_dz = G.z_scale;
     for (int k = 0; k < 3; ++k) {
         du[k][0] = dtr[k] * dtr_dr * drdx + dtt[k] * dthdx;
         du[k][1] = dtr[k] * dtr_dr * drdy + dtt[k] * dthdy;
@@ -217,7 +218,8 @@ __device__ __forceinline__ void local_step(const AdjArgs& A, const ClassK& c, co
         L.a[0] = kq * sx; L.a[1] = kq * sy; L.a[2] = kq * sz;
     }
     if (K.forces & PDQ_F_GRAVITY) {
-        L.a[0] += (T)K.grav[0]; L.a[1] += (T)K.grav[1]; L.a[2] += (T)K.grav[2];
+        if constexpr (P == PDQ_FP64) { L.a[0] += K.grav[0]; L.a[1] += K.grav[1]; L.a[2] += K.grav[2]; }
+        else { L.a[0] += K.gravf[0]; L.a[1] += K.gravf[1]; L.a[2] += K.gravf[2]; }
     }
     L.r = sqrt(L.x * L.x + L.y * L.y);
     L.A = 0.0; L.dAdr = 0.0; L.img_q = 0.0; L.vdw_z = 0.0;
@@ -262,7 +264,7 @@ __device__ __forceinline__ void local_step(const AdjArgs& A, const ClassK& c, co
         const T fd = (T)1 + (T)0.15 * (L.Re > (T)0 ? pow_(L.Re, (T)0.687) : (T)0);
         L.lam = fd * (P == PDQ_FP64 ? (T)(1.0 / c.tau) : (T)c.inv_tau_f);
     }
-    const T h = (T)K.dt;
+    const T h = P == PDQ_FP64 ? (T)K.dt : (T)K.dtf;
     L.zz = -L.lam * h;
     phi12(L.zz, L.p1, L.p2);
     L.e = exp_(L.zz);
@@ -276,8 +278,9 @@ __device__ __forceinline__ void local_step(const AdjArgs& A, const ClassK& c, co
     L.xn = L.x + (double)dxv[0];
     L.yn = L.y + (double)dxv[1];
     T zn = L.z + dxv[2];
-    zn -= (T)K.L * floor_(zn * (T)K.invL);
-    if (zn >= (T)K.L) zn -= (T)K.L;
+    const T Lz = P == PDQ_FP64 ? (T)K.L : (T)K.Lf, invLz = P == PDQ_FP64 ? (T)K.invL : (T)K.invLf;
+    zn -= Lz * floor_(zn * invLz);
+    if (zn >= Lz) zn -= Lz;
     if (zn < (T)0) zn = (T)0;
     L.zn = zn;
     L.rn = sqrt(L.xn * L.xn + L.yn * L.yn);

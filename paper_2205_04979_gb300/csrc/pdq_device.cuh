@@ -66,6 +66,22 @@ __device__ __forceinline__ float4 grid_at(const StepConst& K, const float4*, int
 
 // Trilinear interpolation in (s(r), theta, z) index space: s = atanh(r tanh(beta)/R)/beta
 // inverts the node stretching; theta and z are periodic; s is clamped to [0, 1].
+// The field-geometry constants in T: for float the FP32 copies rounded once on the host (the
+// same values as converting the doubles here, without the per-particle conversions and the FP64
+// division n_th / 2 pi); for double the doubles.
+template <class T>
+struct GridT {
+    T R, tanh_b, inv_b, th_scale, z_scale;
+    __device__ __forceinline__ explicit GridT(const StepConst& K) {
+        if constexpr (std::is_same<T, float>::value) {
+            R = K.Rf; tanh_b = K.tanh_beta_f; inv_b = K.inv_beta_f; th_scale = K.th_scale_f; z_scale = K.z_scale_f;
+        } else {
+            R = K.R; tanh_b = K.tanh_beta; inv_b = K.inv_beta; th_scale = K.n_th / (2.0 * kPi);
+            z_scale = K.n_z * K.invL;
+        }
+    }
+};
+
 template <class T, class T4>
 __device__ __forceinline__ void interp(const StepConst& K, T r, T x, T y, T z, T u[3]) {
     if (!(isfinite(r) && isfinite(x) && isfinite(y) && isfinite(z))) {
@@ -73,13 +89,8 @@ __device__ __forceinline__ void interp(const StepConst& K, T r, T x, T y, T z, T
         u[0] = u[1] = u[2] = (T)NAN;
         return;
     }
-    // the constants in T (their FP32 copies rounded once on the host, so no conversion here)
-    T R, tanh_b, inv_b, th_scale, z_scale;
-    if constexpr (std::is_same<T, float>::value) {
-        R = K.Rf; tanh_b = K.tanh_beta_f; inv_b = K.inv_beta_f; th_scale = K.th_scale_f; z_scale = K.z_scale_f;
-    } else {
-        R = K.R; tanh_b = K.tanh_beta; inv_b = K.inv_beta; th_scale = K.n_th / (2.0 * kPi); z_scale = K.n_z * K.invL;
-    }
+    const GridT<T> G(K);
+    const T R = G.R, tanh_b = G.tanh_b, inv_b = G.inv_b, th_scale = G.th_scale, z_scale = G.z_scale;
     const T rho = fmin(r / R, (T)1);
     const T s = atanh_(rho * tanh_b) * inv_b;
     const T fi = s * (T)(K.n_r - 1);
