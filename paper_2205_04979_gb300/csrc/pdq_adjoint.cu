@@ -867,7 +867,8 @@ __device__ __forceinline__ void vjp_pair_x2_sym(f2 xm, f2 ym, f2 zm, f2 nQm, f2 
 
 // Pair VJP with Newton pairs (MIXED), the scheme of newton_tile: grid (samples, m-tiles of
 // NT*U), heavy first tiles first; warp w holds the m-particles [32 U w, 32 U (w + 1)) of the
-// tile, a contiguous run of the z-binned checkpoint (narrow z range: fewer clamped groups); the tile's own block one-sided (the j sums of vjp_pair_x2_sym left unused), every
+// tile, a contiguous run of the z-binned checkpoint (narrow z range: fewer clamped groups); the
+// tile's own block one-sided (the j sums of vjp_pair_x2_sym left unused), every
 // later particle of the sample as a Newton pair with 32-j groups walked by skewed lanes.  Sums
 // (x-bar x, y, z, Qp) go to A.acc4 by float4 atomics; k_adj_pairs_finish applies them.
 template <int NT, int U>

@@ -994,8 +994,8 @@ __global__ void __launch_bounds__(NT, ((V == 4 || V == 6) && P == PDQ_MIXED) ? 6
 // device count return at once.  The hardware hands out CTAs in index order as SMs free up,
 // which balances the triangular per-tile work like a queue would: a persistent CTA looping
 // over a queue measured ~5 more register moves per packed pair evaluation in the hot loop.
-// Each CTA sums its tile's pairs with newton_tile (its own block one-sided, every later
-// particle of the sample as Newton pairs).
+// Each CTA sums its tile's pairs with newton_tile (Newton pairs between the warps' blocks of the
+// tile and with every later particle of the sample; one-sided only within a warp's block).
 // Register budget: 3 CTAs of 128 threads per SM (168 registers) for 12 particles per thread (8 per
 // thread ran 1 % faster at 4 CTAs and 128 registers than at 3), 6 CTAs of 64.
 template <int NT, int U>
@@ -1547,7 +1547,8 @@ static int launch_newton(const StepArgs& A, cudaStream_t s) {
 }
 
 // variant: MIXED pair math, 0 = all packed f32x2, 1 = packed with scalar accumulation,
-// 2 = as 0 with 8 particles per thread, 3 = Newton pairs (A.acc4 set; not with contact).
+// 2 = as 0 with 8 particles per thread, 3 = Newton pairs (A.acc4 set: k_pairs_sym, then the
+// given-sums step, or with contact the contact variant that takes the sums).
 // contact: the particle-particle contact variant (V = 4), whatever the variant; given
 // Coulomb sums (A.ext, P3M): V = 5, no pair loop.
 static int dispatch_step(int prec, int NT, int variant, bool contact, const StepArgs& A, cudaStream_t s) {
