@@ -552,8 +552,13 @@ def run_adjoint_config4(args):
         prm = pdq.params_tensor(params)
         C = len(w["st_plus"])
         gbar = torch.ones((1, S, C), dtype=torch.float64, device="cuda")   # d(sum_c J_c)/d(xi, zeta, theta)
-        ws = pdq.adjoint_workspace(batch.b, steps, K)
+        # keep every step's Newton-pair sums for the reverse sweep when the GPU has room for them
+        need = pdq.adjoint_workspace_bytes(batch.b, steps, K)
+        extra = pdq.adjoint_workspace_bytes(batch.b, steps, K, store_sums=True) - need
+        store = torch.cuda.mem_get_info()[0] > need + extra + (8 << 30)
+        ws = pdq.adjoint_workspace(batch.b, steps, K, store_sums=store)
         out["workspace_bytes"] = int(ws.numel())
+        out["stored_sums"] = bool(store)
         pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, 4, 2, w["eps"][0], w["particle_seed"], gbar=gbar,
                                stream=stream)             # warm-up
         for eps in w["eps"]:
@@ -577,7 +582,9 @@ def run_adjoint_config4(args):
 
 
 def run_adjoint(args):
-    """Forward + reverse sweep of the smoothed-V_dep adjoint on 256 samples x 16,384 particles."""
+    """Forward + reverse sweep of the smoothed-V_dep adjoint on 256 samples x 16,384 particles, with
+    the forward sweep's Newton-pair sums kept for the reverse sweep (and, for comparison, with the
+    reverse sweep recomputing them)."""
     import torch
     import paper_2205_04979_gb300.pdq as pdq
     if args.adjoint_config4:
@@ -596,27 +603,36 @@ def run_adjoint(args):
         cfg = pdq.step_cfg(w["dt"], window_start=0)
         prm = pdq.params_tensor(params)
         gbar = torch.ones((1, S, len(w["st_plus"])), dtype=torch.float64, device="cuda")
-        pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, max(2, args.warmup), 1, w["eps"][1],
-                               w["particle_seed"], gbar=gbar, stream=stream)
-        stream.synchronize()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        e[0].record(stream)
-        J, _ = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, args.steps, K, w["eps"][1],
-                                      w["particle_seed"], stream=stream)
-        e[1].record(stream)
-        J2, pbar = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, args.steps, K, w["eps"][1],
-                                          w["particle_seed"], gbar=gbar, stream=stream)
-        e[2].record(stream)
-        e[2].synchronize()
-    fwd_ms, tot_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        timed = {}
+        for store in (False, True):
+            pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, max(2, args.warmup), 1, w["eps"][1],
+                                   w["particle_seed"], gbar=gbar, stream=stream, store_sums=store)
+            ws = pdq.adjoint_workspace(batch.b, args.steps, K, store_sums=store)
+            stream.synchronize()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            J, _ = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, args.steps, K, w["eps"][1],
+                                          w["particle_seed"], stream=stream, ws=ws)
+            e[1].record(stream)
+            J2, pbar = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, args.steps, K, w["eps"][1],
+                                              w["particle_seed"], gbar=gbar, stream=stream, ws=ws)
+            e[2].record(stream)
+            e[2].synchronize()
+            timed[store] = (e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), J2, pbar)
+            del ws
+    fwd_ms, tot_ms, J2, pbar = timed[True]
+    rec_ms = timed[False][1]
     psteps = float(S) * w["count"] * args.steps
     out = {"metric": "gradient particle-steps/s (smoothed V_dep, forward + reverse sweep)",
            "value": psteps / (tot_ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": "adjoint: %d samples x %d particles, classes %s, checkpoint every %d steps, "
-                                  "eps+=%g" % (S, w["count"], w["st_plus"], K, w["eps"][1])},
+                                  "eps+=%g, forward sweep's pair sums kept for the reverse sweep"
+                                  % (S, w["count"], w["st_plus"], K, w["eps"][1])},
            "forward_only": {"value": psteps / (fwd_ms / 1e3), "unit": "particle-steps/s"},
+           "recomputed_sums": {"value": psteps / (rec_ms / 1e3), "unit": "particle-steps/s",
+                               "ms_per_step": rec_ms / args.steps},
            "grad_mean_abs": np.abs(pbar.cpu().numpy()).mean(axis=(0, 1)).tolist(),
            "J_mean": J2.mean(0).cpu().numpy().tolist()}
     print(json.dumps(out), flush=True)

@@ -387,6 +387,21 @@ typedef struct pdq_batch {
 int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_steps, int32_t K, size_t* bytes);
 int pdq_adjoint_state_workspace_size(const pdq_state* init, int64_t n_steps, int32_t K, size_t* bytes);
 
+/* Extra workspace bytes that let PDQ_MIXED adjoints with Coulomb forces keep
+ * the forward sweep's Newton-pair sums (App. A.2 Coulomb sum, one float4 per
+ * particle per step: 16 B x capacity x n_steps, plus a 256-byte marker).
+ * When the workspace passed to pdq_adjoint_run(_seeded) holds at least the
+ * layout size plus these bytes, the forward sweep accumulates each step's sums
+ * in this region and the reverse sweep's recompute of each segment reuses them
+ * instead of summing the pairs again (the recomputed states then equal the
+ * forward sweep's exactly); J and pbar are the same functional and gradient.
+ * pdq_adjoint_reverse decides the same way from its workspace_bytes, so pass
+ * it the size the forward call had; with the extra bytes it returns
+ * INVALID_ARG unless the region holds the sums of a forward sweep with the
+ * same n_steps, K and capacity.  FP64 or Coulomb-free runs ignore the region.
+ * Errors: INVALID_ARG (capacity < 0, n_steps < 1, bytes NULL).              */
+int pdq_adjoint_stored_sums_size(int64_t capacity, int64_t n_steps, size_t* bytes);
+
 /* Smoothed deposition functional and its hand-written reverse-mode adjoint,
  * starting from the caller's particle state `init` (e.g. one that
  * pdq_step_particles has advanced through a transient).
@@ -419,7 +434,8 @@ int pdq_adjoint_state_workspace_size(const pdq_state* init, int64_t n_steps, int
  * particles (float sums through atomics, so not bit-reproducible from run to
  * run) and takes at most 33,553,920 particles per sample.  Contact forces
  * (PDQ_F_CONTACT) are not differentiated: cfg->forces must lie in PDQ_F_ALL.
- * workspace: device, 256-byte aligned, >= pdq_adjoint_state_workspace_size.
+ * workspace: device, 256-byte aligned, >= pdq_adjoint_state_workspace_size
+ * (plus pdq_adjoint_stored_sums_size to keep the forward sweep's pair sums).
  * Errors: INVALID_ARG, WORKSPACE, UNSUPPORTED (sample too large), CUDA.     */
 int pdq_adjoint_run(const pdq_field* field, const pdq_phys* phys, const pdq_state* init,
                     const pdq_sample_params* params, const pdq_step_cfg* cfg, int64_t n_steps, int32_t K,

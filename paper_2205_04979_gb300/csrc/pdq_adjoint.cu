@@ -1106,9 +1106,21 @@ static AdjLayout adj_layout(int64_t N, int32_t S, int32_t C, int64_t n_steps, in
     return L;
 }
 
+// Stored Newton-pair sums, past the layout: a 256-byte marker, then one float4 [capacity] array
+// per step.
+static size_t adj_sums_bytes(int64_t N, int64_t n_steps) {
+    return 256 + a256(sizeof(float) * 4 * (size_t)(N > 0 ? N : 1)) * (size_t)n_steps;
+}
+
 }  // namespace pdq
 
 using namespace pdq;
+
+extern "C" int pdq_adjoint_stored_sums_size(int64_t capacity, int64_t n_steps, size_t* bytes) {
+    if (!bytes || capacity < 0 || n_steps < 1) return PDQ_ERR_INVALID_ARG;
+    *bytes = adj_sums_bytes(capacity, n_steps);
+    return PDQ_OK;
+}
 
 extern "C" int pdq_adjoint_workspace_size(const pdq_batch* batch, int64_t n_steps, int32_t K, size_t* bytes) {
     if (!batch || !bytes || batch->n_samples < 1 || batch->n_classes < 1 || batch->n_classes > PDQ_MAX_CLASSES ||
@@ -1212,6 +1224,16 @@ static int adjoint_impl(const pdq_field* field, const pdq_phys* phys, const pdq_
     double* nbar = (double*)take(sc);
     double* dbar = (double*)take(sc);
     A.nbar = nbar; A.dbar = dbar;
+    // MIXED with Coulomb forces and room past the layout: every step's Newton-pair sums are kept
+    // (the forward sweep accumulates them in place), so the reverse sweep's segment recompute
+    // reruns only the local part; the marker ties them to the forward sweep that wrote them
+    const bool newton_sums = batch->precision == PDQ_MIXED && (A.K.forces & PDQ_F_COULOMB);
+    const bool store = newton_sums && workspace_bytes >= need + adj_sums_bytes(N, n_steps);
+    int64_t* const marker = store ? (int64_t*)take(256) : nullptr;
+    const size_t sums_stride = a256(sizeof(float) * 4 * (size_t)(N > 0 ? N : 1));
+    char* const sums_base = store ? p : nullptr;
+    float4* const acc_scratch = A.acc4;
+    const int64_t mark[4] = {0x70647153756d7331LL, n_steps, K, N};
 
     // largest sample -> tiles per grid row
     std::vector<int64_t> off(A.S + 1);
@@ -1236,13 +1258,19 @@ static int adjoint_impl(const pdq_field* field, const pdq_phys* phys, const pdq_
     constexpr int US = 12;   // forward sums: 12 particles per thread (as the step's Newton kernel)
     const dim3 grid_sums((unsigned)A.S, (unsigned)((nmax + US * NTN - 1) / (US * NTN)));
     const dim3 grid_vjp((unsigned)A.S, (unsigned)((nmax + 4 * NTN - 1) / (4 * NTN)));
-    auto fwd = [&](const Slot& in, const Slot& out, int64_t step, int tally) -> cudaError_t {
+    // one forward step; `recompute`: a step of the reverse sweep's segment recompute, which takes
+    // the stored sums when there are any
+    auto fwd = [&](const Slot& in, const Slot& out, int64_t step, int tally, bool recompute) -> cudaError_t {
         A.in = in; A.out = out; A.step = step; A.tally = tally;
         if (newton) {
-            const cudaError_t e = cudaMemsetAsync(A.acc4, 0, acc_bytes, s);
-            if (e != cudaSuccess) return e;
-            k_adj_sums_sym<NTN, US><<<grid_sums, NTN, 0, s>>>(A);
+            A.acc4 = store ? (float4*)(sums_base + sums_stride * (size_t)step) : acc_scratch;
+            if (!(store && recompute)) {
+                const cudaError_t e = cudaMemsetAsync(A.acc4, 0, acc_bytes, s);
+                if (e != cudaSuccess) return e;
+                k_adj_sums_sym<NTN, US><<<grid_sums, NTN, 0, s>>>(A);
+            }
             k_adj_forward<PDQ_MIXED, NT, true><<<grid, NT, 0, s>>>(A);
+            A.acc4 = acc_scratch;
         } else if (mixed) {
             k_adj_forward<PDQ_MIXED, NT><<<grid, NT, 0, s>>>(A);
         } else {
@@ -1293,8 +1321,9 @@ static int adjoint_impl(const pdq_field* field, const pdq_phys* phys, const pdq_
         PDQ_CUDA(cudaMemsetAsync(A.den, 0, sc, s));
         PDQ_CUDA(checkpoint(0, seg[0]));
         // forward sweep: ping-pong between segment slots 0 and 1, checkpoint every K steps
+        if (store) PDQ_CUDA(cudaMemcpyAsync(marker, mark, sizeof(mark), cudaMemcpyHostToDevice, s));
         for (int64_t n = 0; n < n_steps; ++n) {
-            PDQ_CUDA(fwd(seg[n & 1], seg[(n + 1) & 1], n, 1));
+            PDQ_CUDA(fwd(seg[n & 1], seg[(n + 1) & 1], n, 1, false));
             if ((n + 1) % K == 0 && (n + 1) < n_steps) PDQ_CUDA(checkpoint((n + 1) / K, seg[(n + 1) & 1]));
         }
         k_adj_finish<<<(nsc + 255) / 256, 256, 0, s>>>(A.num, A.den, nullptr, nsc, A.K.R, A.K.dt, J, nullptr,
@@ -1302,6 +1331,12 @@ static int adjoint_impl(const pdq_field* field, const pdq_phys* phys, const pdq_
         PDQ_CUDA(cudaGetLastError());
     }
 
+    if (store && !forward) {   // the stored sums must come from a forward sweep of this layout
+        int64_t got[4];
+        PDQ_CUDA(cudaMemcpyAsync(got, marker, sizeof(got), cudaMemcpyDeviceToHost, s));
+        PDQ_CUDA(cudaStreamSynchronize(s));
+        if (memcmp(got, mark, sizeof(got)) != 0) return PDQ_ERR_INVALID_ARG;
+    }
     // backward sweeps, one per cotangent vector
     for (int v = 0; v < n_vec; ++v) {
         k_adj_finish<<<(nsc + 255) / 256, 256, 0, s>>>(A.num, A.den, gbar + (size_t)v * nsc, nsc, A.K.R, A.K.dt,
@@ -1315,7 +1350,7 @@ static int adjoint_impl(const pdq_field* field, const pdq_phys* phys, const pdq_
             A.qhat = ck_qh[kseg];
             A.cls = ck_cl[kseg];
             PDQ_CUDA(copy_state(seg[0], ck[kseg]));
-            for (int64_t t = 0; t < len; ++t) PDQ_CUDA(fwd(seg[t], seg[t + 1], n0 + t, 0));
+            for (int64_t t = 0; t < len; ++t) PDQ_CUDA(fwd(seg[t], seg[t + 1], n0 + t, 0, true));
             for (int64_t t = len - 1; t >= 0; --t) {
                 A.in = seg[t];
                 A.step = n0 + t;

@@ -110,6 +110,7 @@ def lib():
                                                      C.POINTER(C.c_size_t)]),
             "pdq_adjoint_state_workspace_size": (C.c_int, [C.POINTER(StateStruct), C.c_int64, C.c_int32,
                                                            C.POINTER(C.c_size_t)]),
+            "pdq_adjoint_stored_sums_size": (C.c_int, [C.c_int64, C.c_int64, C.POINTER(C.c_size_t)]),
             "pdq_adjoint_run": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P, C.POINTER(StepCfg),
                                           C.c_int64, C.c_int32, C.c_double, C.c_double, C.c_int32, P, P, P, P,
                                           C.c_size_t, P]),
@@ -484,22 +485,39 @@ def _adjoint_outputs(S, Cn, gbar):
     return J, nv, pbar, g
 
 
-def adjoint_workspace(batch_struct, n_steps, K):
+def _stored_sums_bytes(capacity, n_steps, store_sums):
+    if not store_sums:
+        return 0
+    n = C.c_size_t()
+    _check(lib().pdq_adjoint_stored_sums_size(int(capacity), int(n_steps), C.byref(n)), "adjoint_stored_sums_size")
+    return n.value
+
+
+def adjoint_workspace_bytes(batch_struct, n_steps, K, store_sums=False):
+    """Bytes of the adjoint's workspace; store_sums adds room for every step's Newton-pair sums (MIXED
+    with Coulomb forces: the reverse sweep's recompute then skips the pair sums)."""
     n = C.c_size_t()
     _check(lib().pdq_adjoint_workspace_size(C.byref(batch_struct), int(n_steps), int(K), C.byref(n)),
            "adjoint_workspace_size")
-    return torch.empty(n.value, dtype=torch.uint8, device="cuda")
+    return n.value + _stored_sums_bytes(batch_struct.capacity, n_steps, store_sums)
+
+
+def adjoint_workspace(batch_struct, n_steps, K, store_sums=False):
+    """The adjoint's workspace (device bytes), see adjoint_workspace_bytes."""
+    return torch.empty(adjoint_workspace_bytes(batch_struct, n_steps, K, store_sums), dtype=torch.uint8,
+                       device="cuda")
 
 
 def adjoint_run(field, phys, state, params_dev, cfg, n_steps, K, eps, gbar=None, stream=None, eps_stick=10.0,
-                ws=None):
+                ws=None, store_sums=False):
     """pdq_adjoint_run from the current half of `state`: J [S, C] and, for cotangents gbar [V, S, C],
     pbar [V, S, 3] = gbar . dJ/d(xi, zeta, theta).  Returns (J, pbar or None, workspace)."""
     if ws is None:
         n = C.c_size_t()
         _check(lib().pdq_adjoint_state_workspace_size(C.byref(state.st), int(n_steps), int(K), C.byref(n)),
                "adjoint_state_workspace_size")
-        ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+        extra = _stored_sums_bytes(state.st.capacity, n_steps, store_sums)
+        ws = torch.empty(n.value + extra, dtype=torch.uint8, device="cuda")
     J, nv, pbar, g = _adjoint_outputs(state.n_samples, state.n_classes, gbar)
     _check(lib().pdq_adjoint_run(field.handle, C.byref(phys), C.byref(state.st), _ptr(params_dev), C.byref(cfg),
                                  int(n_steps), int(K), float(eps), float(eps_stick), nv, _ptr(g), _ptr(J),
@@ -508,10 +526,10 @@ def adjoint_run(field, phys, state, params_dev, cfg, n_steps, K, eps, gbar=None,
 
 
 def adjoint_run_seeded(field, phys, batch, params_dev, cfg, n_steps, K, eps, seed, charge_sigma=0.0, gbar=None,
-                       stream=None, eps_stick=10.0, ws=None):
+                       stream=None, eps_stick=10.0, ws=None, store_sums=False):
     """pdq_adjoint_run_seeded: J [S, C] and, for cotangents gbar [V, S, C], pbar [V, S, 3]."""
     if ws is None:
-        ws = adjoint_workspace(batch.b, n_steps, K)
+        ws = adjoint_workspace(batch.b, n_steps, K, store_sums)
     J, nv, pbar, g = _adjoint_outputs(batch.n_samples, batch.n_classes, gbar)
     _check(lib().pdq_adjoint_run_seeded(field.handle, C.byref(phys), C.byref(batch.b), _ptr(params_dev),
                                         charge_sigma, seed, C.byref(cfg), int(n_steps), int(K), float(eps),
@@ -536,14 +554,15 @@ class PdqDeposition(torch.autograd.Function):
     """J = smoothed V_dep+ [S, C] of the particle model as a function of params [S, 3] = (xi, zeta, theta).
 
     forward runs the smoothed forward sweep (pdq_adjoint_run_seeded with no cotangent) and keeps
-    its workspace, checkpoints included, until backward; backward runs only the reverse sweep
-    (pdq_adjoint_reverse) with the incoming gradient as cotangent.
+    its workspace, checkpoints included (and with store_sums every step's pair sums), until
+    backward; backward runs only the reverse sweep (pdq_adjoint_reverse) with the incoming
+    gradient as cotangent.
     """
 
     @staticmethod
-    def forward(ctx, params, field, phys, batch, cfg, n_steps, K, eps, seed, charge_sigma):
+    def forward(ctx, params, field, phys, batch, cfg, n_steps, K, eps, seed, charge_sigma, store_sums=False):
         prm = params_tensor(params.detach())
-        ws = adjoint_workspace(batch.b, n_steps, K)
+        ws = adjoint_workspace(batch.b, n_steps, K, store_sums)
         J, _ = adjoint_run_seeded(field, phys, batch, prm, cfg, n_steps, K, eps, seed, charge_sigma, ws=ws)
         ctx.save_for_backward(params.detach())
         ctx.args = (field, phys, batch, cfg, n_steps, K, eps, prm, ws)
@@ -556,7 +575,7 @@ class PdqDeposition(torch.autograd.Function):
         pbar = adjoint_reverse(field, phys, batch.b, prm, cfg, n_steps, K, eps,
                                grad_out.detach().to(torch.float64).unsqueeze(0), ws)
         ctx.args = None
-        return (pbar[0].to(device=params.device, dtype=params.dtype),) + (None,) * 9
+        return (pbar[0].to(device=params.device, dtype=params.dtype),) + (None,) * 10
 
 
 def dgsm_bounds(grad, y, width, stream=None):

@@ -183,3 +183,16 @@ def test_adjoint_workspace_holds_the_newton_pair_sums(pdq):
     per = 10 * (8 * 8 + 2 * 4) + 11 * 10 * 8 + 19 * 8 + 16
     assert n.value >= per * 4096
     assert L.pdq_adjoint_workspace_size(C.byref(b), 0, 10, C.byref(n)) == -1
+
+
+def test_adjoint_stored_sums_size(pdq):
+    # a 256-byte marker, then one float4 [capacity] array (256-byte aligned) per step
+    L = pdq.lib()
+    n = C.c_size_t()
+    for cap, steps in ((4096, 100), (1000, 7), (0, 1)):
+        assert L.pdq_adjoint_stored_sums_size(cap, steps, C.byref(n)) == 0
+        stride = -(-16 * max(cap, 1) // 256) * 256
+        assert n.value == 256 + stride * steps
+    assert L.pdq_adjoint_stored_sums_size(-1, 10, C.byref(n)) == -1
+    assert L.pdq_adjoint_stored_sums_size(4096, 0, C.byref(n)) == -1
+    assert L.pdq_adjoint_stored_sums_size(4096, 10, None) == -1

@@ -226,6 +226,52 @@ def test_adjoint_across_newton_tiles_matches_dual_numbers(pdq, precision, eps):
         _check_grad(got, dJ_ref, 3e-2, (0,))
 
 
+@pytest.mark.parametrize("eps", [0.5, 0.02])
+def test_stored_pair_sums_match_dual_numbers(pdq, eps):
+    # MIXED with the forward sweep's Newton-pair sums kept for the reverse sweep's recompute
+    # (workspace + pdq_adjoint_stored_sums_size): the same bar against the dual numbers as the
+    # recomputing path, and that path's J and gradients up to float summation order
+    J_ref, dJ_ref, _, _ = _tile_ref(eps)
+    field = pdq.Field(pdq.field_desc(**GRID), 0)
+    cfg = pdq.step_cfg(TILE["dt"], window_start=TILE["win"], gravity=TILE["gravity"])
+    out = {}
+    for store in (False, True):
+        batch = pdq.Batch(1, TILE_COUNTS, TILE["st"])
+        J, pbar = pdq.adjoint_run_seeded(field, pdq.phys_default(), batch, pdq.params_tensor(TILE_PARAMS), cfg,
+                                         TILE["steps"], 5, eps, SEED, gbar=_onehot_sc(5, 2), store_sums=store)
+        out[store] = (J.cpu().numpy(), np.transpose(pbar.cpu().numpy(), (1, 0, 2)))
+    J, got = out[True]
+    assert np.all(J[4] == 0) and np.all(got[4] == 0)
+    assert np.allclose(J, J_ref, rtol=3e-3, atol=1e-6 * np.max(J_ref))
+    _check_grad(got, dJ_ref, 3e-2, (0,))
+    J0, got0 = out[False]
+    assert np.allclose(J, J0, rtol=1e-5, atol=1e-9 * np.max(J0))
+    sc = np.max(np.abs(got0[..., 0]))
+    assert np.max(np.abs(got[..., 0] - got0[..., 0])) <= 1e-3 * sc
+
+
+def test_stored_pair_sums_reverse_alone(pdq):
+    # forward sweep with the sums kept, then pdq_adjoint_reverse on the same workspace, against
+    # one combined call; a workspace whose forward sweep kept no sums is refused before any work
+    field = pdq.Field(pdq.field_desc(**GRID), 0)
+    phys = pdq.phys_default()
+    cfg = pdq.step_cfg(TILE["dt"], window_start=TILE["win"], gravity=TILE["gravity"])
+    prm = pdq.params_tensor(TILE_PARAMS)
+    batch = pdq.Batch(1, TILE_COUNTS, TILE["st"])
+    g = _onehot_sc(5, 2)
+    J1, p1 = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, TILE["steps"], 5, 0.5, SEED, gbar=g,
+                                    store_sums=True)
+    ws = pdq.adjoint_workspace(batch.b, TILE["steps"], 5, store_sums=True)
+    J2, _ = pdq.adjoint_run_seeded(field, phys, batch, prm, cfg, TILE["steps"], 5, 0.5, SEED, ws=ws)
+    p2 = pdq.adjoint_reverse(field, phys, batch.b, prm, cfg, TILE["steps"], 5, 0.5, g, ws)
+    assert np.allclose(J1.cpu().numpy(), J2.cpu().numpy(), rtol=1e-5, atol=0)
+    a, b = p1.cpu().numpy(), p2.cpu().numpy()
+    assert np.max(np.abs(a - b)) <= 1e-3 * np.max(np.abs(a))
+    fresh = torch.zeros_like(ws)
+    with pytest.raises(pdq.PdqError, match="adjoint_reverse"):
+        pdq.adjoint_reverse(field, phys, batch.b, prm, cfg, TILE["steps"], 5, 0.5, g, fresh)
+
+
 # ---------------------------------------------------------------------------
 # The adjoint started from a caller's state: pdq_step_particles advances a transient (with
 # deposits; with and without compaction), then pdq_adjoint_run differentiates the next steps
