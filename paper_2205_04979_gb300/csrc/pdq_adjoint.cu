@@ -822,6 +822,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 6) k_adj_sums_sym(const Ad
 // with the opposite sign.  The charge term Qp_m = sum_j (d.c_j)/r^3 (Q-bar_m = -Qp_m) gets
 // -(d.c_m)/r^3 for j.  One j against two m-particles, packed: T is added to (tx, ty, tz) and
 // (jx, jy, jz), (d.c_j)/r^3 to qp and (d.c_m)/r^3 to jq; the caller negates the j sums.
+// 38 packed operations (d.u taken from d.c_m and d.c_j, T from c_m and c_j scaled by Q/r^3).
 // nQm = -Q_m; MINIMG / CLAMP as in vjp_pair_x2.
 template <bool MINIMG, bool CLAMP>
 __device__ __forceinline__ void vjp_pair_x2_sym(f2 xm, f2 ym, f2 zm, f2 nQm, f2 cmx, f2 cmy, f2 cmz, const VjpJ& J,
@@ -845,22 +846,22 @@ __device__ __forceinline__ void vjp_pair_x2_sym(f2 xm, f2 ym, f2 zm, f2 nQm, f2 
         mask3 = f2_pack(-3.f, -3.f);
     }
     const f2 ri2 = f2_mul(ri, ri), ri3 = f2_mul(ri2, ri);
-    const f2 ux = f2_fma(J.Q, cmx, f2_mul(nQm, J.cx));
-    const f2 uy = f2_fma(J.Q, cmy, f2_mul(nQm, J.cy));
-    const f2 uz = f2_fma(J.Q, cmz, f2_mul(nQm, J.cz));
-    const f2 du = f2_fma(dx, ux, f2_fma(dy, uy, f2_mul(dz, uz)));
+    const f2 dcj = f2_fma(dx, J.cx, f2_fma(dy, J.cy, f2_mul(dz, J.cz)));
+    const f2 dcm = f2_fma(dx, cmx, f2_fma(dy, cmy, f2_mul(dz, cmz)));
+    // d.u = Q_j (d.c_m) - Q_m (d.c_j), from the products the charge terms need anyway
+    const f2 du = f2_fma(J.Q, dcm, f2_mul(nQm, dcj));
     const f2 kk = f2_mul(f2_mul(f2_mul(ri3, ri2), mask3), du);
-    const f2 Tx = f2_fma(kk, dx, f2_mul(ux, ri3));
-    const f2 Ty = f2_fma(kk, dy, f2_mul(uy, ri3));
-    const f2 Tz = f2_fma(kk, dz, f2_mul(uz, ri3));
+    // T = (Q_j / r^3) c_m - (Q_m / r^3) c_j + kk d
+    const f2 a = f2_mul(ri3, J.Q), b = f2_mul(ri3, nQm);
+    const f2 Tx = f2_fma(a, cmx, f2_fma(b, J.cx, f2_mul(kk, dx)));
+    const f2 Ty = f2_fma(a, cmy, f2_fma(b, J.cy, f2_mul(kk, dy)));
+    const f2 Tz = f2_fma(a, cmz, f2_fma(b, J.cz, f2_mul(kk, dz)));
     tx = f2_add(tx, Tx);
     ty = f2_add(ty, Ty);
     tz = f2_add(tz, Tz);
     jx = f2_add(jx, Tx);
     jy = f2_add(jy, Ty);
     jz = f2_add(jz, Tz);
-    const f2 dcj = f2_fma(dx, J.cx, f2_fma(dy, J.cy, f2_mul(dz, J.cz)));
-    const f2 dcm = f2_fma(dx, cmx, f2_fma(dy, cmy, f2_mul(dz, cmz)));
     qp = f2_fma(ri3, dcj, qp);
     jq = f2_fma(ri3, dcm, jq);
 }
