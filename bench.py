@@ -73,6 +73,13 @@ def parse():
     ap.add_argument("--particles", type=int, default=100_000, help="P3M workload: particles in the sample")
     ap.add_argument("--p3m-mesh", type=int, nargs=2, default=None, metavar=("M", "NZ"),
                     help="P3M mesh: cells across the diameter and nodes along z (default by particle count)")
+    ap.add_argument("--lf", default="particle", choices=["particle", "eulerian"],
+                    help="--workload mfmc: low-fidelity model (the particle model without the pair sum, or the "
+                         "1-D Eulerian model of App. B)")
+    ap.add_argument("--hf-particles", type=int, default=4096, help="--workload mfmc: particles per HF sample")
+    ap.add_argument("--hf-steps", type=int, default=600, help="--workload mfmc: HF steps at dt+ = 0.05")
+    ap.add_argument("--replicates", type=int, default=100,
+                    help="--workload mfmc: replicate studies (0: pilot and allocation only)")
     ap.add_argument("--contact", action="store_true",
                     help="half the charges negative, soft-sphere collisions and particle-particle vdW on")
     return ap.parse_args()
@@ -264,6 +271,21 @@ def workload_label(name, counts, contact=False):
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload == "lf_eulerian":
+        w = workloads.WORKLOADS["lf_eulerian"]
+        S = args.samples or w["samples"]
+        params = workloads.sample_params(S, w["param_seed"], spread=w["spread"])
+        base = lf_cpu_baseline(w, params, seconds=max(5.0, 2.0 * (args.steps + args.warmup)))
+        print(json.dumps({"impl": "reference", "metric": "low-fidelity evaluations/s (1-D Eulerian model of App. B, "
+                                                         "sample x class items)",
+                          "value": base["value"], "unit": "evaluations/s", "n_gpus": args.gpus, "steps": args.steps,
+                          "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "lf_eulerian: %d samples x %d St+ classes" % (S, len(w["st_plus"]))},
+                          "cpu_baseline": base,
+                          "e2e": {"value": base["value"], "unit": "evaluations/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
         return
     params, counts = workloads.workload_inputs(args.workload, args.samples)
     base = cpu_baseline(args.workload, params, counts, seconds=max(5.0, 4.0 * (args.steps + args.warmup)),
@@ -671,13 +693,17 @@ def run_mfmc(args):
 
     High fidelity: the batched particle model, 4,096 particles per sample, dt+ = 0.05, 600 steps.
     Low fidelity: the same particles without the particle-particle Coulomb sum and with 2x dt
-    (300 steps to the same t+ = 30); the paper's 1-D Eulerian model needs closures it does not
-    print.  A pilot gives rho, sigma and the measured GPU time per sample w of each model;
+    (300 steps to the same t+ = 30).  A pilot gives rho, sigma and the measured GPU time per sample w of each model;
     pdq_mfmc_allocate gives m and alpha.  R replicate studies, each with fresh pick-freeze
     groups, measure the variance of the MFMC and plain-MC estimates of the mean V_dep+ and of
     the Sobol' indices at the same budget; the variance ratio of the mean is reported beside
     gamma(rho, w).  Then one MFMC and one plain-MC Sobol' study at a larger budget, and the
     MIXED-vs-FP64 comparison of the Sobol' indices on the same inputs.
+
+    --lf eulerian: the low-fidelity model is the 1-D Eulerian model of App. B (pdq_lf_vdep, the
+    paper's own choice of low-fidelity model), its cost per sample measured on a batch of 65,536
+    samples; the MIXED-vs-FP64 comparison is left to the default mode.  --hf-particles and
+    --hf-steps size the particle model; --replicates 0 stops after the pilot and the allocation.
     """
     import torch
     from paper_2205_04979_gb300 import pdq, uq
@@ -686,13 +712,32 @@ def run_mfmc(args):
     ranges = ((0.0, 0.1), (0.0, 1.0), (0.0, 1.0))
     lo, hi = np.array([r[0] for r in ranges]), np.array([r[1] for r in ranges])
     d, C = 3, len(st_plus)
-    hf = dict(particles=4096, steps=600, dt=0.05, forces=pdq.F_ALL)
-    lf = dict(particles=4096, steps=300, dt=0.10, forces=pdq.F_ALL & ~pdq.F_COULOMB)
+    hf = dict(particles=args.hf_particles, steps=args.hf_steps, dt=0.05, forces=pdq.F_ALL)
+    lf = dict(particles=args.hf_particles, steps=args.hf_steps // 2, dt=0.10, forces=pdq.F_ALL & ~pdq.F_COULOMB)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         field = pdq.Field(pdq.field_desc(n_r=64, n_th=32, n_z=64), 0, stream)
 
+    eulerian = args.lf == "eulerian"
+    if eulerian:
+        with torch.cuda.stream(stream):
+            lf_var = pdq.lf_fluid_variance(field, stream)
+        lf_desc = pdq.lf_desc()
+        lf_phys = pdq.phys_default()
+
+    def run_eulerian(inputs):
+        with torch.cuda.stream(stream):
+            prm = pdq.params_tensor(np.asarray(inputs, np.float64))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            y = pdq.lf_vdep(field, lf_phys, lf_desc, lf_var, st_plus, prm, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+        return y.cpu().numpy(), e0.elapsed_time(e1)
+
     def run(model, inputs, precision=pdq.MIXED, chunk=12000):
+        if eulerian and model is lf:
+            return run_eulerian(inputs)
         outs, ms = [], 0.0
         for a in range(0, len(inputs), chunk):
             y, t = uq.vdep_runs(inputs[a:a + chunk], model["particles"], model["steps"], st_plus=st_plus,
@@ -716,6 +761,10 @@ def run_mfmc(args):
     yh, th = run(hf, xpil)
     yl, tl = run(lf, xpil)
     w = np.array([th / npil, tl / npil])                    # ms per sample
+    if eulerian:                                            # cost per sample on a batch that fills the GPU
+        nb = 65536
+        _, tb = run(lf, lo + (hi - lo) * np.random.Generator(np.random.Philox(12)).random((nb, d)))
+        w[1] = tb / nb
     rho = np.array([np.corrcoef(yh[:, c], yl[:, c])[0, 1] for c in range(C)])
     sig = np.stack([yh.std(0, ddof=1), yl.std(0, ddof=1)], 1)
     cq = int(np.argmax(yh.mean(0)))                         # allocate for the class with most deposition
@@ -729,8 +778,26 @@ def run_mfmc(args):
         return
     m1, m2 = max(2, int(m[0])), int(m[1])
     gam = [float((np.sqrt(1 - r ** 2) + r * np.sqrt(w[1] / w[0])) ** 2) for r in rho]
+
+    def fin(a):
+        return _finite(np.asarray(a).tolist())
+    pilot = {"samples": npil, "rho": fin(rho), "sigma": fin(sig.T), "w_ms_per_sample": fin(w),
+             "allocation_class": st_plus[cq], "m": [m1, m2], "alpha": fin(alpha),
+             "gamma_predicted_per_class": fin(gam), "gamma_allocation": gamma,
+             "hf_mean": fin(yh.mean(0)), "lf_mean": fin(yl.mean(0)),
+             "hf_deposits_per_sample_approx": fin(yh.mean(0) * (args.hf_particles / C) *
+                                                (hf["steps"] * hf["dt"] - 10.0) / 90.0)}
+    hf_label = ("HF = particle model %d particles/sample, dt+ 0.05, %d steps" % (args.hf_particles, args.hf_steps))
+    if args.replicates == 0:
+        print(json.dumps({"metric": "MFMC pilot: correlation of the low-fidelity model with the particle model",
+                          "config": {"workload": "mfmc pilot: %s; LF = %s; classes %s; inputs xi [0,0.1], zeta "
+                                                 "[0,1], theta [0,1]" % (hf_label, "1-D Eulerian model" if eulerian
+                                                                         else "particle model without the pair "
+                                                                              "sum, 2x dt", list(st_plus))},
+                          "pilot": pilot}), flush=True)
+        return
     # replicates: HF on the first p_eff groups (MC uses them all, MFMC the first m1), LF on m2
-    R = 100
+    R = args.replicates
     groups = [draw(max(p_eff, m2), 1000 + r) for r in range(R)]
     y_hf, t_hf = run(hf, np.concatenate([g[:p_eff] for g in groups]).reshape(-1, d))
     y_lf, t_lf = run(lf, np.concatenate([g[:m2] for g in groups]).reshape(-1, d))
@@ -760,6 +827,21 @@ def run_mfmc(args):
     big_mc = pdq.mfmc_sobol([yhb], [pb], [1.0], n_boot=200, seed=3, stream=stream)
     big_mf = pdq.mfmc_sobol([yhb[:int(mb[0])], ylb], [int(mb[0]), int(mb[1])], ab, n_boot=200, seed=3,
                             stream=stream)
+    if eulerian:
+        print(json.dumps({
+            "metric": "MFMC vs plain MC at equal GPU cost, low fidelity = the 1-D Eulerian model (App. B)",
+            "config": {"workload": "mfmc: %s; LF = 1-D Eulerian model, %d wall-normal nodes; classes %s; inputs xi "
+                                   "[0,0.1], zeta [0,1], theta [0,1]" % (hf_label, lf_desc.n_y, list(st_plus))},
+            "pilot": pilot,
+            "replicates": {"R": R, "budget_hf_groups": p_eff, "mc_groups": p_eff, "mfmc_groups": [m1, m2],
+                           "var_ratio_mean": fin(ratio_mean), "var_ratio_s_main": fin(ratio_sm),
+                           "var_ratio_s_total": fin(ratio_st),
+                           "gpu_ms": {"hf_all": t_hf, "lf_all": t_lf, "mc_per_study": w[0] * p_eff * (d + 2),
+                                      "mfmc_per_study": (w[0] * m1 + w[1] * m2) * (d + 2)}},
+            "study": {"budget_hf_groups": pb, "mfmc_m": [int(mb[0]), int(mb[1])], "gamma": gb,
+                      "mc": {k: fin(v) for k, v in big_mc.items()},
+                      "mfmc": {k: fin(v) for k, v in big_mf.items()}}}), flush=True)
+        return
     # MIXED vs FP64 Sobol' indices of the high-fidelity model on the same 64 groups
     g64 = draw(64, 9).reshape(-1, d)
     ym, tm = run(hf, g64, pdq.MIXED)
@@ -769,9 +851,6 @@ def run_mfmc(args):
     half = 0.5 * (sf["s_main_ci"][..., 1] - sf["s_main_ci"][..., 0])
     halft = 0.5 * (sf["s_total_ci"][..., 1] - sf["s_total_ci"][..., 0])
     dm, dt_ = np.abs(sm["s_main"] - sf["s_main"]), np.abs(sm["s_total"] - sf["s_total"])
-
-    def fin(a):
-        return _finite(np.asarray(a).tolist())
     out = {"metric": "MFMC vs plain MC at equal GPU cost: variance of the estimates over replicate studies",
            "config": {"workload": "mfmc: HF = particle model 4,096 particles/sample, dt+ 0.05, 600 steps; LF = same "
                                   "without the Coulomb pair sum, dt+ 0.1, 300 steps; classes %s; inputs xi [0,0.1], "
@@ -862,6 +941,140 @@ def run_p3m(args):
            "all_pairs_fp64_ms_per_step": ref_ms, "clocks": clocks,
            "gpu_launches": int(args.steps * 16)}
     print(json.dumps(out), flush=True)
+
+
+# FP64 operations per (item, cell) of the low-fidelity march, as written in k_lf_vdep: momentum
+# c = V^2/2 + dw + dPhi (7), root -2c/(a + sqrt(a^2 + 2c)) (7, sqrt and the division counted as
+# one each), cell means and exponential fitting vm, a', expm1, G = em/vm, E (6), Q += P G, P *= E (3)
+LF_FLOPS_PER_CELL = 23
+# FP64-pipe lane instructions per (item, cell) as executed (ncu instruction counters on a launch of
+# 16,384 samples x 10 classes: the square root, divisions and expm1 expand to seeds plus Newton or
+# polynomial steps) and the DRAM bytes of that launch (read + write), scaled by samples
+LF_FP64_OPS_PER_CELL = 61.41
+LF_DRAM_BYTES_PER_SAMPLE = 1.053e6 / 16384
+
+
+def lf_cpu_baseline(w, params, seconds):
+    """Time the numpy FP64 oracle of the 1-D Eulerian model on a bounded sample of the samples."""
+    import oracle
+    from oracle import lf_eulerian as lfo
+    of = oracle.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
+    var = lfo.fluid_variance(oracle.field_grid(of, oracle.field_modes(of, w["field_seed"])))
+    p = oracle.phys()
+    n, done, t = 8, 0, 0.0
+    while t < seconds and done < len(params):
+        k = min(n, len(params) - done)
+        t0 = time.perf_counter()
+        lfo.lf_vdep(p, w["st_plus"], params[done:done + k], var, of.r_plus, of.beta, lfo.lf_params(n_y=w["n_y"]))
+        t += time.perf_counter() - t0
+        done += k
+        n *= 2
+    C = len(w["st_plus"])
+    return {"value": done * C / t, "unit": "low-fidelity evaluations/s (sample x class)", "cores": 1,
+            "kind": "oracle", "sample": "numpy FP64 oracle (vectorised over the items of a chunk, one thread), "
+                                        "%d samples x %d classes in %.1f s" % (done, C, t)}
+
+
+def run_lf(args):
+    """The 1-D Eulerian low-fidelity model (App. B) at the Sobol' study's low-fidelity size.
+
+    One bench step = one evaluation of V_dep+ for every (sample, class) item: 262,144 samples x 10
+    St+ classes at 2,048 wall-normal nodes (pdq_lf_vdep, one kernel launch).  L2 is flushed
+    between timed steps.  e2e: the inputs uploaded from pinned host memory and V_dep+ downloaded
+    every step.
+    """
+    import torch
+    import paper_2205_04979_gb300.pdq as pdq
+    torch.cuda.set_device(0)
+    w = workloads.WORKLOADS["lf_eulerian"]
+    S = args.samples or w["samples"]
+    params = workloads.sample_params(S, w["param_seed"], spread=w["spread"])
+    st = w["st_plus"]
+    C = len(st)
+    phys = pdq.phys_default()
+    desc = pdq.field_desc(n_r=w["grid"][0], n_th=w["grid"][1], n_z=w["grid"][2], n_modes=w["n_modes"])
+    stream = torch.cuda.Stream()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        pass
+    with torch.cuda.stream(stream):
+        field = pdq.Field(desc, w["field_seed"], stream)
+        var = pdq.lf_fluid_variance(field, stream)
+        lfd = pdq.lf_desc(n_y=w["n_y"])
+        prm = pdq.params_tensor(params)
+        out = torch.empty((S, C), dtype=torch.float64, device="cuda")
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        for _ in range(args.warmup):
+            pdq.lf_vdep(field, phys, lfd, var, st, prm, out=out, stream=stream)
+        stream.synchronize()
+        clk = ClockSampler(uuid)
+        clk.start()
+        evs = []
+        for k in range(args.steps):
+            flush.fill_(k & 255)                    # evict L2 between timed evaluations
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pdq.lf_vdep(field, phys, lfd, var, st, prm, out=out, stream=stream)
+            e1.record(stream)
+            evs.append((e0, e1))
+        stream.synchronize()
+        clocks = clk.stop()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        vd = out.cpu().numpy()
+        # end to end: pinned host inputs in, V_dep+ out, every step
+        host_in = torch.zeros((S, 4), dtype=torch.float64).pin_memory()
+        host_in[:, :3] = torch.from_numpy(params)
+        host_out = torch.empty((S, C), dtype=torch.float64).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            prm.copy_(host_in, non_blocking=True)
+            pdq.lf_vdep(field, phys, lfd, var, st, prm, out=out, stream=stream)
+            host_out.copy_(out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms_e2e = e0.elapsed_time(e1)
+        assert np.array_equal(host_out.numpy(), vd)
+    from paper_2205_04979_gb300 import peaks as pk
+    rec = pk.load(PEAKS_FILE)
+    peak_ops = rec["kernels"]["dfma"]["lane_ops_per_s"] / 1e9 if rec else None
+    peak = rec["kernels"]["dfma"]["flops_per_s"] / 1e12 if rec else None
+    items = S * C
+    cells = w["n_y"] - 1
+    sec = ms / args.steps / 1e3
+    achieved_ops = LF_FP64_OPS_PER_CELL * cells * items / sec / 1e9
+    achieved = LF_FLOPS_PER_CELL * cells * items / sec / 1e12
+    out_json = {
+        "metric": "low-fidelity evaluations/s (1-D Eulerian model of App. B, sample x class items)",
+        "value": items * args.steps / (ms / 1e3), "unit": "evaluations/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "lf_eulerian: %d samples x %d St+ classes (log-spaced 0.1..100), inputs xi in "
+                               "[0, 0.1], zeta in [0, 1], theta in [0, 1], %d wall-normal nodes, v_f'^2 from the "
+                               "128x64x128 field" % (S, C, w["n_y"]),
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak_ops, "unit": "Gop/s",
+                     "frac": achieved_ops / peak_ops if peak_ops else None,
+                     "traffic": LF_DRAM_BYTES_PER_SAMPLE * S,
+                     "kernel": "k_lf_vdep",
+                     "note": "FP64 pipe: %.2f FP64 lane operations per (item, cell) as executed (ncu instruction "
+                             "counters), against the measured DFMA lane-operation rate; traffic scaled from a "
+                             "16,384-sample capture" % LF_FP64_OPS_PER_CELL,
+                     "algorithmic": {"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": achieved / peak if peak else None,
+                                     "note": "%d FP64 operations per (item, cell), sqrt, expm1 and divisions "
+                                             "counted as one each; measured DFMA peak" % LF_FLOPS_PER_CELL}},
+        "clocks": clocks, "gpu_launches": args.steps,
+        "e2e": {"value": items * args.steps / (ms_e2e / 1e3), "unit": "evaluations/s",
+                "h2d_bytes_per_step": int(S * 32), "d2h_bytes_per_step": int(S * C * 8)},
+        "us_per_sample_all_classes": ms / args.steps / S * 1e3,
+        "vdep_mean": np.mean(vd, 0).tolist(),
+    }
+    if not args.no_cpu_baseline:
+        out_json["cpu_baseline"] = lf_cpu_baseline(w, params, min(args.cpu_seconds, 15.0))
+    print(json.dumps(out_json), flush=True)
 
 
 def clamp_check(pdq, stream, block, variant, samples, count, steps, st_plus, dt=0.05, t_window=10.0,
@@ -955,6 +1168,8 @@ def main():
         run_vdep_validation(args)
     elif args.workload == "mfmc":
         run_mfmc(args)
+    elif args.workload == "lf_eulerian":
+        run_lf(args)
     else:
         run_ours(args)
 

@@ -518,6 +518,58 @@ int pdq_dgsm_workspace_size(int32_t C, int32_t d, size_t* bytes);
 int pdq_dgsm_bounds(int32_t S, int32_t C, int32_t d, const double* grad, const double* y, const double* width,
                     double* nu, double* bound, void* workspace, size_t workspace_bytes, pdq_stream_t stream);
 
+/* ------------------------------------ 1-D Eulerian low-fidelity model
+ * The low-fidelity model of App. B (the unified advection-diffusion deposition
+ * model with the kinetic wall condition, Eqs. momentum/mom_modified and
+ * continuity, F_elec and F_vdw as printed), evaluated for every (sample, size
+ * class) item, as model 2 of the multi-fidelity estimators (Sec. 3).  App. B
+ * cites its closures without printing them; this library reads them as:
+ *   v_f'^2(y)  the variance over (theta, z) of the carrier field's radial
+ *              velocity at r = R - y (pdq_lf_fluid_variance), linear in the
+ *              field's stretched radial coordinate between its nodes;
+ *   R_ratio    T_L/(T_L + tau_p);  eps/nu = v_f'^2 T_L;  tau_1 = tau_p;
+ *   D_B        k_B T tau_p / m_p;  D_T term 0 (isothermal gas);
+ *   M_r        -V_w/(sqrt(2) sigma), sigma^2 = R_ratio v_f'^2 + k_B T/m_p at
+ *              contact, i.e. the one-way flux of a Gaussian wall-normal
+ *              velocity into an absorbing wall.
+ * Charge q = xi q_max of the class, Hamaker constant A = zeta A0; theta does
+ * not enter (the isothermal STICK model).  Grid: n_y nodes from contact
+ * y = d/2 to the axis, y_k = d/2 + (R - d/2) expm1(gamma k/(n_y-1))/expm1(gamma);
+ * the momentum equation in energy form with the drag implicit, marched from
+ * V = 0 on the axis (V = 0 wherever the net force would drive particles away
+ * from the wall); the continuity equation solved exactly on each cell with V
+ * and D at their cell means.  The result converges at first order in the node
+ * spacing (about 1 % at 2,048 nodes for St+ = 10).                           */
+#define PDQ_LF_MAX_NODES 4096
+typedef struct pdq_lf_desc {
+    int32_t n_y;          /* wall-normal nodes, 3..PDQ_LF_MAX_NODES (default 2048)          */
+    int32_t reserved;     /* 0                                                              */
+    double stretch;       /* near-wall refinement gamma, 0 < gamma <= 700 (default 8)      */
+    double t_lagr;        /* fluid Lagrangian integral time T_L+ > 0 (default 10)          */
+    double temperature;   /* gas temperature, K > 0 (default 293.15)                       */
+    double vdw_cutoff;    /* gap below which F_vdw is held constant, m > 0 (1e-12, App. B) */
+} pdq_lf_desc;
+void pdq_lf_desc_default(pdq_lf_desc* out);
+
+/* v_f'^2 at the field's radial nodes r_i: var device [n_r] (caller-owned),
+ * the population variance over the n_th x n_z nodes of u_r = cos(theta_j) u_x
+ * + sin(theta_j) u_y of the FP64 grid (mean removed; fixed-order reductions,
+ * deterministic).  Enqueued on `stream`.  Errors: INVALID_ARG, CUDA.          */
+int pdq_lf_fluid_variance(const pdq_field* field, double* var, pdq_stream_t stream);
+
+/* V_dep+ of the low-fidelity model for n_samples >= 0 samples and n_classes
+ * size classes (host st_plus [C], 1 <= C <= 16): params device [S] (xi and
+ * zeta used), var device [n_r] any v_f'^2 profile at `field`'s radial nodes
+ * (normally pdq_lf_fluid_variance's), vdep device [S][C] (row = sample, the
+ * deposition velocity over the centreline particle density; caller-owned).
+ * FP64; one thread per item, 5 (n_y - 1) doubles of shared memory per CTA of
+ * 256 samples.  Enqueued on `stream`; no allocation, no synchronisation.
+ * Errors: INVALID_ARG (sizes, desc out of range, field radius != phys
+ * Re_tau, NULL pointers), CUDA.                                              */
+int pdq_lf_vdep(const pdq_field* field, const pdq_phys* phys, const pdq_lf_desc* lf, const double* var,
+                int32_t n_classes, const double* st_plus, int64_t n_samples, const pdq_sample_params* params,
+                double* vdep, pdq_stream_t stream);
+
 /* ------------------------------------------------------------------ P3M
  * Electrostatics by P3M (App. A.2: the particle-particle particle-mesh method
  * the paper uses for ~1e6 particles per sample), for the periodic pipe:

@@ -63,6 +63,11 @@ class BatchStruct(C.Structure):
                 ("st_plus", C.c_double * MAX_CLASSES), ("capacity", C.c_int64), ("offset", C.c_void_p)]
 
 
+class LfDesc(C.Structure):
+    _fields_ = [("n_y", C.c_int32), ("reserved", C.c_int32), ("stretch", C.c_double), ("t_lagr", C.c_double),
+                ("temperature", C.c_double), ("vdw_cutoff", C.c_double)]
+
+
 class TallyStruct(C.Structure):
     _fields_ = [("n_dep", C.c_void_p), ("n_alive", C.c_void_p)]
 
@@ -130,6 +135,9 @@ def lib():
             "pdq_p3m_coulomb": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P, P]),
             "pdq_step_particles_p3m": (C.c_int, [P, C.POINTER(Phys), C.POINTER(StateStruct), P, C.POINTER(StepCfg),
                                                  C.c_int64, C.POINTER(TallyStruct), P, P, C.c_size_t, P]),
+            "pdq_lf_desc_default": (None, [C.POINTER(LfDesc)]),
+            "pdq_lf_fluid_variance": (C.c_int, [P, P, P]),
+            "pdq_lf_vdep": (C.c_int, [P, C.POINTER(Phys), C.POINTER(LfDesc), P, C.c_int32, P, C.c_int64, P, P, P]),
             "pdq_mfmc_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                                   C.POINTER(C.c_size_t)]),
             "pdq_mfmc_sobol": (C.c_int, [C.c_int32, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
@@ -311,6 +319,34 @@ def step_cfg(dt, forces=F_ALL, mode=STICK, gravity=(0.0, 0.0, 1.0), window_start
     # use_graph: False/0 direct, True/1 captured graph (replayed on later calls), 2 capture only
     c.compact_every, c.block, c.use_graph, c.variant = compact_every, block, int(use_graph), variant
     return c
+
+
+def lf_desc(n_y=None, stretch=None, t_lagr=None, temperature=None, vdw_cutoff=None):
+    """Parameters of the 1-D Eulerian low-fidelity model (library defaults where None)."""
+    d = LfDesc()
+    lib().pdq_lf_desc_default(C.byref(d))
+    for k, v in dict(n_y=n_y, stretch=stretch, t_lagr=t_lagr, temperature=temperature,
+                     vdw_cutoff=vdw_cutoff).items():
+        if v is not None:
+            setattr(d, k, v)
+    return d
+
+
+def lf_fluid_variance(field, stream=None):
+    """v_f'^2 [n_r] (float64, device) of the field's radial velocity at its radial nodes."""
+    out = torch.empty(field.desc.n_r, dtype=torch.float64, device="cuda")
+    _check(lib().pdq_lf_fluid_variance(field.handle, _ptr(out), _stream(stream)), "lf_fluid_variance")
+    return out
+
+
+def lf_vdep(field, phys, desc, var, st_plus, params_dev, out=None, stream=None):
+    """V_dep+ [S, C] (float64, device) of the 1-D Eulerian model for params_dev (pdq_sample_params[S])."""
+    S, Cn = int(params_dev.shape[0]), len(st_plus)
+    out = out if out is not None else torch.empty((S, Cn), dtype=torch.float64, device="cuda")
+    st = (C.c_double * Cn)(*[float(x) for x in st_plus])
+    _check(lib().pdq_lf_vdep(field.handle, C.byref(phys), C.byref(desc), _ptr(var), Cn, C.cast(st, C.c_void_p), S,
+                             _ptr(params_dev), _ptr(out), _stream(stream)), "lf_vdep")
+    return out
 
 
 def params_tensor(params, device="cuda"):

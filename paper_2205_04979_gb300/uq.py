@@ -3,11 +3,12 @@
 The uncertain inputs (xi, zeta, theta) of Secs. 2.1 and 4.3 are drawn uniform
 over their ranges; each pick-freeze group (x, x', z^(1..d)) becomes d + 2
 Monte Carlo samples of one batched run of the particle step (common random
-particle seeds), whose V_dep+ per size class feeds pdq_mfmc_sobol.  Only the
-high-fidelity model is available here (the paper's 1-D Eulerian model needs
-closures it does not print), so the estimator is the one-model case of the MFMC
-formulas (k = 1), with bootstrap intervals.  Every numerical step runs in
-libpdq; this module only arranges the inputs.
+particle seeds), whose V_dep+ per size class feeds pdq_mfmc_sobol.
+sobol_deposition runs the particle model alone, i.e. the one-model case of the
+MFMC formulas (k = 1), with bootstrap intervals; a low-fidelity model (the 1-D
+Eulerian model, pdq_lf_vdep, or a cheaper particle model) joins as model 2 of
+pdq_mfmc_sobol.  Every numerical step runs in libpdq; this module only arranges
+the inputs.
 """
 import numpy as np
 import torch

@@ -41,3 +41,19 @@ def test_measured_pipe_peaks_are_read_from_the_committed_summary():
     # the Newton-pair mix: 16 pipe operations for 24 flops
     assert abs(mix32["peak"] - 2 * rec["kernels"]["ffma2"]["lane_ops_per_s"] * 1.5 / 1e12) < 1e-9
     assert mix64 is None
+
+
+def test_reference_arm_of_the_low_fidelity_workload():
+    env = dict(os.environ)
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "lf_eulerian", "--samples", "24", "--steps", "1", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "evaluations/s" and d["value"] > 0
+    assert d["config"]["workload"] == "lf_eulerian: 24 samples x 10 St+ classes"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]

@@ -196,3 +196,15 @@ def test_adjoint_stored_sums_size(pdq):
     assert L.pdq_adjoint_stored_sums_size(-1, 10, C.byref(n)) == -1
     assert L.pdq_adjoint_stored_sums_size(4096, 0, C.byref(n)) == -1
     assert L.pdq_adjoint_stored_sums_size(4096, 10, None) == -1
+
+
+def test_low_fidelity_defaults_and_arguments_rejected_on_host(pdq):
+    L = pdq.lib()
+    d = pdq.lf_desc()
+    assert (d.n_y, d.stretch, d.t_lagr, d.temperature, d.vdw_cutoff) == (2048, 8.0, 10.0, 293.15, 1e-12)
+    p = pdq.phys_default()
+    st = (C.c_double * 1)(1.0)
+    # NULL field / variance / descriptor fail before any CUDA call
+    assert L.pdq_lf_fluid_variance(None, None, None) == -1
+    assert L.pdq_lf_vdep(None, C.byref(p), C.byref(d), None, 1, C.cast(st, C.c_void_p), 1, None, None, None) == -1
+    assert L.pdq_lf_vdep(None, C.byref(p), None, None, 1, C.cast(st, C.c_void_p), 0, None, None, None) == -1

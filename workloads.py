@@ -18,6 +18,9 @@ temperature theta in [0, 1], Secs. 2.1 and 4.3):
 * ``batched_mixed``: 1,024 samples, inputs uniform over +-50 % of nominal,
   counts uniform in 4,096..32,768, 5 St+ classes, 10,000 steps at dt+ = 0.05.
 * ``adjoint``: 256 samples x 16,384 particles, 2,000 steps, checkpoints every 100.
+* ``lf_eulerian``: the low-fidelity side of the MFMC Sobol' study, the 1-D
+  Eulerian model of App. B on 262,144 samples x 10 St+ classes (log-spaced
+  0.1..100), inputs uniform over the paper's ranges, the 128x64x128 field.
 """
 import numpy as np
 
@@ -42,6 +45,8 @@ WORKLOADS = {
     "adjoint": dict(samples=256, count=16384, st_plus=[0.1, 1.0, 10.0], grid=(64, 32, 64), n_modes=64,
                     field_seed=0, particle_seed=1, param_seed=3, dt=0.05, steps=2000, checkpoint=100,
                     t_window=10.0, eps=(0.5, 0.1, 0.02), precision="mixed"),
+    "lf_eulerian": dict(samples=262144, st_plus=st_plus_log(10), grid=(128, 64, 128), n_modes=64, field_seed=0,
+                        param_seed=5, spread=1.0, n_y=2048, precision="fp64"),
 }
 
 
