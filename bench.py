@@ -952,6 +952,10 @@ LF_FLOPS_PER_CELL = 23
 # polynomial steps) and the DRAM bytes of that launch (read + write), scaled by samples
 LF_FP64_OPS_PER_CELL = 61.41
 LF_DRAM_BYTES_PER_SAMPLE = 1.053e6 / 16384
+# the FP32 march: (what bounds it, thread instructions per (item, cell) as executed (ncu, same capture
+# size), the measured rate it is compared with): every instruction takes an issue slot, and the issue
+# limit of 4 warp instructions per clock per SM equals the measured scalar FFMA lane rate
+LF_F32_PIPE = ("instruction issue", 101.03, "ffma")
 
 
 def lf_cpu_baseline(w, params, seconds):
@@ -979,9 +983,10 @@ def run_lf(args):
     """The 1-D Eulerian low-fidelity model (App. B) at the Sobol' study's low-fidelity size.
 
     One bench step = one evaluation of V_dep+ for every (sample, class) item: 262,144 samples x 10
-    St+ classes at 2,048 wall-normal nodes (pdq_lf_vdep, one kernel launch).  L2 is flushed
-    between timed steps.  e2e: the inputs uploaded from pinned host memory and V_dep+ downloaded
-    every step.
+    St+ classes at 2,048 wall-normal nodes (pdq_lf_vdep, one kernel launch).  The headline is the
+    PDQ_MIXED march (FP32, wall condition and ratio in FP64); the FP64 march is timed beside it and
+    every item of the two is compared.  L2 is flushed between timed steps.  e2e: the inputs
+    uploaded from pinned host memory and V_dep+ downloaded every step.
     """
     import torch
     import paper_2205_04979_gb300.pdq as pdq
@@ -1002,27 +1007,32 @@ def run_lf(args):
     with torch.cuda.stream(stream):
         field = pdq.Field(desc, w["field_seed"], stream)
         var = pdq.lf_fluid_variance(field, stream)
-        lfd = pdq.lf_desc(n_y=w["n_y"])
         prm = pdq.params_tensor(params)
         out = torch.empty((S, C), dtype=torch.float64, device="cuda")
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        for _ in range(args.warmup):
-            pdq.lf_vdep(field, phys, lfd, var, st, prm, out=out, stream=stream)
-        stream.synchronize()
-        clk = ClockSampler(uuid)
-        clk.start()
-        evs = []
-        for k in range(args.steps):
-            flush.fill_(k & 255)                    # evict L2 between timed evaluations
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pdq.lf_vdep(field, phys, lfd, var, st, prm, out=out, stream=stream)
-            e1.record(stream)
-            evs.append((e0, e1))
-        stream.synchronize()
-        clocks = clk.stop()
-        ms = sum(a.elapsed_time(b) for a, b in evs)
-        vd = out.cpu().numpy()
+
+        def timed(lfd):
+            for _ in range(args.warmup):
+                pdq.lf_vdep(field, phys, lfd, var, st, prm, out=out, stream=stream)
+            stream.synchronize()
+            clk = ClockSampler(uuid)
+            clk.start()
+            evs = []
+            for k in range(args.steps):
+                flush.fill_(k & 255)                    # evict L2 between timed evaluations
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pdq.lf_vdep(field, phys, lfd, var, st, prm, out=out, stream=stream)
+                e1.record(stream)
+                evs.append((e0, e1))
+            stream.synchronize()
+            clocks = clk.stop()
+            return sum(a.elapsed_time(b) for a, b in evs), out.cpu().numpy(), clocks
+
+        lfm = pdq.lf_desc(n_y=w["n_y"], precision=pdq.MIXED)
+        lfd = pdq.lf_desc(n_y=w["n_y"], precision=pdq.FP64)
+        ms, vd, clocks = timed(lfm)
+        ms64, vd64, clocks64 = timed(lfd)
         # end to end: pinned host inputs in, V_dep+ out, every step
         host_in = torch.zeros((S, 4), dtype=torch.float64).pin_memory()
         host_in[:, :3] = torch.from_numpy(params)
@@ -1031,7 +1041,7 @@ def run_lf(args):
         e0.record(stream)
         for k in range(args.steps):
             prm.copy_(host_in, non_blocking=True)
-            pdq.lf_vdep(field, phys, lfd, var, st, prm, out=out, stream=stream)
+            pdq.lf_vdep(field, phys, lfm, var, st, prm, out=out, stream=stream)
             host_out.copy_(out, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
@@ -1039,38 +1049,49 @@ def run_lf(args):
         assert np.array_equal(host_out.numpy(), vd)
     from paper_2205_04979_gb300 import peaks as pk
     rec = pk.load(PEAKS_FILE)
-    peak_ops = rec["kernels"]["dfma"]["lane_ops_per_s"] / 1e9 if rec else None
-    peak = rec["kernels"]["dfma"]["flops_per_s"] / 1e12 if rec else None
+    k = rec["kernels"] if rec else None
     items = S * C
     cells = w["n_y"] - 1
-    sec = ms / args.steps / 1e3
-    achieved_ops = LF_FP64_OPS_PER_CELL * cells * items / sec / 1e9
-    achieved = LF_FLOPS_PER_CELL * cells * items / sec / 1e12
+    sec, sec64 = ms / args.steps / 1e3, ms64 / args.steps / 1e3
+    rel = np.abs(vd / vd64 - 1)
+    roof = {"bound": "alu", "kernel": "k_lf_vdep<float>", "unit": "TFLOP/s", "traffic": LF_DRAM_BYTES_PER_SAMPLE * S,
+            "achieved": LF_FLOPS_PER_CELL * cells * items / sec / 1e12,
+            "peak": k["ffma2"]["flops_per_s"] / 1e12 if k else None,
+            "note": "%d operations per (item, cell) of the scheme, sqrt, expm1 and divisions counted as one each "
+                    "(each expands to several FP32 instructions), against the measured FFMA2 peak; traffic "
+                    "scaled from a 16,384-sample capture" % LF_FLOPS_PER_CELL}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
+    if LF_F32_PIPE is not None and k:
+        # the pipe that bounds the FP32 march, its instructions as executed against the measured rate
+        name, per_cell, rate = LF_F32_PIPE
+        got = per_cell * cells * items / sec
+        roof["pipe"] = {"pipe": name, "lane_ops_per_cell": per_cell, "achieved_gops": got / 1e9,
+                        "peak_gops": k[rate]["lane_ops_per_s"] / 1e9, "frac": got / k[rate]["lane_ops_per_s"]}
     out_json = {
         "metric": "low-fidelity evaluations/s (1-D Eulerian model of App. B, sample x class items)",
         "value": items * args.steps / (ms / 1e3), "unit": "evaluations/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "lf_eulerian: %d samples x %d St+ classes (log-spaced 0.1..100), inputs xi in "
                                "[0, 0.1], zeta in [0, 1], theta in [0, 1], %d wall-normal nodes, v_f'^2 from the "
                                "128x64x128 field" % (S, C, w["n_y"]),
-                   "l2": "flushed between timed steps (256 MiB write)"},
-        "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak_ops, "unit": "Gop/s",
-                     "frac": achieved_ops / peak_ops if peak_ops else None,
-                     "traffic": LF_DRAM_BYTES_PER_SAMPLE * S,
-                     "kernel": "k_lf_vdep",
-                     "note": "FP64 pipe: %.2f FP64 lane operations per (item, cell) as executed (ncu instruction "
-                             "counters), against the measured DFMA lane-operation rate; traffic scaled from a "
-                             "16,384-sample capture" % LF_FP64_OPS_PER_CELL,
-                     "algorithmic": {"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                                     "frac": achieved / peak if peak else None,
-                                     "note": "%d FP64 operations per (item, cell), sqrt, expm1 and divisions "
-                                             "counted as one each; measured DFMA peak" % LF_FLOPS_PER_CELL}},
+                   "l2": "flushed between timed steps (256 MiB write)", "precision": "PDQ_MIXED (FP32 march)"},
+        "roofline": roof,
         "clocks": clocks, "gpu_launches": args.steps,
         "e2e": {"value": items * args.steps / (ms_e2e / 1e3), "unit": "evaluations/s",
                 "h2d_bytes_per_step": int(S * 32), "d2h_bytes_per_step": int(S * C * 8)},
+        "fp64": {"value": items * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps, "clocks": clocks64,
+                 "roofline": {"bound": "alu", "kernel": "k_lf_vdep<double>", "unit": "Gop/s",
+                              "achieved": LF_FP64_OPS_PER_CELL * cells * items / sec64 / 1e9,
+                              "peak": k["dfma"]["lane_ops_per_s"] / 1e9 if k else None,
+                              "frac": (LF_FP64_OPS_PER_CELL * cells * items / sec64 / k["dfma"]["lane_ops_per_s"]
+                                       if k else None),
+                              "note": "%.2f FP64-pipe lane operations per (item, cell) as executed (ncu "
+                                      "instruction counters), against the measured DFMA lane-operation rate"
+                                      % LF_FP64_OPS_PER_CELL}},
+        "mixed_vs_fp64": {"max_rel": float(rel.max()), "median_rel": float(np.median(rel)), "items": int(items)},
         "us_per_sample_all_classes": ms / args.steps / S * 1e3,
-        "vdep_mean": np.mean(vd, 0).tolist(),
+        "vdep_mean": np.mean(vd64, 0).tolist(),
     }
     if not args.no_cpu_baseline:
         out_json["cpu_baseline"] = lf_cpu_baseline(w, params, min(args.cpu_seconds, 15.0))

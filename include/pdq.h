@@ -543,7 +543,10 @@ int pdq_dgsm_bounds(int32_t S, int32_t C, int32_t d, const double* grad, const d
 #define PDQ_LF_MAX_NODES 4096
 typedef struct pdq_lf_desc {
     int32_t n_y;          /* wall-normal nodes, 3..PDQ_LF_MAX_NODES (default 2048)          */
-    int32_t reserved;     /* 0                                                              */
+    int32_t precision;    /* PDQ_FP64 (default): the march in FP64; PDQ_MIXED: the cell     */
+                          /* table and the march in FP32 (Q summed with compensation), the  */
+                          /* wall condition and the final ratio in FP64: within ~1e-5 of    */
+                          /* the FP64 result, dozens of times faster on the FP32 pipe       */
     double stretch;       /* near-wall refinement gamma, 0 < gamma <= 700 (default 8)      */
     double t_lagr;        /* fluid Lagrangian integral time T_L+ > 0 (default 10)          */
     double temperature;   /* gas temperature, K > 0 (default 293.15)                       */
@@ -562,8 +565,8 @@ int pdq_lf_fluid_variance(const pdq_field* field, double* var, pdq_stream_t stre
  * zeta used), var device [n_r] any v_f'^2 profile at `field`'s radial nodes
  * (normally pdq_lf_fluid_variance's), vdep device [S][C] (row = sample, the
  * deposition velocity over the centreline particle density; caller-owned).
- * FP64; one thread per item, 5 (n_y - 1) doubles of shared memory per CTA of
- * 256 samples.  Enqueued on `stream`; no allocation, no synchronisation.
+ * One thread per item, 5 (n_y - 1) doubles (PDQ_MIXED: floats) of shared
+ * memory per CTA of 256 samples.  Enqueued on `stream`; no allocation, no synchronisation.
  * Errors: INVALID_ARG (sizes, desc out of range, field radius != phys
  * Re_tau, NULL pointers), CUDA.                                              */
 int pdq_lf_vdep(const pdq_field* field, const pdq_phys* phys, const pdq_lf_desc* lf, const double* var,

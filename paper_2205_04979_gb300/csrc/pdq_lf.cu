@@ -27,8 +27,10 @@
 //   a' = V_m dy/D_m,
 // inward as rho_axis = P rho_k - J Q (P <- P E_k, Q <- Q + P G_k), so nothing
 // per node is stored.  At the wall J = rho_w K and rho_axis = 1 give
-// V_dep+ = -K/(P - K Q).  Everything is FP64: the work is ~2,000 cells per
-// item, bound by the FP64 pipe, and tiny next to one high-fidelity sample.
+// V_dep+ = -K/(P - K Q).  PDQ_FP64 marches in FP64 (bound by the FP64 pipe);
+// PDQ_MIXED marches in FP32 with the wall condition and the final ratio in
+// FP64.  Either way the ~2,000 cells per item are tiny next to one
+// high-fidelity sample.
 #include <math.h>
 #include <string.h>
 
@@ -93,58 +95,72 @@ __device__ __forceinline__ LfNode lf_node(const LfArgs& A, const LfClass& K, int
     return n;
 }
 
+// T = double: the march in FP64.  T = float (PDQ_MIXED): the cell table and the
+// march in FP32 (IEEE square root, division and expm1f; Q summed with Kahan
+// compensation), the wall condition and the final ratio in FP64.
+template <typename T>
 __global__ void __launch_bounds__(kLfThreads) k_lf_vdep(const LfArgs A) {
-    extern __shared__ double tab[];   // 5 arrays of n_y - 1 cells: dw, dinv_y, dpsi, dy/tau, dy/D_m
+    extern __shared__ __align__(16) unsigned char lf_smem[];
+    T* tab = reinterpret_cast<T*>(lf_smem);   // 5 arrays of n_y - 1 cells: dw, dinv_y, dpsi, dy/tau, dy/D_m
     const int c = blockIdx.y;
     const LfClass K = A.cls[c];
     const int ncell = A.n_y - 1;
-    double* t_dw = tab;
-    double* t_de = tab + ncell;
-    double* t_dv = tab + 2 * ncell;
-    double* t_a = tab + 3 * ncell;
-    double* t_h = tab + 4 * ncell;
+    T* t_dw = tab;
+    T* t_de = tab + ncell;
+    T* t_dv = tab + 2 * ncell;
+    T* t_a = tab + 3 * ncell;
+    T* t_h = tab + 4 * ncell;
     __shared__ double s_sigma;
     for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
         const LfNode lo = lf_node(A, K, k), hi = lf_node(A, K, k + 1);
         const double dy = hi.y - lo.y;
-        t_dw[k] = hi.w - lo.w;
-        t_de[k] = hi.inv_y - lo.inv_y;
-        t_dv[k] = hi.psi - lo.psi;
-        t_a[k] = dy / K.tau;
-        t_h[k] = dy / (0.5 * (lo.D + hi.D));
+        t_dw[k] = (T)(hi.w - lo.w);
+        t_de[k] = (T)(hi.inv_y - lo.inv_y);
+        t_dv[k] = (T)(hi.psi - lo.psi);
+        t_a[k] = (T)(dy / K.tau);
+        t_h[k] = (T)(dy / (0.5 * (lo.D + hi.D)));
         if (k == 0) s_sigma = sqrt(K.resp * lf_var_at(A, lo.y) + K.thermal);
     }
     __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= A.S) return;
     const double xi = A.params[s].xi, zeta = A.params[s].zeta;
-    const double ae = -K.ce * xi * xi, av = -K.cv * zeta;
-    double v_out = 0.0;   // V at node k + 1 (the axis: 0)
-    double P = 1.0, Q = 0.0;
+    const T ae = (T)(-K.ce * xi * xi), av = (T)(-K.cv * zeta);
+    const T half = (T)0.5, two = (T)2, zero = (T)0, one = (T)1;
+    T v_out = zero;   // V at node k + 1 (the axis: 0)
+    T P = one, Q = zero, Qc = zero;
     for (int k = ncell - 1; k >= 0; --k) {
         // momentum: implicit drag, root <= 0 of V^2/2 - a V = c
-        const double a = t_a[k];
-        const double c2 = 0.5 * v_out * v_out + t_dw[k] + (ae * t_de[k] + av * t_dv[k]);
-        double v_in = 0.0;
-        if (c2 > 0.0) v_in = -2.0 * c2 / (a + sqrt(fma(a, a, 2.0 * c2)));
+        const T a = t_a[k];
+        const T c2 = half * v_out * v_out + t_dw[k] + (ae * t_de[k] + av * t_dv[k]);
+        T v_in = zero;
+        if (c2 > zero) v_in = -two * c2 / (a + sqrt(fma(a, a, two * c2)));
         // continuity: exact cell solution with the cell-mean V and D
-        const double vm = 0.5 * (v_in + v_out);
-        const double am = vm * t_h[k];
-        double G = t_h[k], E = 1.0;
-        if (am != 0.0) {
-            const double em = expm1(am);
+        const T vm = half * (v_in + v_out);
+        const T am = vm * t_h[k];
+        T G = t_h[k], E = one;
+        if (am != zero) {
+            const T em = expm1(am);
             G = em / vm;
-            E = 1.0 + em;
+            E = one + em;
         }
-        Q = fma(P, G, Q);
+        if constexpr (sizeof(T) == sizeof(double)) {
+            Q = fma(P, G, Q);
+        } else {
+            const T yq = fma(P, G, -Qc);
+            const T tq = Q + yq;
+            Qc = (tq - Q) - yq;
+            Q = tq;
+        }
         P *= E;
         v_out = v_in;
     }
-    // kinetic wall condition: one-way flux of a Gaussian velocity (mean V_w, sd sigma)
-    const double u = -v_out, sg = s_sigma;
+    // kinetic wall condition: one-way flux of a Gaussian velocity (mean V_w, sd sigma), FP64
+    const double u = -(double)v_out, sg = s_sigma;
     const double M = u / (1.4142135623730951 * sg);
     const double Kw = -(0.5 * u * (1.0 + erf(M)) + sg * exp(-M * M) * 0.3989422804014327);
-    A.vdep[s * A.C + c] = -Kw / (P - Kw * Q);
+    const double Qd = (double)Q - (double)Qc;
+    A.vdep[s * A.C + c] = -Kw / ((double)P - Kw * Qd);
 }
 
 // Population variance over (theta, z) of u_r = cos(theta) u_x + sin(theta) u_y
@@ -188,6 +204,7 @@ extern "C" void pdq_lf_desc_default(pdq_lf_desc* out) {
     if (!out) return;
     memset(out, 0, sizeof(*out));
     out->n_y = 2048;
+    out->precision = PDQ_FP64;
     out->stretch = 8.0;
     out->t_lagr = 10.0;
     out->temperature = 293.15;
@@ -202,7 +219,7 @@ extern "C" int pdq_lf_fluid_variance(const pdq_field* field, double* var, pdq_st
     return PDQ_OK;
 }
 
-static size_t lf_shared_bytes(int32_t n_y) { return (size_t)5 * (size_t)(n_y - 1) * sizeof(double); }
+static size_t lf_shared_bytes(int32_t n_y, size_t elem) { return (size_t)5 * (size_t)(n_y - 1) * elem; }
 
 extern "C" int pdq_lf_vdep(const pdq_field* field, const pdq_phys* phys, const pdq_lf_desc* lf, const double* var,
                            int32_t n_classes, const double* st_plus, int64_t n_samples,
@@ -210,6 +227,7 @@ extern "C" int pdq_lf_vdep(const pdq_field* field, const pdq_phys* phys, const p
     if (!field || !phys || !lf || !var || !st_plus || n_samples < 0) return PDQ_ERR_INVALID_ARG;
     if (n_classes < 1 || n_classes > PDQ_MAX_CLASSES) return PDQ_ERR_INVALID_ARG;
     if (lf->n_y < 3 || lf->n_y > PDQ_LF_MAX_NODES) return PDQ_ERR_INVALID_ARG;
+    if (lf->precision != PDQ_FP64 && lf->precision != PDQ_MIXED) return PDQ_ERR_INVALID_ARG;
     if (!(lf->stretch > 0.0) || !(lf->stretch <= 700.0) || !(lf->t_lagr > 0.0) || !(lf->temperature > 0.0) ||
         !(lf->vdw_cutoff > 0.0))
         return PDQ_ERR_INVALID_ARG;
@@ -256,10 +274,16 @@ extern "C" int pdq_lf_vdep(const pdq_field* field, const pdq_phys* phys, const p
     A.var = var;
     A.params = params;
     A.vdep = vdep;
-    const size_t smem = lf_shared_bytes(lf->n_y);
-    PDQ_CUDA(cudaFuncSetAttribute(k_lf_vdep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const dim3 grid((unsigned)((n_samples + kLfThreads - 1) / kLfThreads), (unsigned)n_classes);
-    k_lf_vdep<<<grid, kLfThreads, smem, (cudaStream_t)stream>>>(A);
+    if (lf->precision == PDQ_FP64) {
+        const size_t smem = lf_shared_bytes(lf->n_y, sizeof(double));
+        PDQ_CUDA(cudaFuncSetAttribute(k_lf_vdep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_lf_vdep<double><<<grid, kLfThreads, smem, (cudaStream_t)stream>>>(A);
+    } else {
+        const size_t smem = lf_shared_bytes(lf->n_y, sizeof(float));
+        PDQ_CUDA(cudaFuncSetAttribute(k_lf_vdep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_lf_vdep<float><<<grid, kLfThreads, smem, (cudaStream_t)stream>>>(A);
+    }
     PDQ_CUDA(cudaGetLastError());
     return PDQ_OK;
 }

@@ -64,7 +64,7 @@ class BatchStruct(C.Structure):
 
 
 class LfDesc(C.Structure):
-    _fields_ = [("n_y", C.c_int32), ("reserved", C.c_int32), ("stretch", C.c_double), ("t_lagr", C.c_double),
+    _fields_ = [("n_y", C.c_int32), ("precision", C.c_int32), ("stretch", C.c_double), ("t_lagr", C.c_double),
                 ("temperature", C.c_double), ("vdw_cutoff", C.c_double)]
 
 
@@ -321,12 +321,12 @@ def step_cfg(dt, forces=F_ALL, mode=STICK, gravity=(0.0, 0.0, 1.0), window_start
     return c
 
 
-def lf_desc(n_y=None, stretch=None, t_lagr=None, temperature=None, vdw_cutoff=None):
+def lf_desc(n_y=None, stretch=None, t_lagr=None, temperature=None, vdw_cutoff=None, precision=None):
     """Parameters of the 1-D Eulerian low-fidelity model (library defaults where None)."""
     d = LfDesc()
     lib().pdq_lf_desc_default(C.byref(d))
     for k, v in dict(n_y=n_y, stretch=stretch, t_lagr=t_lagr, temperature=temperature,
-                     vdw_cutoff=vdw_cutoff).items():
+                     vdw_cutoff=vdw_cutoff, precision=precision).items():
         if v is not None:
             setattr(d, k, v)
     return d

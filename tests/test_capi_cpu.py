@@ -201,7 +201,8 @@ def test_adjoint_stored_sums_size(pdq):
 def test_low_fidelity_defaults_and_arguments_rejected_on_host(pdq):
     L = pdq.lib()
     d = pdq.lf_desc()
-    assert (d.n_y, d.stretch, d.t_lagr, d.temperature, d.vdw_cutoff) == (2048, 8.0, 10.0, 293.15, 1e-12)
+    assert (d.n_y, d.precision, d.stretch, d.t_lagr, d.temperature, d.vdw_cutoff) == (2048, 0, 8.0, 10.0, 293.15,
+                                                                                     1e-12)
     p = pdq.phys_default()
     st = (C.c_double * 1)(1.0)
     # NULL field / variance / descriptor fail before any CUDA call

@@ -20,6 +20,10 @@ import oracle  # noqa: E402
 from oracle import lf_eulerian as lfo  # noqa: E402
 
 RTOL = 1e-10
+# PDQ_MIXED (FP32 march, FP64 wall condition and ratio): a float32 restatement of the march, with
+# IEEE operations, stays within 3.3e-6 of the FP64 oracle (median 5e-7) on 2,000 items at 2,048
+# nodes (rounding ~6e-8 per operation over ~2,000 cells); the bar leaves a factor of 6
+RTOL_MIXED = 2e-5
 ST5 = [0.1, 0.316, 1.0, 3.16, 10.0]
 
 
@@ -72,6 +76,20 @@ def test_vdep_matches_oracle(pdq, fields, n_y):
     ref = lfo.lf_vdep(oracle.phys(), ST5, prm, var_o, of.r_plus, of.beta, lfo.lf_params(n_y=n_y))
     assert np.all(np.isfinite(got)) and np.all(got > 0)
     assert np.max(np.abs(got / ref - 1)) < RTOL
+
+
+@pytest.mark.parametrize("n_y", [3, 129, 2048, 4096])
+def test_mixed_vdep_matches_oracle(pdq, fields, n_y):
+    f, of, var_o = fields[(64, 32, 64)]
+    S = 600 if n_y <= 2048 else 130
+    prm = _params(S, 100 + n_y)
+    prm[0] = [0.0, 0.0, 0.5]
+    var = pdq.lf_fluid_variance(f)
+    got = pdq.lf_vdep(f, pdq.phys_default(), pdq.lf_desc(n_y=n_y, precision=pdq.MIXED), var, ST5,
+                      pdq.params_tensor(prm)).cpu().numpy()
+    ref = lfo.lf_vdep(oracle.phys(), ST5, prm, var_o, of.r_plus, of.beta, lfo.lf_params(n_y=n_y))
+    assert np.all(np.isfinite(got)) and np.all(got > 0)
+    assert np.max(np.abs(got / ref - 1)) < RTOL_MIXED
 
 
 def test_vdep_parameters_and_class_edge_cases(pdq, fields):
@@ -138,7 +156,7 @@ def test_empty_and_invalid_arguments(pdq, fields):
     torch.cuda.synchronize()
     assert torch.all(out == -7.0)
     for bad in [dict(n_y=2), dict(n_y=4097), dict(stretch=0.0), dict(stretch=701.0), dict(t_lagr=0.0),
-                dict(temperature=-1.0), dict(vdw_cutoff=0.0)]:
+                dict(temperature=-1.0), dict(vdw_cutoff=0.0), dict(precision=2), dict(precision=-1)]:
         assert call(pdq.lf_desc(**bad)) == -1, bad
     assert call(pdq.lf_desc(), n_classes=0) == -1
     assert call(pdq.lf_desc(), n_classes=17) == -1
@@ -168,3 +186,6 @@ def test_full_size_sampled(pdq, fields):
     idx[0], idx[1] = 0, S - 1
     ref = lfo.lf_vdep(oracle.phys(), st10, prm[idx], var_o, of.r_plus, of.beta)
     assert np.max(np.abs(got[idx] / ref - 1)) < RTOL
+    # the FP32 march on the same items: every item within the MIXED bar of the FP64 march
+    mix = pdq.lf_vdep(f, phys, pdq.lf_desc(precision=pdq.MIXED), var, st10, pdq.params_tensor(prm)).cpu().numpy()
+    assert np.all(np.isfinite(mix)) and np.max(np.abs(mix / got - 1)) < RTOL_MIXED
