@@ -949,13 +949,13 @@ def run_p3m(args):
 LF_FLOPS_PER_CELL = 23
 # FP64-pipe lane instructions per (item, cell) as executed (ncu instruction counters on a launch of
 # 16,384 samples x 10 classes: the square root, divisions and expm1 expand to seeds plus Newton or
-# polynomial steps) and the DRAM bytes of that launch (read + write), scaled by samples
+# polynomial steps), and the DRAM bytes (read + write) of a 65,536-sample launch, scaled by samples
 LF_FP64_OPS_PER_CELL = 61.41
-LF_DRAM_BYTES_PER_SAMPLE = 1.053e6 / 16384
+LF_DRAM_BYTES_PER_SAMPLE = 2.172e6 / 65536
 # the FP32 march: (what bounds it, thread instructions per (item, cell) as executed (ncu, same capture
 # size), the measured rate it is compared with): every instruction takes an issue slot, and the issue
 # limit of 4 warp instructions per clock per SM equals the measured scalar FFMA lane rate
-LF_F32_PIPE = ("instruction issue", 101.03, "ffma")
+LF_F32_PIPE = ("instruction issue", 56.48, "ffma")
 
 
 def lf_cpu_baseline(w, params, seconds):
@@ -1059,7 +1059,7 @@ def run_lf(args):
             "peak": k["ffma2"]["flops_per_s"] / 1e12 if k else None,
             "note": "%d operations per (item, cell) of the scheme, sqrt, expm1 and divisions counted as one each "
                     "(each expands to several FP32 instructions), against the measured FFMA2 peak; traffic "
-                    "scaled from a 16,384-sample capture" % LF_FLOPS_PER_CELL}
+                    "scaled from a 65,536-sample capture" % LF_FLOPS_PER_CELL}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
     if LF_F32_PIPE is not None and k:
         # the pipe that bounds the FP32 march, its instructions as executed against the measured rate

@@ -14,8 +14,8 @@
 // eps = v_f'^2 T_L, tau_1 = tau_p, D_B = k_B T tau_p/m_p, isothermal gas,
 // M_r = -V_w/(sqrt(2) sigma) with sigma^2 = R v_f'^2 + k_B T/m_p at contact.
 //
-// Layout: one CTA per (class, block of 256 samples).  The CTA first writes the
-// class's per-cell table into shared memory (differences of the turbophoretic
+// Layout: CTAs per class in one wave, each walking blocks of 256 samples.  A CTA
+// first writes the class's per-cell table into shared memory (differences of the turbophoretic
 // term and of the two potential shapes, dy/tau and dy/D across each cell: 40 B
 // per cell); then each thread marches one sample from the axis (V = 0) to the
 // wall.  At every cell it solves the implicit momentum step
@@ -95,72 +95,116 @@ __device__ __forceinline__ LfNode lf_node(const LfArgs& A, const LfClass& K, int
     return n;
 }
 
+// One cell of the class table: differences of R v_f'^2 and of the two potential
+// shapes across the cell and dy/tau (16 B in FP32, one shared-memory load; the
+// cell's dy/D_m sits in a second array).
+template <typename T>
+struct __align__(16) LfCell {
+    T dw, de, dv, a;
+};
+
+// exp(x) - 1 over x, for the FP32 march (x <= 0): Taylor polynomial below
+// |x| = 0.5 (terms to x^8/9!, truncation < 1e-9 relative), the approximate
+// exponential beyond (E - 1 then stays below -0.39, so its relative rounding
+// does not grow).  Returns phi and E = 1 + x phi.
+__device__ __forceinline__ float lf_phi(float x, float* E) {
+    if (x > -0.5f) {
+        float p = 2.7557319e-6f;                  // 1/9!
+        p = fmaf(p, x, 2.4801587e-5f);            // 1/8!
+        p = fmaf(p, x, 1.9841270e-4f);            // 1/7!
+        p = fmaf(p, x, 1.3888889e-3f);            // 1/6!
+        p = fmaf(p, x, 8.3333333e-3f);            // 1/5!
+        p = fmaf(p, x, 4.1666667e-2f);            // 1/4!
+        p = fmaf(p, x, 1.6666667e-1f);            // 1/3!
+        p = fmaf(p, x, 0.5f);                     // 1/2!
+        p = fmaf(p, x, 1.0f);
+        *E = fmaf(x, p, 1.0f);
+        return p;
+    }
+    const float e = __expf(x);
+    *E = e;
+    return __fdividef(e - 1.0f, x);
+}
+
 // T = double: the march in FP64.  T = float (PDQ_MIXED): the cell table and the
-// march in FP32 (IEEE square root, division and expm1f; Q summed with Kahan
-// compensation), the wall condition and the final ratio in FP64.
+// march in FP32 (root by x rsqrt(x) and an approximate division, the cell's
+// exponential by lf_phi; Q summed with Kahan compensation), the wall
+// condition and the final ratio in FP64.  Each CTA builds its class's table
+// once and walks blocks of 256 samples blockIdx.x, blockIdx.x + gridDim.x, ...
 template <typename T>
 __global__ void __launch_bounds__(kLfThreads) k_lf_vdep(const LfArgs A) {
     extern __shared__ __align__(16) unsigned char lf_smem[];
-    T* tab = reinterpret_cast<T*>(lf_smem);   // 5 arrays of n_y - 1 cells: dw, dinv_y, dpsi, dy/tau, dy/D_m
     const int c = blockIdx.y;
     const LfClass K = A.cls[c];
     const int ncell = A.n_y - 1;
-    T* t_dw = tab;
-    T* t_de = tab + ncell;
-    T* t_dv = tab + 2 * ncell;
-    T* t_a = tab + 3 * ncell;
-    T* t_h = tab + 4 * ncell;
+    LfCell<T>* cell = reinterpret_cast<LfCell<T>*>(lf_smem);
+    T* t_h = reinterpret_cast<T*>(cell + ncell);
     __shared__ double s_sigma;
     for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
         const LfNode lo = lf_node(A, K, k), hi = lf_node(A, K, k + 1);
         const double dy = hi.y - lo.y;
-        t_dw[k] = (T)(hi.w - lo.w);
-        t_de[k] = (T)(hi.inv_y - lo.inv_y);
-        t_dv[k] = (T)(hi.psi - lo.psi);
-        t_a[k] = (T)(dy / K.tau);
+        LfCell<T> e;
+        e.dw = (T)(hi.w - lo.w);
+        e.de = (T)(hi.inv_y - lo.inv_y);
+        e.dv = (T)(hi.psi - lo.psi);
+        e.a = (T)(dy / K.tau);
+        cell[k] = e;
         t_h[k] = (T)(dy / (0.5 * (lo.D + hi.D)));
         if (k == 0) s_sigma = sqrt(K.resp * lf_var_at(A, lo.y) + K.thermal);
     }
     __syncthreads();
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= A.S) return;
-    const double xi = A.params[s].xi, zeta = A.params[s].zeta;
-    const T ae = (T)(-K.ce * xi * xi), av = (T)(-K.cv * zeta);
-    const T half = (T)0.5, two = (T)2, zero = (T)0, one = (T)1;
-    T v_out = zero;   // V at node k + 1 (the axis: 0)
-    T P = one, Q = zero, Qc = zero;
-    for (int k = ncell - 1; k >= 0; --k) {
-        // momentum: implicit drag, root <= 0 of V^2/2 - a V = c
-        const T a = t_a[k];
-        const T c2 = half * v_out * v_out + t_dw[k] + (ae * t_de[k] + av * t_dv[k]);
-        T v_in = zero;
-        if (c2 > zero) v_in = -two * c2 / (a + sqrt(fma(a, a, two * c2)));
-        // continuity: exact cell solution with the cell-mean V and D
-        const T vm = half * (v_in + v_out);
-        const T am = vm * t_h[k];
-        T G = t_h[k], E = one;
-        if (am != zero) {
-            const T em = expm1(am);
-            G = em / vm;
-            E = one + em;
+    const double sg = s_sigma;
+    const int64_t nblk = (A.S + kLfThreads - 1) / kLfThreads;
+    for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const int64_t s = b * kLfThreads + threadIdx.x;
+        if (s >= A.S) continue;
+        const double xi = A.params[s].xi, zeta = A.params[s].zeta;
+        const T ae = (T)(-K.ce * xi * xi), av = (T)(-K.cv * zeta);
+        const T half = (T)0.5, two = (T)2, zero = (T)0, one = (T)1;
+        T v_out = zero;   // V at node k + 1 (the axis: 0)
+        T P = one, Q = zero, Qc = zero;
+        for (int k = ncell - 1; k >= 0; --k) {
+            const LfCell<T> e = cell[k];
+            const T h = t_h[k];
+            // momentum: implicit drag, root <= 0 of V^2/2 - a V = c
+            const T c2 = half * v_out * v_out + e.dw + (ae * e.de + av * e.dv);
+            T v_in = zero;
+            T G, E;
+            if constexpr (sizeof(T) == sizeof(double)) {
+                if (c2 > zero) v_in = -two * c2 / (e.a + sqrt(fma(e.a, e.a, two * c2)));
+                // continuity: exact cell solution with the cell-mean V and D
+                const T vm = half * (v_in + v_out);
+                const T am = vm * h;
+                G = h;
+                E = one;
+                if (am != zero) {
+                    const T em = expm1(am);
+                    G = em / vm;
+                    E = one + em;
+                }
+                Q = fma(P, G, Q);
+            } else {
+                if (c2 > zero) {
+                    const float x = fmaf(e.a, e.a, two * c2);
+                    v_in = __fdividef(-two * c2, e.a + x * rsqrtf(x));
+                }
+                const float am = half * (v_in + v_out) * h;   // <= 0
+                G = h * lf_phi(am, &E);
+                const T yq = fma(P, G, -Qc);
+                const T tq = Q + yq;
+                Qc = (tq - Q) - yq;
+                Q = tq;
+            }
+            P *= E;
+            v_out = v_in;
         }
-        if constexpr (sizeof(T) == sizeof(double)) {
-            Q = fma(P, G, Q);
-        } else {
-            const T yq = fma(P, G, -Qc);
-            const T tq = Q + yq;
-            Qc = (tq - Q) - yq;
-            Q = tq;
-        }
-        P *= E;
-        v_out = v_in;
+        // kinetic wall condition: one-way flux of a Gaussian velocity (mean V_w, sd sigma), FP64
+        const double u = -(double)v_out;
+        const double M = u / (1.4142135623730951 * sg);
+        const double Kw = -(0.5 * u * (1.0 + erf(M)) + sg * exp(-M * M) * 0.3989422804014327);
+        const double Qd = (double)Q - (double)Qc;
+        A.vdep[s * A.C + c] = -Kw / ((double)P - Kw * Qd);
     }
-    // kinetic wall condition: one-way flux of a Gaussian velocity (mean V_w, sd sigma), FP64
-    const double u = -(double)v_out, sg = s_sigma;
-    const double M = u / (1.4142135623730951 * sg);
-    const double Kw = -(0.5 * u * (1.0 + erf(M)) + sg * exp(-M * M) * 0.3989422804014327);
-    const double Qd = (double)Q - (double)Qc;
-    A.vdep[s * A.C + c] = -Kw / ((double)P - Kw * Qd);
 }
 
 // Population variance over (theta, z) of u_r = cos(theta) u_x + sin(theta) u_y
@@ -221,6 +265,27 @@ extern "C" int pdq_lf_fluid_variance(const pdq_field* field, double* var, pdq_st
 
 static size_t lf_shared_bytes(int32_t n_y, size_t elem) { return (size_t)5 * (size_t)(n_y - 1) * elem; }
 
+// One wave: as many CTAs per class as fit on the GPU at once (its SMs times the
+// resident CTAs per SM, divided among the classes), each building its class's
+// table once and walking ceil(blocks / CTAs) sample blocks.
+template <typename T>
+static int launch_lf(const LfArgs& A, pdq_stream_t stream) {
+    const size_t smem = lf_shared_bytes(A.n_y, sizeof(T));
+    PDQ_CUDA(cudaFuncSetAttribute(k_lf_vdep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    PDQ_CUDA(cudaGetDevice(&dev));
+    PDQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PDQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lf_vdep<T>, kLfThreads, smem));
+    const int64_t nblk = (A.S + kLfThreads - 1) / kLfThreads;
+    int64_t gx = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) / A.C;
+    if (gx < 1) gx = 1;
+    if (gx > nblk) gx = nblk;
+    const dim3 grid((unsigned)gx, (unsigned)A.C);
+    k_lf_vdep<T><<<grid, kLfThreads, smem, (cudaStream_t)stream>>>(A);
+    PDQ_CUDA(cudaGetLastError());
+    return PDQ_OK;
+}
+
 extern "C" int pdq_lf_vdep(const pdq_field* field, const pdq_phys* phys, const pdq_lf_desc* lf, const double* var,
                            int32_t n_classes, const double* st_plus, int64_t n_samples,
                            const pdq_sample_params* params, double* vdep, pdq_stream_t stream) {
@@ -235,7 +300,6 @@ extern "C" int pdq_lf_vdep(const pdq_field* field, const pdq_phys* phys, const p
     if (fabs(field->desc.r_plus - phys->re_tau) > 1e-9 * phys->re_tau) return PDQ_ERR_INVALID_ARG;
     if (n_samples == 0) return PDQ_OK;
     if (!params || !vdep) return PDQ_ERR_INVALID_ARG;
-    if ((n_samples + kLfThreads - 1) / kLfThreads > 0x7fffffff) return PDQ_ERR_INVALID_ARG;
     const double ustar = phys->re_tau * phys->nu / phys->radius;
     const double ell = phys->nu / ustar;
     const double tauf = phys->nu / (ustar * ustar);
@@ -274,16 +338,6 @@ extern "C" int pdq_lf_vdep(const pdq_field* field, const pdq_phys* phys, const p
     A.var = var;
     A.params = params;
     A.vdep = vdep;
-    const dim3 grid((unsigned)((n_samples + kLfThreads - 1) / kLfThreads), (unsigned)n_classes);
-    if (lf->precision == PDQ_FP64) {
-        const size_t smem = lf_shared_bytes(lf->n_y, sizeof(double));
-        PDQ_CUDA(cudaFuncSetAttribute(k_lf_vdep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_lf_vdep<double><<<grid, kLfThreads, smem, (cudaStream_t)stream>>>(A);
-    } else {
-        const size_t smem = lf_shared_bytes(lf->n_y, sizeof(float));
-        PDQ_CUDA(cudaFuncSetAttribute(k_lf_vdep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_lf_vdep<float><<<grid, kLfThreads, smem, (cudaStream_t)stream>>>(A);
-    }
-    PDQ_CUDA(cudaGetLastError());
-    return PDQ_OK;
+    if (lf->precision == PDQ_FP64) return launch_lf<double>(A, stream);
+    return launch_lf<float>(A, stream);
 }

@@ -189,3 +189,21 @@ def test_full_size_sampled(pdq, fields):
     # the FP32 march on the same items: every item within the MIXED bar of the FP64 march
     mix = pdq.lf_vdep(f, phys, pdq.lf_desc(precision=pdq.MIXED), var, st10, pdq.params_tensor(prm)).cpu().numpy()
     assert np.all(np.isfinite(mix)) and np.max(np.abs(mix / got - 1)) < RTOL_MIXED
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sample_blocks_walked_with_a_ragged_tail(pdq, fields, precision):
+    # one wave of CTAs per class, each walking several 256-sample blocks: 40,001 samples (157
+    # blocks, the last one sample) x 16 classes; the first, last and 30 random items vs the oracle
+    f, of, var_o = fields[(64, 32, 64)]
+    S = 40001
+    st16 = list(10 ** np.linspace(-1, 2, 16))
+    prm = _params(S, 31)
+    prec = pdq.MIXED if precision == "mixed" else pdq.FP64
+    var = pdq.lf_fluid_variance(f)
+    got = pdq.lf_vdep(f, pdq.phys_default(), pdq.lf_desc(n_y=512, precision=prec), var, st16,
+                      pdq.params_tensor(prm)).cpu().numpy()
+    assert np.all(np.isfinite(got)) and np.all(got > 0)
+    idx = np.concatenate([[0, 255, 256, S - 2, S - 1], np.random.default_rng(8).choice(S, 30, replace=False)])
+    ref = lfo.lf_vdep(oracle.phys(), st16, prm[idx], var_o, of.r_plus, of.beta, lfo.lf_params(n_y=512))
+    assert np.max(np.abs(got[idx] / ref - 1)) < (RTOL_MIXED if precision == "mixed" else RTOL)
