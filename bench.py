@@ -78,6 +78,9 @@ def parse():
                          "1-D Eulerian model of App. B)")
     ap.add_argument("--hf-particles", type=int, default=4096, help="--workload mfmc: particles per HF sample")
     ap.add_argument("--hf-steps", type=int, default=600, help="--workload mfmc: HF steps at dt+ = 0.05")
+    ap.add_argument("--mfmc-budget", type=int, default=24, help="--workload mfmc: HF pick-freeze groups per study")
+    ap.add_argument("--study-budget", type=int, default=200,
+                    help="--workload mfmc: HF groups of the single study with bootstrap intervals (0: none)")
     ap.add_argument("--replicates", type=int, default=100,
                     help="--workload mfmc: replicate studies (0: pilot and allocation only)")
     ap.add_argument("--contact", action="store_true",
@@ -768,7 +771,7 @@ def run_mfmc(args):
     rho = np.array([np.corrcoef(yh[:, c], yl[:, c])[0, 1] for c in range(C)])
     sig = np.stack([yh.std(0, ddof=1), yl.std(0, ddof=1)], 1)
     cq = int(np.argmax(yh.mean(0)))                         # allocate for the class with most deposition
-    p_eff = 24                                              # budget: 24 HF pick-freeze groups per study
+    p_eff = args.mfmc_budget                                # budget: HF pick-freeze groups per study
     wn = w / w[0]                                           # costs in units of one HF evaluation
     try:
         m, alpha, m_real, gamma = pdq.mfmc_allocate([1.0, rho[cq]], sig[cq], wn, p_eff)
@@ -816,8 +819,21 @@ def run_mfmc(args):
         a, b = var_of("mfmc", q), var_of("mc", q)
         return np.where(b > 0, a / np.where(b > 0, b, 1.0), np.nan)
     ratio_mean, ratio_sm, ratio_st = ratio("mean"), ratio("s_main"), ratio("s_total")
+    rep_means = {key: fin(np.mean(np.array([e["mean"] for e in est[key]]), axis=0)) for key in est}
+    if eulerian and args.study_budget == 0:
+        print(json.dumps({
+            "metric": "MFMC vs plain MC at equal GPU cost, low fidelity = the 1-D Eulerian model (App. B)",
+            "config": {"workload": "mfmc: %s; LF = 1-D Eulerian model, %d wall-normal nodes; classes %s; inputs xi "
+                                   "[0,0.1], zeta [0,1], theta [0,1]" % (hf_label, lf_desc.n_y, list(st_plus))},
+            "pilot": pilot,
+            "replicates": {"R": R, "budget_hf_groups": p_eff, "mc_groups": p_eff, "mfmc_groups": [m1, m2],
+                           "var_ratio_mean": fin(ratio_mean), "var_ratio_s_main": fin(ratio_sm),
+                           "var_ratio_s_total": fin(ratio_st), "mean_of_estimates": rep_means,
+                           "gpu_ms": {"hf_all": t_hf, "lf_all": t_lf, "mc_per_study": w[0] * p_eff * (d + 2),
+                                      "mfmc_per_study": (w[0] * m1 + w[1] * m2) * (d + 2)}}}), flush=True)
+        return
     # one study at a larger budget, MFMC and plain MC, with bootstrap intervals
-    pb = 200
+    pb = args.study_budget
     mb, ab, _, gb = pdq.mfmc_allocate([1.0, rho[cq]], sig[cq], wn, pb)
     gbig = draw(max(pb, int(mb[1])), 7)
     yhb, thb = run(hf, gbig[:pb].reshape(-1, d))
