@@ -34,6 +34,13 @@ design notes (readings c33-c41):
   F_elec+, F_vdw+  the printed forms per unit mass, q = xi q_max, A = zeta A0,
              the vdW gap cut at vdw_cutoff (1e-12 m, App. B).
 
+Pins (tests/test_oracle_lf.py): every closure, the wall condition, the force
+potentials and both marches against independent references (Lyapunov
+covariances, quadrature, the high-fidelity oracle's wall forces, exact ODE
+solutions, scipy's solvers), the Brownian closed form and the Fig. 5 trends.
+The model's V_dep+ values against the paper's Fig. 5: parity unpinned, because
+the closures are readings, not the cited papers' fits.
+
 Discretisation (App. B: refined near the wall, drag implicit):
   nodes y_k = y_w + (R - y_w) expm1(gamma s_k)/expm1(gamma), s_k = k/(n-1),
   y_w = d+/2 (contact), y_{n-1} = R+ (axis), V_{n-1} = 0;
