@@ -14,11 +14,11 @@
 // eps = v_f'^2 T_L, tau_1 = tau_p, D_B = k_B T tau_p/m_p, isothermal gas,
 // M_r = -V_w/(sqrt(2) sigma) with sigma^2 = R v_f'^2 + k_B T/m_p at contact.
 //
-// Layout: CTAs per class in one wave, each walking blocks of 256 samples.  A CTA
-// first writes the class's per-cell table into shared memory (differences of the turbophoretic
-// term and of the two potential shapes, dy/tau and dy/D across each cell: 40 B
-// per cell); then each thread marches one sample from the axis (V = 0) to the
-// wall.  At every cell it solves the implicit momentum step
+// Layout: CTAs per class in one wave, each walking blocks of 256 samples.  A
+// CTA first writes the class's per-cell table into shared memory (differences
+// of the turbophoretic term and of the two potential shapes, dy/tau and dy/D
+// across each cell: 40 B per cell in FP64, 20 B in FP32); then each thread
+// marches one sample from the axis (V = 0) to the wall.  At every cell it solves the implicit momentum step
 //   V_k^2/2 - a V_k = c,  a = dy/tau,  c = V_{k+1}^2/2 + dw + dPhi,
 // taking the root V_k <= 0 in the cancellation-free form -2c/(a + sqrt(a^2+2c))
 // (V_k = 0 where c < 0), and composes the exact cell solution of the flux
