@@ -8,8 +8,9 @@
  * Waals force Eq. vdw and the rebound model of Sec. 4.3) for many Monte Carlo
  * samples of the uncertain inputs (charge scale xi, Hamaker ratio zeta,
  * temperature theta; Secs. 2.1 and 4.3), tallies the deposition velocity
- * V_dep+ (Sec. 2.1) and evaluates the multi-fidelity Monte Carlo estimators
- * of Sec. 3.  The carrier phase is a frozen synthetic pipe field (log-law mean
+ * V_dep+ (Sec. 2.1), evaluates the 1-D Eulerian low-fidelity deposition
+ * model of App. B for the same samples, and evaluates the multi-fidelity Monte
+ * Carlo estimators of Sec. 3.  The carrier phase is a frozen synthetic pipe field (log-law mean
  * plus divergence-free random Fourier modes) standing in for the paper's DNS.
  *
  * Conventions (every entry point):
