@@ -10,8 +10,9 @@
  * temperature theta; Secs. 2.1 and 4.3), tallies the deposition velocity
  * V_dep+ (Sec. 2.1), evaluates the 1-D Eulerian low-fidelity deposition
  * model of App. B for the same samples, and evaluates the multi-fidelity Monte
- * Carlo estimators of Sec. 3.  The carrier phase is a frozen synthetic pipe field (log-law mean
- * plus divergence-free random Fourier modes) standing in for the paper's DNS.
+ * Carlo estimators of Sec. 3.  The carrier phase is a frozen synthetic pipe
+ * field (log-law mean plus divergence-free random Fourier modes) standing in
+ * for the paper's DNS.
  *
  * Conventions (every entry point):
  *   - Returns an int status: PDQ_OK (0) or a negative PDQ_ERR_* code.  No
