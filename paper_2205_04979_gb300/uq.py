@@ -143,3 +143,79 @@ def dgsm_deposition(samples, particles, steps, st_plus=(0.1, 1.0, 10.0),
         grad = pbar.permute(1, 0, 2).contiguous()          # [S, C, 3]
         nu, bound = pdq.dgsm_bounds(grad, J, hi - lo, stream=stream)
     return {"J": J.cpu().numpy(), "grad": grad.cpu().numpy(), "nu": nu, "bound": bound, "inputs": x}
+
+
+def mfmc_sobol_deposition(budget, particles, steps, st_plus=(0.1, 1.0, 10.0),
+                          ranges=((0.0, 0.1), (0.0, 1.0), (0.0, 1.0)), dt=0.05, t_window=10.0, pilot=64,
+                          alloc_class=None, allocation=None, lf_nodes=2048, lf_precision=pdq.MIXED,
+                          grid=(64, 32, 64), n_modes=64, seed=0, n_boot=200, precision=pdq.MIXED, stream=None):
+    """Two-model MFMC Sobol' study of V_dep+ (Sec. 3): model 1 the batched particle model, model 2
+    the 1-D Eulerian model of App. B (pdq_lf_vdep), as in the paper's study.
+
+    A pilot of `pilot` input samples gives rho and sigma per class and the GPU cost per sample of
+    each model (model 2 timed on a batch of 65,536 samples, large enough to fill the GPU);
+    pdq_mfmc_allocate splits `budget` (in units of one particle-model pick-freeze group) for the
+    class `alloc_class` (default: the class with the largest mean V_dep+) into m_1 groups of both
+    models and m_2 >= m_1 groups of the 1-D model, nested (the first m_1 shared).  `allocation` =
+    (m, alpha) skips the pilot.  Raises PdqError (PDQ_ERR_PRECOND) when the pilot correlation makes
+    MFMC no better than plain Monte Carlo, and ValueError when the pilot's V_dep+ of that class does
+    not vary.  Returns pdq.mfmc_sobol's dict plus the allocation, the
+    pilot statistics, the two models' tables and their device times (ms).
+    """
+    lo = np.array([r[0] for r in ranges])
+    hi = np.array([r[1] for r in ranges])
+    d, C = len(ranges), len(st_plus)
+    rng = np.random.Generator(np.random.Philox(seed))
+    stream = stream or torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        phys = pdq.phys_default()
+        field = pdq.Field(pdq.field_desc(n_r=grid[0], n_th=grid[1], n_z=grid[2], n_modes=n_modes), seed, stream)
+        var = pdq.lf_fluid_variance(field, stream)
+        lfd = pdq.lf_desc(n_y=lf_nodes, precision=lf_precision)
+
+    def hf_run(inputs):
+        return vdep_runs(inputs, particles, steps, st_plus=st_plus, dt=dt, t_window=t_window, precision=precision,
+                         stream=stream, field=field, seed=seed)
+
+    def lf_run(inputs):
+        with torch.cuda.stream(stream):
+            prm = pdq.params_tensor(np.asarray(inputs, np.float64))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            y = pdq.lf_vdep(field, phys, lfd, var, st_plus, prm, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+        return y.cpu().numpy(), e0.elapsed_time(e1)
+
+    info = {}
+    if allocation is None:
+        xp_ = lo + (hi - lo) * rng.random((pilot, d))
+        yh, th = hf_run(xp_)
+        yl, _ = lf_run(xp_)
+        _, tl = lf_run(lo + (hi - lo) * rng.random((65536, d)))
+        w = np.array([th / pilot, tl / 65536])
+        rho = np.array([np.corrcoef(yh[:, c], yl[:, c])[0, 1] if yh[:, c].std() > 0 and yl[:, c].std() > 0
+                        else 0.0 for c in range(C)])
+        sig = np.stack([yh.std(0, ddof=1), yl.std(0, ddof=1)], 1)
+        cq = int(np.argmax(yh.mean(0))) if alloc_class is None else int(alloc_class)
+        if not np.all(sig[cq] > 0):
+            raise ValueError("the pilot saw no variation of V_dep+ in class %d: nothing to allocate for" % cq)
+        m, alpha, m_real, gamma = pdq.mfmc_allocate([1.0, rho[cq]], sig[cq], w / w[0], budget)
+        info.update(pilot={"samples": pilot, "rho": rho, "sigma": sig.T, "w_ms_per_sample": w, "class": cq},
+                    gamma=gamma, m_real=m_real)
+    else:
+        m, alpha = allocation
+    m1, m2 = max(2, int(m[0])), int(m[1])
+    x = lo + (hi - lo) * rng.random((m2, d))
+    xp = lo + (hi - lo) * rng.random((m2, d))
+    groups = pick_freeze(x, xp)                                   # [m2, d+2, d]
+    yh, th = hf_run(groups[:m1].reshape(-1, d))
+    yl, tl = lf_run(groups.reshape(-1, d))
+    yh = yh.reshape(m1, d + 2, C)
+    yl = yl.reshape(m2, d + 2, C)
+    with torch.cuda.stream(stream):
+        out = pdq.mfmc_sobol([torch.tensor(yh, device="cuda"), torch.tensor(yl, device="cuda")], [m1, m2],
+                             np.asarray(alpha, np.float64), n_boot=n_boot, seed=seed + 2, stream=stream)
+    out.update(info)
+    out.update(m=[m1, m2], alpha=np.asarray(alpha, np.float64), hf=yh, lf=yl, hf_ms=th, lf_ms=tl, inputs=groups)
+    return out

@@ -207,3 +207,34 @@ def test_sample_blocks_walked_with_a_ragged_tail(pdq, fields, precision):
     idx = np.concatenate([[0, 255, 256, S - 2, S - 1], np.random.default_rng(8).choice(S, 30, replace=False)])
     ref = lfo.lf_vdep(oracle.phys(), st16, prm[idx], var_o, of.r_plus, of.beta, lfo.lf_params(n_y=512))
     assert np.max(np.abs(got[idx] / ref - 1)) < (RTOL_MIXED if precision == "mixed" else RTOL)
+
+
+def test_two_model_study_with_the_eulerian_model(pdq):
+    # uq.mfmc_sobol_deposition: with a given allocation its estimates equal pdq_mfmc_sobol on the two
+    # tables it returns, the particle-model groups are the first m_1 of the nested groups, and the
+    # low-fidelity table equals pdq_lf_vdep on the same inputs
+    from paper_2205_04979_gb300 import uq
+    st = (10.0,)
+    r = uq.mfmc_sobol_deposition(0, 1024, 600, st_plus=st, allocation=([4, 24], [1.0, 0.7]), grid=(32, 16, 32),
+                                 n_boot=0, seed=3)
+    assert r["m"] == [4, 24] and r["hf"].shape == (4, 5, 1) and r["lf"].shape == (24, 5, 1)
+    assert r["inputs"].shape == (24, 5, 3)
+    ref = pdq.mfmc_sobol([torch.tensor(r["hf"], device="cuda"), torch.tensor(r["lf"], device="cuda")], [4, 24],
+                         [1.0, 0.7])
+    for q in ("mean", "var", "s_main", "s_total"):
+        assert np.array_equal(r[q], ref[q]), q
+    f = pdq.Field(pdq.field_desc(n_r=32, n_th=16, n_z=32), 3)
+    direct = pdq.lf_vdep(f, pdq.phys_default(), pdq.lf_desc(precision=pdq.MIXED), pdq.lf_fluid_variance(f), st,
+                         pdq.params_tensor(r["inputs"].reshape(-1, 3))).cpu().numpy()
+    assert np.array_equal(direct.reshape(24, 5, 1), r["lf"])
+    # the pilot path: an allocation with 2 <= m_1 <= m_2 and finite estimates, or one of the two
+    # documented refusals (MFMC no better than MC; no variation in the pilot)
+    try:
+        r2 = uq.mfmc_sobol_deposition(8, 2048, 1000, st_plus=st, pilot=16, grid=(32, 16, 32), n_boot=0, seed=4)
+    except pdq.PdqError as e:
+        assert e.status == -6
+    except ValueError as e:
+        assert "no variation" in str(e)
+    else:
+        assert 2 <= r2["m"][0] <= r2["m"][1] and np.all(np.isfinite(r2["mean"]))
+        assert -1.0 <= r2["pilot"]["rho"][0] <= 1.0 and np.all(r2["pilot"]["w_ms_per_sample"] > 0)
