@@ -81,7 +81,8 @@ def units(p):
 # ---------------------------------------------------------------------------
 def fluid_variance(grid):
     """Population variance over (theta, z) of u_r = cos(theta) u_x + sin(theta) u_y at each radial
-    node; grid [n_z][n_th][n_r][3] Cartesian velocity at theta_j = 2 pi j / n_th."""
+    node; grid [n_z][n_th][n_r][3] Cartesian velocity at theta_j = 2 pi j / n_th.  The v_f'^2 of
+    Eq. momentum (App. B), reading c33."""
     n_th = grid.shape[1]
     th = 2.0 * np.pi * np.arange(n_th) / n_th
     ur = np.cos(th)[None, :, None] * grid[..., 0] + np.sin(th)[None, :, None] * grid[..., 1]
@@ -106,17 +107,18 @@ def variance_at(var_r, r_plus, beta, y):
 # Closures and force potentials (App. B; readings c33-c41)
 # ---------------------------------------------------------------------------
 def response_ratio(tau_p, t_lagr):
-    """R_ratio = <v_p'^2>/<v_f'^2> = T_L/(T_L + tau_p)."""
+    """R_ratio of Eq. momentum (App. B) = <v_p'^2>/<v_f'^2> = T_L/(T_L + tau_p) (reading c34)."""
     return t_lagr / (t_lagr + tau_p)
 
 
 def eddy_diffusivity(var_f, t_lagr):
-    """eps/nu = v_f'^2 T_L (wall units)."""
+    """eps/nu of Eq. continuity (App. B) = v_f'^2 T_L, wall units (reading c35)."""
     return var_f * t_lagr
 
 
 def brownian(p, cls_row, temperature):
-    """(D_B/nu, k_B T/(m u*^2)): Einstein D_B = k_B T tau_p/m_p and the thermal velocity variance."""
+    """(D_B/nu, k_B T/(m u*^2)): D_B of Eq. continuity (App. B) by Einstein, k_B T tau_p/m_p (reading
+    c37), and the thermal velocity variance of the wall condition (reading c39)."""
     ustar, ell, _ = units(p)
     tau_p = cls_row[0] * p.nu / ustar ** 2          # s
     m = cls_row[3]
@@ -136,7 +138,8 @@ def potential_constants(p, cls_row):
 
 
 def vdw_shape(gap, cut):
-    """psi with -dpsi/dgap = 1/max(gap, cut)^2 and psi = 1/gap beyond the cutoff (linear inside)."""
+    """psi with -dpsi/dgap = 1/max(gap, cut)^2 and psi = 1/gap beyond the cutoff (linear inside):
+    the shape of F_vdw's potential with App. B's gap cutoff (reading c41)."""
     gap = np.asarray(gap, np.float64)
     return np.where(gap >= cut, 1.0 / np.maximum(gap, cut), 2.0 / cut - gap / (cut * cut))
 
@@ -153,6 +156,7 @@ def wall_flux_factor(v_w, sigma):
 
 
 def nodes(y_w, r_plus, n_y, stretch):
+    """Wall-normal nodes refined near the wall (App. B; reading c40), contact y_w to the axis."""
     s = np.arange(n_y) / (n_y - 1)
     return y_w + (r_plus - y_w) * np.expm1(stretch * s) / np.expm1(stretch)
 
@@ -161,8 +165,9 @@ def nodes(y_w, r_plus, n_y, stretch):
 # The two marches on given node tables
 # ---------------------------------------------------------------------------
 def momentum(y, w, phi, tau):
-    """V at the nodes (momentum Eq. with the force potentials phi), marched from the axis:
-    y [n], w and phi [..., n] (broadcast over items), tau scalar or [...]."""
+    """V at the nodes: Eq. mom_modified (App. B) in energy form with the force potentials phi and
+    the drag implicit (reading c40), marched from the axis: y [n], w and phi [..., n] (broadcast
+    over items), tau scalar or [...]."""
     n = y.shape[-1]
     shape = np.broadcast(w[..., 0], phi[..., 0], np.asarray(tau)).shape
     V = np.zeros(shape + (n,))
@@ -177,8 +182,9 @@ def momentum(y, w, phi, tau):
 
 
 def continuity(y, V, D, K):
-    """V_dep+ = -J for the flux J = -D rho' + V rho, J = rho_w K at the wall, rho = 1 on the axis:
-    cell-wise exact solution with V, D at their cell means, marched from rho_w = 1 outward."""
+    """V_dep+ = -J for the flux J = -D rho' + V rho of Eq. continuity (App. B, D_T term zero), J =
+    rho_w K at the wall (the kinetic condition), rho = 1 on the axis: cell-wise exact solution with
+    V, D at their cell means, marched from rho_w = 1 outward (reading c40)."""
     n = V.shape[-1]
     rho = np.ones(V.shape[:-1])
     J = K * rho
